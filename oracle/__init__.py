@@ -1,0 +1,202 @@
+"""ORACLE: test infrastructure only.
+
+Plain, slow, independent CPU implementation of what the accurate-eigensolve path computes:
+
+* ``eigh``: cyclic-by-row complex Jacobi at 320 bits (the plain definition of Hermitian
+  diagonalisation, the dominant cost named in Section 2.1 of the paper);
+* ``residual``: ||A v - lambda v|| and ||V^H V - I|| at 320 bits;
+* ``matmul``: plain 320-bit complex products (the refinement's dense products);
+* ``Statevector``: brute-force state vector at 320 bits, plus Schmidt values at a cut and the
+  amplitudes of a Vidal MPS (Section 1: MPS = nested Schmidt decomposition).
+
+Only ``tests/``, ``__graft_entry__.smoke()`` and ``bench.py``'s CPU-baseline leg may import this
+package.  It shares no code with the CUDA path; both receive their inputs from ``workloads``.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+from fractions import Fraction
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SO = os.path.join(_HERE, "_oracle.so")
+_SRC = ["mp.c", "eigh.c", "statevec.c", "products.c"]
+_lib = None
+_lock = threading.Lock()
+
+WORDS = 6  # 6 doubles cover the 320-bit results
+
+
+def build(force: bool = False) -> str:
+    srcs = [os.path.join(_HERE, s) for s in _SRC] + [os.path.join(_HERE, "mp.h")]
+    newest = max(os.path.getmtime(s) for s in srcs)
+    if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < newest:
+        tmp = _SO + f".{os.getpid()}.tmp"
+        subprocess.check_call(["gcc", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared", "-o", tmp]
+                              + [os.path.join(_HERE, s) for s in _SRC] + ["-lm"])
+        os.replace(tmp, _SO)
+    return _SO
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            build()
+            L = ctypes.CDLL(_SO)
+            P, I, D = ctypes.c_void_p, ctypes.c_int, ctypes.c_double
+            L.oracle_eigh.restype = I
+            L.oracle_eigh.argtypes = [I, P, I, I, P, P, P]
+            L.oracle_residual.restype = I
+            L.oracle_residual.argtypes = [I, P, I, P, P, I, I, P, P, P]
+            L.oracle_matmul.restype = I
+            L.oracle_matmul.argtypes = [I, I, I, I, P, I, P, I, P, I]
+            L.oracle_rewords.restype = None
+            L.oracle_rewords.argtypes = [ctypes.c_long, P, I, P, I]
+            L.oracle_scalar.restype = None
+            L.oracle_scalar.argtypes = [I, P, P, I, P, I]
+            L.oracle_sv_new.restype = P
+            L.oracle_sv_new.argtypes = [I]
+            L.oracle_sv_free.argtypes = [P]
+            for nm in ("oracle_sv_apply1", "oracle_sv_apply2"):
+                getattr(L, nm).restype = I
+                getattr(L, nm).argtypes = [P, I, P, I]
+            L.oracle_sv_apply_mcu.restype = I
+            L.oracle_sv_apply_mcu.argtypes = [P, I, P, P, I]
+            L.oracle_sv_set.argtypes = [P, P, I]
+            L.oracle_sv_get.argtypes = [P, P, I]
+            L.oracle_sv_norm2.argtypes = [P, P, I]
+            L.oracle_sv_schmidt2.restype = I
+            L.oracle_sv_schmidt2.argtypes = [P, I, P, I]
+            L.oracle_mps_amplitudes.restype = I
+            L.oracle_mps_amplitudes.argtypes = [I, P, P, P, I, P, I]
+            _lib = L
+    return _lib
+
+
+def _c(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def eigh(A: np.ndarray, n: int, w_out: int = WORDS):
+    """Eigen-decomposition of the Hermitian n x n matrix given as words (n*n, 2, w).
+
+    Returns (lam (n, w_out) descending, V (n*n, 2, w_out) column-major, sweeps)."""
+    A = _c(A)
+    w = A.shape[-1]
+    lam = np.zeros((n, w_out))
+    V = np.zeros((n * n, 2, w_out))
+    sw = ctypes.c_int(0)
+    rc = _load().oracle_eigh(n, A.ctypes.data, w, w_out, lam.ctypes.data, V.ctypes.data, ctypes.byref(sw))
+    if rc != 0:
+        raise RuntimeError(f"oracle_eigh failed with code {rc}")
+    return lam, V, sw.value
+
+
+def residual(A: np.ndarray, n: int, lam: np.ndarray, V: np.ndarray, cols=None):
+    """(max-norm residual per column, orthonormality defect per column) at 320 bits."""
+    A, lam, V = _c(A), _c(lam), _c(V)
+    wv = V.shape[-1]
+    if lam.shape[-1] != wv:
+        lam2 = np.zeros((n, wv)); lam2[:, :min(wv, lam.shape[-1])] = lam[:, :min(wv, lam.shape[-1])]
+        if lam.shape[-1] > wv:
+            raise ValueError("lam has more words than V")
+        lam = lam2
+    cols_arr = None if cols is None else np.ascontiguousarray(cols, dtype=np.int32)
+    nc = n if cols is None else len(cols_arr)
+    res = np.zeros(nc); orth = np.zeros(nc)
+    rc = _load().oracle_residual(n, A.ctypes.data, A.shape[-1], lam.ctypes.data, V.ctypes.data, wv, nc,
+                                 None if cols_arr is None else cols_arr.ctypes.data, res.ctypes.data, orth.ctypes.data)
+    if rc != 0:
+        raise RuntimeError("oracle_residual failed")
+    return res, orth
+
+
+def matmul(A, B, m, n, k, opA=0, w_out=WORDS):
+    A, B = _c(A), _c(B)
+    C = np.zeros((m * n, 2, w_out))
+    rc = _load().oracle_matmul(m, n, k, opA, A.ctypes.data, A.shape[-1], B.ctypes.data, B.shape[-1], C.ctypes.data, w_out)
+    if rc != 0:
+        raise RuntimeError("oracle_matmul failed")
+    return C
+
+
+def scalar(op: str, a, b=(0.0,), w_out: int = WORDS):
+    ops = {"add": 0, "sub": 1, "mul": 2, "div": 3, "sqrt": 4}
+    a = _c(a); b = _c(b)
+    w = max(a.size, b.size)
+    aa = np.zeros(w); aa[:a.size] = a
+    bb = np.zeros(w); bb[:b.size] = b
+    out = np.zeros(w_out)
+    _load().oracle_scalar(ops[op], aa.ctypes.data, bb.ctypes.data, w, out.ctypes.data, w_out)
+    return out
+
+
+class Statevector:
+    """2^n amplitudes at 320 bits."""
+
+    def __init__(self, n: int):
+        self.n = n
+        self._h = _load().oracle_sv_new(n)
+        if not self._h:
+            raise ValueError("statevector size out of range")
+
+    def __del__(self):
+        if getattr(self, "_h", None):
+            _load().oracle_sv_free(self._h)
+            self._h = None
+
+    def apply1(self, site, U):
+        U = _c(U)
+        assert _load().oracle_sv_apply1(self._h, site, U.ctypes.data, U.shape[-1]) == 0
+
+    def apply2(self, site, G):
+        G = _c(G)
+        assert _load().oracle_sv_apply2(self._h, site, G.ctypes.data, G.shape[-1]) == 0
+
+    def apply_mcu(self, target, ctrl, U):
+        U = _c(U)
+        c = np.ascontiguousarray(ctrl, dtype=np.int32)
+        assert _load().oracle_sv_apply_mcu(self._h, target, c.ctypes.data, U.ctypes.data, U.shape[-1]) == 0
+
+    def set(self, amps):
+        amps = _c(amps)
+        _load().oracle_sv_set(self._h, amps.ctypes.data, amps.shape[-1])
+
+    def amplitudes(self, w=WORDS):
+        out = np.zeros((1 << self.n, 2, w))
+        _load().oracle_sv_get(self._h, out.ctypes.data, w)
+        return out
+
+    def norm2(self, w=WORDS):
+        out = np.zeros(w)
+        _load().oracle_sv_norm2(self._h, out.ctypes.data, w)
+        return out
+
+    def schmidt2(self, cut, w=WORDS):
+        m = 1 << min(cut, self.n - cut)
+        out = np.zeros((m, w))
+        rc = _load().oracle_sv_schmidt2(self._h, cut, out.ctypes.data, w)
+        if rc:
+            raise RuntimeError("schmidt2 failed")
+        return out
+
+
+def mps_amplitudes(n, chi, gammas, lambdas, w, w_out=WORDS):
+    """Amplitudes (2^n, 2, w_out) of the Vidal MPS (Gamma tensors (s, alpha, beta) row-major, lambda
+    vectors), both as concatenated word arrays."""
+    chi = np.ascontiguousarray(chi, dtype=np.int32)
+    g = _c(gammas); l = _c(lambdas) if len(lambdas) else np.zeros(1)
+    out = np.zeros((1 << n, 2, w_out))
+    rc = _load().oracle_mps_amplitudes(n, chi.ctypes.data, g.ctypes.data, l.ctypes.data, w, out.ctypes.data, w_out)
+    if rc:
+        raise RuntimeError(f"oracle_mps_amplitudes failed ({rc})")
+    return out
+
+
+def to_fraction(words) -> Fraction:
+    return sum((Fraction(float(x)) for x in np.asarray(words).ravel()), Fraction(0))

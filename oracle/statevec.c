@@ -1,0 +1,187 @@
+/*
+ * ORACLE (test infrastructure only).  Brute-force statevector simulator in 320-bit arithmetic, the plain
+ * definition of what an MPS simulation of a circuit computes (Section 1: the MPS is a nested Schmidt
+ * decomposition whose time evolution must equal that of the state vector).
+ *
+ * Basis index x = sum_l s_l 2^(n-1-l): site 0 is the most significant bit.  A two-qubit gate G on
+ * (site, site+1) is a 4x4 matrix, row-major, whose row/column index is 2 i + j with i the bit of `site`
+ * and j the bit of `site+1`.
+ */
+#include "mp.h"
+#include <stdlib.h>
+#include <string.h>
+
+typedef struct { int n; size_t dim; cmp_t* psi; } sv_t;
+
+void* oracle_sv_new(int n) {
+  if (n < 1 || n > 24) return NULL;
+  sv_t* h = (sv_t*)malloc(sizeof(sv_t));
+  h->n = n; h->dim = (size_t)1 << n;
+  h->psi = (cmp_t*)malloc(sizeof(cmp_t) * h->dim);
+  for (size_t x = 0; x < h->dim; ++x) cmp_zero(&h->psi[x]);
+  mp_from_double(&h->psi[0].re, 1.0);
+  return h;
+}
+void oracle_sv_free(void* hv) { sv_t* h = (sv_t*)hv; if (h) { free(h->psi); free(h); } }
+
+/* set amplitudes from words (dim x 2 x w) */
+void oracle_sv_set(void* hv, const double* amps, int w) {
+  sv_t* h = (sv_t*)hv;
+  for (size_t x = 0; x < h->dim; ++x) {
+    mp_from_words(&h->psi[x].re, amps + (x * 2 + 0) * w, w);
+    mp_from_words(&h->psi[x].im, amps + (x * 2 + 1) * w, w);
+  }
+}
+void oracle_sv_get(void* hv, double* amps, int w) {
+  sv_t* h = (sv_t*)hv;
+  for (size_t x = 0; x < h->dim; ++x) {
+    mp_to_words(&h->psi[x].re, amps + (x * 2 + 0) * w, w);
+    mp_to_words(&h->psi[x].im, amps + (x * 2 + 1) * w, w);
+  }
+}
+
+static void load_mat(cmp_t* g, const double* G, int dim, int w) {
+  for (int k = 0; k < dim * dim; ++k) {
+    mp_from_words(&g[k].re, G + ((size_t)k * 2 + 0) * w, w);
+    mp_from_words(&g[k].im, G + ((size_t)k * 2 + 1) * w, w);
+  }
+}
+
+int oracle_sv_apply1(void* hv, int site, const double* U, int w) {
+  sv_t* h = (sv_t*)hv;
+  if (site < 0 || site >= h->n) return 1;
+  cmp_t g[4]; load_mat(g, U, 2, w);
+  size_t bit = (size_t)1 << (h->n - 1 - site);
+  for (size_t x = 0; x < h->dim; ++x) {
+    if (x & bit) continue;
+    cmp_t a0 = h->psi[x], a1 = h->psi[x | bit], t, r0, r1;
+    cmp_mul(&r0, &g[0], &a0); cmp_mul(&t, &g[1], &a1); cmp_add(&r0, &r0, &t);
+    cmp_mul(&r1, &g[2], &a0); cmp_mul(&t, &g[3], &a1); cmp_add(&r1, &r1, &t);
+    h->psi[x] = r0; h->psi[x | bit] = r1;
+  }
+  return 0;
+}
+
+int oracle_sv_apply2(void* hv, int site, const double* G, int w) {
+  sv_t* h = (sv_t*)hv;
+  if (site < 0 || site + 1 >= h->n) return 1;
+  cmp_t g[16]; load_mat(g, G, 4, w);
+  size_t bi = (size_t)1 << (h->n - 1 - site), bj = (size_t)1 << (h->n - 2 - site);
+  for (size_t x = 0; x < h->dim; ++x) {
+    if (x & (bi | bj)) continue;
+    size_t idx[4] = {x, x | bj, x | bi, x | bi | bj};     /* index 2i + j */
+    cmp_t in[4], out[4], t;
+    for (int r = 0; r < 4; ++r) in[r] = h->psi[idx[r]];
+    for (int r = 0; r < 4; ++r) {
+      cmp_zero(&out[r]);
+      for (int c = 0; c < 4; ++c) { cmp_mul(&t, &g[r * 4 + c], &in[c]); cmp_add(&out[r], &out[r], &t); }
+    }
+    for (int r = 0; r < 4; ++r) h->psi[idx[r]] = out[r];
+  }
+  return 0;
+}
+
+/* multi-controlled single-qubit gate: U on `target` when every site l != target has bit ctrl[l]
+ * (ctrl[l] = -1: not a control) */
+int oracle_sv_apply_mcu(void* hv, int target, const int* ctrl, const double* U, int w) {
+  sv_t* h = (sv_t*)hv;
+  cmp_t g[4]; load_mat(g, U, 2, w);
+  size_t tb = (size_t)1 << (h->n - 1 - target);
+  for (size_t x = 0; x < h->dim; ++x) {
+    if (x & tb) continue;
+    int ok = 1;
+    for (int l = 0; l < h->n && ok; ++l) {
+      if (l == target || ctrl[l] < 0) continue;
+      int bit = (int)((x >> (h->n - 1 - l)) & 1);
+      ok = bit == ctrl[l];
+    }
+    if (!ok) continue;
+    cmp_t a0 = h->psi[x], a1 = h->psi[x | tb], t, r0, r1;
+    cmp_mul(&r0, &g[0], &a0); cmp_mul(&t, &g[1], &a1); cmp_add(&r0, &r0, &t);
+    cmp_mul(&r1, &g[2], &a0); cmp_mul(&t, &g[3], &a1); cmp_add(&r1, &r1, &t);
+    h->psi[x] = r0; h->psi[x | tb] = r1;
+  }
+  return 0;
+}
+
+void oracle_sv_norm2(void* hv, double* out, int w) {
+  sv_t* h = (sv_t*)hv;
+  mp acc, t; mp_zero(&acc);
+  for (size_t x = 0; x < h->dim; ++x) { cmp_abs2(&t, &h->psi[x]); mp_add(&acc, &acc, &t); }
+  mp_to_words(&acc, out, w);
+}
+
+int oracle_jacobi_mp(int n, cmp_t* a, cmp_t* v, int max_sweeps);
+void oracle_finish_mp(int n, const cmp_t* a, cmp_t* v, mp* lam, int* order);
+
+/* squared Schmidt coefficients across the cut between sites cut-1 and cut (1 <= cut <= n-1):
+ * eigenvalues (descending) of the Gram matrix of the smaller side; writes min(2^cut, 2^(n-cut)) values */
+int oracle_sv_schmidt2(void* hv, int cut, double* out, int w) {
+  sv_t* h = (sv_t*)hv;
+  if (cut < 1 || cut >= h->n) return 1;
+  size_t L = (size_t)1 << cut, R = (size_t)1 << (h->n - cut);
+  int left_small = L <= R;
+  size_t m = left_small ? L : R;
+  cmp_t* g = (cmp_t*)malloc(sizeof(cmp_t) * m * m);
+  cmp_t* v = (cmp_t*)malloc(sizeof(cmp_t) * m * m);
+  mp* lam = (mp*)malloc(sizeof(mp) * m);
+  int* order = (int*)malloc(sizeof(int) * m);
+  /* psi[x] with x = l * R + r;  left Gram: G_ab = sum_r psi[a,r] conj(psi[b,r]) */
+  for (size_t a = 0; a < m; ++a) for (size_t b = 0; b < m; ++b) {
+    cmp_t s, t; cmp_zero(&s);
+    if (left_small) for (size_t r = 0; r < R; ++r) { cmp_mul_conj(&t, &h->psi[b * R + r], &h->psi[a * R + r]); cmp_add(&s, &s, &t); }
+    else for (size_t l = 0; l < L; ++l) { cmp_mul_conj(&t, &h->psi[l * R + b], &h->psi[l * R + a]); cmp_add(&s, &s, &t); }
+    g[a + b * m] = s;
+  }
+  int sw = oracle_jacobi_mp((int)m, g, v, 80);
+  if (sw < 0) { free(g); free(v); free(lam); free(order); return 2; }
+  oracle_finish_mp((int)m, g, v, lam, order);
+  for (size_t i = 0; i < m; ++i) mp_to_words(&lam[i], out + i * w, w);
+  free(g); free(v); free(lam); free(order);
+  return 0;
+}
+
+/* Amplitudes of a Vidal MPS: psi(s_0..s_{n-1}) = Gamma[0]^{s_0} lam[0] Gamma[1]^{s_1} lam[1] ... Gamma[n-1]^{s_{n-1}}.
+ * chi[l] = bond dimension between sites l and l+1 (l = 0..n-2).  Gamma[l] is stored row-major in
+ * (s, alpha, beta) with alpha < chi[l-1] (1 for l = 0) and beta < chi[l] (1 for l = n-1), complex with
+ * w words per real, concatenated over l; lam[l] (w words per value) concatenated over l.
+ * amps: 2^n x 2 x w_out words. */
+int oracle_mps_amplitudes(int n, const int* chi, const double* gam, const double* lam, int w,
+                          double* amps, int w_out) {
+  if (n < 1 || n > 22) return 1;
+  size_t goff = 0, loff = 0;
+  /* T: current partial contraction, rows = 2^l prefixes, cols = chi[l] */
+  size_t rows = 1; int cols = 1;
+  cmp_t* T = (cmp_t*)malloc(sizeof(cmp_t)); cmp_zero(&T[0]); mp_from_double(&T[0].re, 1.0);
+  for (int l = 0; l < n; ++l) {
+    int cl = l == 0 ? 1 : chi[l - 1], cr = l == n - 1 ? 1 : chi[l];
+    if (cl != cols) { free(T); return 2; }
+    mp* lw = NULL;
+    if (l > 0) {                                        /* weights lam[l-1] on the left index */
+      lw = (mp*)malloc(sizeof(mp) * cl);
+      for (int a = 0; a < cl; ++a) mp_from_words(&lw[a], lam + (loff + a) * w, w);
+      loff += cl;
+    }
+    cmp_t* Tn = (cmp_t*)malloc(sizeof(cmp_t) * rows * 2 * cr);
+    for (size_t x = 0; x < rows; ++x) for (int s = 0; s < 2; ++s) for (int b = 0; b < cr; ++b) {
+      cmp_t acc, g, t, u; cmp_zero(&acc);
+      for (int a = 0; a < cl; ++a) {
+        size_t gi = goff + ((size_t)s * cl + a) * cr + b;
+        mp_from_words(&g.re, gam + (gi * 2 + 0) * w, w);
+        mp_from_words(&g.im, gam + (gi * 2 + 1) * w, w);
+        u = T[x * cl + a];
+        if (lw) cmp_scale(&u, &u, &lw[a]);
+        cmp_mul(&t, &u, &g); cmp_add(&acc, &acc, &t);
+      }
+      Tn[(x * 2 + s) * cr + b] = acc;
+    }
+    goff += (size_t)2 * cl * cr;
+    free(T); free(lw); T = Tn; rows *= 2; cols = cr;
+  }
+  for (size_t x = 0; x < rows; ++x) {
+    mp_to_words(&T[x].re, amps + (x * 2 + 0) * w_out, w_out);
+    mp_to_words(&T[x].im, amps + (x * 2 + 1) * w_out, w_out);
+  }
+  free(T);
+  return 0;
+}

@@ -1,0 +1,327 @@
+"""Pins for the oracle against things other than itself: exact rationals, closed forms, mpmath,
+invariants.  CPU only."""
+from __future__ import annotations
+
+from decimal import Decimal, getcontext
+from fractions import Fraction
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import workloads as W
+from tests._util import (conj_herm_product, dyadic_unitary, exact_words_ok, fr, to_words_matrix, words, cmul,
+                         cconj, cadd)
+
+TWO = Fraction(2)
+
+
+def rel_close(x: Fraction, y: Fraction, bits: int) -> bool:
+    scale = max(abs(y), Fraction(1, 2**1000))
+    return abs(x - y) <= scale / TWO**bits
+
+
+# ------------------------------- the 320-bit arithmetic itself ------------------------------------
+@pytest.mark.parametrize("op", ["add", "sub", "mul", "div"])
+def test_mp_scalar_ops_match_exact_rationals(op):
+    rng = np.random.default_rng(11)
+    for trial in range(300):
+        # random 4-word expansions with assorted exponents (cancellation-prone for add/sub)
+        a = [float(x) for x in rng.standard_normal(1)] 
+        e = int(rng.integers(-60, 60))
+        a = [math.ldexp(float(rng.standard_normal()), e)]
+        a += [a[-1] * 2**-55 * float(rng.standard_normal()) for _ in range(3)]
+        if trial % 3 == 0:   # near-cancellation partner
+            b = [-a[0]] + [math.ldexp(float(rng.standard_normal()), e - 70 - k * 50) for k in range(3)]
+        else:
+            eb = int(rng.integers(-60, 60))
+            b = [math.ldexp(float(rng.standard_normal()), eb)]
+            b += [b[-1] * 2**-55 * float(rng.standard_normal()) for _ in range(3)]
+        A, B = fr(a), fr(b)
+        got = fr(oracle.scalar(op, a, b))
+        exact = {"add": A + B, "sub": A - B, "mul": A * B, "div": A / B if B else None}[op]
+        if exact is None:
+            continue
+        # each operand converts exactly (span < 320 bits); the result is within a few ulps of 2^-320
+        assert rel_close(got, exact, 312), (op, trial)
+
+
+def test_mp_sqrt_matches_integer_sqrt():
+    rng = np.random.default_rng(12)
+    for _ in range(200):
+        e = int(rng.integers(-400, 400))
+        a = [math.ldexp(abs(float(rng.standard_normal())) + 1e-3, e)]
+        a += [a[0] * 2**-56 * float(rng.standard_normal()) for _ in range(2)]
+        A = fr(a)
+        s = fr(oracle.scalar("sqrt", a))
+        # compare s^2 with A: relative error of s ~ half that of s^2
+        assert rel_close(s * s, A, 310)
+
+
+def test_mp_word_roundtrip_is_exact():
+    rng = np.random.default_rng(13)
+    for _ in range(200):
+        x = Fraction(int(rng.integers(1, 2**62)), 2**int(rng.integers(0, 200))) * (1 + Fraction(1, 2**100))
+        w = words(x, 6)
+        out = np.zeros(6)
+        oracle._load().oracle_rewords(1, np.ascontiguousarray(w).ctypes.data, 6, out.ctypes.data, 6)
+        assert fr(out) == fr(w)
+
+
+# ------------------------------- the eigensolver ---------------------------------------------------
+def test_eigh_2x2_closed_form():
+    getcontext().prec = 130
+    rng = np.random.default_rng(21)
+    for _ in range(20):
+        a, d = Fraction(float(rng.standard_normal())), Fraction(float(rng.standard_normal()))
+        br, bi = Fraction(float(rng.standard_normal())), Fraction(float(rng.standard_normal()))
+        M = [[(a, Fraction(0)), (br, bi)], [(br, -bi), (d, Fraction(0))]]
+        A = to_words_matrix(M, 2)
+        lam, V, _ = oracle.eigh(A, 2)
+        mid = (a + d) / 2
+        q = ((a - d) / 2) ** 2 + br * br + bi * bi
+        rad = (Decimal(q.numerator) / Decimal(q.denominator)).sqrt()
+        exp_hi = Decimal(mid.numerator) / Decimal(mid.denominator) + rad
+        exp_lo = Decimal(mid.numerator) / Decimal(mid.denominator) - rad
+        for got, want in ((lam[0], exp_hi), (lam[1], exp_lo)):
+            g = fr(got)
+            assert abs(Decimal(g.numerator) / Decimal(g.denominator) - want) <= Decimal(2) ** -300 * (abs(exp_hi) + abs(exp_lo))
+
+
+@pytest.mark.parametrize("n,seed", [(3, 1), (6, 2), (9, 3), (12, 4)])
+def test_eigh_exact_known_spectrum(n, seed):
+    """A = U diag(lam) U^H with U exactly unitary (dyadic) and dyadic lam spanning 2^0 .. 2^-230,
+    including a negative and an exactly repeated eigenvalue: every eigenvalue to 2^-300 ||A||."""
+    U = dyadic_unitary(n, layers=3 * n, seed=seed)
+    lam = [Fraction(1)] + [Fraction((-1) ** k * (2 * k + 1), 2 ** (23 * k)) for k in range(1, n)]
+    lam[-1] = lam[-2]                                 # exact double eigenvalue
+    A = conj_herm_product(U, lam)
+    Aw = to_words_matrix(A, 8)
+    assert exact_words_ok(A, Aw, 8)
+    got, V, _ = oracle.eigh(Aw, n)
+    want = sorted(lam, reverse=True)
+    for g, w_ in zip(got, want):
+        assert abs(fr(g) - w_) <= Fraction(1, 2**300)
+    res, orth = oracle.residual(Aw, n, got, V)
+    assert res.max() < 2.0**-295 and orth.max() < 2.0**-300
+
+
+def test_eigh_eigenvectors_of_distinct_spectrum_match_exact_columns():
+    n = 6
+    U = dyadic_unitary(n, layers=20, seed=9)
+    lam = [Fraction(1, 2**(40 * k)) * (1 + Fraction(k, 8)) for k in range(n)]
+    A = conj_herm_product(U, lam)
+    Aw = to_words_matrix(A, 8)
+    assert exact_words_ok(A, Aw, 8)
+    got, V, _ = oracle.eigh(Aw, n)
+    order = sorted(range(n), key=lambda k: -lam[k])
+    for c, k in enumerate(order):
+        u = [U[i][k] for i in range(n)]
+        v = [(fr(V[i + c * n, 0]), fr(V[i + c * n, 1])) for i in range(n)]
+        # phase-align: ph = <u, v>/|<u, v>|, compare |v - ph u|^2 via exact inner products
+        ip = (Fraction(0), Fraction(0))
+        for i in range(n):
+            ip = cadd(ip, cmul(cconj(u[i]), v[i]))
+        mag2 = ip[0] ** 2 + ip[1] ** 2
+        vv = sum(a * a + b * b for a, b in v)
+        # sin^2(angle(u, v)) = 1 - |<u,v>|^2 / (|u|^2 |v|^2), |u| = 1 exactly; Davis-Kahan with the
+        # solver's absolute accuracy 2^-300 ||A|| over the gap to the nearest other eigenvalue
+        gap = min(abs(lam[k] - lam[j]) for j in range(n) if j != k)
+        assert 1 - mag2 / vv <= (Fraction(1, 2**300) / gap) ** 2
+        assert abs(vv - 1) <= Fraction(1, 2**310)
+
+
+def test_eigh_matches_mpmath_eighe():
+    mpmath = pytest.importorskip("mpmath")
+    mpmath.mp.prec = 400
+    for n, seed in ((5, 31), (8, 32)):
+        p = W.herm_spectrum(seed, 0, W.spectrum_graded(n, 120), 4)
+        M = mpmath.matrix(n, n)
+        for i in range(n):
+            for j in range(n):
+                re = fr(p.A[i + j * n, 0]); im = fr(p.A[i + j * n, 1])
+                M[i, j] = mpmath.mpc(mpmath.mpf(re.numerator) / re.denominator, mpmath.mpf(im.numerator) / im.denominator)
+        E, Q = mpmath.eighe(M)
+        ref = sorted([E[i] for i in range(n)], reverse=True)
+        got, V, _ = oracle.eigh(p.A, n)
+        for g, r in zip(got, ref):
+            gf = fr(g)
+            assert abs(mpmath.mpf(gf.numerator) / gf.denominator - r) < mpmath.mpf(2) ** -300
+
+
+def test_eigh_trace_and_invariants_on_generated_batch_problem():
+    lam, lo, pairs, w = W.batch_problem_spec(2, 1, 0, 24)
+    p = W.herm_spectrum(1, 0, lam, w, lam_lo=lo, pairs=pairs)
+    got, V, sweeps = oracle.eigh(p.A, 24)
+    tr = sum(fr(p.A[i + i * 24, 0]) for i in range(24))
+    assert abs(sum(fr(g) for g in got) - tr) <= Fraction(1, 2**300)
+    res, orth = oracle.residual(p.A, 24, got, V)
+    assert res.max() < 2.0**-290 and orth.max() < 2.0**-300
+    # the generator keeps the near-degenerate pairs split (relative 2^-60 here) up to the rounding of
+    # A to quad-double words (absolute ~n 2^-212 ||A||)
+    vals = [fr(g) for g in got]
+    for (a, b) in pairs:
+        split = vals[a] - vals[b]
+        want = Fraction(float(lam[a])) / 2**60
+        assert abs(split - want) <= want * Fraction(1, 2**40) + Fraction(24, 2**212)
+
+
+def test_eigh_rejects_non_hermitian():
+    A = np.zeros((4, 2, 1)); A[1, 0, 0] = 1.0  # a_10 = 1, a_01 = 0
+    with pytest.raises(RuntimeError):
+        oracle.eigh(A, 2)
+
+
+# ------------------------------- footnote closed form ---------------------------------------------
+def _footnote_rho(p: Fraction, u0, u1):
+    """rho_target = (1-p)|-><-| + p |u><u| with |u> = U|-> (exact 2x2)."""
+    mm = [[Fraction(1, 2), Fraction(-1, 2)], [Fraction(-1, 2), Fraction(1, 2)]]
+    uu = [[cmul(a, cconj(b)) for b in (u0, u1)] for a in (u0, u1)]
+    return [[((1 - p) * mm[i][j] + p * uu[i][j][0], p * uu[i][j][1]) for j in range(2)] for i in range(2)]
+
+
+@pytest.mark.parametrize("n", [2, 10, 60, 120, 180])
+def test_eigh_footnote_reduced_matrix_u_is_z(n):
+    """Footnote: C^{n-1}-Z on |+..+>|-> leaves the target with eigenvalues 1 - 2^-(n-1) and 2^-(n-1)."""
+    p = Fraction(1, 2 ** (n - 1))
+    half = Fraction(1, 2)
+    rho = _footnote_rho(p, (half, Fraction(0)), (half, Fraction(0)))   # Z|-> = |+> = (1/2, 1/2) * sqrt2...
+    # |+> has components 1/sqrt2; |u><u| = 1/2 [[1,1],[1,1]] -> use exact form directly
+    rho = [[((1 - p) * Fraction(1, 2) + p * Fraction(1, 2), Fraction(0)), ((1 - p) * Fraction(-1, 2) + p * Fraction(1, 2), Fraction(0))],
+           [((1 - p) * Fraction(-1, 2) + p * Fraction(1, 2), Fraction(0)), ((1 - p) * Fraction(1, 2) + p * Fraction(1, 2), Fraction(0))]]
+    # embed in a larger exactly-unitary conjugation so the solver does real work
+    U = dyadic_unitary(4, layers=10, seed=n)
+    blk = [[rho[0][0], rho[0][1], (Fraction(0), Fraction(0)), (Fraction(0), Fraction(0))],
+           [rho[1][0], rho[1][1], (Fraction(0), Fraction(0)), (Fraction(0), Fraction(0))],
+           [(Fraction(0),) * 2, (Fraction(0),) * 2, (Fraction(1, 4), Fraction(0)), (Fraction(0),) * 2],
+           [(Fraction(0),) * 2, (Fraction(0),) * 2, (Fraction(0),) * 2, (Fraction(1, 8), Fraction(0))]]
+    A = [[(Fraction(0), Fraction(0))] * 4 for _ in range(4)]
+    for i in range(4):
+        for j in range(4):
+            s = (Fraction(0), Fraction(0))
+            for k in range(4):
+                for l in range(4):
+                    s = cadd(s, cmul(cmul(U[i][k], blk[k][l]), cconj(U[j][l])))
+            A[i][j] = s
+    Aw = to_words_matrix(A, 8)
+    assert exact_words_ok(A, Aw, 8)
+    got, _, _ = oracle.eigh(Aw, 4)
+    vals = sorted([1 - p, p, Fraction(1, 4), Fraction(1, 8)], reverse=True)
+    for g, v in zip(got, vals):
+        assert abs(fr(g) - v) <= Fraction(1, 2**300)
+
+
+# ------------------------------- statevector --------------------------------------------------------
+def _exact_pm_state(n):
+    """|+>^{n-1}|-> for even n: every amplitude is +-2^(-n/2) exactly."""
+    amps = np.zeros((1 << n, 2, 1))
+    a = 2.0 ** (-n / 2)
+    for x in range(1 << n):
+        amps[x, 0, 0] = -a if (x & 1) else a      # target = site n-1 = least significant bit
+    return amps
+
+
+@pytest.mark.parametrize("n", [4, 8, 12])
+def test_statevector_footnote_schmidt_values_u_is_z(n):
+    sv = oracle.Statevector(n)
+    sv.set(_exact_pm_state(n))
+    rng = np.random.default_rng(n)
+    ctrl = [int(b) for b in rng.integers(0, 2, n)]
+    ctrl[-1] = -1
+    Z = np.zeros((4, 2, 1)); Z[0, 0, 0] = 1.0; Z[3, 0, 0] = -1.0
+    sv.apply_mcu(n - 1, ctrl, Z)
+    lam2 = sv.schmidt2(n - 1)      # cut between controls and target: target side (2 values)
+    eps = Fraction(1, 2 ** (n - 1))
+    assert abs(fr(lam2[0]) - (1 - eps)) <= Fraction(1, 2**300)
+    assert abs(fr(lam2[1]) - eps) <= Fraction(1, 2**300)
+
+
+def test_statevector_footnote_general_u():
+    n = 10
+    sv = oracle.Statevector(n)
+    sv.set(_exact_pm_state(n))
+    G = W.haar_gate(77, 0, w=4, dim=2)
+    ctrl = [1, 0, 1, 1, 0, 0, 1, 0, 1, -1]
+    sv.apply_mcu(n - 1, ctrl, G)
+    lam2 = sv.schmidt2(n - 1)
+    p = Fraction(1, 2 ** (n - 1))
+    u = [(fr(G[0, 0]), fr(G[0, 1])), (fr(G[1, 0]), fr(G[1, 1])), (fr(G[2, 0]), fr(G[2, 1])), (fr(G[3, 0]), fr(G[3, 1]))]
+    # |u> = U|->, scaled by sqrt2: (u00 - u01, u10 - u11); |u><u| carries the 1/2
+    v0 = (u[0][0] - u[1][0], u[0][1] - u[1][1]); v1 = (u[2][0] - u[3][0], u[2][1] - u[3][1])
+    r00 = (1 - p) / 2 + p * (v0[0] ** 2 + v0[1] ** 2) / 2
+    r11 = (1 - p) / 2 + p * (v1[0] ** 2 + v1[1] ** 2) / 2
+    off = cmul(v0, cconj(v1)); r01 = (-(1 - p) / 2 + p * off[0] / 2, p * off[1] / 2)
+    getcontext().prec = 130
+    D = lambda f: Decimal(f.numerator) / Decimal(f.denominator)
+    tr, det = r00 + r11, r00 * r11 - r01[0] ** 2 - r01[1] ** 2
+    rad = (D(tr) ** 2 / 4 - D(det)).sqrt()
+    want = (D(tr) / 2 + rad, D(tr) / 2 - rad)
+    for g, w_ in zip(lam2, want):
+        assert abs(D(fr(g)) - w_) < Decimal(2) ** -300
+    # unitary U: closed form 1/2 (1 +- sqrt(1 - 4 p (1-p) (1 - |f|^2))) within U's rounding (2^-200)
+    f = cmul((Fraction(1, 2), Fraction(0)), (u[0][0] - u[1][0] - u[2][0] + u[3][0], u[0][1] - u[1][1] - u[2][1] + u[3][1]))
+    f2 = f[0] ** 2 + f[1] ** 2
+    closed = (1 + (1 - 4 * D(p) * (1 - D(p)) * (1 - D(f2))).sqrt()) / 2
+    assert abs(D(fr(lam2[0])) - closed) < Decimal(2) ** -200
+
+
+def test_statevector_ghz_and_norm_and_reversibility():
+    n = 6
+    sv = oracle.Statevector(n)
+    # exactly unitary dyadic 4x4 gate and its exact inverse
+    U = dyadic_unitary(4, layers=7, seed=5)
+    G = to_words_matrix([[U[c][r] for r in range(4)] for c in range(4)], 4)   # row-major r*4+c
+    Gh = to_words_matrix([[cconj(U[r][c]) for r in range(4)] for c in range(4)], 4)
+    amps0 = np.zeros((1 << n, 2, 1)); amps0[0, 0, 0] = 0.5; amps0[5, 1, 0] = -0.5; amps0[17, 0, 0] = 0.5; amps0[40, 0, 0] = 0.5
+    sv.set(amps0)
+    for s in (0, 2, 4, 1, 3):
+        sv.apply2(s, G)
+    assert abs(fr(sv.norm2()) - 1) <= Fraction(1, 2**300)
+    for s in (3, 1, 4, 2, 0):
+        sv.apply2(s, Gh)
+    back = sv.amplitudes()
+    for x in range(1 << n):
+        for part in range(2):
+            assert abs(fr(back[x, part]) - Fraction(float(amps0[x, part, 0]))) <= Fraction(1, 2**300)
+
+
+def test_mps_amplitudes_ghz():
+    """GHZ-shaped Vidal MPS with identity-like Gammas and dyadic weights: amplitudes are the products
+    of the weights along the two branches."""
+    n = 3
+    half = 0.5
+    chi = [2, 2]
+    g0 = np.zeros((2 * 1 * 2, 2, 1)); g0[0 * 2 + 0, 0, 0] = 1; g0[1 * 2 + 1, 0, 0] = 1
+    g1 = np.zeros((2 * 2 * 2, 2, 1)); g1[(0 * 2 + 0) * 2 + 0, 0, 0] = 1; g1[(1 * 2 + 1) * 2 + 1, 0, 0] = 1
+    g2 = np.zeros((2 * 2 * 1, 2, 1)); g2[(0 * 2 + 0), 0, 0] = 1; g2[(1 * 2 + 1), 0, 0] = 1
+    lam = np.array([[1.0], [1.0], [half], [1.0]])
+    amps = oracle.mps_amplitudes(n, chi, np.concatenate([g0, g1, g2]), lam, 1)
+    for x in range(8):
+        # psi(000) = 1 * 1 * 1 * lam1[0] * 1 = 1/2, psi(111) = 1 * 1 * 1 * lam1[1] * 1 = 1
+        want = Fraction(1, 2) if x == 0 else (Fraction(1) if x == 7 else Fraction(0))
+        assert fr(amps[x, 0]) == want and fr(amps[x, 1]) == 0
+
+
+def test_matmul_matches_exact_rationals():
+    rng = np.random.default_rng(41)
+    m, n, k = 3, 4, 5
+    A = np.zeros((m * k, 2, 2)); B = np.zeros((k * n, 2, 2))
+    for X in (A, B):
+        X[:, :, 0] = rng.standard_normal(X.shape[:2])
+        X[:, :, 1] = X[:, :, 0] * 2**-60 * rng.standard_normal(X.shape[:2])
+    C = oracle.matmul(A, B, m, n, k)
+    for i in range(m):
+        for j in range(n):
+            s = (Fraction(0), Fraction(0))
+            for l in range(k):
+                s = cadd(s, cmul((fr(A[i + l * m, 0]), fr(A[i + l * m, 1])), (fr(B[l + j * k, 0]), fr(B[l + j * k, 1]))))
+            assert abs(fr(C[i + j * m, 0]) - s[0]) <= Fraction(1, 2**300)
+            assert abs(fr(C[i + j * m, 1]) - s[1]) <= Fraction(1, 2**300)
+    Ch = oracle.matmul(A, A, k, k, m, opA=1)    # A^H A
+    for i in range(k):
+        for j in range(k):
+            s = (Fraction(0), Fraction(0))
+            for l in range(m):
+                s = cadd(s, cmul(cconj((fr(A[l + i * m, 0]), fr(A[l + i * m, 1]))), (fr(A[l + j * m, 0]), fr(A[l + j * m, 1]))))
+            assert abs(fr(Ch[i + j * k, 0]) - s[0]) <= Fraction(1, 2**300)
