@@ -1,0 +1,129 @@
+/*
+ * zkq: accurate batched Hermitian eigensolves for matrix-product-state (MPS) circuit simulation on
+ * GB300 (sm_103a).  C ABI: plain pointers and sizes only.
+ *
+ * The computation follows arXiv:2402.11868 (SaiToh, "Recent Extensions of the ZKCM Library for
+ * Parallel and Accurate MPS Simulation of Quantum Circuits"):
+ *   - Section 2.1: Hermitian matrix diagonalisation is the dominant cost of the MPS simulation;
+ *   - Section 2, ZKCM_CUS paragraph: a double-precision eigensolve followed by Rayleigh quotient
+ *     iteration that recovers the precision;
+ *   - Section 1 and its footnote: the working precision must be exponentially small in the number of
+ *     qubits, because Schmidt coefficients as small as ~2^{-(n-1)/2} occur and must be kept.
+ *
+ * Conventions shared by every entry point
+ *   Multi-word numbers: a real value is an unevaluated sum of w doubles, highest first, non-overlapping
+ *     (w = 1: double; 2: double-double, ~106 bits; 4: quad-double, ~212 bits).
+ *   Complex element layout: re words then im words: double[2][w] per element.
+ *   Matrices: column-major, element (i, j) at index i + j*n.  A batch packs problem b's n_b x n_b
+ *     matrix at element offset a_off[b] (elements, not doubles).
+ *   Eigenvalues of problem b occupy positions w_off[b] .. w_off[b] + n_b - 1 of the eigenvalue array,
+ *     with w_off[b] = n_0 + ... + n_{b-1}; they are sorted descending (ties keep the original order).
+ *   Eigenvector c of problem b is column c of the n_b x n_b matrix at element offset a_off[b]; its first
+ *     component of largest modulus is real and positive.
+ *   Ownership: the caller owns every array passed in (device or host as stated per argument); the
+ *     library never frees them.  A context owns its workspace.
+ *   Streams: `stream` is a cudaStream_t (NULL = legacy default stream).  Calls are asynchronous on that
+ *     stream; argument and launch errors return synchronously; per-problem convergence is reported in
+ *     device `info` arrays, readable after the stream synchronises.  No call aborts or traps.
+ */
+#ifndef ZKQ_H
+#define ZKQ_H
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  ZKQ_OK = 0,
+  ZKQ_EINVAL = 1,    /* invalid argument (sizes, word counts, null pointers, method) */
+  ZKQ_ENOMEM = 2,    /* device workspace could not be allocated */
+  ZKQ_ENOCONV = 3,   /* reserved: a problem did not converge (per-problem detail is in info[]) */
+  ZKQ_ETIMEOUT = 4,  /* a bounded device-side wait expired */
+  ZKQ_ECUDA = 5,     /* a CUDA runtime call failed; see zkq_last_cuda_error() */
+  ZKQ_EADMIT = 6     /* reserved: request refused by admission control */
+} zkq_status;
+
+typedef enum { ZKQ_FP64 = 1, ZKQ_DD = 2, ZKQ_QD = 4 } zkq_prec;   /* value = words per real */
+
+typedef enum {
+  ZKQ_PLAIN_RQI = 0,  /* per-eigenpair Rayleigh quotient iteration in the target precision */
+  ZKQ_OA_OZAKI = 1    /* block Ogita-Aishima refinement with tensor-core split products */
+} zkq_method;
+
+typedef struct zkq_ctx zkq_ctx;
+
+typedef struct {
+  int device;             /* CUDA device ordinal */
+  int max_sweeps;         /* Jacobi sweep limit (0: default 40) */
+  int rqi_max_iter;       /* RQI steps per eigenpair (0: default 5) */
+  int oa_max_iter;        /* Ogita-Aishima iterations (0: default 12) */
+  int jacobi_cluster;     /* CTAs per large Jacobi problem (0: default chosen by size) */
+} zkq_config;
+
+/* Human-readable name of a status code.  Never NULL. */
+const char* zkq_status_string(zkq_status s);
+/* Last CUDA error code recorded by the library in this process (0 if none). */
+int zkq_last_cuda_error(void);
+
+/* Create a context on cfg->device (cfg may be NULL: device 0, defaults).  *ctx receives the handle.
+ * Errors: ZKQ_EINVAL (ctx NULL), ZKQ_ECUDA. */
+zkq_status zkq_ctx_create(zkq_ctx** ctx, const zkq_config* cfg);
+/* Free the context and its workspace (synchronises its device first).  NULL is accepted. */
+zkq_status zkq_ctx_destroy(zkq_ctx* ctx);
+
+/*
+ * zkq_eigh_batched: double-precision eigen-decomposition of a batch of Hermitian matrices
+ * (the FP64 stage of Section 2, ZKCM_CUS paragraph) by a two-sided complex Jacobi method.
+ *   batch          number of problems (>= 0)
+ *   n (host)       n[b] >= 1, matrix orders
+ *   a_off (host)   element offsets of each matrix in A and V
+ *   A (device)     input matrices, a_words words per real (1, 2 or 4); only the leading word is used;
+ *                  the matrix must be Hermitian (the strictly lower triangle's conjugate is assumed)
+ *   W (device)     out: double[sum n], eigenvalues per problem, descending
+ *   V (device)     out: complex FP64 eigenvectors (double[2] per element) at a_off[b]
+ *   info (device)  out: int32[batch]; 0 converged, > 0 sweep limit reached
+ * Errors: ZKQ_EINVAL, ZKQ_ENOMEM, ZKQ_ECUDA.
+ */
+zkq_status zkq_eigh_batched(zkq_ctx* ctx, int batch, const int32_t* n, const int64_t* a_off,
+                            const double* A, int a_words, double* W, double* V, int32_t* info, void* stream);
+
+/*
+ * zkq_rqi_refine: recover the eigenpairs to the target precision from the FP64 ones
+ * (Section 2, ZKCM_CUS paragraph: Rayleigh quotient iteration recovers the precision after the
+ * double-precision eigensolve).
+ *   A (device)        input matrices with a_words words per real (1, 2, 4), offsets a_off (host)
+ *   W, V (device)     FP64 eigenpairs from zkq_eigh_batched (same layout)
+ *   target_words      2 (double-double) or 4 (quad-double)
+ *   method            ZKQ_PLAIN_RQI or ZKQ_OA_OZAKI
+ *   W_out (device)    out: double[sum n][target_words], refined eigenvalues (descending)
+ *   V_out (device)    out: eigenvectors, target_words words per real, element offsets a_off
+ *   err_est (device)  out: double[sum n], ||A v - lambda v||_2 / max|lambda| per eigenpair (FP64 estimate)
+ *   info (device)     out: int32[batch]; 0 ok; > 0 iteration limit reached on some eigenpair
+ * Errors: ZKQ_EINVAL, ZKQ_ENOMEM, ZKQ_ECUDA.
+ */
+zkq_status zkq_rqi_refine(zkq_ctx* ctx, int batch, const int32_t* n, const int64_t* a_off,
+                          const double* A, int a_words, const double* W, const double* V,
+                          int target_words, int method, double* W_out, double* V_out, double* err_est,
+                          int32_t* info, void* stream);
+
+/*
+ * zkq_mw_op: element-wise multi-word arithmetic, the building block of every refinement step
+ * (the paper's multiple-precision numbers, Section 1; here double-double / quad-double made of FP64
+ * error-free transformations).  Diagnostic entry point used to check the arithmetic.
+ *   op        0 add, 1 sub, 2 mul, 3 div, 4 sqrt(a), 5 complex mul, 6 complex div
+ *   words     1, 2 or 4
+ *   count     number of operands (real ops: count values; complex ops: count complex values)
+ *   a, b, out arrays of count x words (real) or count x 2 x words (complex) doubles
+ *   on_device 0: host arrays, computed on the CPU with the same header; 1: device arrays, one GPU thread
+ *             per element on `stream`
+ * Errors: ZKQ_EINVAL, ZKQ_ECUDA.
+ */
+zkq_status zkq_mw_op(int op, int words, int64_t count, const double* a, const double* b, double* out,
+                     int on_device, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,175 @@
+"""Python binding of libzkq (argument marshalling only; every compute step runs in the CUDA library).
+
+Accurate batched Hermitian eigensolves for MPS circuit simulation (arXiv:2402.11868, Section 2):
+an FP64 Jacobi eigensolve followed by precision recovery to double-double or quad-double.
+
+Functions mirror the C ABI in include/zkq.h and take either integers (raw pointers) or torch tensors
+(their data_ptr is passed).  Streams may be a torch.cuda.Stream, an int handle, or None.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libzkq.so")
+_lib = None
+_lock = threading.Lock()
+
+ZKQ_OK, ZKQ_EINVAL, ZKQ_ENOMEM, ZKQ_ENOCONV, ZKQ_ETIMEOUT, ZKQ_ECUDA, ZKQ_EADMIT = range(7)
+ZKQ_FP64, ZKQ_DD, ZKQ_QD = 1, 2, 4
+ZKQ_PLAIN_RQI, ZKQ_OA_OZAKI = 0, 1
+
+
+class ZkqError(RuntimeError):
+    def __init__(self, status: int, what: str):
+        msg = lib().zkq_status_string(status).decode()
+        if status == ZKQ_ECUDA:
+            msg += f" (cuda error {lib().zkq_last_cuda_error()})"
+        super().__init__(f"{what}: {msg}")
+        self.status = status
+
+
+class _Config(ctypes.Structure):
+    _fields_ = [("device", ctypes.c_int), ("max_sweeps", ctypes.c_int), ("rqi_max_iter", ctypes.c_int),
+                ("oa_max_iter", ctypes.c_int), ("jacobi_cluster", ctypes.c_int)]
+
+
+def build(force: bool = False) -> str:
+    from . import buildlib as _b
+    return _b.build(force=force)
+
+
+def lib():
+    """Load libzkq.so; raises if it has not been built (there is no fallback path)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise RuntimeError(f"libzkq.so not built at {LIB_PATH}; run paper_2402_11868_gb300.build()")
+            L = ctypes.CDLL(LIB_PATH)
+            P, I, I64 = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64
+            L.zkq_status_string.restype = ctypes.c_char_p
+            L.zkq_status_string.argtypes = [I]
+            L.zkq_last_cuda_error.restype = I
+            L.zkq_ctx_create.restype = I
+            L.zkq_ctx_create.argtypes = [ctypes.POINTER(P), ctypes.POINTER(_Config)]
+            L.zkq_ctx_destroy.restype = I
+            L.zkq_ctx_destroy.argtypes = [P]
+            L.zkq_eigh_batched.restype = I
+            L.zkq_eigh_batched.argtypes = [P, I, P, P, P, I, P, P, P, P]
+            L.zkq_rqi_refine.restype = I
+            L.zkq_rqi_refine.argtypes = [P, I, P, P, P, I, P, P, I, I, P, P, P, P, P]
+            L.zkq_mw_op.restype = I
+            L.zkq_mw_op.argtypes = [I, I, I64, P, P, P, I, P]
+            _lib = L
+    return _lib
+
+
+def _ptr(x):
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if hasattr(x, "data_ptr"):
+        return x.data_ptr()
+    if hasattr(x, "ctypes"):
+        return x.ctypes.data
+    raise TypeError(f"cannot pass {type(x)} as a pointer")
+
+
+def _stream(s):
+    if s is None:
+        return None
+    if isinstance(s, int):
+        return s
+    return s.cuda_stream
+
+
+def _host_array(x, ctype):
+    import numpy as np
+    dt = np.int32 if ctype is ctypes.c_int32 else np.int64
+    a = np.ascontiguousarray(x, dtype=dt)
+    return a, a.ctypes.data
+
+
+def _check(st, what):
+    if st != ZKQ_OK:
+        raise ZkqError(st, what)
+
+
+class Context:
+    """Owns a zkq_ctx (and its device workspace)."""
+
+    def __init__(self, device: int = 0, max_sweeps: int = 0, rqi_max_iter: int = 0, oa_max_iter: int = 0,
+                 jacobi_cluster: int = 0):
+        cfg = _Config(device, max_sweeps, rqi_max_iter, oa_max_iter, jacobi_cluster)
+        h = ctypes.c_void_p()
+        _check(lib().zkq_ctx_create(ctypes.byref(h), ctypes.byref(cfg)), "zkq_ctx_create")
+        self.handle = h.value
+        self.device = device
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib().zkq_ctx_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+
+def zkq_eigh_batched(ctx: Context, n, a_off, A, a_words, W, V, info, stream=None):
+    n_arr, n_p = _host_array(n, ctypes.c_int32)
+    o_arr, o_p = _host_array(a_off, ctypes.c_int64)
+    _check(lib().zkq_eigh_batched(ctx.handle, len(n_arr), n_p, o_p, _ptr(A), a_words, _ptr(W), _ptr(V), _ptr(info),
+                                  _stream(stream)), "zkq_eigh_batched")
+
+
+def zkq_rqi_refine(ctx: Context, n, a_off, A, a_words, W, V, target_words, method, W_out, V_out, err_est, info,
+                   stream=None):
+    n_arr, n_p = _host_array(n, ctypes.c_int32)
+    o_arr, o_p = _host_array(a_off, ctypes.c_int64)
+    _check(lib().zkq_rqi_refine(ctx.handle, len(n_arr), n_p, o_p, _ptr(A), a_words, _ptr(W), _ptr(V), target_words,
+                                method, _ptr(W_out), _ptr(V_out), _ptr(err_est), _ptr(info), _stream(stream)),
+           "zkq_rqi_refine")
+
+
+def zkq_mw_op(op: int, words: int, count: int, a, b, out, on_device: bool, stream=None):
+    _check(lib().zkq_mw_op(op, words, count, _ptr(a), _ptr(b), _ptr(out), int(bool(on_device)), _stream(stream)),
+           "zkq_mw_op")
+
+
+# --------------------------------------------------------------------------------------------------
+# batch helpers (host-side packing; no arithmetic of the method)
+def batch_offsets(ns):
+    """Element offsets a_off and eigenvalue offsets w_off for a list of matrix orders."""
+    a_off, w_off, a, w = [], [], 0, 0
+    for n in ns:
+        a_off.append(a); w_off.append(w)
+        a += n * n; w += n
+    return a_off, w_off, a, w
+
+
+def pack(mats, words):
+    """Concatenate (n*n, 2, w) word arrays (numpy) into one flat float64 array with `words` words."""
+    import numpy as np
+    parts = []
+    for M in mats:
+        M = np.asarray(M, dtype=np.float64)
+        if M.shape[-1] < words:
+            pad = np.zeros(M.shape[:-1] + (words - M.shape[-1],))
+            M = np.concatenate([M, pad], axis=-1)
+        elif M.shape[-1] > words:
+            raise ValueError("matrix has more words than requested")
+        parts.append(M.reshape(-1))
+    return np.concatenate(parts) if parts else np.zeros(0)

@@ -1,0 +1,299 @@
+// Batched complex Hermitian FP64 Jacobi eigensolver: the double-precision diagonalisation stage that
+// precedes precision recovery (Section 2, ZKCM_CUS paragraph: a double-precision eigensolve whose
+// result Rayleigh quotient iteration then refines).  The paper calls a cuSOLVER routine here; this is a
+// hand-written two-sided Jacobi method instead.
+//
+// Parallel ordering: a sweep has m-1 rounds (m = n rounded up to even); in a round the m/2 disjoint
+// pairs of the circle method rotate at once.  For pair k = (p, q) with b = a_pq = |b| e^{i phi}:
+//   tau = (a_qq - a_pp) / (2|b|), t = sign(tau)/(|tau| + sqrt(1 + tau^2)), c = 1/sqrt(1+t^2), s = t c,
+//   J_k = [[c, z2], [-z1, c]] with z1 = s e^{-i phi}, z2 = s e^{i phi}.
+// The whole round is A <- J^H A J with J = prod_k J_k.  It is applied as 2x2-block updates
+//   A[{p,q},{p',q'}] <- J_k^H A[{p,q},{p',q'}] J_k'
+// on the upper block triangle k <= k' (the lower one is its conjugate transpose), so one barrier per
+// round suffices and Hermitian symmetry halves the arithmetic; diagonal blocks use the closed form
+// (a_pp - t|b|, a_qq + t|b|, 0).  V <- V J accumulates the eigenvectors.
+// Rotations with |a_pq| <= tol = sqrt(n) 2^-53 ||A||_F are skipped; a sweep without rotation ends the
+// iteration.  Output: eigenvalues descending, eigenvectors with their first largest-modulus component
+// real and positive.
+#include "common.cuh"
+#include "mw.cuh"
+#include <cooperative_groups.h>
+namespace cg = cooperative_groups;
+
+namespace zkq {
+
+struct RotParams { double c, tb; c64 z1, z2; int rot; int p, q; };
+
+// Storage policy: matrix element (i, j) of a column-major matrix with leading dimension ld.
+// SMEM: plain loads/stores.  GLOBAL: L2-only loads (other CTAs of the cluster write the same matrix).
+template <bool SMEM> struct Mat {
+  c64* base; int ld;
+  __device__ __forceinline__ c64 get(int i, int j) const {
+    if (SMEM) return base[i + (size_t)j * ld];
+    const double2 v = __ldcg(reinterpret_cast<const double2*>(base + i + (size_t)j * ld));
+    return {v.x, v.y};
+  }
+  __device__ __forceinline__ void set(int i, int j, c64 v) const {
+    if (SMEM) base[i + (size_t)j * ld] = v;
+    else __stcg(reinterpret_cast<double2*>(base + i + (size_t)j * ld), make_double2(v.re, v.im));
+  }
+};
+
+// One problem, processed by `nparts` cooperating CTAs (part = rank in the cluster; 1 CTA if nparts = 1).
+__device__ __forceinline__ void cluster_barrier() { __threadfence(); cg::this_cluster().sync(); }
+
+template <bool SMEM, bool CLUSTER, int WA>
+__device__ void jacobi_problem(int n, const double* __restrict__ A_in, Mat<SMEM> A, Mat<SMEM> V,
+                               RotParams* rp, double* red, int max_sweeps,
+                               double* __restrict__ W_out, double* __restrict__ V_out, int32_t* info,
+                               int part, int nparts) {
+  auto sync = [] { if constexpr (CLUSTER) cluster_barrier(); else __syncthreads(); };
+  const int tid = threadIdx.x, nth = blockDim.x;
+  const int gtid = part * nth + tid, gnth = nparts * nth;
+  const int m = n + (n & 1);               // even number of players; index n is a dummy when n is odd
+  const int P = m / 2;
+  // load A (leading word of each real part; the expansions are normalised so it is the nearest double)
+  double fro_part = 0.0;
+  for (int e = gtid; e < n * n; e += gnth) {
+    int i = e % n, j = e / n;
+    const double* q = A_in + (size_t)e * 2 * WA;
+    c64 v = {q[0], q[WA]};
+    if (i == j) v.im = 0.0;
+    A.set(i, j, v);
+    V.set(i, j, c64{i == j ? 1.0 : 0.0, 0.0});
+    fro_part += v.re * v.re + v.im * v.im;
+  }
+  // ||A||_F: block reduction; with several CTAs each keeps its own partial, combined via red[] in global
+  __shared__ double s_red[32];
+  __shared__ double s_tol;
+  __shared__ int s_rot;
+  for (int o = 16; o > 0; o >>= 1) fro_part += __shfl_down_sync(0xffffffffu, fro_part, o);
+  if ((tid & 31) == 0) s_red[tid >> 5] = fro_part;
+  __syncthreads();
+  if (tid == 0) {
+    double s = 0; for (int w = 0; w < (nth + 31) / 32; ++w) s += s_red[w];
+    if (nparts > 1) red[part] = s; else s_tol = s;
+  }
+  sync();
+  if (tid == 0) {
+    double s = s_tol;
+    if (nparts > 1) { s = 0; for (int k = 0; k < nparts; ++k) s += __ldcg(red + k); }
+    s_tol = sqrt((double)n) * 0x1p-53 * sqrt(s);
+  }
+  __syncthreads();
+  const double tol = s_tol;
+  int sweep = 0, converged = 0;
+  for (sweep = 0; sweep < max_sweeps && !converged; ++sweep) {
+    if (tid == 0) s_rot = 0;
+    __syncthreads();
+    int my_rot = 0;
+    for (int r = 0; r < m - 1; ++r) {
+      // phase 1: rotation parameters (every CTA computes all pairs into its own shared memory)
+      for (int k = tid; k < P; k += nth) {
+        int p, q; rr_pair(m, r, k, p, q);
+        RotParams pr; pr.p = p; pr.q = q; pr.rot = 0; pr.c = 1.0; pr.tb = 0.0; pr.z1 = {0, 0}; pr.z2 = {0, 0};
+        if (q < n) {
+          c64 b = A.get(p, q);
+          double ab = hypot(b.re, b.im);
+          if (ab > tol) {
+            double app = A.get(p, p).re, aqq = A.get(q, q).re;
+            double tau = (aqq - app) / (2.0 * ab);
+            double t = (tau >= 0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
+            double c = 1.0 / sqrt(1.0 + t * t), s = t * c;
+            double er = b.re / ab, ei = b.im / ab;
+            pr.c = c; pr.tb = t * ab; pr.rot = 1;
+            pr.z1 = {s * er, -s * ei};
+            pr.z2 = {s * er, s * ei};
+            ++my_rot;
+          }
+        }
+        rp[k] = pr;
+      }
+      sync();
+      // phase 2: 2x2 block updates on the upper block triangle + V <- V J
+      const int nblk = P * (P + 1) / 2;
+      for (int it = gtid; it < nblk + n * P; it += gnth) {
+        if (it < nblk) {
+          // decode (k, k2) with k <= k2 from the linear index
+          int k = (int)((sqrtf(8.0f * (float)it + 1.0f) - 1.0f) * 0.5f);
+          while ((k + 1) * (k + 2) / 2 <= it) ++k;
+          while (k * (k + 1) / 2 > it) --k;
+          int k2 = it - k * (k + 1) / 2;           // k2 <= k
+          const RotParams a = rp[k2], b = rp[k];   // rows from pair k2, columns from pair k
+          if (k2 == k) {
+            if (a.rot) {
+              c64 dp = A.get(a.p, a.p), dq = A.get(a.q, a.q);
+              A.set(a.p, a.p, c64{dp.re - a.tb, 0.0});
+              A.set(a.q, a.q, c64{dq.re + a.tb, 0.0});
+              A.set(a.p, a.q, c64{0.0, 0.0});
+              A.set(a.q, a.p, c64{0.0, 0.0});
+            }
+            continue;
+          }
+          if (!a.rot && !b.rot) continue;
+          const int r0 = a.p, r1 = a.q, c0 = b.p, c1 = b.q;
+          const bool hr1 = r1 < n, hc1 = c1 < n;
+          c64 x00 = A.get(r0, c0);
+          c64 x01 = hc1 ? A.get(r0, c1) : c64{0, 0};
+          c64 x10 = hr1 ? A.get(r1, c0) : c64{0, 0};
+          c64 x11 = (hr1 && hc1) ? A.get(r1, c1) : c64{0, 0};
+          // T = X J_b : col0 = X[:,0] c - X[:,1] z1, col1 = X[:,0] z2 + X[:,1] c
+          c64 t00, t01, t10, t11;
+          if (b.rot) {
+            c64 u = cmul(b.z1, x01), v = cmul(b.z2, x00);
+            t00 = {b.c * x00.re - u.re, b.c * x00.im - u.im};
+            t01 = {v.re + b.c * x01.re, v.im + b.c * x01.im};
+            u = cmul(b.z1, x11); v = cmul(b.z2, x10);
+            t10 = {b.c * x10.re - u.re, b.c * x10.im - u.im};
+            t11 = {v.re + b.c * x11.re, v.im + b.c * x11.im};
+          } else { t00 = x00; t01 = x01; t10 = x10; t11 = x11; }
+          // Y = J_a^H T : row0 = c T[0,:] - z2 T[1,:], row1 = z1 T[0,:] + c T[1,:]
+          c64 y00, y01, y10, y11;
+          if (a.rot) {
+            c64 u = cmul(a.z2, t10), v = cmul(a.z1, t00);
+            y00 = {a.c * t00.re - u.re, a.c * t00.im - u.im};
+            y10 = {v.re + a.c * t10.re, v.im + a.c * t10.im};
+            u = cmul(a.z2, t11); v = cmul(a.z1, t01);
+            y01 = {a.c * t01.re - u.re, a.c * t01.im - u.im};
+            y11 = {v.re + a.c * t11.re, v.im + a.c * t11.im};
+          } else { y00 = t00; y01 = t01; y10 = t10; y11 = t11; }
+          A.set(r0, c0, y00); A.set(c0, r0, cconj(y00));
+          if (hc1) { A.set(r0, c1, y01); A.set(c1, r0, cconj(y01)); }
+          if (hr1) { A.set(r1, c0, y10); A.set(c0, r1, cconj(y10)); }
+          if (hr1 && hc1) { A.set(r1, c1, y11); A.set(c1, r1, cconj(y11)); }
+        } else {
+          int e = it - nblk;
+          int i = e % n, k = e / n;
+          const RotParams b = rp[k];
+          if (!b.rot) continue;
+          c64 x = V.get(i, b.p), y = V.get(i, b.q);
+          c64 u = cmul(b.z1, y), v = cmul(b.z2, x);
+          V.set(i, b.p, c64{b.c * x.re - u.re, b.c * x.im - u.im});
+          V.set(i, b.q, c64{v.re + b.c * y.re, v.im + b.c * y.im});
+        }
+      }
+      sync();
+    }
+    if (my_rot) atomicAdd(&s_rot, my_rot);
+    __syncthreads();
+    if constexpr (CLUSTER) {
+      // every CTA computed the same parameters, but take part 0's count so the barrier counts of the
+      // cluster's CTAs cannot diverge
+      if (tid == 0) red[nparts + part] = (double)s_rot;
+      sync();
+      converged = (__ldcg(red + nparts) == 0.0);
+      sync();
+    } else {
+      converged = (s_rot == 0);
+    }
+    __syncthreads();
+  }
+  // eigenvalues: rank sort (descending, ties by index), then eigenvector phase normalisation
+  for (int i = gtid; i < n; i += gnth) {
+    double li = A.get(i, i).re;
+    int rank = 0;
+    for (int j = 0; j < n; ++j) {
+      double lj = A.get(j, j).re;
+      rank += (lj > li) || (lj == li && j < i);
+    }
+    W_out[rank] = li;
+    // phase: first index with the largest modulus
+    int best = 0; double bm = -1.0;
+    for (int r = 0; r < n; ++r) { c64 v = V.get(r, i); double m2 = v.re * v.re + v.im * v.im; if (m2 > bm) { bm = m2; best = r; } }
+    c64 vb = V.get(best, i);
+    double inv = 1.0 / sqrt(bm);
+    c64 ph = {vb.re * inv, -vb.im * inv};    // conj(v_best)/|v_best|
+    for (int r = 0; r < n; ++r) {
+      c64 v = cmul(V.get(r, i), ph);
+      if (r == best) v.im = 0.0;
+      V_out[((size_t)r + (size_t)rank * n) * 2 + 0] = v.re;
+      V_out[((size_t)r + (size_t)rank * n) * 2 + 1] = v.im;
+    }
+  }
+  if (part == 0 && tid == 0) *info = converged ? 0 : sweep;
+}
+
+struct JacobiBatch {
+  const int32_t* n; const int64_t* a_off; const int64_t* w_off; const int32_t* order;
+  const double* A; double* W; double* V; int32_t* info; double* ws; const int64_t* ws_off; double* red;
+  int max_sweeps;
+};
+
+// small problems: matrix and eigenvectors in shared memory, one CTA per problem
+template <int WA>
+__global__ void __launch_bounds__(256) jacobi_smem_kernel(JacobiBatch jb, int first, int count) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  if ((int)blockIdx.x >= count) return;
+  const int b = jb.order[first + blockIdx.x];
+  const int n = jb.n[b];
+  const int ld = n + 1;                       // padding avoids bank conflicts on row access
+  c64* sA = reinterpret_cast<c64*>(smem);
+  c64* sV = sA + (size_t)ld * n;
+  RotParams* rp = reinterpret_cast<RotParams*>(sV + (size_t)ld * n);
+  Mat<true> A{sA, ld}, V{sV, ld};
+  jacobi_problem<true, false, WA>(n, jb.A + jb.a_off[b] * 2 * WA, A, V, rp, nullptr, jb.max_sweeps,
+                                  jb.W + jb.w_off[b], jb.V + jb.a_off[b] * 2, jb.info + b, 0, 1);
+}
+
+// large problems: matrix and eigenvectors in global workspace, one cluster of CTAs per problem
+template <int WA>
+__global__ void __launch_bounds__(256) jacobi_global_kernel(JacobiBatch jb, int first) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  cg::cluster_group cl = cg::this_cluster();
+  const int part = (int)cl.block_rank(), nparts = (int)cl.num_blocks();
+  const int b = jb.order[first + blockIdx.x / nparts];
+  const int n = jb.n[b];
+  double* wsA = jb.ws + jb.ws_off[b];
+  double* wsV = wsA + (size_t)n * n * 2;
+  RotParams* rp = reinterpret_cast<RotParams*>(smem);
+  Mat<false> A{reinterpret_cast<c64*>(wsA), n}, V{reinterpret_cast<c64*>(wsV), n};
+  double* red = jb.red + (size_t)64 * (blockIdx.x / nparts);   // 2 * cluster (<= 32) entries used
+  if (nparts > 1)
+    jacobi_problem<false, true, WA>(n, jb.A + jb.a_off[b] * 2 * WA, A, V, rp, red, jb.max_sweeps,
+                                    jb.W + jb.w_off[b], jb.V + jb.a_off[b] * 2, jb.info + b, part, nparts);
+  else
+    jacobi_problem<false, false, WA>(n, jb.A + jb.a_off[b] * 2 * WA, A, V, rp, red, jb.max_sweeps,
+                                     jb.W + jb.w_off[b], jb.V + jb.a_off[b] * 2, jb.info + b, 0, 1);
+}
+
+size_t jacobi_smem_bytes(int n) { return (size_t)2 * (n + 1) * n * sizeof(c64) + (size_t)(n / 2 + 1) * sizeof(RotParams); }
+
+template <int WA>
+static zkq_status launch_words(const JacobiBatch& jb, int n_small, int n_large, int max_small_n, int max_large_n,
+                               int cluster, cudaStream_t st) {
+  if (n_small > 0) {
+    size_t sm = jacobi_smem_bytes(max_small_n);
+    ZKQ_CUDA_TRY(cudaFuncSetAttribute(jacobi_smem_kernel<WA>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    jacobi_smem_kernel<WA><<<n_small, 256, sm, st>>>(jb, 0, n_small);
+    ZKQ_CUDA_TRY(cudaGetLastError());
+  }
+  if (n_large > 0) {
+    size_t sm = (size_t)(max_large_n / 2 + 1) * sizeof(RotParams);
+    ZKQ_CUDA_TRY(cudaFuncSetAttribute(jacobi_global_kernel<WA>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    if (cluster > 8)
+      ZKQ_CUDA_TRY(cudaFuncSetAttribute(jacobi_global_kernel<WA>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(n_large * cluster);
+    cfg.blockDim = dim3(256);
+    cfg.dynamicSmemBytes = sm;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = cluster; attr[0].val.clusterDim.y = 1; attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr; cfg.numAttrs = 1;
+    ZKQ_CUDA_TRY(cudaLaunchKernelEx(&cfg, jacobi_global_kernel<WA>, jb, n_small));
+  }
+  return ZKQ_OK;
+}
+
+zkq_status launch_jacobi(const JacobiBatch& jb, int a_words, int n_small, int n_large, int max_small_n,
+                         int max_large_n, int cluster, cudaStream_t st) {
+  switch (a_words) {
+    case 1: return launch_words<1>(jb, n_small, n_large, max_small_n, max_large_n, cluster, st);
+    case 2: return launch_words<2>(jb, n_small, n_large, max_small_n, max_large_n, cluster, st);
+    case 4: return launch_words<4>(jb, n_small, n_large, max_small_n, max_large_n, cluster, st);
+    default: return ZKQ_EINVAL;
+  }
+}
+
+}  // namespace zkq

@@ -1,0 +1,95 @@
+"""CPU checks of the C ABI library: it loads without a GPU, exports every declared symbol, rejects bad
+arguments, and its host-compiled multi-word arithmetic meets the double-double / quad-double error
+bounds against the 320-bit oracle."""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+import subprocess
+
+import numpy as np
+import pytest
+
+import oracle
+from tests._util import fr
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def zkq():
+    import paper_2402_11868_gb300 as Z
+    Z.build()
+    return Z
+
+
+def declared_symbols():
+    txt = open(os.path.join(ROOT, "include", "zkq.h")).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"\b(zkq_[a-z0-9_]+)\s*\(", txt)))
+
+
+def test_library_exports_every_declared_symbol(zkq):
+    syms = declared_symbols()
+    assert len(syms) >= 6
+    L = ctypes.CDLL(zkq.LIB_PATH)
+    for s in syms:
+        assert hasattr(L, s), s
+    out = subprocess.run(["nm", "-D", "--defined-only", zkq.LIB_PATH], capture_output=True, text=True).stdout
+    for s in syms:
+        assert re.search(rf"\bT {s}\b", out), s
+
+
+def test_status_strings(zkq):
+    for s in range(7):
+        assert zkq.lib().zkq_status_string(s)
+
+
+def test_invalid_arguments_are_rejected_without_gpu(zkq):
+    L = zkq.lib()
+    assert L.zkq_ctx_create(None, None) == zkq.ZKQ_EINVAL
+    assert L.zkq_eigh_batched(None, 1, None, None, None, 4, None, None, None, None) == zkq.ZKQ_EINVAL
+    assert L.zkq_mw_op(9, 4, 1, None, None, None, 0, None) == zkq.ZKQ_EINVAL
+    assert L.zkq_mw_op(0, 3, 1, None, None, None, 0, None) == zkq.ZKQ_EINVAL
+
+
+# published relative error bounds (unit roundoff u = 2^-53): double-double add 3u^2 (accurate sum),
+# mul ~4u^2 (Joldes-Muller-Popescu 2017); quad-double ops ~2^-208 (Hida-Li-Bailey 2001 report ~2^-209).
+BOUND = {2: {0: 2.0**-103, 1: 2.0**-103, 2: 2.0**-102, 3: 2.0**-101, 4: 2.0**-101},
+         4: {0: 2.0**-206, 1: 2.0**-206, 2: 2.0**-206, 3: 2.0**-205, 4: 2.0**-205}}
+
+
+def random_mw(rng, count, words, spread=30):
+    x = np.zeros((count, words))
+    e = rng.integers(-spread, spread, count)
+    x[:, 0] = np.ldexp(rng.standard_normal(count), e)
+    for k in range(1, words):
+        x[:, k] = x[:, k - 1] * 2.0**-54 * rng.uniform(-1, 1, count)
+    return x
+
+
+@pytest.mark.parametrize("words", [2, 4])
+@pytest.mark.parametrize("op", [0, 1, 2, 3, 4])
+def test_host_multiword_ops_within_published_bounds(zkq, words, op):
+    rng = np.random.default_rng(100 * words + op)
+    count = 400
+    a = random_mw(rng, count, words)
+    b = random_mw(rng, count, words)
+    if op == 4:
+        a = np.abs(a) * np.sign(a[:, :1])
+    if op in (0, 1):       # force heavy cancellation for a third of the operands
+        k = count // 3
+        b[:k, 0] = -a[:k, 0] if op == 0 else a[:k, 0]
+    out = np.zeros_like(a)
+    zkq.zkq_mw_op(op, words, count, a, b, out, on_device=False)
+    name = {0: "add", 1: "sub", 2: "mul", 3: "div", 4: "sqrt"}[op]
+    for i in range(count):
+        ref = fr(oracle.scalar(name, a[i], b[i]))
+        got = fr(out[i])
+        if op in (0, 1):
+            # accurate addition: error relative to the exact result (or to the operands after cancellation)
+            scale = max(abs(ref), abs(fr(a[i])) * 2.0**-(53 * words - 10))
+        else:
+            scale = abs(ref)
+        assert abs(got - ref) <= BOUND[words][op] * scale, (op, i)
