@@ -21,7 +21,10 @@ struct RqiBatch {
   double* ws; int64_t ws_stride; int64_t total_pairs; int max_iter; int* counter;
 };
 
-template <int W> __device__ __forceinline__ double target_exp() { return W == 4 ? -205.0 : (W == 2 ? -101.0 : -50.0); }
+// Convergence: the computed residual cannot drop below the rounding floor ~ n 2^(-53W) ||A||, so the
+// iteration counts as converged at 16 n 2^(-53W) ||A|| and then takes one more (cubically convergent)
+// step to settle at the floor.
+template <int W> __device__ __forceinline__ int word_bits() { return 53 * W; }
 
 template <int W, int WA>
 __global__ void __launch_bounds__(256) rqi_kernel(RqiBatch rb) {
@@ -50,7 +53,7 @@ __global__ void __launch_bounds__(256) rqi_kernel(RqiBatch rb) {
     // ||A|| estimate: max |lambda| from the FP64 stage (eigenvalues are sorted)
     const double* Wb = rb.W + rb.w_off[b];
     const double anorm = fmax(fabs(Wb[0]), fabs(Wb[n - 1]));
-    const double thresh = ldexp(anorm, (int)target_exp<W>());
+    const double thresh = ldexp(anorm * n, 4 - word_bits<W>());
     // x <- v, normalised
     mw<W> nrm2 = mw_zero<W>();
     for (int i = tid; i < n; i += nth) {
@@ -91,7 +94,8 @@ __global__ void __launch_bounds__(256) rqi_kernel(RqiBatch rb) {
       }
       rr = block_sum_r(rr, reinterpret_cast<mw<W>*>(red));
       res = sqrt(fmax(rr.x[0], 0.0)) / sqrt(xx.x[0]);
-      if (res <= thresh) { converged = 1; break; }
+      if (converged) break;                        // the polishing step has been taken
+      if (res <= thresh) converged = 1;
       if (it == rb.max_iter) break;
       // B = [A - mu I | x]
       for (size_t e = tid; e < (size_t)n * (n + 1); e += nth) {

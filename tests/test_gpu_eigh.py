@@ -136,4 +136,8 @@ def test_plain_rqi_matches_oracle_small(ctx, oracle_cache, target):
             assert abs(fr(lam[i]) - fr(L[i])) <= anorm / 2**bound_bits, (p.n, i)
         r, o = oracle.residual(p.A, p.n, lam, V)
         assert r.max() <= float(anorm) * 2.0**-bound_bits, (p.n, r.max())
-        assert o.max() <= 2.0**-bound_bits, (p.n, o.max())
+        # eigenvectors come from independent inverse iterations: their mutual orthogonality is limited by
+        # residual / gap (Davis-Kahan), not by the working precision
+        vals = [float(fr(L[i])) for i in range(p.n)]
+        gap = min([abs(vals[i] - vals[j]) for i in range(p.n) for j in range(p.n) if i != j] or [1.0])
+        assert o.max() <= 4 * float(anorm) * 2.0**-bound_bits / gap + 2.0**-bound_bits, (p.n, o.max())
