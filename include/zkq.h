@@ -49,7 +49,8 @@ typedef enum { ZKQ_FP64 = 1, ZKQ_DD = 2, ZKQ_QD = 4 } zkq_prec;   /* value = wor
 
 typedef enum {
   ZKQ_PLAIN_RQI = 0,  /* per-eigenpair Rayleigh quotient iteration in the target precision */
-  ZKQ_OA_OZAKI = 1    /* block Ogita-Aishima refinement with tensor-core split products */
+  ZKQ_OA_OZAKI = 1,   /* block Ogita-Aishima refinement with tensor-core split (Ozaki) products */
+  ZKQ_OA_FP64 = 2     /* the same refinement with its products in multi-word arithmetic on the FP64 pipe */
 } zkq_method;
 
 typedef struct zkq_ctx zkq_ctx;
@@ -96,7 +97,7 @@ zkq_status zkq_eigh_batched(zkq_ctx* ctx, int batch, const int32_t* n, const int
  *   A (device)        input matrices with a_words words per real (1, 2, 4), offsets a_off (host)
  *   W, V (device)     FP64 eigenpairs from zkq_eigh_batched (same layout)
  *   target_words      2 (double-double) or 4 (quad-double)
- *   method            ZKQ_PLAIN_RQI or ZKQ_OA_OZAKI
+ *   method            ZKQ_PLAIN_RQI, ZKQ_OA_OZAKI or ZKQ_OA_FP64 (the refinement methods need n[b] <= 2048)
  *   W_out (device)    out: double[sum n][target_words], refined eigenvalues (descending)
  *   V_out (device)    out: eigenvectors, target_words words per real, element offsets a_off
  *   err_est (device)  out: double[sum n], ||A v - lambda v||_2 / max|lambda| per eigenpair (FP64 estimate)
@@ -107,6 +108,28 @@ zkq_status zkq_rqi_refine(zkq_ctx* ctx, int batch, const int32_t* n, const int64
                           const double* A, int a_words, const double* W, const double* V,
                           int target_words, int method, double* W_out, double* V_out, double* err_est,
                           int32_t* info, void* stream);
+
+/*
+ * zkq_mw_gemm: batched multi-word complex products C_i = op(A_i) B_i, the dense products of the refinement
+ * step (A X, X^H X, X^H (A X), X E) that recover the precision of the FP64 eigenpairs (Section 2, ZKCM_CUS
+ * paragraph).  Method 1 splits both operands into exact 8-bit (7-bit when k > 512) integer digits scaled
+ * per row / column by powers of two, multiplies digit matrices on the tensor cores with exact fp32
+ * accumulation and recombines the integer results exactly (Ozaki, Ogita, Oishi, Rump 2012); method 0
+ * computes the same products directly in multi-word arithmetic on the FP64 pipe.
+ *   count (>= 0)   number of products; m, n, k, opA (host, int32[count])
+ *   opA[i]         0: A_i is m x k (column-major, ld m);  1: A_i is stored k x m (ld k), op(A) = A^H
+ *   A, B, C        device arrays; product i uses element offsets a_off[i], b_off[i], c_off[i] (host int64)
+ *   wa, wb, wc     words per real of A, B, C (1, 2 or 4); B_i is k x n (ld k), C_i is m x n (ld m)
+ *   p_bits         requested accuracy: |C - op(A) B| <= k 2^-p_bits 2^(e_row + f_col) per element, where
+ *                  2^e_row, 2^f_col bound the largest |entry| of the row of op(A) and the column of B
+ *                  (method 1; method 0 rounds in wc-word arithmetic); 1 <= p_bits <= 252
+ * Constraints: k <= 2048.  C must not overlap A or B.
+ * Errors: ZKQ_EINVAL, ZKQ_ENOMEM, ZKQ_ECUDA.
+ */
+zkq_status zkq_mw_gemm(zkq_ctx* ctx, int count, const int32_t* m, const int32_t* n, const int32_t* k,
+                       const int32_t* opA, const double* A, const int64_t* a_off, int wa, const double* B,
+                       const int64_t* b_off, int wb, double* C, const int64_t* c_off, int wc, int p_bits, int method,
+                       void* stream);
 
 /*
  * zkq_mw_op: element-wise multi-word arithmetic, the building block of every refinement step

@@ -19,7 +19,7 @@ _lock = threading.Lock()
 
 ZKQ_OK, ZKQ_EINVAL, ZKQ_ENOMEM, ZKQ_ENOCONV, ZKQ_ETIMEOUT, ZKQ_ECUDA, ZKQ_EADMIT = range(7)
 ZKQ_FP64, ZKQ_DD, ZKQ_QD = 1, 2, 4
-ZKQ_PLAIN_RQI, ZKQ_OA_OZAKI = 0, 1
+ZKQ_PLAIN_RQI, ZKQ_OA_OZAKI, ZKQ_OA_FP64 = 0, 1, 2
 
 
 class ZkqError(RuntimeError):
@@ -61,6 +61,8 @@ def lib():
             L.zkq_eigh_batched.argtypes = [P, I, P, P, P, I, P, P, P, P]
             L.zkq_rqi_refine.restype = I
             L.zkq_rqi_refine.argtypes = [P, I, P, P, P, I, P, P, I, I, P, P, P, P, P]
+            L.zkq_mw_gemm.restype = I
+            L.zkq_mw_gemm.argtypes = [P, I, P, P, P, P, P, P, I, P, P, I, P, P, I, I, I, P]
             L.zkq_mw_op.restype = I
             L.zkq_mw_op.argtypes = [I, I, I64, P, P, P, I, P]
             _lib = L
@@ -142,6 +144,14 @@ def zkq_rqi_refine(ctx: Context, n, a_off, A, a_words, W, V, target_words, metho
     _check(lib().zkq_rqi_refine(ctx.handle, len(n_arr), n_p, o_p, _ptr(A), a_words, _ptr(W), _ptr(V), target_words,
                                 method, _ptr(W_out), _ptr(V_out), _ptr(err_est), _ptr(info), _stream(stream)),
            "zkq_rqi_refine")
+
+
+def zkq_mw_gemm(ctx: Context, m, n, k, opA, A, a_off, wa, B, b_off, wb, C, c_off, wc, p_bits, method, stream=None):
+    arrs = [_host_array(x, ctypes.c_int32) for x in (m, n, k, opA)]
+    offs = [_host_array(x, ctypes.c_int64) for x in (a_off, b_off, c_off)]
+    _check(lib().zkq_mw_gemm(ctx.handle, len(arrs[0][0]), arrs[0][1], arrs[1][1], arrs[2][1], arrs[3][1], _ptr(A),
+                             offs[0][1], wa, _ptr(B), offs[1][1], wb, _ptr(C), offs[2][1], wc, p_bits, method,
+                             _stream(stream)), "zkq_mw_gemm")
 
 
 def zkq_mw_op(op: int, words: int, count: int, a, b, out, on_device: bool, stream=None):

@@ -24,7 +24,13 @@ struct RqiBatch { const int32_t* n; const int64_t* a_off; const int64_t* w_off; 
 zkq_status launch_rqi(const RqiBatch& rb, int W, int WA, int grid, cudaStream_t st);
 size_t rqi_slot_doubles(int nmax, int W);
 
+struct OaBuffers { void** ws; size_t* ws_bytes; void** oz_ws; size_t* oz_bytes; void** oz_meta; size_t* oz_meta_bytes; };
+zkq_status oa_refine(void* ctx, const OaBuffers& buf, int batch, const int32_t* n, const int64_t* a_off,
+                     const double* A, int wa, const double* V, int W, double* W_out, double* V_out, double* err,
+                     int32_t* info, int max_iter, int prod_method, cudaStream_t st);
+
 }  // namespace zkq
+#include "ozaki.cuh"
 
 using namespace zkq;
 
@@ -36,6 +42,12 @@ struct zkq_ctx {
   size_t ws_bytes = 0;
   void* meta = nullptr;     // per-call metadata (offsets, orders)
   size_t meta_bytes = 0;
+  void* oa_ws = nullptr;    // refinement state (X, P, S, R, E, lambda, clusters)
+  size_t oa_bytes = 0;
+  void* oz_ws = nullptr;    // split-product scratch (digit slices, level sums)
+  size_t oz_bytes = 0;
+  void* oz_meta = nullptr;
+  size_t oz_meta_bytes = 0;
 };
 
 static zkq_status ensure(void** p, size_t* have, size_t need) {
@@ -88,21 +100,19 @@ zkq_status zkq_ctx_destroy(zkq_ctx* ctx) {
   if (!ctx) return ZKQ_OK;
   cudaSetDevice(ctx->device);
   cudaDeviceSynchronize();
-  if (ctx->ws) cudaFree(ctx->ws);
-  if (ctx->meta) cudaFree(ctx->meta);
+  for (void* p : {ctx->ws, ctx->meta, ctx->oa_ws, ctx->oz_ws, ctx->oz_meta}) if (p) cudaFree(p);
   delete ctx;
   return ZKQ_OK;
 }
 
 static constexpr int kSmallMax = 80;
 
-zkq_status zkq_eigh_batched(zkq_ctx* ctx, int batch, const int32_t* n, const int64_t* a_off,
-                            const double* A, int a_words, double* W, double* V, int32_t* info, void* stream) {
-  if (!ctx || batch < 0 || (batch > 0 && (!n || !a_off || !A || !W || !V || !info))) return ZKQ_EINVAL;
-  if (a_words != 1 && a_words != 2 && a_words != 4) return ZKQ_EINVAL;
-  if (batch == 0) return ZKQ_OK;
-  ZKQ_CUDA_TRY(cudaSetDevice(ctx->device));
-  cudaStream_t st = (cudaStream_t)stream;
+}  // extern "C"
+
+namespace zkq {
+zkq_status eigh_internal(void* vctx, int batch, const int32_t* n, const int64_t* a_off, const double* A, int a_words,
+                         double* W, double* V, int32_t* info, cudaStream_t st) {
+  zkq_ctx* ctx = (zkq_ctx*)vctx;
   std::vector<int64_t> w_off(batch), ws_off(batch, 0);
   std::vector<int32_t> small, large;
   int64_t acc = 0; size_t ws_need = 0; int max_small = 0, max_large = 0;
@@ -137,6 +147,19 @@ zkq_status zkq_eigh_batched(zkq_ctx* ctx, int batch, const int32_t* n, const int
                  (double*)((char*)ctx->ws + ws_need), ctx->cfg.max_sweeps};
   return launch_jacobi(jb, a_words, (int)small.size(), (int)large.size(), max_small, max_large, cluster, st);
 }
+}  // namespace zkq
+
+extern "C" {
+
+zkq_status zkq_eigh_batched(zkq_ctx* ctx, int batch, const int32_t* n, const int64_t* a_off,
+                            const double* A, int a_words, double* W, double* V, int32_t* info, void* stream) {
+  if (!ctx || batch < 0 || (batch > 0 && (!n || !a_off || !A || !W || !V || !info))) return ZKQ_EINVAL;
+  if (a_words != 1 && a_words != 2 && a_words != 4) return ZKQ_EINVAL;
+  if (batch == 0) return ZKQ_OK;
+  for (int b = 0; b < batch; ++b) if (n[b] < 1 || n[b] > 4096 || a_off[b] < 0) return ZKQ_EINVAL;
+  ZKQ_CUDA_TRY(cudaSetDevice(ctx->device));
+  return eigh_internal(ctx, batch, n, a_off, A, a_words, W, V, info, (cudaStream_t)stream);
+}
 
 zkq_status zkq_rqi_refine(zkq_ctx* ctx, int batch, const int32_t* n, const int64_t* a_off,
                           const double* A, int a_words, const double* W, const double* V,
@@ -145,11 +168,16 @@ zkq_status zkq_rqi_refine(zkq_ctx* ctx, int batch, const int32_t* n, const int64
   if (!ctx || batch < 0 || (batch > 0 && (!n || !a_off || !A || !W || !V || !W_out || !V_out || !err_est || !info)))
     return ZKQ_EINVAL;
   if ((a_words != 1 && a_words != 2 && a_words != 4) || (target_words != 2 && target_words != 4)) return ZKQ_EINVAL;
-  if (method != ZKQ_PLAIN_RQI && method != ZKQ_OA_OZAKI) return ZKQ_EINVAL;
+  if (method != ZKQ_PLAIN_RQI && method != ZKQ_OA_OZAKI && method != ZKQ_OA_FP64) return ZKQ_EINVAL;
   if (batch == 0) return ZKQ_OK;
-  if (method == ZKQ_OA_OZAKI) return ZKQ_EINVAL;   // provided by the refinement module when built
   ZKQ_CUDA_TRY(cudaSetDevice(ctx->device));
   cudaStream_t st = (cudaStream_t)stream;
+  if (method != ZKQ_PLAIN_RQI) {
+    for (int b = 0; b < batch; ++b) if (n[b] < 1 || n[b] > 2048 || a_off[b] < 0) return ZKQ_EINVAL;
+    OaBuffers ob{&ctx->oa_ws, &ctx->oa_bytes, &ctx->oz_ws, &ctx->oz_bytes, &ctx->oz_meta, &ctx->oz_meta_bytes};
+    return oa_refine(ctx, ob, batch, n, a_off, A, a_words, V, target_words, W_out, V_out, err_est, info,
+                     ctx->cfg.oa_max_iter, method == ZKQ_OA_OZAKI ? 1 : 0, st);
+  }
   std::vector<int64_t> w_off(batch);
   int64_t total = 0; int nmax = 0;
   for (int b = 0; b < batch; ++b) {
@@ -177,6 +205,26 @@ zkq_status zkq_rqi_refine(zkq_ctx* ctx, int batch, const int32_t* n, const int64
   RqiBatch rb{d_n, d_a, d_w, d_p, A, W, V, W_out, V_out, err_est, info, (double*)ctx->ws, (int64_t)slot, total,
               ctx->cfg.rqi_max_iter, d_c};
   return launch_rqi(rb, target_words, a_words, grid, st);
+}
+
+zkq_status zkq_mw_gemm(zkq_ctx* ctx, int count, const int32_t* m, const int32_t* n, const int32_t* k,
+                       const int32_t* opA, const double* A, const int64_t* a_off, int wa, const double* B,
+                       const int64_t* b_off, int wb, double* C, const int64_t* c_off, int wc, int p_bits, int method,
+                       void* stream) {
+  if (!ctx || count < 0 || (count > 0 && (!m || !n || !k || !opA || !A || !a_off || !B || !b_off || !C || !c_off)))
+    return ZKQ_EINVAL;
+  if (method != 0 && method != 1) return ZKQ_EINVAL;
+  if (p_bits < 1 || p_bits > 53 * 4 + 40) return ZKQ_EINVAL;
+  if (count == 0) return ZKQ_OK;
+  ZKQ_CUDA_TRY(cudaSetDevice(ctx->device));
+  std::vector<MwProd> pr(count);
+  for (int i = 0; i < count; ++i) {
+    if (m[i] < 1 || n[i] < 1 || k[i] < 1 || k[i] > 2048 || (opA[i] != 0 && opA[i] != 1) || a_off[i] < 0 || b_off[i] < 0 || c_off[i] < 0)
+      return ZKQ_EINVAL;
+    pr[i] = {m[i], n[i], k[i], opA[i], A + a_off[i] * 2 * wa, B + b_off[i] * 2 * wb, C + c_off[i] * 2 * wc, nullptr, 1.0, 0};
+  }
+  return mw_gemm_batched(pr.data(), count, wa, wb, wc, p_bits, method, &ctx->oz_ws, &ctx->oz_bytes, &ctx->oz_meta,
+                         &ctx->oz_meta_bytes, (cudaStream_t)stream);
 }
 
 }  // extern "C"

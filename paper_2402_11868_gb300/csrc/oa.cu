@@ -1,0 +1,456 @@
+// Precision recovery by block Ogita-Aishima refinement (Ogita & Aishima 2018; clustered eigenvalues:
+// Ogita & Aishima 2019), the build's chosen form of the paper's precision-recovery step (Section 2,
+// ZKCM_CUS paragraph).  With X the current eigenvector matrix (target precision, W words per real):
+//   P = A X,  S = X^H P,  R = I - X^H X                                  (split products, ozaki.cu)
+//   lambda_i = s_ii / (1 - r_ii)
+//   delta = 2 (||S - diag(lambda)||_F + ||A|| ||R||_F)
+//   e_ij = (s_ij + lambda_j r_ij) / (lambda_j - lambda_i)   if |lambda_i - lambda_j| > delta
+//   e_ij = r_ij / 2                                         otherwise (and on the diagonal)
+//   X <- X + X E
+// Columns stay sorted by eigenvalue, so a cluster is a maximal run of consecutive columns whose
+// neighbouring lambdas are within delta.  A cluster J whose block S_JJ is not yet diagonal is separated by
+// diagonalising T = S_JJ - mu I (mu = mean lambda over J, rounded to FP64 after the shift) with the FP64
+// Jacobi kernel and rotating X_J <- X_J W.  For spectra graded far below 2^-53 ||A|| each pass resolves
+// about 53 more bits of the small eigenvalues.  E only needs double-double: its entries are of the size of
+// the current error, so their relative accuracy requirement is at most ~106 bits.
+// A problem is converged once max |e_ij| <= 2^-(53W-6) and every cluster block is diagonal to that level;
+// it then takes one more (polishing) iteration, and lambda, X of the last iteration are reported.
+#include <vector>
+#include <algorithm>
+#include <cstring>
+#include "common.cuh"
+#include "mw.cuh"
+#include "reduce.cuh"
+#include "ozaki.cuh"
+
+namespace zkq {
+
+struct OaProb {
+  int n; int64_t xoff;         // element offset of the problem's n x n matrices in X, P, S, R, E
+  int64_t loff;                // offset (in eigenpairs) of lambda, cluster arrays
+  int64_t a_off;               // element offset of A, V, V_out
+};
+
+// ---- X <- promote(V) -------------------------------------------------------------------------
+template <int W>
+__global__ void oa_init_kernel(const OaProb* __restrict__ pr, const double* __restrict__ V, double* __restrict__ X) {
+  const OaProb p = pr[blockIdx.y];
+  int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= p.n * p.n) return;
+  const double* v = V + (p.a_off + e) * 2;
+  c_store(X + p.xoff * 2 * W, e, c_make(mw_from<W>(v[0]), mw_from<W>(v[1])));
+}
+
+// ---- per-problem statistics: lambda, delta, clusters -----------------------------------------
+struct OaStat { double maxE; double delta; double anorm; int nclusters; int clustered; double cl_off; int pad; };
+
+template <int W>
+__global__ void __launch_bounds__(256) oa_stats_kernel(const OaProb* __restrict__ pr, const double* __restrict__ S,
+                                                       const double* __restrict__ R, double* __restrict__ lam,
+                                                       int32_t* __restrict__ cl_start, int32_t* __restrict__ cl_len,
+                                                       OaStat* __restrict__ st, double tol) {
+  const OaProb p = pr[blockIdx.x];
+  const int n = p.n, tid = threadIdx.x;
+  __shared__ double sbuf[32];
+  const double* Sb = S + p.xoff * 2 * W;
+  const double* Rb = R + p.xoff * 2 * W;
+  double* lb = lam + p.loff * W;
+  // lambda_i = s_ii / (1 - r_ii)
+  double amax = 0.0;
+  for (int i = tid; i < n; i += blockDim.x) {
+    mw<W> s = c_load<W, W>(Sb, (size_t)i + (size_t)i * n).re;
+    mw<W> r = c_load<W, W>(Rb, (size_t)i + (size_t)i * n).re;
+    mw<W> l = mw_div(s, mw_add_d(mw_neg(r), 1.0));
+    mw_store(lb, i, l);
+    amax = fmax(amax, fabs(l.x[0]));
+  }
+  amax = block_max_d(amax, sbuf);
+  // Frobenius norms (leading words) of S - diag(lambda) and R
+  double sf = 0.0, rf = 0.0;
+  for (int e = tid; e < n * n; e += blockDim.x) {
+    int i = e % n, j = e / n;
+    const double* sp = Sb + (size_t)e * 2 * W;
+    const double* rp = Rb + (size_t)e * 2 * W;
+    double sr = sp[0], si = sp[W];
+    if (i == j) { sr = mw_sub(mw_load<W, W>(Sb + (size_t)e * 2 * W, 0), mw_load<W, W>(lb, i)).x[0]; si = 0.0; }
+    sf += sr * sr + si * si;
+    rf += rp[0] * rp[0] + rp[W] * rp[W];
+  }
+  for (int o = 16; o > 0; o >>= 1) { sf += __shfl_down_sync(0xffffffffu, sf, o); rf += __shfl_down_sync(0xffffffffu, rf, o); }
+  __shared__ double s_sf[8], s_rf[8];
+  if ((tid & 31) == 0) { s_sf[tid >> 5] = sf; s_rf[tid >> 5] = rf; }
+  __syncthreads();
+  if (tid == 0) {
+    double a = 0, b = 0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) { a += s_sf[w]; b += s_rf[w]; }
+    double delta = 2.0 * (sqrt(a) + amax * sqrt(b));
+    // clusters: runs of consecutive columns whose neighbouring lambdas are within delta
+    int ncl = 0, clustered = 0;
+    int start = 0;
+    for (int i = 1; i <= n; ++i) {
+      bool brk = (i == n);
+      if (!brk) {
+        mw<W> d = mw_sub(mw_load<W, W>(lb, i - 1), mw_load<W, W>(lb, i));
+        brk = fabs(d.x[0]) > delta;
+      }
+      if (brk) {
+        int len = i - start;
+        for (int c = start; c < i; ++c) { cl_start[p.loff + c] = start; cl_len[p.loff + c] = len; }
+        if (len > 1) { ++ncl; clustered += len; }
+        start = i;
+      }
+    }
+    st[blockIdx.x].delta = delta;
+    st[blockIdx.x].anorm = amax;
+    st[blockIdx.x].nclusters = ncl;
+    st[blockIdx.x].clustered = clustered;
+    st[blockIdx.x].maxE = 0.0;
+    st[blockIdx.x].cl_off = 0.0;
+  }
+  __syncthreads();
+  // largest off-diagonal |s_ij| inside clusters (relative to ||A||)
+  double off = 0.0;
+  for (int e = tid; e < n * n; e += blockDim.x) {
+    int i = e % n, j = e / n;
+    if (i == j || cl_start[p.loff + i] != cl_start[p.loff + j]) continue;
+    const double* sp = Sb + (size_t)e * 2 * W;
+    off = fmax(off, hypot(sp[0], sp[W]));
+  }
+  off = block_max_d(off, sbuf);
+  if (tid == 0) st[blockIdx.x].cl_off = amax > 0 ? off / amax : 0.0;
+  (void)tol;
+}
+
+__device__ __forceinline__ void atomic_max_nonneg(double* a, double v) {
+  atomicMax(reinterpret_cast<unsigned long long*>(a), (unsigned long long)__double_as_longlong(v));
+}
+
+// ---- E (double-double) -----------------------------------------------------------------------------
+template <int W>
+__global__ void oa_E_kernel(const OaProb* __restrict__ pr, const double* __restrict__ S, const double* __restrict__ R,
+                            const double* __restrict__ lam, const int32_t* __restrict__ cl_start,
+                            double* __restrict__ E, OaStat* __restrict__ st) {
+  const OaProb p = pr[blockIdx.y];
+  int e = blockIdx.x * blockDim.x + threadIdx.x;
+  double mag = 0.0;
+  if (e < p.n * p.n) {
+    const int n = p.n, i = e % n, j = e / n;
+    cmw<W> r = c_load<W, W>(R + p.xoff * 2 * W, e);
+    cmw<2> rr = c_make(mw_from_words<2, W>(r.re.x), mw_from_words<2, W>(r.im.x));
+    cmw<2> out;
+    if (i == j || cl_start[p.loff + i] == cl_start[p.loff + j]) {
+      out = c_scale_d(rr, 0.5);
+      if (i == j) out.im = mw_zero<2>();
+    } else {
+      cmw<W> s = c_load<W, W>(S + p.xoff * 2 * W, e);
+      mw<W> li = mw_load<W, W>(lam + p.loff * W, i), lj = mw_load<W, W>(lam + p.loff * W, j);
+      cmw<W> num = c_add(s, c_scale(r, lj));
+      mw<W> den = mw_sub(lj, li);
+      cmw<2> n2 = c_make(mw_from_words<2, W>(num.re.x), mw_from_words<2, W>(num.im.x));
+      mw<2> d2 = mw_from_words<2, W>(den.x);
+      mw<2> inv = mw_recip(d2);
+      out = c_scale(n2, inv);
+    }
+    c_store(E + p.xoff * 2 * 2, e, out);
+    mag = fmax(fabs(out.re.x[0]), fabs(out.im.x[0]));
+  }
+  for (int o = 16; o > 0; o >>= 1) mag = fmax(mag, __shfl_down_sync(0xffffffffu, mag, o));
+  if ((threadIdx.x & 31) == 0 && mag > 0) atomic_max_nonneg(&st[blockIdx.y].maxE, mag);
+}
+
+// ---- cluster blocks: T = S_JJ - mu I  (FP64) ---------------------------------------------------
+struct OaCluster { int prob; int start; int len; int64_t toff; int64_t woff; };
+
+template <int W>
+__global__ void oa_cluster_T_kernel(const OaProb* __restrict__ pr, const OaCluster* __restrict__ cl,
+                                    const double* __restrict__ S, const double* __restrict__ R,
+                                    const double* __restrict__ lam, double* __restrict__ T) {
+  const OaCluster c = cl[blockIdx.y];
+  const OaProb p = pr[c.prob];
+  int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= c.len * c.len) return;
+  int a = e % c.len, b = e / c.len;
+  // mu = mean of lambda over the cluster (recomputed by every thread; clusters are short)
+  mw<W> mu = mw_zero<W>();
+  for (int q = 0; q < c.len; ++q) mu = mw_add(mu, mw_load<W, W>(lam + p.loff * W, c.start + q));
+  mu = mw_mul_d(mu, 1.0 / c.len);
+  int i = c.start + a, j = c.start + b;
+  // T = X_J^H (A - mu I) X_J = S_JJ - mu (I - R_JJ): the shift acts through the computed metric, so the
+  // non-orthonormality of X (size of R) does not blur splits far below it
+  cmw<W> s = c_load<W, W>(S + p.xoff * 2 * W, (size_t)i + (size_t)j * p.n);
+  cmw<W> r = c_load<W, W>(R + p.xoff * 2 * W, (size_t)i + (size_t)j * p.n);
+  s = c_add(s, c_scale(r, mu));
+  if (a == b) { s.re = mw_sub(s.re, mu); s.im = mw_zero<W>(); }
+  T[(c.toff + e) * 2 + 0] = s.re.x[0] + (W > 1 ? s.re.x[1] : 0.0);
+  T[(c.toff + e) * 2 + 1] = a == b ? 0.0 : s.im.x[0] + (W > 1 ? s.im.x[1] : 0.0);
+}
+
+// copy rotated cluster columns (from Y = old X buffer) back into X
+template <int W>
+__global__ void oa_cluster_copy_kernel(const OaProb* __restrict__ pr, const OaCluster* __restrict__ cl,
+                                       const double* __restrict__ Y, double* __restrict__ X) {
+  const OaCluster c = cl[blockIdx.y];
+  const OaProb p = pr[c.prob];
+  int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= p.n * c.len) return;
+  size_t idx = (size_t)c.start * p.n + e;
+  const double* s = Y + (p.xoff + idx) * 2 * W;
+  double* d = X + (p.xoff + idx) * 2 * W;
+  for (int k = 0; k < 2 * W; ++k) d[k] = s[k];
+}
+
+// ---- output: sort, phase, residual estimate --------------------------------------------------------
+template <int W>
+__device__ __forceinline__ bool mw_greater(const mw<W>& a, const mw<W>& b) {
+  mw<W> d = mw_sub(a, b);
+  return d.x[0] > 0.0;
+}
+
+template <int W>
+__global__ void __launch_bounds__(256) oa_output_kernel(const OaProb* __restrict__ pr, const int32_t* __restrict__ which,
+                                                        const double* __restrict__ X, const double* __restrict__ P,
+                                                        const double* __restrict__ lam, const OaStat* __restrict__ st,
+                                                        double* __restrict__ W_out, double* __restrict__ V_out,
+                                                        double* __restrict__ err) {
+  const int b = which[blockIdx.x];
+  const OaProb p = pr[b];
+  const int n = p.n;
+  const double* lb = lam + p.loff * W;
+  const double anorm = fmax(st[b].anorm, 1e-300);
+  for (int c = threadIdx.x; c < n; c += blockDim.x) {
+    mw<W> lc = mw_load<W, W>(lb, c);
+    int rank = 0;
+    for (int d = 0; d < n; ++d) {
+      if (d == c) continue;
+      mw<W> ld = mw_load<W, W>(lb, d);
+      mw<W> df = mw_sub(ld, lc);
+      rank += (df.x[0] > 0.0) || (df.x[0] == 0.0 && d < c);
+    }
+    mw_store(W_out, p.loff + rank, lc);
+    const double* xc = X + (p.xoff + (size_t)c * n) * 2 * W;
+    const double* pc = P + (p.xoff + (size_t)c * n) * 2 * W;
+    int best = 0; double bm = -1.0;
+    mw<W> rr = mw_zero<W>();
+    for (int r = 0; r < n; ++r) {
+      double m2 = xc[r * 2 * W] * xc[r * 2 * W] + xc[r * 2 * W + W] * xc[r * 2 * W + W];
+      if (m2 > bm) { bm = m2; best = r; }
+      cmw<W> res = c_sub(c_load<W, W>(pc, r), c_scale(c_load<W, W>(xc, r), lc));
+      rr = mw_add(rr, c_abs2(res));
+    }
+    err[p.loff + rank] = sqrt(fmax(rr.x[0], 0.0)) / anorm;
+    cmw<W> xb = c_load<W, W>(xc, best);
+    mw<W> mag = mw_sqrt(c_abs2(xb));
+    cmw<W> ph = c_make(mw_div(xb.re, mag), mw_neg(mw_div(xb.im, mag)));
+    double* vo = V_out + (p.a_off + (size_t)rank * n) * 2 * W;
+    for (int r = 0; r < n; ++r) {
+      cmw<W> v = c_mul(c_load<W, W>(xc, r), ph);
+      if (r == best) v.im = mw_zero<W>();
+      c_store(vo, r, v);
+    }
+  }
+}
+
+// --------------------------------------------------------------------------------------------------
+struct OaBuffers { void** ws; size_t* ws_bytes; void** oz_ws; size_t* oz_bytes; void** oz_meta; size_t* oz_meta_bytes; };
+
+zkq_status eigh_internal(void* ctx, int batch, const int32_t* n, const int64_t* a_off, const double* A, int a_words,
+                         double* W, double* V, int32_t* info, cudaStream_t st);
+
+static size_t alg(size_t x) { return (x + 255) & ~(size_t)255; }
+
+static zkq_status grow_buf(void** p, size_t* have, size_t need) {
+  if (need <= *have) return ZKQ_OK;
+  if (*p) { cudaFree(*p); *p = nullptr; *have = 0; }
+  size_t want = std::max(need + need / 8, (size_t)1 << 20);
+  cudaError_t e = cudaMalloc(p, want);
+  if (e != cudaSuccess) { set_last_cuda_error(e); *p = nullptr; return ZKQ_ENOMEM; }
+  *have = want;
+  return ZKQ_OK;
+}
+
+template <int W>
+zkq_status oa_refine_t(void* ctx, const OaBuffers& buf, int batch, const int32_t* n, const int64_t* a_off,
+                       const double* A, int wa, const double* V, double* W_out, double* V_out, double* err,
+                       int32_t* info, int max_iter, int prod_method, cudaStream_t st) {
+  std::vector<OaProb> probs(batch);
+  int64_t xe = 0, le = 0; int nmax = 0;
+  for (int b = 0; b < batch; ++b) {
+    probs[b] = {n[b], xe, le, a_off[b]};
+    xe += (int64_t)n[b] * n[b]; le += n[b]; nmax = std::max(nmax, n[b]);
+  }
+  const size_t mat = (size_t)xe * 2 * W * sizeof(double);
+  size_t off = 0;
+  auto take = [&](size_t bytes) { size_t o = off; off += alg(bytes); return o; };
+  size_t oX = take(mat), oX2 = take(mat), oP = take(mat), oS = take(mat), oR = take(mat);
+  size_t oE = take((size_t)xe * 2 * 2 * sizeof(double));
+  size_t oL = take((size_t)le * W * sizeof(double));
+  size_t oCS = take((size_t)le * 4), oCL = take((size_t)le * 4);
+  size_t oST = take(sizeof(OaStat) * batch);
+  size_t oPR = take(sizeof(OaProb) * batch);
+  size_t oWH = take(sizeof(int32_t) * batch);
+  size_t oT = take((size_t)xe * 2 * sizeof(double));          // cluster T blocks (FP64), bounded by sum n^2
+  size_t oTW = take((size_t)le * sizeof(double));              // cluster eigenvalues
+  size_t oTV = take((size_t)xe * 2 * sizeof(double));         // cluster eigenvectors
+  size_t oTI = take((size_t)le * sizeof(int32_t));
+  size_t oCLD = take(sizeof(OaCluster) * le);
+  zkq_status s = grow_buf(buf.ws, buf.ws_bytes, off);
+  if (s != ZKQ_OK) return s;
+  char* base = (char*)*buf.ws;
+  double *X = (double*)(base + oX), *X2 = (double*)(base + oX2), *Pm = (double*)(base + oP), *Sm = (double*)(base + oS),
+         *Rm = (double*)(base + oR), *Em = (double*)(base + oE), *Lm = (double*)(base + oL);
+  int32_t *CS = (int32_t*)(base + oCS), *CL = (int32_t*)(base + oCL), *WH = (int32_t*)(base + oWH), *TI = (int32_t*)(base + oTI);
+  OaStat* ST = (OaStat*)(base + oST);
+  OaProb* PR = (OaProb*)(base + oPR);
+  double *T = (double*)(base + oT), *TW = (double*)(base + oTW), *TV = (double*)(base + oTV);
+  OaCluster* CLD = (OaCluster*)(base + oCLD);
+  ZKQ_CUDA_TRY(cudaMemcpyAsync(PR, probs.data(), sizeof(OaProb) * batch, cudaMemcpyHostToDevice, st));
+  ZKQ_CUDA_TRY(cudaMemsetAsync(info, 0, sizeof(int32_t) * batch, st));
+  {
+    dim3 g((nmax * nmax + 255) / 256, batch);
+    oa_init_kernel<W><<<g, 256, 0, st>>>(PR, V, X);
+    ZKQ_CUDA_TRY(cudaGetLastError());
+  }
+  const double tol = ldexp(1.0, -(53 * W - 6));
+  std::vector<int> active(batch, 1), polish(batch, 0), iters(batch, 0);
+  std::vector<OaStat> hst(batch);
+  std::vector<int32_t> hcl_len(le);
+  const int p_bits = 53 * W + 6;
+  for (int it = 0; it <= max_iter; ++it) {
+    std::vector<int> act;
+    for (int b = 0; b < batch; ++b) if (active[b]) act.push_back(b);
+    if (act.empty()) break;
+    // P = A X ; S = X^H P ; R = I - X^H X
+    std::vector<MwProd> p1, p2;
+    for (int b : act) {
+      const OaProb& q = probs[b];
+      double* Xb = X + q.xoff * 2 * W;
+      p1.push_back({q.n, q.n, q.n, 0, A + q.a_off * 2 * wa, Xb, Pm + q.xoff * 2 * W, nullptr, 1.0, 0});
+    }
+    s = mw_gemm_batched(p1.data(), (int)p1.size(), wa, W, W, p_bits, prod_method, buf.oz_ws, buf.oz_bytes, buf.oz_meta, buf.oz_meta_bytes, st);
+    if (s != ZKQ_OK) return s;
+    for (int b : act) {
+      const OaProb& q = probs[b];
+      double* Xb = X + q.xoff * 2 * W;
+      p2.push_back({q.n, q.n, q.n, 1, Xb, Pm + q.xoff * 2 * W, Sm + q.xoff * 2 * W, nullptr, 1.0, 0});
+      p2.push_back({q.n, q.n, q.n, 1, Xb, Xb, Rm + q.xoff * 2 * W, nullptr, -1.0, 1});
+    }
+    s = mw_gemm_batched(p2.data(), (int)p2.size(), W, W, W, p_bits, prod_method, buf.oz_ws, buf.oz_bytes, buf.oz_meta, buf.oz_meta_bytes, st);
+    if (s != ZKQ_OK) return s;
+    // statistics for every problem (inactive ones keep their last values: recompute is harmless but skipped)
+    std::vector<OaProb> ap; for (int b : act) ap.push_back(probs[b]);
+    OaProb* APR = PR;   // the stats/E kernels index PR by the active list
+    std::vector<int32_t> actv(act.begin(), act.end());
+    ZKQ_CUDA_TRY(cudaMemcpyAsync(WH, actv.data(), sizeof(int32_t) * actv.size(), cudaMemcpyHostToDevice, st));
+    // pack the active problems' descriptors at the front of a scratch copy
+    OaProb* PRA = (OaProb*)(base + oCLD);   // reuse: cluster list is built after these kernels
+    ZKQ_CUDA_TRY(cudaMemcpyAsync(PRA, ap.data(), sizeof(OaProb) * ap.size(), cudaMemcpyHostToDevice, st));
+    oa_stats_kernel<W><<<(unsigned)ap.size(), 256, 0, st>>>(PRA, Sm, Rm, Lm, CS, CL, ST, tol);
+    ZKQ_CUDA_TRY(cudaGetLastError());
+    {
+      int mx = 0; for (auto& q : ap) mx = std::max(mx, q.n * q.n);
+      dim3 g((mx + 255) / 256, (unsigned)ap.size());
+      oa_E_kernel<W><<<g, 256, 0, st>>>(PRA, Sm, Rm, Lm, CS, Em, ST);
+      ZKQ_CUDA_TRY(cudaGetLastError());
+    }
+    std::vector<OaStat> ast(ap.size());
+    ZKQ_CUDA_TRY(cudaMemcpyAsync(ast.data(), ST, sizeof(OaStat) * ap.size(), cudaMemcpyDeviceToHost, st));
+    ZKQ_CUDA_TRY(cudaMemcpyAsync(hcl_len.data(), CL, sizeof(int32_t) * le, cudaMemcpyDeviceToHost, st));
+    ZKQ_CUDA_TRY(cudaStreamSynchronize(st));
+    (void)APR;
+    // convergence decisions
+    std::vector<int> finish, upd;
+    for (size_t a = 0; a < act.size(); ++a) {
+      int b = act[a];
+      hst[b] = ast[a];
+      iters[b] = it;
+      bool conv = ast[a].maxE <= tol && ast[a].cl_off <= tol;
+      if (polish[b] || it == max_iter) finish.push_back(b);
+      else { if (conv) polish[b] = 1; upd.push_back(b); }
+    }
+    if (!finish.empty()) {
+      // statistics of finishing problems are in ST at their active index: copy to a per-problem array
+      std::vector<OaStat> fst(batch);
+      for (size_t a = 0; a < act.size(); ++a) fst[act[a]] = ast[a];
+      ZKQ_CUDA_TRY(cudaMemcpyAsync(ST, fst.data(), sizeof(OaStat) * batch, cudaMemcpyHostToDevice, st));
+      ZKQ_CUDA_TRY(cudaMemcpyAsync(WH, finish.data(), sizeof(int32_t) * finish.size(), cudaMemcpyHostToDevice, st));
+      ZKQ_CUDA_TRY(cudaMemcpyAsync(PR, probs.data(), sizeof(OaProb) * batch, cudaMemcpyHostToDevice, st));
+      oa_output_kernel<W><<<(unsigned)finish.size(), 256, 0, st>>>(PR, WH, X, Pm, Lm, ST, W_out, V_out, err);
+      ZKQ_CUDA_TRY(cudaGetLastError());
+      std::vector<int32_t> hinfo(batch, 0);
+      bool any = false;
+      for (int b : finish) {
+        active[b] = 0;
+        if (!polish[b]) { hinfo[b] = it > 0 ? it : 1; any = true; }
+      }
+      if (any) {
+        for (int b : finish) if (hinfo[b]) ZKQ_CUDA_TRY(cudaMemcpyAsync(info + b, &hinfo[b], sizeof(int32_t), cudaMemcpyHostToDevice, st));
+        ZKQ_CUDA_TRY(cudaStreamSynchronize(st));
+      }
+    }
+    if (upd.empty()) continue;
+    // X2 = X + X E  (E double-double)
+    std::vector<MwProd> p3;
+    for (int b : upd) {
+      const OaProb& q = probs[b];
+      double* Xb = X + q.xoff * 2 * W;
+      p3.push_back({q.n, q.n, q.n, 0, Xb, Em + q.xoff * 2 * 2, X2 + q.xoff * 2 * W, Xb, 1.0, 0});
+    }
+    // E is indexed by the active order in the E kernel: it wrote at each problem's own xoff, so p3 is direct
+    s = mw_gemm_batched(p3.data(), (int)p3.size(), W, 2, W, p_bits, prod_method, buf.oz_ws, buf.oz_bytes, buf.oz_meta, buf.oz_meta_bytes, st);
+    if (s != ZKQ_OK) return s;
+    // clusters that still need separation
+    std::vector<OaCluster> cls;
+    int64_t toff = 0, woff = 0;
+    for (int b : upd) {
+      const OaProb& q = probs[b];
+      bool need = hst[b].cl_off > tol && hst[b].nclusters > 0;
+      if (!need) continue;
+      for (int c = 0; c < q.n;) {
+        int len = hcl_len[q.loff + c];
+        if (len > 1) { cls.push_back({b, c, len, toff, woff}); toff += (int64_t)len * len; woff += len; }
+        c += std::max(len, 1);
+      }
+    }
+    if (!cls.empty()) {
+      int maxl = 0; for (auto& c : cls) maxl = std::max(maxl, c.len);
+      ZKQ_CUDA_TRY(cudaMemcpyAsync(PR, probs.data(), sizeof(OaProb) * batch, cudaMemcpyHostToDevice, st));
+      ZKQ_CUDA_TRY(cudaMemcpyAsync(CLD, cls.data(), sizeof(OaCluster) * cls.size(), cudaMemcpyHostToDevice, st));
+      dim3 g((maxl * maxl + 255) / 256, (unsigned)cls.size());
+      oa_cluster_T_kernel<W><<<g, 256, 0, st>>>(PR, CLD, Sm, Rm, Lm, T);
+      ZKQ_CUDA_TRY(cudaGetLastError());
+      std::vector<int32_t> cn(cls.size()); std::vector<int64_t> co(cls.size());
+      for (size_t c = 0; c < cls.size(); ++c) { cn[c] = cls[c].len; co[c] = cls[c].toff; }
+      s = eigh_internal(ctx, (int)cls.size(), cn.data(), co.data(), T, 1, TW, TV, TI, st);
+      if (s != ZKQ_OK) return s;
+      // Y_J = X2_J W_J into the X buffer (free now), then copy back into X2
+      std::vector<MwProd> p4;
+      for (auto& c : cls) {
+        const OaProb& q = probs[c.prob];
+        p4.push_back({q.n, c.len, c.len, 0, X2 + (q.xoff + (int64_t)c.start * q.n) * 2 * W, TV + c.toff * 2,
+                      X + (q.xoff + (int64_t)c.start * q.n) * 2 * W, nullptr, 1.0, 0});
+      }
+      s = mw_gemm_batched(p4.data(), (int)p4.size(), W, 1, W, p_bits, prod_method, buf.oz_ws, buf.oz_bytes, buf.oz_meta, buf.oz_meta_bytes, st);
+      if (s != ZKQ_OK) return s;
+      dim3 g2((nmax * maxl + 255) / 256, (unsigned)cls.size());
+      oa_cluster_copy_kernel<W><<<g2, 256, 0, st>>>(PR, CLD, X, X2);
+      ZKQ_CUDA_TRY(cudaGetLastError());
+    }
+    // X <- X2 for updated problems (swap buffers by copying the updated problems' matrices)
+    for (int b : upd) {
+      const OaProb& q = probs[b];
+      ZKQ_CUDA_TRY(cudaMemcpyAsync(X + q.xoff * 2 * W, X2 + q.xoff * 2 * W, (size_t)q.n * q.n * 2 * W * sizeof(double),
+                                   cudaMemcpyDeviceToDevice, st));
+    }
+  }
+  return ZKQ_OK;
+}
+
+zkq_status oa_refine(void* ctx, const OaBuffers& buf, int batch, const int32_t* n, const int64_t* a_off,
+                     const double* A, int wa, const double* V, int W, double* W_out, double* V_out, double* err,
+                     int32_t* info, int max_iter, int prod_method, cudaStream_t st) {
+  if (W == 2) return oa_refine_t<2>(ctx, buf, batch, n, a_off, A, wa, V, W_out, V_out, err, info, max_iter, prod_method, st);
+  if (W == 4) return oa_refine_t<4>(ctx, buf, batch, n, a_off, A, wa, V, W_out, V_out, err, info, max_iter, prod_method, st);
+  return ZKQ_EINVAL;
+}
+
+}  // namespace zkq

@@ -1,0 +1,514 @@
+// Ozaki-style split products of multi-word complex matrices on tensor cores.
+//
+// Every row of op(A) is scaled by 2^{-e_i} and every column of B by 2^{-f_j} (powers of two, so |x| < 1/2),
+// turned into a fixed-point integer (64-bit limbs, truncating below 2^{-b s}) and split into s balanced
+// digits sigma_t in [-2^{b-1}, 2^{b-1}]:  x ~ 2^{e} sum_t sigma_t 2^{-b t}.  Then
+//   op(A) B = 2^{e_i + f_j} sum_{t,u} 2^{-b(t+u)} (Ahat_t Bhat_u),
+// and every digit product Ahat_t Bhat_u is an integer matrix product that fp16 tensor cores with fp32
+// accumulation compute exactly while every partial sum stays below 2^24.  Pairs with t + u > S are
+// dropped (their total is below the requested precision).  Pairs of the same level d = t + u are summed
+// in chunks of G pairs per fp32 accumulator (G K' 2^{2(b-1)} <= 2^24), each chunk is added exactly into an
+// int32 level sum D_d, and D_d (d = 2..S) are recombined exactly as one wide integer
+//   I = sum_d D_d 2^{b(S-d)},  value = 2^{e_i + f_j - b S} I,
+// rounded once into the output's double words.  Complex products use the real embedding
+//   Re C = [Re op(A) | Im op(A)] [Re B ; -Im B],  Im C = [Re op(A) | Im op(A)] [Im B ; Re B]   (K' = 2k).
+#include "ozaki.cuh"
+#include "mw.cuh"
+#include <vector>
+#include <algorithm>
+#include <cstring>
+
+namespace zkq {
+
+// ------------------------------------------------------------------------------------------------
+// 320-bit two's complement integers in five 64-bit limbs (little endian)
+struct Big { uint64_t l[5]; };
+
+__device__ __forceinline__ void big_zero(Big& x) { for (int i = 0; i < 5; ++i) x.l[i] = 0; }
+__device__ __forceinline__ bool big_neg(const Big& x) { return (int64_t)x.l[4] < 0; }
+__device__ __forceinline__ void big_negate(Big& x) {
+  uint64_t c = 1;
+  for (int i = 0; i < 5; ++i) { uint64_t v = ~x.l[i] + c; c = (c && v == 0) ? 1 : 0; x.l[i] = v; }
+}
+// x += (neg ? -1 : 1) * m * 2^shift   (m < 2^63, 0 <= shift, shift + 64 <= 320)
+__device__ __forceinline__ void big_add_shifted(Big& x, uint64_t m, int shift, bool neg) {
+  if (m == 0) return;
+  uint64_t w[5] = {0, 0, 0, 0, 0};
+  int li = shift >> 6, bs = shift & 63;
+  if (li < 5) w[li] = m << bs;
+  if (bs && li + 1 < 5) w[li + 1] = m >> (64 - bs);
+  if (!neg) {
+    uint64_t c = 0;
+    for (int i = 0; i < 5; ++i) { uint64_t a = x.l[i], t = a + w[i]; uint64_t c1 = t < a; uint64_t t2 = t + c; c = c1 | (t2 < t); x.l[i] = t2; }
+  } else {
+    uint64_t br = 0;
+    for (int i = 0; i < 5; ++i) { uint64_t a = x.l[i], t = a - w[i]; uint64_t b1 = a < w[i]; uint64_t t2 = t - br; br = b1 | (t < br); x.l[i] = t2; }
+  }
+}
+// x += v * 2^shift for a signed 64-bit v
+__device__ __forceinline__ void big_add_signed(Big& x, int64_t v, int shift) {
+  if (v >= 0) big_add_shifted(x, (uint64_t)v, shift, false);
+  else big_add_shifted(x, (uint64_t)(-v), shift, true);
+}
+// arithmetic shift right by s (< 64) bits
+__device__ __forceinline__ void big_sar(Big& x, int s) {
+  for (int i = 0; i < 4; ++i) x.l[i] = (x.l[i] >> s) | (x.l[i + 1] << (64 - s));
+  x.l[4] = (uint64_t)((int64_t)x.l[4] >> s);
+}
+__device__ __forceinline__ int big_top_bit(const Big& x) {
+  for (int i = 4; i >= 0; --i) if (x.l[i]) return 64 * i + 63 - __clzll(x.l[i]);
+  return -1;
+}
+__device__ __forceinline__ int big_bit(const Big& x, int i) { return i < 0 ? 0 : (int)((x.l[i >> 6] >> (i & 63)) & 1); }
+
+// decompose a finite double: |x| = m 2^q, m < 2^53
+__device__ __forceinline__ void dsplit(double x, uint64_t& m, int& q, bool& neg) {
+  uint64_t b = (uint64_t)__double_as_longlong(x);
+  neg = (b >> 63) != 0;
+  int be = (int)((b >> 52) & 0x7FF);
+  uint64_t f = b & 0xFFFFFFFFFFFFFULL;
+  if (be == 0) { m = f; q = -1074; } else { m = f | (1ULL << 52); q = be - 1075; }
+}
+
+// fixed point: X = trunc(x * 2^{fix}) summed word by word (each word truncated toward zero)
+template <int K>
+__device__ __forceinline__ void to_fixed(const double* w, int fix, bool negate, Big& X) {
+  big_zero(X);
+  for (int k = 0; k < K; ++k) {
+    double v = w[k];
+    if (v == 0.0) continue;
+    uint64_t m; int q; bool ng; dsplit(v, m, q, ng);
+    int sh = q + fix;
+    if (sh < 0) { if (-sh >= 64) continue; m >>= -sh; sh = 0; }
+    if (sh > 256) continue;              // cannot happen for scaled inputs (|x 2^-e| < 1/2)
+    big_add_shifted(X, m, sh, ng != negate);
+  }
+}
+
+// s balanced base-2^b digits of X (|X| < 2^{b s - 1}); digit t (1-based, most significant first)
+template <typename F>
+__device__ __forceinline__ void digits(Big X, int b, int s, F&& emit) {
+  const int64_t half = 1LL << (b - 1), base = 1LL << b;
+  for (int t = s; t >= 1; --t) {
+    int64_t d = (int64_t)(X.l[0] & (uint64_t)(base - 1));
+    if (d > half) d -= base;
+    big_add_signed(X, -d, 0);
+    big_sar(X, b);
+    emit(t, (int)d);
+  }
+}
+
+// round the signed big integer R to the nearest double times 2^scale, subtract that double from R
+__device__ double big_round_off(Big& R, int scale) {
+  bool ng = big_neg(R);
+  Big M = R; if (ng) big_negate(M);
+  int tb = big_top_bit(M);
+  if (tb < 0) return 0.0;
+  int lo = tb - 52;
+  uint64_t m = 0;
+  if (lo >= 0) {
+    int li = lo >> 6, bs = lo & 63;
+    m = M.l[li] >> bs;
+    if (bs && li + 1 < 5) m |= M.l[li + 1] << (64 - bs);
+    m &= (1ULL << 53) - 1;
+    int rnd = big_bit(M, lo - 1);
+    bool sticky = false;
+    for (int i = 0; i < ((lo - 1) >> 6) && !sticky; ++i) sticky = M.l[i] != 0;
+    if (!sticky && lo - 1 > 0) {
+      int li2 = (lo - 1) >> 6, b2 = (lo - 1) & 63;
+      sticky = (M.l[li2] & ((1ULL << b2) - 1)) != 0;
+    }
+    if (rnd && (sticky || (m & 1))) m += 1;
+  } else {
+    m = M.l[0];                          // fewer than 53 significant bits: exact
+    lo = 0;
+  }
+  // R -= sign * m * 2^lo
+  big_add_shifted(R, m, lo, !ng);
+  double v = ldexp((double)m, lo + scale);
+  return ng ? -v : v;
+}
+
+// ------------------------------------------------------------------------------------------------
+OzPlan ozaki_plan(int max_kprime, int wa, int wb, int p_out_bits) {
+  OzPlan p;
+  p.b = max_kprime <= 1024 ? 8 : 7;
+  int lg = 0; while ((1 << lg) < max_kprime) ++lg;
+  auto need = [&](int words) {
+    int bits_in = 53 * words + 2;
+    int bits = std::min(bits_in, p_out_bits + 2 + lg);
+    return (bits + p.b - 1) / p.b + 1;
+  };
+  p.sA = need(wa);
+  p.sB = need(wb);
+  p.S = std::min(p.sA + p.sB, (p_out_bits + 2 * (p.b - 1) + lg + 8 + p.b - 1) / p.b + 1);
+  long long cap = (1LL << 24) / ((long long)max_kprime << (2 * (p.b - 1)));
+  p.G = (int)std::max(1LL, cap);
+  p.npairs = 0;
+  return p;
+}
+
+static std::vector<OzPair> make_pairs(const OzPlan& p) {
+  std::vector<OzPair> v;
+  for (int d = 2; d <= p.S; ++d) {
+    int cnt = 0;
+    int first = (int)v.size();
+    for (int t = std::max(1, d - p.sB); t <= std::min(p.sA, d - 1); ++t) {
+      OzPair q; q.t = (int16_t)t; q.u = (int16_t)(d - t); q.level = (int16_t)d; q.flags = 0;
+      v.push_back(q);
+      if (++cnt == p.G) { v.back().flags |= 1; cnt = 0; }
+    }
+    if ((int)v.size() > first) v.back().flags |= 3;
+  }
+  return v;
+}
+
+// ------------------------------------------------------------------------------------------------
+// exponents: rows of op(A), columns of B
+template <int WA, int WB>
+__global__ void oz_scale_kernel(const OzProd* __restrict__ P) {
+  const OzProd p = P[blockIdx.y];
+  int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r < p.m) {
+    double mx = 0.0;
+    for (int l = 0; l < p.k; ++l) {
+      const double* q = p.opA ? p.A + ((size_t)l + (size_t)r * p.k) * 2 * WA : p.A + ((size_t)r + (size_t)l * p.m) * 2 * WA;
+      mx = fmax(mx, fmax(fabs(q[0]), fabs(q[WA])));
+    }
+    p.eA[r] = mx > 0 ? ilogb(mx) + 2 : 0;
+  } else if (r < p.m + p.n) {
+    int j = r - p.m;
+    double mx = 0.0;
+    for (int l = 0; l < p.k; ++l) {
+      const double* q = p.B + ((size_t)l + (size_t)j * p.k) * 2 * WB;
+      mx = fmax(mx, fmax(fabs(q[0]), fabs(q[WB])));
+    }
+    p.eB[j] = mx > 0 ? ilogb(mx) + 2 : 0;
+  }
+}
+
+template <int WA>
+__global__ void oz_slice_A_kernel(const OzProd* __restrict__ P, int b, int sA) {
+  const OzProd p = P[blockIdx.y];
+  size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  size_t tot = (size_t)p.mp * p.kp;
+  if (e >= tot) return;
+  int i = (int)(e / p.kp), lp = (int)(e % p.kp);
+  const size_t plane = (size_t)p.mp * p.kp;
+  if (i >= p.m || lp >= 2 * p.k) {
+    for (int t = 0; t < sA; ++t) p.Ahat[t * plane + e] = __float2half_rn(0.0f);
+    return;
+  }
+  bool im = lp >= p.k;
+  int l = im ? lp - p.k : lp;
+  const double* q = p.opA ? p.A + ((size_t)l + (size_t)i * p.k) * 2 * WA : p.A + ((size_t)i + (size_t)l * p.m) * 2 * WA;
+  bool negate = im && p.opA;             // conj for A^H
+  Big X; to_fixed<WA>(q + (im ? WA : 0), b * sA - p.eA[i], negate, X);
+  digits(X, b, sA, [&](int t, int d) { p.Ahat[(size_t)(t - 1) * plane + e] = __int2half_rn(d); });
+}
+
+template <int WB>
+__global__ void oz_slice_B_kernel(const OzProd* __restrict__ P, int b, int sB) {
+  const OzProd p = P[blockIdx.y];
+  size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  size_t tot = (size_t)p.np2 * p.kp;
+  if (e >= tot) return;
+  int jp = (int)(e / p.kp), lp = (int)(e % p.kp);
+  const size_t plane = (size_t)p.np2 * p.kp;
+  if (jp >= 2 * p.n || lp >= 2 * p.k) {
+    for (int t = 0; t < sB; ++t) p.Bhat[t * plane + e] = __float2half_rn(0.0f);
+    return;
+  }
+  bool imcol = jp >= p.n;
+  int j = imcol ? jp - p.n : jp;
+  bool lower = lp >= p.k;
+  int l = lower ? lp - p.k : lp;
+  // re column: [Re B; -Im B];  im column: [Im B; Re B]
+  bool use_im = imcol ? !lower : lower;
+  bool negate = !imcol && lower;
+  const double* q = p.B + ((size_t)l + (size_t)j * p.k) * 2 * WB + (use_im ? WB : 0);
+  Big X; to_fixed<WB>(q, b * sB - p.eB[j], negate, X);
+  digits(X, b, sB, [&](int t, int d) { p.Bhat[(size_t)(t - 1) * plane + e] = __int2half_rn(d); });
+}
+
+// ------------------------------------------------------------------------------------------------
+// slice GEMM: fp16 x fp16 -> fp32 (exact), mma.sync m16n8k16, CTA tile 128 x 128 x 32, 8 warps (2 x 4)
+constexpr int OZ_BM = 128, OZ_BN = 128, OZ_BK = 32, OZ_STAGES = 3;
+
+struct OzTile { int prod, ti, tj; };
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void* src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" :: "r"(dst), "l"(src));
+}
+__device__ __forceinline__ int swz(int row, int chunk) { return row * 64 + ((chunk ^ ((row >> 1) & 3)) << 4); }
+
+__global__ void __launch_bounds__(256) oz_gemm_kernel(const OzProd* __restrict__ P, const OzTile* __restrict__ tiles,
+                                                      const OzPair* __restrict__ pairs, int npairs, int S) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  const OzTile tl = tiles[blockIdx.x];
+  const OzProd p = P[tl.prod];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int wm = warp >> 2, wn = warp & 3;
+  const int nk = p.kp / OZ_BK;
+  const int total = npairs * nk;
+  const size_t planeA = (size_t)p.mp * p.kp, planeB = (size_t)p.np2 * p.kp;
+  const __half* Abase = p.Ahat + (size_t)tl.ti * OZ_BM * p.kp;
+  const __half* Bbase = p.Bhat + (size_t)tl.tj * OZ_BN * p.kp;
+  unsigned char* sA = smem;                                   // STAGES x 8 KB
+  unsigned char* sB = smem + OZ_STAGES * OZ_BM * 64;          // STAGES x 8 KB
+
+  auto load = [&](int step, int stage) {
+    if (step < total) {
+      const OzPair pr = pairs[step / nk];
+      const int kt = step % nk;
+      const __half* a = Abase + (size_t)(pr.t - 1) * planeA + kt * OZ_BK;
+      const __half* bb = Bbase + (size_t)(pr.u - 1) * planeB + kt * OZ_BK;
+      for (int c = tid; c < OZ_BM * 4; c += 256) {
+        int row = c >> 2, ch = c & 3;
+        cp_async16(smem_u32(sA + stage * OZ_BM * 64 + swz(row, ch)), a + (size_t)row * p.kp + ch * 8);
+        cp_async16(smem_u32(sB + stage * OZ_BN * 64 + swz(row, ch)), bb + (size_t)row * p.kp + ch * 8);
+      }
+    }
+    asm volatile("cp.async.commit_group;\n" ::);
+  };
+
+  float acc[4][4][4];
+  int32_t dacc[4][4][4];
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b2 = 0; b2 < 4; ++b2)
+#pragma unroll
+      for (int c = 0; c < 4; ++c) { acc[a][b2][c] = 0.f; dacc[a][b2][c] = 0; }
+
+  for (int s = 0; s < OZ_STAGES - 1; ++s) load(s, s);
+
+  for (int step = 0; step < total; ++step) {
+    asm volatile("cp.async.wait_group %0;\n" :: "n"(OZ_STAGES - 2));
+    __syncthreads();
+    load(step + OZ_STAGES - 1, (step + OZ_STAGES - 1) % OZ_STAGES);
+    const int stage = step % OZ_STAGES;
+    const unsigned char* As = sA + stage * OZ_BM * 64;
+    const unsigned char* Bs = sB + stage * OZ_BN * 64;
+#pragma unroll
+    for (int kk = 0; kk < 2; ++kk) {
+      uint32_t af[4][4], bf[4][2];
+#pragma unroll
+      for (int mi = 0; mi < 4; ++mi) {
+        int row = wm * 64 + mi * 16 + (lane & 15);
+        int ch = kk * 2 + (lane >> 4);
+        asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];\n"
+                     : "=r"(af[mi][0]), "=r"(af[mi][1]), "=r"(af[mi][2]), "=r"(af[mi][3])
+                     : "r"(smem_u32(As + swz(row, ch))));
+      }
+#pragma unroll
+      for (int nj = 0; nj < 2; ++nj) {
+        int row = wn * 32 + nj * 16 + (lane & 7) + ((lane >> 4) << 3);
+        int ch = kk * 2 + ((lane >> 3) & 1);
+        asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];\n"
+                     : "=r"(bf[2 * nj][0]), "=r"(bf[2 * nj][1]), "=r"(bf[2 * nj + 1][0]), "=r"(bf[2 * nj + 1][1])
+                     : "r"(smem_u32(Bs + swz(row, ch))));
+      }
+#pragma unroll
+      for (int mi = 0; mi < 4; ++mi)
+#pragma unroll
+        for (int ni = 0; ni < 4; ++ni)
+          asm volatile("mma.sync.aligned.m16n8k16.row.col.f32.f16.f16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};\n"
+                       : "+f"(acc[mi][ni][0]), "+f"(acc[mi][ni][1]), "+f"(acc[mi][ni][2]), "+f"(acc[mi][ni][3])
+                       : "r"(af[mi][0]), "r"(af[mi][1]), "r"(af[mi][2]), "r"(af[mi][3]), "r"(bf[ni][0]), "r"(bf[ni][1]));
+    }
+    if (step % nk == nk - 1) {
+      const OzPair pr = pairs[step / nk];
+      if (pr.flags & 1) {
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+          for (int b2 = 0; b2 < 4; ++b2)
+#pragma unroll
+            for (int c = 0; c < 4; ++c) { dacc[a][b2][c] += __float2int_rn(acc[a][b2][c]); acc[a][b2][c] = 0.f; }
+      }
+      if (pr.flags & 2) {
+        int32_t* D = p.D + (size_t)pr.level * p.mp * p.np2;
+#pragma unroll
+        for (int mi = 0; mi < 4; ++mi)
+#pragma unroll
+          for (int ni = 0; ni < 4; ++ni) {
+            int r = tl.ti * OZ_BM + wm * 64 + mi * 16 + (lane >> 2);
+            int c = tl.tj * OZ_BN + wn * 32 + ni * 8 + (lane & 3) * 2;
+            *reinterpret_cast<int2*>(D + (size_t)r * p.np2 + c) = make_int2(dacc[mi][ni][0], dacc[mi][ni][1]);
+            *reinterpret_cast<int2*>(D + (size_t)(r + 8) * p.np2 + c) = make_int2(dacc[mi][ni][2], dacc[mi][ni][3]);
+            dacc[mi][ni][0] = dacc[mi][ni][1] = dacc[mi][ni][2] = dacc[mi][ni][3] = 0;
+          }
+      }
+    }
+  }
+  asm volatile("cp.async.wait_group 0;\n" ::);
+}
+
+// ------------------------------------------------------------------------------------------------
+template <int WC>
+__device__ __forceinline__ mw<WC> combine_value(const OzProd& p, int i, int col, int e_sum, int b, int S) {
+  Big I; big_zero(I);
+  for (int d = 2; d <= S; ++d) {
+    int32_t v = p.D[(size_t)d * p.mp * p.np2 + (size_t)i * p.np2 + col];
+    big_add_signed(I, (int64_t)v, b * (S - d));
+  }
+  mw<WC> r;
+  for (int k = 0; k < WC; ++k) r.x[k] = big_round_off(I, e_sum - b * S);
+  return r;
+}
+
+template <int WC>
+__global__ void oz_combine_kernel(const OzProd* __restrict__ P, int b, int S) {
+  const OzProd p = P[blockIdx.y];
+  int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= p.m * p.n) return;
+  int i = e % p.m, j = e / p.m;
+  int es = p.eA[i] + p.eB[j];
+  cmw<WC> v = c_make(combine_value<WC>(p, i, j, es, b, S), combine_value<WC>(p, i, j + p.n, es, b, S));
+  if (p.sgn < 0) v = c_make(mw_neg(v.re), mw_neg(v.im));
+  if (p.base) v = c_add(v, c_load<WC, WC>(p.base, (size_t)e));
+  if (p.base_identity && i == j) v.re = mw_add_d(v.re, 1.0);
+  c_store(p.C, (size_t)e, v);
+}
+
+// ------------------------------------------------------------------------------------------------
+// plain multi-word GEMM on the FP64 pipe (one output element per thread)
+template <int WA, int WB, int WC>
+__global__ void mw_gemm_plain_kernel(const OzProd* __restrict__ P) {
+  const OzProd p = P[blockIdx.y];
+  int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= p.m * p.n) return;
+  int i = e % p.m, j = e / p.m;
+  cmw<WC> s = c_zero<WC>();
+  for (int l = 0; l < p.k; ++l) {
+    cmw<WC> a = p.opA ? c_conj(c_load<WC, WA>(p.A, (size_t)l + (size_t)i * p.k)) : c_load<WC, WA>(p.A, (size_t)i + (size_t)l * p.m);
+    cmw<WC> bb = c_load<WC, WB>(p.B, (size_t)l + (size_t)j * p.k);
+    s = c_add(s, c_mul(a, bb));
+  }
+  if (p.sgn < 0) s = c_make(mw_neg(s.re), mw_neg(s.im));
+  if (p.base) s = c_add(s, c_load<WC, WC>(p.base, (size_t)e));
+  if (p.base_identity && i == j) s.re = mw_add_d(s.re, 1.0);
+  c_store(p.C, (size_t)e, s);
+}
+
+// ------------------------------------------------------------------------------------------------
+static size_t al(size_t x) { return (x + 255) & ~(size_t)255; }
+
+static zkq_status grow(void** p, size_t* have, size_t need) {
+  if (need <= *have) return ZKQ_OK;
+  if (*p) { cudaFree(*p); *p = nullptr; *have = 0; }
+  size_t want = std::max(need + need / 4, (size_t)1 << 20);
+  cudaError_t e = cudaMalloc(p, want);
+  if (e != cudaSuccess) { set_last_cuda_error(e); *p = nullptr; return ZKQ_ENOMEM; }
+  *have = want;
+  return ZKQ_OK;
+}
+
+#define ZKQ_DISPATCH_W(w, F, ...) \
+  do { if ((w) == 1) { F<1> __VA_ARGS__; } else if ((w) == 2) { F<2> __VA_ARGS__; } else { F<4> __VA_ARGS__; } } while (0)
+
+zkq_status mw_gemm_batched(const MwProd* prods, int count, int wa, int wb, int wc, int p_out_bits, int method,
+                           void** ws, size_t* ws_bytes, void** meta, size_t* meta_bytes, cudaStream_t st) {
+  if (count <= 0) return ZKQ_OK;
+  for (int w : {wa, wb, wc}) if (w != 1 && w != 2 && w != 4) return ZKQ_EINVAL;
+  std::vector<OzProd> dp(count);
+  int max_kp = 0, max_mn = 0;
+  for (int i = 0; i < count; ++i) {
+    const MwProd& q = prods[i];
+    if (q.m < 1 || q.n < 1 || q.k < 1 || 2 * q.k > 4096) return ZKQ_EINVAL;
+    OzProd& o = dp[i];
+    std::memset(&o, 0, sizeof(o));
+    o.m = q.m; o.n = q.n; o.k = q.k; o.opA = q.opA;
+    o.A = q.A; o.B = q.B; o.C = q.C; o.base = q.base; o.sgn = q.sgn; o.base_identity = q.base_identity;
+    o.mp = (q.m + OZ_BM - 1) / OZ_BM * OZ_BM;
+    o.np2 = (2 * q.n + OZ_BN - 1) / OZ_BN * OZ_BN;
+    o.kp = (2 * q.k + OZ_BK - 1) / OZ_BK * OZ_BK;
+    max_kp = std::max(max_kp, 2 * q.k);
+    max_mn = std::max(max_mn, q.m * q.n);
+  }
+  if (method == 0) {
+    zkq_status s = grow(meta, meta_bytes, al(sizeof(OzProd) * count));
+    if (s != ZKQ_OK) return s;
+    ZKQ_CUDA_TRY(cudaMemcpyAsync(*meta, dp.data(), sizeof(OzProd) * count, cudaMemcpyHostToDevice, st));
+    dim3 grid((max_mn + 127) / 128, count);
+    const OzProd* d = (const OzProd*)*meta;
+#define ZKQ_PLAIN(A_, B_, C_) if (wa == A_ && wb == B_ && wc == C_) mw_gemm_plain_kernel<A_, B_, C_><<<grid, 128, 0, st>>>(d);
+    ZKQ_PLAIN(1,1,1) ZKQ_PLAIN(1,1,2) ZKQ_PLAIN(1,1,4) ZKQ_PLAIN(1,2,2) ZKQ_PLAIN(1,2,4) ZKQ_PLAIN(1,4,4)
+    ZKQ_PLAIN(2,1,2) ZKQ_PLAIN(2,2,2) ZKQ_PLAIN(2,4,4) ZKQ_PLAIN(2,1,4) ZKQ_PLAIN(2,2,4) ZKQ_PLAIN(2,4,2)
+    ZKQ_PLAIN(4,1,4) ZKQ_PLAIN(4,2,4) ZKQ_PLAIN(4,4,4) ZKQ_PLAIN(4,4,2) ZKQ_PLAIN(4,1,2) ZKQ_PLAIN(4,2,2)
+    ZKQ_PLAIN(1,4,2) ZKQ_PLAIN(2,1,1) ZKQ_PLAIN(4,1,1)
+#undef ZKQ_PLAIN
+    ZKQ_CUDA_TRY(cudaGetLastError());
+    return ZKQ_OK;
+  }
+  OzPlan plan = ozaki_plan(max_kp, wa, wb, p_out_bits);
+  std::vector<OzPair> pairs = make_pairs(plan);
+  plan.npairs = (int)pairs.size();
+  // workspace layout
+  size_t off = 0;
+  std::vector<size_t> oA(count), oB(count), oD(count), oe(count);
+  size_t max_mkp = 0, max_nkp = 0;
+  for (int i = 0; i < count; ++i) {
+    OzProd& o = dp[i];
+    oA[i] = off; off += al((size_t)plan.sA * o.mp * o.kp * sizeof(__half));
+    oB[i] = off; off += al((size_t)plan.sB * o.np2 * o.kp * sizeof(__half));
+    oD[i] = off; off += al((size_t)(plan.S + 1) * o.mp * o.np2 * sizeof(int32_t));
+    oe[i] = off; off += al((size_t)(o.m + o.n) * sizeof(int32_t));
+    max_mkp = std::max(max_mkp, (size_t)o.mp * o.kp);
+    max_nkp = std::max(max_nkp, (size_t)o.np2 * o.kp);
+  }
+  zkq_status s = grow(ws, ws_bytes, off);
+  if (s != ZKQ_OK) return s;
+  char* base = (char*)*ws;
+  std::vector<OzTile> tiles;
+  for (int i = 0; i < count; ++i) {
+    OzProd& o = dp[i];
+    o.Ahat = (__half*)(base + oA[i]); o.Bhat = (__half*)(base + oB[i]);
+    o.D = (int32_t*)(base + oD[i]); o.eA = (int32_t*)(base + oe[i]); o.eB = o.eA + o.m;
+    for (int ti = 0; ti < o.mp / OZ_BM; ++ti)
+      for (int tj = 0; tj < o.np2 / OZ_BN; ++tj) tiles.push_back({i, ti, tj});
+  }
+  // biggest problems first (their tiles run longest: K' is larger)
+  std::stable_sort(tiles.begin(), tiles.end(), [&](const OzTile& a, const OzTile& c) { return dp[a.prod].kp > dp[c.prod].kp; });
+  size_t m_p = al(sizeof(OzProd) * count), m_t = al(sizeof(OzTile) * tiles.size()), m_q = al(sizeof(OzPair) * pairs.size());
+  s = grow(meta, meta_bytes, m_p + m_t + m_q);
+  if (s != ZKQ_OK) return s;
+  char* mb = (char*)*meta;
+  OzProd* d_p = (OzProd*)mb; OzTile* d_t = (OzTile*)(mb + m_p); OzPair* d_q = (OzPair*)(mb + m_p + m_t);
+  ZKQ_CUDA_TRY(cudaMemcpyAsync(d_p, dp.data(), sizeof(OzProd) * count, cudaMemcpyHostToDevice, st));
+  ZKQ_CUDA_TRY(cudaMemcpyAsync(d_t, tiles.data(), sizeof(OzTile) * tiles.size(), cudaMemcpyHostToDevice, st));
+  ZKQ_CUDA_TRY(cudaMemcpyAsync(d_q, pairs.data(), sizeof(OzPair) * pairs.size(), cudaMemcpyHostToDevice, st));
+  int max_rows = 0;
+  for (auto& o : dp) max_rows = std::max(max_rows, o.m + o.n);
+  {
+    dim3 g((max_rows + 127) / 128, count);
+#define ZKQ_SC(A_, B_) if (wa == A_ && wb == B_) oz_scale_kernel<A_, B_><<<g, 128, 0, st>>>(d_p);
+    ZKQ_SC(1,1) ZKQ_SC(1,2) ZKQ_SC(1,4) ZKQ_SC(2,1) ZKQ_SC(2,2) ZKQ_SC(2,4) ZKQ_SC(4,1) ZKQ_SC(4,2) ZKQ_SC(4,4)
+#undef ZKQ_SC
+    ZKQ_CUDA_TRY(cudaGetLastError());
+  }
+  {
+    dim3 gA((unsigned)((max_mkp + 255) / 256), count), gB((unsigned)((max_nkp + 255) / 256), count);
+    ZKQ_DISPATCH_W(wa, oz_slice_A_kernel, <<<gA, 256, 0, st>>>(d_p, plan.b, plan.sA));
+    ZKQ_DISPATCH_W(wb, oz_slice_B_kernel, <<<gB, 256, 0, st>>>(d_p, plan.b, plan.sB));
+    ZKQ_CUDA_TRY(cudaGetLastError());
+  }
+  {
+    size_t sm = (size_t)OZ_STAGES * (OZ_BM + OZ_BN) * 64;
+    ZKQ_CUDA_TRY(cudaFuncSetAttribute(oz_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    oz_gemm_kernel<<<(unsigned)tiles.size(), 256, sm, st>>>(d_p, d_t, d_q, plan.npairs, plan.S);
+    ZKQ_CUDA_TRY(cudaGetLastError());
+  }
+  {
+    dim3 g((max_mn + 127) / 128, count);
+    if (wc == 1) oz_combine_kernel<1><<<g, 128, 0, st>>>(d_p, plan.b, plan.S);
+    else if (wc == 2) oz_combine_kernel<2><<<g, 128, 0, st>>>(d_p, plan.b, plan.S);
+    else oz_combine_kernel<4><<<g, 128, 0, st>>>(d_p, plan.b, plan.S);
+    ZKQ_CUDA_TRY(cudaGetLastError());
+  }
+  return ZKQ_OK;
+}
+
+}  // namespace zkq

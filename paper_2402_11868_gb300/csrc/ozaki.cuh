@@ -1,0 +1,48 @@
+// Ozaki-style error-free split products for multi-word complex matrices (Ozaki, Ogita, Oishi, Rump 2012),
+// the dense products A X, X^H X, X^H (A X) and X E of the refinement step.
+#pragma once
+#include <cstdint>
+#include <cuda_fp16.h>
+#include "common.cuh"
+
+namespace zkq {
+
+// One product C = base + sgn * op(A) B of multi-word complex matrices (column-major, packed):
+//   opA = 0: A is m x k (ld m);  opA = 1: A is stored k x m (ld k) and op(A) = A^H.
+//   B is k x n (ld k);  C is m x n (ld m); base (m x n, wc words) may be null, or equal C when C is not
+//   an input of the product; base_identity adds the identity instead of a base matrix.
+struct MwProd {
+  int m, n, k, opA;
+  const double* A; const double* B; double* C; const double* base;
+  double sgn; int base_identity;
+};
+
+// device-side layout of one product inside the Ozaki workspace
+struct OzProd {
+  int m, n, k, opA;
+  int mp, np2, kp;               // padded: rows of op(A), columns of [Re|Im] output, K' = 2k
+  const double* A; const double* B; double* C; const double* base; double sgn; int base_identity;
+  __half* Ahat;                  // [sA][mp][kp]
+  __half* Bhat;                  // [sB][np2][kp]
+  int32_t* D;                    // [S+1][mp][np2] (levels 2..S used)
+  int32_t* eA;                   // row exponents of op(A) (m)
+  int32_t* eB;                   // column exponents of B (n)
+};
+
+struct OzPair { int16_t t, u; int16_t level; int16_t flags; };   // flags: 1 chunk end, 2 level end
+
+struct OzPlan {
+  int b;            // digit width (bits)
+  int sA, sB, S;    // digit counts and the highest level kept
+  int G;            // pairs per exact fp32 chunk
+  int npairs;
+};
+
+OzPlan ozaki_plan(int max_kprime, int wa, int wb, int p_out_bits);
+
+// Run a batch of products (all with the same word counts and output precision).  method 1: Ozaki
+// tensor-core slices; method 0: plain multi-word GEMM on the FP64 pipe.
+zkq_status mw_gemm_batched(const MwProd* prods, int count, int wa, int wb, int wc, int p_out_bits, int method,
+                           void** ws, size_t* ws_bytes, void** meta, size_t* meta_bytes, cudaStream_t st);
+
+}  // namespace zkq

@@ -1,0 +1,130 @@
+"""GPU parity of the split (Ozaki) products and of the Ogita-Aishima refinement against the oracle."""
+from __future__ import annotations
+
+from fractions import Fraction
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import workloads as W
+from tests._util import fr
+from tests import _gpu
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    import paper_2402_11868_gb300 as Z
+    Z.build()
+    c = Z.Context(0)
+    yield c
+    c.close()
+
+
+def rand_mw(rng, count, w, spread=6):
+    """complex multi-word entries (count, 2, w) with per-entry exponents spread over 2^-spread..2^spread"""
+    x = np.zeros((count, 2, w))
+    e = rng.integers(-spread, spread + 1, size=(count, 2))
+    x[:, :, 0] = np.ldexp(rng.standard_normal((count, 2)), e)
+    for k in range(1, w):
+        x[:, :, k] = x[:, :, k - 1] * 2.0**-54 * rng.uniform(-1, 1, (count, 2))
+    return x
+
+
+CASES = [(1, 1, 1, 0), (3, 5, 7, 1), (17, 33, 16, 0), (130, 40, 70, 1), (64, 48, 512, 0), (40, 3, 600, 1)]
+
+
+@pytest.mark.parametrize("method", [1, 0])
+@pytest.mark.parametrize("wa,wb,wc", [(4, 4, 4), (4, 2, 4), (2, 1, 2), (1, 4, 4)])
+def test_split_products_match_exact(ctx, method, wa, wb, wc):
+    import torch
+    import paper_2402_11868_gb300 as Z
+    rng = np.random.default_rng(1000 * wa + 100 * wb + 10 * wc + method)
+    As, Bs, ms, ns, ks, ops = [], [], [], [], [], []
+    for (m, n, k, op) in CASES:
+        A = rand_mw(rng, m * k, wa)
+        B = rand_mw(rng, k * n, wb)
+        As.append(A); Bs.append(B); ms.append(m); ns.append(n); ks.append(k); ops.append(op)
+    a_off = np.cumsum([0] + [a.shape[0] for a in As[:-1]]); b_off = np.cumsum([0] + [b.shape[0] for b in Bs[:-1]])
+    c_sz = [m * n for m, n in zip(ms, ns)]; c_off = np.cumsum([0] + c_sz[:-1])
+    dA = torch.from_numpy(np.concatenate([a.reshape(-1) for a in As])).cuda()
+    dB = torch.from_numpy(np.concatenate([b.reshape(-1) for b in Bs])).cuda()
+    dC = torch.zeros(sum(c_sz) * 2 * wc, dtype=torch.float64, device="cuda")
+    p_bits = 53 * wc + 6
+    Z.zkq_mw_gemm(ctx, ms, ns, ks, ops, dA, a_off, wa, dB, b_off, wb, dC, c_off, wc, p_bits, method)
+    torch.cuda.synchronize()
+    Ch = dC.cpu().numpy()
+    for i, (m, n, k, op) in enumerate(CASES):
+        ref = oracle.matmul(As[i], Bs[i], m, n, k, opA=op)
+        got = Ch[2 * wc * c_off[i]: 2 * wc * (c_off[i] + m * n)].reshape(m * n, 2, wc)
+        Am = np.abs(As[i][:, :, 0]).max(axis=1)
+        # row maxima of op(A): A is m x k (element i + l m) or, for op = A^H, k x m (element l + i k)
+        rowmax = Am.reshape(k, m).max(axis=0) if op == 0 else Am.reshape(m, k).max(axis=1)
+        colmax = np.abs(Bs[i][:, :, 0]).max(axis=1).reshape(k, n, order="F").max(axis=0)
+        for jj in range(n):
+            for ii in range(m):
+                e = ii + jj * m
+                if method == 1:
+                    bound = k * 2.0 ** -p_bits * (4 * rowmax[ii]) * (4 * colmax[jj]) * 2
+                else:
+                    bound = k * 2.0 ** -(53 * wc - 4) * rowmax[ii] * colmax[jj] * 4
+                for part in range(2):
+                    d = abs(float(fr(got[e, part]) - fr(ref[e, part])))
+                    assert d <= bound, (i, ii, jj, part, d, bound)
+
+
+def oracle_eig(cache, key, p):
+    if key not in cache:
+        cache[key] = oracle.eigh(p.A, p.n)
+    return cache[key]
+
+
+@pytest.fixture(scope="module")
+def cache():
+    return {}
+
+
+def check_refined(res, probs, target, bits, cache, tag):
+    for b, p in enumerate(probs):
+        lam, V = _gpu.problem_views(res, b, target)
+        L, _, _ = oracle_eig(cache, (tag, b), p)
+        anorm = abs(fr(L[0]))
+        worst = max(abs(fr(lam[i]) - fr(L[i])) for i in range(p.n))
+        assert worst <= anorm / 2**bits, (p.n, float(worst / anorm))
+        r, o = oracle.residual(p.A, p.n, lam, V)
+        assert r.max() <= float(anorm) * 2.0**-bits, (p.n, r.max())
+
+
+@pytest.mark.parametrize("method", [1, 2])
+def test_oa_refine_double_double_graded_with_pairs(ctx, cache, method):
+    sizes = [2, 16, 24, 40, 66]
+    probs = []
+    for i, n in enumerate(sizes):
+        lam, lo, pairs, w = W.batch_problem_spec(1, 5, i, n)
+        probs.append(W.herm_spectrum(5, i, lam, w, lam_lo=lo, pairs=pairs))
+    res = _gpu.refine_batch(ctx, probs, 2, 2, method)
+    assert (res["rinfo"].cpu().numpy() == 0).all(), res["rinfo"]
+    check_refined(res, probs, 2, 100, cache, "dd5")
+
+
+@pytest.mark.parametrize("method", [1, 2])
+def test_oa_refine_quad_double_graded_2m180_with_pairs(ctx, cache, method):
+    sizes = [3, 16, 32, 48, 96]
+    probs = []
+    for i, n in enumerate(sizes):
+        lam, lo, pairs, w = W.batch_problem_spec(2, 6, i, n)
+        probs.append(W.herm_spectrum(6, i, lam, w, lam_lo=lo, pairs=pairs))
+    res = _gpu.refine_batch(ctx, probs, 4, 4, method)
+    assert (res["rinfo"].cpu().numpy() == 0).all(), res["rinfo"]
+    check_refined(res, probs, 4, 200, cache, "qd6")
+
+
+def test_oa_refine_quad_double_single128_spectrum(ctx, cache):
+    import paper_2402_11868_gb300 as Z
+    probs = [W.herm_spectrum(8, 0, W.spectrum_single128(64), 4), W.herm_spectrum(8, 1, W.spectrum_single128(17), 4)]
+    res = _gpu.refine_batch(ctx, probs, 4, 4, Z.ZKQ_OA_OZAKI)
+    assert (res["rinfo"].cpu().numpy() == 0).all(), res["rinfo"]
+    check_refined(res, probs, 4, 200, cache, "s8")
