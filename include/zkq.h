@@ -121,7 +121,8 @@ zkq_status zkq_rqi_refine(zkq_ctx* ctx, int batch, const int32_t* n, const int64
  *   A, B, C        device arrays; product i uses element offsets a_off[i], b_off[i], c_off[i] (host int64)
  *   wa, wb, wc     words per real of A, B, C (1, 2 or 4); B_i is k x n (ld k), C_i is m x n (ld m)
  *   p_bits         requested accuracy: |C - op(A) B| <= k 2^-p_bits 2^(e_row + f_col) per element, where
- *                  2^e_row, 2^f_col bound the largest |entry| of the row of op(A) and the column of B
+ *                  2^e_row <= 8 max|row of op(A)| and 2^f_col <= 8 max|column of B| are the power-of-two
+ *                  scales of the split
  *                  (method 1; method 0 rounds in wc-word arithmetic); 1 <= p_bits <= 252
  * Constraints: k <= 2048.  C must not overlap A or B.
  * Errors: ZKQ_EINVAL, ZKQ_ENOMEM, ZKQ_ECUDA.

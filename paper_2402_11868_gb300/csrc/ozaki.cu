@@ -1,6 +1,8 @@
 // Ozaki-style split products of multi-word complex matrices on tensor cores.
 //
-// Every row of op(A) is scaled by 2^{-e_i} and every column of B by 2^{-f_j} (powers of two, so |x| < 1/2),
+// Every row of op(A) is scaled by 2^{-e_i} and every column of B by 2^{-f_j} (powers of two, so |x| < 1/4;
+// the spare bit keeps the most significant balanced digit strictly inside [-2^{b-1}, 2^{b-1}] after the
+// lower digits' rounding carries),
 // turned into a fixed-point integer (64-bit limbs, truncating below 2^{-b s}) and split into s balanced
 // digits sigma_t in [-2^{b-1}, 2^{b-1}]:  x ~ 2^{e} sum_t sigma_t 2^{-b t}.  Then
 //   op(A) B = 2^{e_i + f_j} sum_{t,u} 2^{-b(t+u)} (Ahat_t Bhat_u),
@@ -80,12 +82,13 @@ __device__ __forceinline__ void to_fixed(const double* w, int fix, bool negate, 
     uint64_t m; int q; bool ng; dsplit(v, m, q, ng);
     int sh = q + fix;
     if (sh < 0) { if (-sh >= 64) continue; m >>= -sh; sh = 0; }
-    if (sh > 256) continue;              // cannot happen for scaled inputs (|x 2^-e| < 1/2)
+    if (sh > 256) continue;              // cannot happen for scaled inputs (|x 2^-e| < 1/4)
     big_add_shifted(X, m, sh, ng != negate);
   }
 }
 
-// s balanced base-2^b digits of X (|X| < 2^{b s - 1}); digit t (1-based, most significant first)
+// s balanced base-2^b digits of X (|X| < 2^{b s - 2}); digit t (1-based, most significant first).
+// Lower digits lie in (-2^{b-1}, 2^{b-1}]; what remains for the top digit has |.| <= 2^{b-2} + 1.
 template <typename F>
 __device__ __forceinline__ void digits(Big X, int b, int s, F&& emit) {
   const int64_t half = 1LL << (b - 1), base = 1LL << b;
@@ -135,8 +138,8 @@ OzPlan ozaki_plan(int max_kprime, int wa, int wb, int p_out_bits) {
   p.b = max_kprime <= 1024 ? 8 : 7;
   int lg = 0; while ((1 << lg) < max_kprime) ++lg;
   auto need = [&](int words) {
-    int bits_in = 53 * words + 2;
-    int bits = std::min(bits_in, p_out_bits + 2 + lg);
+    int bits_in = 53 * words + 3;
+    int bits = std::min(bits_in, p_out_bits + 3 + lg);
     return (bits + p.b - 1) / p.b + 1;
   };
   p.sA = need(wa);
@@ -175,7 +178,7 @@ __global__ void oz_scale_kernel(const OzProd* __restrict__ P) {
       const double* q = p.opA ? p.A + ((size_t)l + (size_t)r * p.k) * 2 * WA : p.A + ((size_t)r + (size_t)l * p.m) * 2 * WA;
       mx = fmax(mx, fmax(fabs(q[0]), fabs(q[WA])));
     }
-    p.eA[r] = mx > 0 ? ilogb(mx) + 2 : 0;
+    p.eA[r] = mx > 0 ? ilogb(mx) + 3 : 0;
   } else if (r < p.m + p.n) {
     int j = r - p.m;
     double mx = 0.0;
@@ -183,7 +186,7 @@ __global__ void oz_scale_kernel(const OzProd* __restrict__ P) {
       const double* q = p.B + ((size_t)l + (size_t)j * p.k) * 2 * WB;
       mx = fmax(mx, fmax(fabs(q[0]), fabs(q[WB])));
     }
-    p.eB[j] = mx > 0 ? ilogb(mx) + 2 : 0;
+    p.eB[j] = mx > 0 ? ilogb(mx) + 3 : 0;
   }
 }
 

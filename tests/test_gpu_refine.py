@@ -68,7 +68,7 @@ def test_split_products_match_exact(ctx, method, wa, wb, wc):
             for ii in range(m):
                 e = ii + jj * m
                 if method == 1:
-                    bound = k * 2.0 ** -p_bits * (4 * rowmax[ii]) * (4 * colmax[jj]) * 2
+                    bound = k * 2.0 ** -p_bits * (8 * rowmax[ii]) * (8 * colmax[jj]) * 2
                 else:
                     bound = k * 2.0 ** -(53 * wc - 4) * rowmax[ii] * colmax[jj] * 4
                 for part in range(2):

@@ -159,7 +159,11 @@ def batch_sizes(seed: int, count: int = 256, step: int = 16, smax: int = 512) ->
 
 
 def pair_indices(seed: int, idx: int, n: int, npairs: int = 8) -> list[tuple[int, int]]:
-    """npairs non-overlapping adjacent (k, k+1) eigen-index pairs (0-based), drawn by seed."""
+    """npairs non-overlapping adjacent (k, k+1) eigen-index pairs (0-based), drawn by seed.
+
+    The exact-split construction needs an even order, so odd orders get no pairs."""
+    if n % 2:
+        return []
     if n < 2 * npairs + 1:
         npairs = max(0, (n - 1) // 2)
     u = uniform(seed, (2 << 40) + idx, 64 * npairs + 64)
