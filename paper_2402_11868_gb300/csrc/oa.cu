@@ -18,6 +18,8 @@
 #include <vector>
 #include <algorithm>
 #include <cstring>
+#include <cstdio>
+#include <cstdlib>
 #include "common.cuh"
 #include "mw.cuh"
 #include "reduce.cuh"
@@ -258,6 +260,13 @@ zkq_status eigh_internal(void* ctx, int batch, const int32_t* n, const int64_t* 
 
 static size_t alg(size_t x) { return (x + 255) & ~(size_t)255; }
 
+// ZKQ_DEBUG=1 in the environment prints per-iteration refinement statistics to stderr
+static bool debug_log() {
+  static int v = -1;
+  if (v < 0) { const char* e = getenv("ZKQ_DEBUG"); v = (e && e[0] == '1') ? 1 : 0; }
+  return v == 1;
+}
+
 static zkq_status grow_buf(void** p, size_t* have, size_t need) {
   if (need <= *have) return ZKQ_OK;
   if (*p) { cudaFree(*p); *p = nullptr; *have = 0; }
@@ -357,6 +366,11 @@ zkq_status oa_refine_t(void* ctx, const OaBuffers& buf, int batch, const int32_t
     ZKQ_CUDA_TRY(cudaMemcpyAsync(hcl_len.data(), CL, sizeof(int32_t) * le, cudaMemcpyDeviceToHost, st));
     ZKQ_CUDA_TRY(cudaStreamSynchronize(st));
     (void)APR;
+    if (debug_log()) {
+      for (size_t a = 0; a < act.size(); ++a)
+        fprintf(stderr, "[zkq oa] it %d prob %d n %d maxE %.3e delta %.3e clusters %d (%d cols) cl_off %.3e\n", it, act[a],
+                probs[act[a]].n, ast[a].maxE, ast[a].delta, ast[a].nclusters, ast[a].clustered, ast[a].cl_off);
+    }
     // convergence decisions
     std::vector<int> finish, upd;
     for (size_t a = 0; a < act.size(); ++a) {

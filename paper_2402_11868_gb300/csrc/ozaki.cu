@@ -137,9 +137,12 @@ OzPlan ozaki_plan(int max_kprime, int wa, int wb, int p_out_bits) {
   OzPlan p;
   p.b = max_kprime <= 1024 ? 8 : 7;
   int lg = 0; while ((1 << lg) < max_kprime) ++lg;
+  // Digits are counted from each row's / column's power-of-two scale, not per element: an entry far below
+  // its row maximum has significant bits far below the scale, so the count follows the requested accuracy
+  // whatever the number of input words.
   auto need = [&](int words) {
-    int bits_in = 53 * words + 3;
-    int bits = std::min(bits_in, p_out_bits + 3 + lg);
+    (void)words;
+    int bits = p_out_bits + 3 + lg;
     return (bits + p.b - 1) / p.b + 1;
   };
   p.sA = need(wa);

@@ -164,12 +164,13 @@ def pair_indices(seed: int, idx: int, n: int, npairs: int = 8) -> list[tuple[int
     The exact-split construction needs an even order, so odd orders get no pairs."""
     if n % 2:
         return []
-    if n < 2 * npairs + 1:
-        npairs = max(0, (n - 1) // 2)
-    u = uniform(seed, (2 << 40) + idx, 64 * npairs + 64)
-    taken, out, t = set(), [], 0
-    while len(out) < npairs:
-        k = int(u[t] * (n - 1)); t += 1          # pair (k, k+1), k in 0..n-2
+    # visit the candidate starts k = 0..n-2 in a seeded random order and keep non-overlapping ones
+    u = uniform(seed, (2 << 40) + idx, max(n - 1, 1))
+    order = sorted(range(n - 1), key=lambda k: (u[k], k))
+    taken, out = set(), []
+    for k in order:
+        if len(out) == npairs:
+            break
         if k in taken or (k + 1) in taken:
             continue
         taken.update((k, k + 1)); out.append((k, k + 1))
