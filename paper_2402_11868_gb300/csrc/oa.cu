@@ -8,13 +8,14 @@
 //   e_ij = r_ij / 2                                         otherwise (and on the diagonal)
 //   X <- X + X E
 // Columns stay sorted by eigenvalue, so a cluster is a maximal run of consecutive columns whose
-// neighbouring lambdas are within delta.  A cluster J whose block S_JJ is not yet diagonal is separated by
-// diagonalising T = S_JJ - mu I (mu = mean lambda over J, rounded to FP64 after the shift) with the FP64
-// Jacobi kernel and rotating X_J <- X_J W.  For spectra graded far below 2^-53 ||A|| each pass resolves
+// neighbouring lambdas are within delta.  A cluster J whose block S_JJ is not yet diagonal is separated
+// after the update: T = X_J^H (A - mu I) X_J is formed from the updated X (mu = mean lambda over J), rounded
+// to FP64, diagonalised with the FP64 Jacobi kernel, and X_J <- X_J W.  For spectra graded far below 2^-53 ||A|| each pass resolves
 // about 53 more bits of the small eigenvalues.  E only needs double-double: its entries are of the size of
 // the current error, so their relative accuracy requirement is at most ~106 bits.
-// A problem is converged once max |e_ij| <= 2^-(53W-6) and every cluster block is diagonal to that level;
-// it then takes one more (polishing) iteration, and lambda, X of the last iteration are reported.
+// A problem is converged once every coupling |s_ij + lambda_j r_ij| <= 2^-(53W-6) ||A|| and |r_ij| <=
+// 2^-(53W-6) (E itself can stay at noise / gap for near-degenerate pairs); it then takes one more
+// (polishing) iteration, and lambda, X of the last iteration are reported.
 #include <vector>
 #include <algorithm>
 #include <cstring>
@@ -44,7 +45,7 @@ __global__ void oa_init_kernel(const OaProb* __restrict__ pr, const double* __re
 }
 
 // ---- per-problem statistics: lambda, delta, clusters -----------------------------------------
-struct OaStat { double maxE; double delta; double anorm; int nclusters; int clustered; double cl_off; int pad; };
+struct OaStat { double maxE; double delta; double anorm; int nclusters; int clustered; double cl_off; double maxNum; double maxR; };
 
 template <int W>
 __global__ void __launch_bounds__(256) oa_stats_kernel(const OaProb* __restrict__ pr, const double* __restrict__ S,
@@ -108,6 +109,8 @@ __global__ void __launch_bounds__(256) oa_stats_kernel(const OaProb* __restrict_
     st[blockIdx.x].clustered = clustered;
     st[blockIdx.x].maxE = 0.0;
     st[blockIdx.x].cl_off = 0.0;
+    st[blockIdx.x].maxNum = 0.0;
+    st[blockIdx.x].maxR = 0.0;
   }
   __syncthreads();
   // largest off-diagonal |s_ij| inside clusters (relative to ||A||)
@@ -134,57 +137,71 @@ __global__ void oa_E_kernel(const OaProb* __restrict__ pr, const double* __restr
                             double* __restrict__ E, OaStat* __restrict__ st) {
   const OaProb p = pr[blockIdx.y];
   int e = blockIdx.x * blockDim.x + threadIdx.x;
-  double mag = 0.0;
+  double mag = 0.0, cpl = 0.0, rmag = 0.0;
   if (e < p.n * p.n) {
     const int n = p.n, i = e % n, j = e / n;
     cmw<W> r = c_load<W, W>(R + p.xoff * 2 * W, e);
     cmw<2> rr = c_make(mw_from_words<2, W>(r.re.x), mw_from_words<2, W>(r.im.x));
+    rmag = hypot(r.re.x[0], r.im.x[0]);
     cmw<2> out;
-    if (i == j || cl_start[p.loff + i] == cl_start[p.loff + j]) {
-      out = c_scale_d(rr, 0.5);
-      if (i == j) out.im = mw_zero<2>();
-    } else {
+    if (i != j) {
+      // coupling s_ij + lambda_j r_ij: the residual-like quantity the refinement drives to zero,
+      // independent of the gap (near-degenerate pairs keep E itself at noise / gap)
       cmw<W> s = c_load<W, W>(S + p.xoff * 2 * W, e);
-      mw<W> li = mw_load<W, W>(lam + p.loff * W, i), lj = mw_load<W, W>(lam + p.loff * W, j);
+      mw<W> lj = mw_load<W, W>(lam + p.loff * W, j);
       cmw<W> num = c_add(s, c_scale(r, lj));
-      mw<W> den = mw_sub(lj, li);
-      cmw<2> n2 = c_make(mw_from_words<2, W>(num.re.x), mw_from_words<2, W>(num.im.x));
-      mw<2> d2 = mw_from_words<2, W>(den.x);
-      mw<2> inv = mw_recip(d2);
-      out = c_scale(n2, inv);
+      cpl = hypot(num.re.x[0], num.im.x[0]);
+      if (cl_start[p.loff + i] == cl_start[p.loff + j]) {
+        out = c_scale_d(rr, 0.5);
+      } else {
+        mw<W> li = mw_load<W, W>(lam + p.loff * W, i);
+        mw<W> den = mw_sub(lj, li);
+        cmw<2> n2 = c_make(mw_from_words<2, W>(num.re.x), mw_from_words<2, W>(num.im.x));
+        mw<2> inv = mw_recip(mw_from_words<2, W>(den.x));
+        out = c_scale(n2, inv);
+      }
+    } else {
+      out = c_scale_d(rr, 0.5);
+      out.im = mw_zero<2>();
     }
     c_store(E + p.xoff * 2 * 2, e, out);
     mag = fmax(fabs(out.re.x[0]), fabs(out.im.x[0]));
   }
-  for (int o = 16; o > 0; o >>= 1) mag = fmax(mag, __shfl_down_sync(0xffffffffu, mag, o));
-  if ((threadIdx.x & 31) == 0 && mag > 0) atomic_max_nonneg(&st[blockIdx.y].maxE, mag);
+  for (int o = 16; o > 0; o >>= 1) {
+    mag = fmax(mag, __shfl_down_sync(0xffffffffu, mag, o));
+    cpl = fmax(cpl, __shfl_down_sync(0xffffffffu, cpl, o));
+    rmag = fmax(rmag, __shfl_down_sync(0xffffffffu, rmag, o));
+  }
+  if ((threadIdx.x & 31) == 0) {
+    if (mag > 0) atomic_max_nonneg(&st[blockIdx.y].maxE, mag);
+    if (cpl > 0) atomic_max_nonneg(&st[blockIdx.y].maxNum, cpl);
+    if (rmag > 0) atomic_max_nonneg(&st[blockIdx.y].maxR, rmag);
+  }
 }
 
-// ---- cluster blocks: T = S_JJ - mu I  (FP64) ---------------------------------------------------
+// ---- cluster blocks: T = X_J^H (A - mu I) X_J  (FP64), from the updated X ---------------------------
 struct OaCluster { int prob; int start; int len; int64_t toff; int64_t woff; };
 
+// CT = X_J^H A X_J and CG = X_J^H X_J (W words, len x len at toff) were formed by split products from the
+// updated X, so the components of X_J outside the cluster are second order and do not blur the small
+// splittings; mu = mean of the current lambdas over J.
 template <int W>
 __global__ void oa_cluster_T_kernel(const OaProb* __restrict__ pr, const OaCluster* __restrict__ cl,
-                                    const double* __restrict__ S, const double* __restrict__ R,
+                                    const double* __restrict__ CT, const double* __restrict__ CG,
                                     const double* __restrict__ lam, double* __restrict__ T) {
   const OaCluster c = cl[blockIdx.y];
   const OaProb p = pr[c.prob];
   int e = blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= c.len * c.len) return;
   int a = e % c.len, b = e / c.len;
-  // mu = mean of lambda over the cluster (recomputed by every thread; clusters are short)
   mw<W> mu = mw_zero<W>();
   for (int q = 0; q < c.len; ++q) mu = mw_add(mu, mw_load<W, W>(lam + p.loff * W, c.start + q));
   mu = mw_mul_d(mu, 1.0 / c.len);
-  int i = c.start + a, j = c.start + b;
-  // T = X_J^H (A - mu I) X_J = S_JJ - mu (I - R_JJ): the shift acts through the computed metric, so the
-  // non-orthonormality of X (size of R) does not blur splits far below it
-  cmw<W> s = c_load<W, W>(S + p.xoff * 2 * W, (size_t)i + (size_t)j * p.n);
-  cmw<W> r = c_load<W, W>(R + p.xoff * 2 * W, (size_t)i + (size_t)j * p.n);
-  s = c_add(s, c_scale(r, mu));
-  if (a == b) { s.re = mw_sub(s.re, mu); s.im = mw_zero<W>(); }
-  T[(c.toff + e) * 2 + 0] = s.re.x[0] + (W > 1 ? s.re.x[1] : 0.0);
-  T[(c.toff + e) * 2 + 1] = a == b ? 0.0 : s.im.x[0] + (W > 1 ? s.im.x[1] : 0.0);
+  cmw<W> t = c_load<W, W>(CT + c.toff * 2 * W, e);
+  cmw<W> g = c_load<W, W>(CG + c.toff * 2 * W, e);
+  t = c_sub(t, c_scale(g, mu));
+  T[(c.toff + e) * 2 + 0] = t.re.x[0] + (W > 1 ? t.re.x[1] : 0.0);
+  T[(c.toff + e) * 2 + 1] = a == b ? 0.0 : t.im.x[0] + (W > 1 ? t.im.x[1] : 0.0);
 }
 
 // copy rotated cluster columns (from Y = old X buffer) back into X
@@ -302,6 +319,7 @@ zkq_status oa_refine_t(void* ctx, const OaBuffers& buf, int batch, const int32_t
   size_t oTV = take((size_t)xe * 2 * sizeof(double));         // cluster eigenvectors
   size_t oTI = take((size_t)le * sizeof(int32_t));
   size_t oCLD = take(sizeof(OaCluster) * le);
+  size_t oCT = take(mat), oCG = take(mat);                     // cluster blocks X_J^H A X_J, X_J^H X_J
   zkq_status s = grow_buf(buf.ws, buf.ws_bytes, off);
   if (s != ZKQ_OK) return s;
   char* base = (char*)*buf.ws;
@@ -312,6 +330,7 @@ zkq_status oa_refine_t(void* ctx, const OaBuffers& buf, int batch, const int32_t
   OaProb* PR = (OaProb*)(base + oPR);
   double *T = (double*)(base + oT), *TW = (double*)(base + oTW), *TV = (double*)(base + oTV);
   OaCluster* CLD = (OaCluster*)(base + oCLD);
+  double *CT = (double*)(base + oCT), *CG = (double*)(base + oCG);
   ZKQ_CUDA_TRY(cudaMemcpyAsync(PR, probs.data(), sizeof(OaProb) * batch, cudaMemcpyHostToDevice, st));
   ZKQ_CUDA_TRY(cudaMemsetAsync(info, 0, sizeof(int32_t) * batch, st));
   {
@@ -368,8 +387,9 @@ zkq_status oa_refine_t(void* ctx, const OaBuffers& buf, int batch, const int32_t
     (void)APR;
     if (debug_log()) {
       for (size_t a = 0; a < act.size(); ++a)
-        fprintf(stderr, "[zkq oa] it %d prob %d n %d maxE %.3e delta %.3e clusters %d (%d cols) cl_off %.3e\n", it, act[a],
-                probs[act[a]].n, ast[a].maxE, ast[a].delta, ast[a].nclusters, ast[a].clustered, ast[a].cl_off);
+        fprintf(stderr, "[zkq oa] it %d prob %d n %d maxE %.3e coupling %.3e maxR %.3e delta %.3e clusters %d (%d cols) cl_off %.3e\n",
+                it, act[a], probs[act[a]].n, ast[a].maxE, ast[a].maxNum / (ast[a].anorm > 0 ? ast[a].anorm : 1.0), ast[a].maxR,
+                ast[a].delta, ast[a].nclusters, ast[a].clustered, ast[a].cl_off);
     }
     // convergence decisions
     std::vector<int> finish, upd;
@@ -377,7 +397,8 @@ zkq_status oa_refine_t(void* ctx, const OaBuffers& buf, int batch, const int32_t
       int b = act[a];
       hst[b] = ast[a];
       iters[b] = it;
-      bool conv = ast[a].maxE <= tol && ast[a].cl_off <= tol;
+      const double an = ast[a].anorm > 0 ? ast[a].anorm : 1.0;
+      bool conv = ast[a].maxNum <= tol * an && ast[a].maxR <= tol;
       if (polish[b] || it == max_iter) finish.push_back(b);
       else { if (conv) polish[b] = 1; upd.push_back(b); }
     }
@@ -417,7 +438,7 @@ zkq_status oa_refine_t(void* ctx, const OaBuffers& buf, int batch, const int32_t
     int64_t toff = 0, woff = 0;
     for (int b : upd) {
       const OaProb& q = probs[b];
-      bool need = hst[b].cl_off > tol && hst[b].nclusters > 0;
+      bool need = hst[b].cl_off > tol && hst[b].nclusters > 0 && !polish[b];
       if (!need) continue;
       for (int c = 0; c < q.n;) {
         int len = hcl_len[q.loff + c];
@@ -429,8 +450,22 @@ zkq_status oa_refine_t(void* ctx, const OaBuffers& buf, int batch, const int32_t
       int maxl = 0; for (auto& c : cls) maxl = std::max(maxl, c.len);
       ZKQ_CUDA_TRY(cudaMemcpyAsync(PR, probs.data(), sizeof(OaProb) * batch, cudaMemcpyHostToDevice, st));
       ZKQ_CUDA_TRY(cudaMemcpyAsync(CLD, cls.data(), sizeof(OaCluster) * cls.size(), cudaMemcpyHostToDevice, st));
+      // Q_J = A X2_J (into the P buffer's cluster columns), then CT = X2_J^H Q_J, CG = X2_J^H X2_J
+      std::vector<MwProd> p5, p6;
+      for (auto& c : cls) {
+        const OaProb& q = probs[c.prob];
+        double* XJ = X2 + (q.xoff + (int64_t)c.start * q.n) * 2 * W;
+        double* QJ = Pm + (q.xoff + (int64_t)c.start * q.n) * 2 * W;
+        p5.push_back({q.n, c.len, q.n, 0, A + q.a_off * 2 * wa, XJ, QJ, nullptr, 1.0, 0});
+        p6.push_back({c.len, c.len, q.n, 1, XJ, QJ, CT + c.toff * 2 * W, nullptr, 1.0, 0});
+        p6.push_back({c.len, c.len, q.n, 1, XJ, XJ, CG + c.toff * 2 * W, nullptr, 1.0, 0});
+      }
+      s = mw_gemm_batched(p5.data(), (int)p5.size(), wa, W, W, p_bits, prod_method, buf.oz_ws, buf.oz_bytes, buf.oz_meta, buf.oz_meta_bytes, st);
+      if (s != ZKQ_OK) return s;
+      s = mw_gemm_batched(p6.data(), (int)p6.size(), W, W, W, p_bits, prod_method, buf.oz_ws, buf.oz_bytes, buf.oz_meta, buf.oz_meta_bytes, st);
+      if (s != ZKQ_OK) return s;
       dim3 g((maxl * maxl + 255) / 256, (unsigned)cls.size());
-      oa_cluster_T_kernel<W><<<g, 256, 0, st>>>(PR, CLD, Sm, Rm, Lm, T);
+      oa_cluster_T_kernel<W><<<g, 256, 0, st>>>(PR, CLD, CT, CG, Lm, T);
       ZKQ_CUDA_TRY(cudaGetLastError());
       std::vector<int32_t> cn(cls.size()); std::vector<int64_t> co(cls.size());
       for (size_t c = 0; c < cls.size(); ++c) { cn[c] = cls[c].len; co[c] = cls[c].toff; }
