@@ -112,17 +112,6 @@ __global__ void __launch_bounds__(256) oa_stats_kernel(const OaProb* __restrict_
     st[blockIdx.x].maxNum = 0.0;
     st[blockIdx.x].maxR = 0.0;
   }
-  __syncthreads();
-  // largest off-diagonal |s_ij| inside clusters (relative to ||A||)
-  double off = 0.0;
-  for (int e = tid; e < n * n; e += blockDim.x) {
-    int i = e % n, j = e / n;
-    if (i == j || cl_start[p.loff + i] != cl_start[p.loff + j]) continue;
-    const double* sp = Sb + (size_t)e * 2 * W;
-    off = fmax(off, hypot(sp[0], sp[W]));
-  }
-  off = block_max_d(off, sbuf);
-  if (tid == 0) st[blockIdx.x].cl_off = amax > 0 ? off / amax : 0.0;
   (void)tol;
 }
 
@@ -137,7 +126,7 @@ __global__ void oa_E_kernel(const OaProb* __restrict__ pr, const double* __restr
                             double* __restrict__ E, OaStat* __restrict__ st) {
   const OaProb p = pr[blockIdx.y];
   int e = blockIdx.x * blockDim.x + threadIdx.x;
-  double mag = 0.0, cpl = 0.0, rmag = 0.0;
+  double mag = 0.0, cpl = 0.0, rmag = 0.0, incl = 0.0;
   if (e < p.n * p.n) {
     const int n = p.n, i = e % n, j = e / n;
     cmw<W> r = c_load<W, W>(R + p.xoff * 2 * W, e);
@@ -152,6 +141,7 @@ __global__ void oa_E_kernel(const OaProb* __restrict__ pr, const double* __restr
       cmw<W> num = c_add(s, c_scale(r, lj));
       cpl = hypot(num.re.x[0], num.im.x[0]);
       if (cl_start[p.loff + i] == cl_start[p.loff + j]) {
+        incl = cpl;                                    // mixing left inside the cluster
         out = c_scale_d(rr, 0.5);
       } else {
         mw<W> li = mw_load<W, W>(lam + p.loff * W, i);
@@ -171,11 +161,13 @@ __global__ void oa_E_kernel(const OaProb* __restrict__ pr, const double* __restr
     mag = fmax(mag, __shfl_down_sync(0xffffffffu, mag, o));
     cpl = fmax(cpl, __shfl_down_sync(0xffffffffu, cpl, o));
     rmag = fmax(rmag, __shfl_down_sync(0xffffffffu, rmag, o));
+    incl = fmax(incl, __shfl_down_sync(0xffffffffu, incl, o));
   }
   if ((threadIdx.x & 31) == 0) {
     if (mag > 0) atomic_max_nonneg(&st[blockIdx.y].maxE, mag);
     if (cpl > 0) atomic_max_nonneg(&st[blockIdx.y].maxNum, cpl);
     if (rmag > 0) atomic_max_nonneg(&st[blockIdx.y].maxR, rmag);
+    if (incl > 0) atomic_max_nonneg(&st[blockIdx.y].cl_off, incl);
   }
 }
 
@@ -389,7 +381,7 @@ zkq_status oa_refine_t(void* ctx, const OaBuffers& buf, int batch, const int32_t
       for (size_t a = 0; a < act.size(); ++a)
         fprintf(stderr, "[zkq oa] it %d prob %d n %d maxE %.3e coupling %.3e maxR %.3e delta %.3e clusters %d (%d cols) cl_off %.3e\n",
                 it, act[a], probs[act[a]].n, ast[a].maxE, ast[a].maxNum / (ast[a].anorm > 0 ? ast[a].anorm : 1.0), ast[a].maxR,
-                ast[a].delta, ast[a].nclusters, ast[a].clustered, ast[a].cl_off);
+                ast[a].delta, ast[a].nclusters, ast[a].clustered, ast[a].cl_off / (ast[a].anorm > 0 ? ast[a].anorm : 1.0));
     }
     // convergence decisions
     std::vector<int> finish, upd;
@@ -438,7 +430,9 @@ zkq_status oa_refine_t(void* ctx, const OaBuffers& buf, int batch, const int32_t
     int64_t toff = 0, woff = 0;
     for (int b : upd) {
       const OaProb& q = probs[b];
-      bool need = hst[b].cl_off > tol && hst[b].nclusters > 0 && !polish[b];
+      // rotate only clusters whose members are still coupled (gap-free measure |s_ij + lambda_j r_ij|);
+      // non-orthonormality alone is removed by the r/2 part of E
+      bool need = hst[b].cl_off > tol * (hst[b].anorm > 0 ? hst[b].anorm : 1.0) && hst[b].nclusters > 0 && !polish[b];
       if (!need) continue;
       for (int c = 0; c < q.n;) {
         int len = hcl_len[q.loff + c];
