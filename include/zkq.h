@@ -59,7 +59,7 @@ typedef struct {
   int device;             /* CUDA device ordinal */
   int max_sweeps;         /* Jacobi sweep limit (0: default 40) */
   int rqi_max_iter;       /* RQI steps per eigenpair (0: default 5) */
-  int oa_max_iter;        /* Ogita-Aishima iterations (0: default 12) */
+  int oa_max_iter;        /* Ogita-Aishima iterations (0: default 40) */
   int jacobi_cluster;     /* CTAs per large Jacobi problem (0: default chosen by size) */
 } zkq_config;
 

@@ -91,7 +91,7 @@ zkq_status zkq_ctx_create(zkq_ctx** ctx, const zkq_config* cfg) {
   if (e != cudaSuccess) { set_last_cuda_error(e); delete c; return ZKQ_ECUDA; }
   if (c->cfg.max_sweeps <= 0) c->cfg.max_sweeps = 40;
   if (c->cfg.rqi_max_iter <= 0) c->cfg.rqi_max_iter = 5;
-  if (c->cfg.oa_max_iter <= 0) c->cfg.oa_max_iter = 12;
+  if (c->cfg.oa_max_iter <= 0) c->cfg.oa_max_iter = 40;
   *ctx = c;
   return ZKQ_OK;
 }

@@ -7,6 +7,7 @@
 //   e_ij = (s_ij + lambda_j r_ij) / (lambda_j - lambda_i)   if |lambda_i - lambda_j| > delta
 //   e_ij = r_ij / 2                                         otherwise (and on the diagonal)
 //   X <- X + X E
+// (E is evaluated as R/2 plus an exactly anti-Hermitian part, see oa_E_kernel.)
 // Columns stay sorted by eigenvalue, so a cluster is a maximal run of consecutive columns whose
 // neighbouring lambdas are within delta.  A cluster J whose block S_JJ is not yet diagonal is separated
 // after the update: T = X_J^H (A - mu I) X_J is formed from the updated X (mu = mean lambda over J), rounded
@@ -120,6 +121,11 @@ __device__ __forceinline__ void atomic_max_nonneg(double* a, double v) {
 }
 
 // ---- E (double-double) -----------------------------------------------------------------------------
+// E = R/2 + K with K anti-Hermitian:  k_ij = (s_ij + (lambda_i + lambda_j)/2 r_ij) / (lambda_j - lambda_i)
+// for separated pairs (the Ogita-Aishima e_ij minus r_ij/2), k_ij = 0 inside clusters.  k is evaluated
+// once per unordered pair from the upper-triangle entries (i < j) and mirrored as k_ji = -conj(k_ij), so
+// E + E^H = R holds to rounding even where the computed S carries noise / gap for near-degenerate pairs;
+// that noise then only rotates inside the pair's span.
 template <int W>
 __global__ void oa_E_kernel(const OaProb* __restrict__ pr, const double* __restrict__ S, const double* __restrict__ R,
                             const double* __restrict__ lam, const int32_t* __restrict__ cl_start,
@@ -129,30 +135,33 @@ __global__ void oa_E_kernel(const OaProb* __restrict__ pr, const double* __restr
   double mag = 0.0, cpl = 0.0, rmag = 0.0, incl = 0.0;
   if (e < p.n * p.n) {
     const int n = p.n, i = e % n, j = e / n;
-    cmw<W> r = c_load<W, W>(R + p.xoff * 2 * W, e);
-    cmw<2> rr = c_make(mw_from_words<2, W>(r.re.x), mw_from_words<2, W>(r.im.x));
+    const int a = i < j ? i : j, b = i < j ? j : i;           // upper-triangle representative (a, b)
+    const size_t eu = (size_t)a + (size_t)b * n;
+    cmw<W> r = c_load<W, W>(R + p.xoff * 2 * W, eu);
     rmag = hypot(r.re.x[0], r.im.x[0]);
+    cmw<2> r2 = c_make(mw_from_words<2, W>(r.re.x), mw_from_words<2, W>(r.im.x));
     cmw<2> out;
-    if (i != j) {
-      // coupling s_ij + lambda_j r_ij: the residual-like quantity the refinement drives to zero,
-      // independent of the gap (near-degenerate pairs keep E itself at noise / gap)
-      cmw<W> s = c_load<W, W>(S + p.xoff * 2 * W, e);
-      mw<W> lj = mw_load<W, W>(lam + p.loff * W, j);
-      cmw<W> num = c_add(s, c_scale(r, lj));
-      cpl = hypot(num.re.x[0], num.im.x[0]);
-      if (cl_start[p.loff + i] == cl_start[p.loff + j]) {
-        incl = cpl;                                    // mixing left inside the cluster
-        out = c_scale_d(rr, 0.5);
-      } else {
-        mw<W> li = mw_load<W, W>(lam + p.loff * W, i);
-        mw<W> den = mw_sub(lj, li);
-        cmw<2> n2 = c_make(mw_from_words<2, W>(num.re.x), mw_from_words<2, W>(num.im.x));
-        mw<2> inv = mw_recip(mw_from_words<2, W>(den.x));
-        out = c_scale(n2, inv);
-      }
-    } else {
-      out = c_scale_d(rr, 0.5);
+    if (i == j) {
+      out = c_scale_d(r2, 0.5);
       out.im = mw_zero<2>();
+      rmag = fabs(r.re.x[0]);
+    } else {
+      cmw<W> s = c_load<W, W>(S + p.xoff * 2 * W, eu);
+      mw<W> la = mw_load<W, W>(lam + p.loff * W, a), lb = mw_load<W, W>(lam + p.loff * W, b);
+      mw<W> hsum = mw_mul_d(mw_add(la, lb), 0.5);
+      cmw<W> num = c_add(s, c_scale(r, hsum));                // coupling (gap-free)
+      cpl = hypot(num.re.x[0], num.im.x[0]);
+      cmw<2> k = c_zero<2>();
+      if (cl_start[p.loff + a] == cl_start[p.loff + b]) {
+        incl = cpl;
+      } else {
+        mw<W> den = mw_sub(lb, la);
+        cmw<2> n2 = c_make(mw_from_words<2, W>(num.re.x), mw_from_words<2, W>(num.im.x));
+        k = c_scale(n2, mw_recip(mw_from_words<2, W>(den.x)));
+      }
+      cmw<2> half_r = c_scale_d(r2, 0.5);
+      if (i < j) out = c_add(half_r, k);                       // e_ab = r_ab/2 + k_ab
+      else out = c_sub(c_conj(half_r), c_conj(k));             // e_ba = conj(r_ab)/2 - conj(k_ab)
     }
     c_store(E + p.xoff * 2 * 2, e, out);
     mag = fmax(fabs(out.re.x[0]), fabs(out.im.x[0]));
