@@ -3,7 +3,7 @@
 // ZKCM_CUS paragraph).  With X the current eigenvector matrix (target precision, W words per real):
 //   P = A X,  S = X^H P,  R = I - X^H X                                  (split products, ozaki.cu)
 //   lambda_i = s_ii / (1 - r_ii)
-//   delta = 2 (||S - diag(lambda)||_F + ||A|| ||R||_F)
+//   delta = 2 (||S - diag(lambda)||_F + ||A|| ||R||_F)   (used here in a local form, oa_cluster_kernel)
 //   e_ij = (s_ij + lambda_j r_ij) / (lambda_j - lambda_i)   if |lambda_i - lambda_j| > delta
 //   e_ij = r_ij / 2                                         otherwise (and on the diagonal)
 //   X <- X + X E
@@ -45,79 +45,106 @@ __global__ void oa_init_kernel(const OaProb* __restrict__ pr, const double* __re
   c_store(X + p.xoff * 2 * W, e, c_make(mw_from<W>(v[0]), mw_from<W>(v[1])));
 }
 
-// ---- per-problem statistics: lambda, delta, clusters -----------------------------------------
+// ---- per-problem statistics: lambda, couplings, clusters ----------------------------------------
 struct OaStat { double maxE; double delta; double anorm; int nclusters; int clustered; double cl_off; double maxNum; double maxR; };
 
+// lambda_i = s_ii / (1 - r_ii); anorm = max |lambda|; reset the per-iteration accumulators
 template <int W>
-__global__ void __launch_bounds__(256) oa_stats_kernel(const OaProb* __restrict__ pr, const double* __restrict__ S,
-                                                       const double* __restrict__ R, double* __restrict__ lam,
-                                                       int32_t* __restrict__ cl_start, int32_t* __restrict__ cl_len,
-                                                       OaStat* __restrict__ st, double tol) {
+__global__ void __launch_bounds__(256) oa_lambda_kernel(const OaProb* __restrict__ pr, const double* __restrict__ S,
+                                                        const double* __restrict__ R, double* __restrict__ lam,
+                                                        double* __restrict__ colnum, OaStat* __restrict__ st) {
   const OaProb p = pr[blockIdx.x];
   const int n = p.n, tid = threadIdx.x;
   __shared__ double sbuf[32];
   const double* Sb = S + p.xoff * 2 * W;
   const double* Rb = R + p.xoff * 2 * W;
   double* lb = lam + p.loff * W;
-  // lambda_i = s_ii / (1 - r_ii)
   double amax = 0.0;
   for (int i = tid; i < n; i += blockDim.x) {
-    mw<W> s = c_load<W, W>(Sb, (size_t)i + (size_t)i * n).re;
-    mw<W> r = c_load<W, W>(Rb, (size_t)i + (size_t)i * n).re;
-    mw<W> l = mw_div(s, mw_add_d(mw_neg(r), 1.0));
+    mw<W> sv = c_load<W, W>(Sb, (size_t)i + (size_t)i * n).re;
+    mw<W> rv = c_load<W, W>(Rb, (size_t)i + (size_t)i * n).re;
+    mw<W> l = mw_div(sv, mw_add_d(mw_neg(rv), 1.0));
     mw_store(lb, i, l);
     amax = fmax(amax, fabs(l.x[0]));
+    colnum[p.loff + i] = 0.0;
   }
   amax = block_max_d(amax, sbuf);
-  // Frobenius norms (leading words) of S - diag(lambda) and R
-  double sf = 0.0, rf = 0.0;
-  for (int e = tid; e < n * n; e += blockDim.x) {
-    int i = e % n, j = e / n;
-    const double* sp = Sb + (size_t)e * 2 * W;
-    const double* rp = Rb + (size_t)e * 2 * W;
-    double sr = sp[0], si = sp[W];
-    if (i == j) { sr = mw_sub(mw_load<W, W>(Sb + (size_t)e * 2 * W, 0), mw_load<W, W>(lb, i)).x[0]; si = 0.0; }
-    sf += sr * sr + si * si;
-    rf += rp[0] * rp[0] + rp[W] * rp[W];
-  }
-  for (int o = 16; o > 0; o >>= 1) { sf += __shfl_down_sync(0xffffffffu, sf, o); rf += __shfl_down_sync(0xffffffffu, rf, o); }
-  __shared__ double s_sf[8], s_rf[8];
-  if ((tid & 31) == 0) { s_sf[tid >> 5] = sf; s_rf[tid >> 5] = rf; }
-  __syncthreads();
   if (tid == 0) {
-    double a = 0, b = 0;
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) { a += s_sf[w]; b += s_rf[w]; }
-    double delta = 2.0 * (sqrt(a) + amax * sqrt(b));
-    // clusters: runs of consecutive columns whose neighbouring lambdas are within delta
-    int ncl = 0, clustered = 0;
-    int start = 0;
-    for (int i = 1; i <= n; ++i) {
-      bool brk = (i == n);
-      if (!brk) {
-        mw<W> d = mw_sub(mw_load<W, W>(lb, i - 1), mw_load<W, W>(lb, i));
-        brk = fabs(d.x[0]) > delta;
-      }
-      if (brk) {
-        int len = i - start;
-        for (int c = start; c < i; ++c) { cl_start[p.loff + c] = start; cl_len[p.loff + c] = len; }
-        if (len > 1) { ++ncl; clustered += len; }
-        start = i;
-      }
-    }
-    st[blockIdx.x].delta = delta;
-    st[blockIdx.x].anorm = amax;
-    st[blockIdx.x].nclusters = ncl;
-    st[blockIdx.x].clustered = clustered;
-    st[blockIdx.x].maxE = 0.0;
-    st[blockIdx.x].cl_off = 0.0;
-    st[blockIdx.x].maxNum = 0.0;
-    st[blockIdx.x].maxR = 0.0;
+    OaStat z; z.maxE = 0; z.delta = 0; z.anorm = amax; z.nclusters = 0; z.clustered = 0; z.cl_off = 0; z.maxNum = 0; z.maxR = 0;
+    st[blockIdx.x] = z;
   }
-  (void)tol;
 }
 
 __device__ __forceinline__ void atomic_max_nonneg(double* a, double v) {
   atomicMax(reinterpret_cast<unsigned long long*>(a), (unsigned long long)__double_as_longlong(v));
+}
+
+// couplings num_ij = s_ij + (lambda_i + lambda_j)/2 r_ij (i != j): first-order insensitive to the
+// non-orthonormality of X, (lambda_i - lambda_j)/2 times the rotation error of the pair.  Accumulates
+// column norms ||num_{:,c}||^2, max |num| and max |r|.
+template <int W>
+__global__ void oa_coupling_kernel(const OaProb* __restrict__ pr, const double* __restrict__ S, const double* __restrict__ R,
+                                   const double* __restrict__ lam, double* __restrict__ colnum, OaStat* __restrict__ st) {
+  const OaProb p = pr[blockIdx.y];
+  int e = blockIdx.x * blockDim.x + threadIdx.x;
+  double cpl = 0.0, rmag = 0.0;
+  if (e < p.n * p.n) {
+    const int n = p.n, i = e % n, j = e / n;
+    cmw<W> r = c_load<W, W>(R + p.xoff * 2 * W, e);
+    rmag = hypot(r.re.x[0], r.im.x[0]);
+    if (i != j) {
+      cmw<W> sv = c_load<W, W>(S + p.xoff * 2 * W, e);
+      mw<W> hs = mw_mul_d(mw_add(mw_load<W, W>(lam + p.loff * W, i), mw_load<W, W>(lam + p.loff * W, j)), 0.5);
+      cmw<W> num = c_add(sv, c_scale(r, hs));
+      cpl = hypot(num.re.x[0], num.im.x[0]);
+      if (cpl > 0) atomicAdd(&colnum[p.loff + j], cpl * cpl);
+    }
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    cpl = fmax(cpl, __shfl_down_sync(0xffffffffu, cpl, o));
+    rmag = fmax(rmag, __shfl_down_sync(0xffffffffu, rmag, o));
+  }
+  if ((threadIdx.x & 31) == 0) {
+    if (cpl > 0) atomic_max_nonneg(&st[blockIdx.y].maxNum, cpl);
+    if (rmag > 0) atomic_max_nonneg(&st[blockIdx.y].maxR, rmag);
+  }
+}
+
+// clusters: consecutive columns c, c+1 stay together while
+//   |lambda_c - lambda_{c+1}| <= delta_c = 2 (||num_{:,c}|| + ||num_{:,c+1}||) + 2^-(53W-4) max(|lambda_c|, |lambda_{c+1}|),
+// a local version of the Ogita-Aishima threshold: the couplings bound the eigenvalue errors of the two
+// columns, so a non-orthonormality confined to tiny-eigenvalue columns cannot merge the whole spectrum.
+template <int W>
+__global__ void oa_cluster_kernel(const OaProb* __restrict__ pr, const double* __restrict__ lam,
+                                  const double* __restrict__ colnum, int32_t* __restrict__ cl_start,
+                                  int32_t* __restrict__ cl_len, OaStat* __restrict__ st) {
+  const OaProb p = pr[blockIdx.x];
+  if (threadIdx.x != 0) return;
+  const int n = p.n;
+  const double* lb = lam + p.loff * W;
+  const double floor_rel = ldexp(1.0, -(53 * W - 4));
+  int ncl = 0, clustered = 0, start = 0;
+  double dmax = 0.0;
+  for (int i = 1; i <= n; ++i) {
+    bool brk = (i == n);
+    if (!brk) {
+      mw<W> a = mw_load<W, W>(lb, i - 1), b = mw_load<W, W>(lb, i);
+      double gap = fabs(mw_sub(a, b).x[0]);
+      double d = 2.0 * (sqrt(colnum[p.loff + i - 1]) + sqrt(colnum[p.loff + i])) +
+                 floor_rel * fmax(fabs(a.x[0]), fabs(b.x[0]));
+      dmax = fmax(dmax, d);
+      brk = gap > d;
+    }
+    if (brk) {
+      int len = i - start;
+      for (int c = start; c < i; ++c) { cl_start[p.loff + c] = start; cl_len[p.loff + c] = len; }
+      if (len > 1) { ++ncl; clustered += len; }
+      start = i;
+    }
+  }
+  st[blockIdx.x].delta = dmax;
+  st[blockIdx.x].nclusters = ncl;
+  st[blockIdx.x].clustered = clustered;
 }
 
 // ---- E (double-double) -----------------------------------------------------------------------------
@@ -174,8 +201,6 @@ __global__ void oa_E_kernel(const OaProb* __restrict__ pr, const double* __restr
   }
   if ((threadIdx.x & 31) == 0) {
     if (mag > 0) atomic_max_nonneg(&st[blockIdx.y].maxE, mag);
-    if (cpl > 0) atomic_max_nonneg(&st[blockIdx.y].maxNum, cpl);
-    if (rmag > 0) atomic_max_nonneg(&st[blockIdx.y].maxR, rmag);
     if (incl > 0) atomic_max_nonneg(&st[blockIdx.y].cl_off, incl);
   }
 }
@@ -203,6 +228,27 @@ __global__ void oa_cluster_T_kernel(const OaProb* __restrict__ pr, const OaClust
   t = c_sub(t, c_scale(g, mu));
   T[(c.toff + e) * 2 + 0] = t.re.x[0] + (W > 1 ? t.re.x[1] : 0.0);
   T[(c.toff + e) * 2 + 1] = a == b ? 0.0 : t.im.x[0] + (W > 1 ? t.im.x[1] : 0.0);
+}
+
+// W (FP64 Jacobi eigenvectors of a cluster block) promoted to W words
+template <int W>
+__global__ void oa_promote_kernel(const OaCluster* __restrict__ cl, const double* __restrict__ V64, double* __restrict__ Wm) {
+  const OaCluster c = cl[blockIdx.y];
+  int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= c.len * c.len) return;
+  const double* v = V64 + (c.toff + e) * 2;
+  c_store(Wm + c.toff * 2 * W, e, c_make(mw_from<W>(v[0]), mw_from<W>(v[1])));
+}
+// H = (3 I - G) / 2 in place (Newton-Schulz step for the unitary polar factor: W <- W H)
+template <int W>
+__global__ void oa_ns_kernel(const OaCluster* __restrict__ cl, double* __restrict__ G) {
+  const OaCluster c = cl[blockIdx.y];
+  int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= c.len * c.len) return;
+  cmw<W> g = c_load<W, W>(G + c.toff * 2 * W, e);
+  g = c_scale_d(g, -0.5);
+  if (e % c.len == e / c.len) g.re = mw_add_d(g.re, 1.5);
+  c_store(G + c.toff * 2 * W, e, g);
 }
 
 // copy rotated cluster columns (from Y = old X buffer) back into X
@@ -320,7 +366,8 @@ zkq_status oa_refine_t(void* ctx, const OaBuffers& buf, int batch, const int32_t
   size_t oTV = take((size_t)xe * 2 * sizeof(double));         // cluster eigenvectors
   size_t oTI = take((size_t)le * sizeof(int32_t));
   size_t oCLD = take(sizeof(OaCluster) * le);
-  size_t oCT = take(mat), oCG = take(mat);                     // cluster blocks X_J^H A X_J, X_J^H X_J
+  size_t oCT = take(mat), oCG = take(mat), oCW = take(mat);   // cluster blocks X_J^H A X_J, X_J^H X_J; rotation
+  size_t oCN = take((size_t)le * sizeof(double));              // column coupling norms
   zkq_status s = grow_buf(buf.ws, buf.ws_bytes, off);
   if (s != ZKQ_OK) return s;
   char* base = (char*)*buf.ws;
@@ -331,7 +378,8 @@ zkq_status oa_refine_t(void* ctx, const OaBuffers& buf, int batch, const int32_t
   OaProb* PR = (OaProb*)(base + oPR);
   double *T = (double*)(base + oT), *TW = (double*)(base + oTW), *TV = (double*)(base + oTV);
   OaCluster* CLD = (OaCluster*)(base + oCLD);
-  double *CT = (double*)(base + oCT), *CG = (double*)(base + oCG);
+  double *CT = (double*)(base + oCT), *CG = (double*)(base + oCG), *CW = (double*)(base + oCW);
+  double* CN = (double*)(base + oCN);
   ZKQ_CUDA_TRY(cudaMemcpyAsync(PR, probs.data(), sizeof(OaProb) * batch, cudaMemcpyHostToDevice, st));
   ZKQ_CUDA_TRY(cudaMemsetAsync(info, 0, sizeof(int32_t) * batch, st));
   {
@@ -373,11 +421,12 @@ zkq_status oa_refine_t(void* ctx, const OaBuffers& buf, int batch, const int32_t
     // pack the active problems' descriptors at the front of a scratch copy
     OaProb* PRA = (OaProb*)(base + oCLD);   // reuse: cluster list is built after these kernels
     ZKQ_CUDA_TRY(cudaMemcpyAsync(PRA, ap.data(), sizeof(OaProb) * ap.size(), cudaMemcpyHostToDevice, st));
-    oa_stats_kernel<W><<<(unsigned)ap.size(), 256, 0, st>>>(PRA, Sm, Rm, Lm, CS, CL, ST, tol);
-    ZKQ_CUDA_TRY(cudaGetLastError());
     {
       int mx = 0; for (auto& q : ap) mx = std::max(mx, q.n * q.n);
       dim3 g((mx + 255) / 256, (unsigned)ap.size());
+      oa_lambda_kernel<W><<<(unsigned)ap.size(), 256, 0, st>>>(PRA, Sm, Rm, Lm, CN, ST);
+      oa_coupling_kernel<W><<<g, 256, 0, st>>>(PRA, Sm, Rm, Lm, CN, ST);
+      oa_cluster_kernel<W><<<(unsigned)ap.size(), 32, 0, st>>>(PRA, Lm, CN, CS, CL, ST);
       oa_E_kernel<W><<<g, 256, 0, st>>>(PRA, Sm, Rm, Lm, CS, Em, ST);
       ZKQ_CUDA_TRY(cudaGetLastError());
     }
@@ -474,14 +523,32 @@ zkq_status oa_refine_t(void* ctx, const OaBuffers& buf, int batch, const int32_t
       for (size_t c = 0; c < cls.size(); ++c) { cn[c] = cls[c].len; co[c] = cls[c].toff; }
       s = eigh_internal(ctx, (int)cls.size(), cn.data(), co.data(), T, 1, TW, TV, TI, st);
       if (s != ZKQ_OK) return s;
+      // The FP64 eigenvector matrix is unitary only to 2^-53; two Newton-Schulz steps W <- W (3I - W^H W)/2
+      // in W-word products make it unitary to working precision, so the rotation does not disturb the
+      // orthonormality of X (which would inflate the cluster thresholds of the next iteration).
+      oa_promote_kernel<W><<<g, 256, 0, st>>>(CLD, TV, CT);
+      ZKQ_CUDA_TRY(cudaGetLastError());
+      double* Wcur = CT; double* Wnext = CW;
+      for (int ns = 0; ns < 2; ++ns) {
+        std::vector<MwProd> pg, pw;
+        for (auto& c : cls) pg.push_back({c.len, c.len, c.len, 1, Wcur + c.toff * 2 * W, Wcur + c.toff * 2 * W, CG + c.toff * 2 * W, nullptr, 1.0, 0});
+        s = mw_gemm_batched(pg.data(), (int)pg.size(), W, W, W, p_bits, prod_method, buf.oz_ws, buf.oz_bytes, buf.oz_meta, buf.oz_meta_bytes, st);
+        if (s != ZKQ_OK) return s;
+        oa_ns_kernel<W><<<g, 256, 0, st>>>(CLD, CG);
+        ZKQ_CUDA_TRY(cudaGetLastError());
+        for (auto& c : cls) pw.push_back({c.len, c.len, c.len, 0, Wcur + c.toff * 2 * W, CG + c.toff * 2 * W, Wnext + c.toff * 2 * W, nullptr, 1.0, 0});
+        s = mw_gemm_batched(pw.data(), (int)pw.size(), W, W, W, p_bits, prod_method, buf.oz_ws, buf.oz_bytes, buf.oz_meta, buf.oz_meta_bytes, st);
+        if (s != ZKQ_OK) return s;
+        std::swap(Wcur, Wnext);
+      }
       // Y_J = X2_J W_J into the X buffer (free now), then copy back into X2
       std::vector<MwProd> p4;
       for (auto& c : cls) {
         const OaProb& q = probs[c.prob];
-        p4.push_back({q.n, c.len, c.len, 0, X2 + (q.xoff + (int64_t)c.start * q.n) * 2 * W, TV + c.toff * 2,
+        p4.push_back({q.n, c.len, c.len, 0, X2 + (q.xoff + (int64_t)c.start * q.n) * 2 * W, Wcur + c.toff * 2 * W,
                       X + (q.xoff + (int64_t)c.start * q.n) * 2 * W, nullptr, 1.0, 0});
       }
-      s = mw_gemm_batched(p4.data(), (int)p4.size(), W, 1, W, p_bits, prod_method, buf.oz_ws, buf.oz_bytes, buf.oz_meta, buf.oz_meta_bytes, st);
+      s = mw_gemm_batched(p4.data(), (int)p4.size(), W, W, W, p_bits, prod_method, buf.oz_ws, buf.oz_bytes, buf.oz_meta, buf.oz_meta_bytes, st);
       if (s != ZKQ_OK) return s;
       dim3 g2((nmax * maxl + 255) / 256, (unsigned)cls.size());
       oa_cluster_copy_kernel<W><<<g2, 256, 0, st>>>(PR, CLD, X, X2);
