@@ -111,9 +111,12 @@ __global__ void oa_coupling_kernel(const OaProb* __restrict__ pr, const double* 
 }
 
 // clusters: consecutive columns c, c+1 stay together while
-//   |lambda_c - lambda_{c+1}| <= delta_c = 2 (||num_{:,c}|| + ||num_{:,c+1}||) + 2^-(53W-4) max(|lambda_c|, |lambda_{c+1}|),
+//   |lambda_c - lambda_{c+1}| <= delta_c = 2 (||num_{:,c}|| + ||num_{:,c+1}||) + 2^-(53W/2+4) max(|lambda_c|, |lambda_{c+1}|),
 // a local version of the Ogita-Aishima threshold: the couplings bound the eigenvalue errors of the two
 // columns, so a non-orthonormality confined to tiny-eigenvalue columns cannot merge the whole spectrum.
+// The relative floor keeps pairs closer than ~2^-(53W/2) apart together: for them the computed coupling
+// (noise ~2^-53W |lambda|) over the gap would give rotations k whose second-order term k^H k exceeds the
+// working precision; the cluster step (exactly unitary rotation) separates them instead.
 template <int W>
 __global__ void oa_cluster_kernel(const OaProb* __restrict__ pr, const double* __restrict__ lam,
                                   const double* __restrict__ colnum, int32_t* __restrict__ cl_start,
@@ -122,7 +125,7 @@ __global__ void oa_cluster_kernel(const OaProb* __restrict__ pr, const double* _
   if (threadIdx.x != 0) return;
   const int n = p.n;
   const double* lb = lam + p.loff * W;
-  const double floor_rel = ldexp(1.0, -(53 * W - 4));
+  const double floor_rel = ldexp(1.0, -(53 * W / 2 + 4));
   int ncl = 0, clustered = 0, start = 0;
   double dmax = 0.0;
   for (int i = 1; i <= n; ++i) {
