@@ -14,9 +14,9 @@
 // to FP64, diagonalised with the FP64 Jacobi kernel, and X_J <- X_J W.  For spectra graded far below 2^-53 ||A|| each pass resolves
 // about 53 more bits of the small eigenvalues.  E only needs double-double: its entries are of the size of
 // the current error, so their relative accuracy requirement is at most ~106 bits.
-// A problem is converged once every coupling |s_ij + lambda_j r_ij| <= 2^-(53W-6) ||A|| and |r_ij| <=
-// 2^-(53W-6) (E itself can stay at noise / gap for near-degenerate pairs); it then takes one more
-// (polishing) iteration, and lambda, X of the last iteration are reported.
+// A problem is converged once every coupling |s_ij + (lambda_i + lambda_j)/2 r_ij| <= 2^-(53W-6) ||A||
+// (E itself can stay at noise / gap for near-degenerate pairs); it then takes one more ordinary iteration
+// and one that only re-orthonormalises (E = R/2), and lambda, X of the following evaluation are reported.
 #include <vector>
 #include <algorithm>
 #include <cstring>
@@ -159,8 +159,9 @@ __global__ void oa_cluster_kernel(const OaProb* __restrict__ pr, const double* _
 template <int W>
 __global__ void oa_E_kernel(const OaProb* __restrict__ pr, const double* __restrict__ S, const double* __restrict__ R,
                             const double* __restrict__ lam, const int32_t* __restrict__ cl_start,
-                            double* __restrict__ E, OaStat* __restrict__ st) {
+                            const int32_t* __restrict__ orth_only, double* __restrict__ E, OaStat* __restrict__ st) {
   const OaProb p = pr[blockIdx.y];
+  const bool no_rot = orth_only[blockIdx.y] != 0;     // polishing step: E = R/2 (orthonormalisation only)
   int e = blockIdx.x * blockDim.x + threadIdx.x;
   double mag = 0.0, cpl = 0.0, rmag = 0.0, incl = 0.0;
   if (e < p.n * p.n) {
@@ -184,7 +185,7 @@ __global__ void oa_E_kernel(const OaProb* __restrict__ pr, const double* __restr
       cmw<2> k = c_zero<2>();
       if (cl_start[p.loff + a] == cl_start[p.loff + b]) {
         incl = cpl;
-      } else {
+      } else if (!no_rot) {
         mw<W> den = mw_sub(lb, la);
         cmw<2> n2 = c_make(mw_from_words<2, W>(num.re.x), mw_from_words<2, W>(num.im.x));
         k = c_scale(n2, mw_recip(mw_from_words<2, W>(den.x)));
@@ -371,6 +372,7 @@ zkq_status oa_refine_t(void* ctx, const OaBuffers& buf, int batch, const int32_t
   size_t oCLD = take(sizeof(OaCluster) * le);
   size_t oCT = take(mat), oCG = take(mat), oCW = take(mat);   // cluster blocks X_J^H A X_J, X_J^H X_J; rotation
   size_t oCN = take((size_t)le * sizeof(double));              // column coupling norms
+  size_t oOO = take(sizeof(int32_t) * batch);                  // per active problem: orthonormalise only
   zkq_status s = grow_buf(buf.ws, buf.ws_bytes, off);
   if (s != ZKQ_OK) return s;
   char* base = (char*)*buf.ws;
@@ -383,6 +385,7 @@ zkq_status oa_refine_t(void* ctx, const OaBuffers& buf, int batch, const int32_t
   OaCluster* CLD = (OaCluster*)(base + oCLD);
   double *CT = (double*)(base + oCT), *CG = (double*)(base + oCG), *CW = (double*)(base + oCW);
   double* CN = (double*)(base + oCN);
+  int32_t* OO = (int32_t*)(base + oOO);
   ZKQ_CUDA_TRY(cudaMemcpyAsync(PR, probs.data(), sizeof(OaProb) * batch, cudaMemcpyHostToDevice, st));
   ZKQ_CUDA_TRY(cudaMemsetAsync(info, 0, sizeof(int32_t) * batch, st));
   {
@@ -430,7 +433,9 @@ zkq_status oa_refine_t(void* ctx, const OaBuffers& buf, int batch, const int32_t
       oa_lambda_kernel<W><<<(unsigned)ap.size(), 256, 0, st>>>(PRA, Sm, Rm, Lm, CN, ST);
       oa_coupling_kernel<W><<<g, 256, 0, st>>>(PRA, Sm, Rm, Lm, CN, ST);
       oa_cluster_kernel<W><<<(unsigned)ap.size(), 32, 0, st>>>(PRA, Lm, CN, CS, CL, ST);
-      oa_E_kernel<W><<<g, 256, 0, st>>>(PRA, Sm, Rm, Lm, CS, Em, ST);
+      std::vector<int32_t> oo; for (int b : act) oo.push_back(polish[b] == 1 ? 1 : 0);
+      ZKQ_CUDA_TRY(cudaMemcpyAsync(OO, oo.data(), sizeof(int32_t) * oo.size(), cudaMemcpyHostToDevice, st));
+      oa_E_kernel<W><<<g, 256, 0, st>>>(PRA, Sm, Rm, Lm, CS, OO, Em, ST);
       ZKQ_CUDA_TRY(cudaGetLastError());
     }
     std::vector<OaStat> ast(ap.size());
@@ -451,9 +456,13 @@ zkq_status oa_refine_t(void* ctx, const OaBuffers& buf, int batch, const int32_t
       hst[b] = ast[a];
       iters[b] = it;
       const double an = ast[a].anorm > 0 ? ast[a].anorm : 1.0;
-      bool conv = ast[a].maxNum <= tol * an && ast[a].maxR <= tol;
-      if (polish[b] || it == max_iter) finish.push_back(b);
-      else { if (conv) polish[b] = 1; upd.push_back(b); }
+      // converged: every coupling (the residual proxy) at the working-precision level; orthonormality only
+      // loosely (near-degenerate noise leaves (noise/gap)^2 in R, removed by the orthonormalising step)
+      bool conv = ast[a].maxNum <= tol * an && ast[a].maxR <= ldexp(1.0, -(53 * W / 3));
+      // polish: 0 iterating; 1 converged, this iteration's update only re-orthonormalises (E = R/2);
+      // 2 report lambda and X of this iteration
+      if (polish[b] == 2 || it == max_iter) finish.push_back(b);
+      else { if (polish[b] == 1) polish[b] = 2; else if (conv) polish[b] = 1; upd.push_back(b); }
     }
     if (!finish.empty()) {
       // statistics of finishing problems are in ST at their active index: copy to a per-problem array
@@ -468,7 +477,7 @@ zkq_status oa_refine_t(void* ctx, const OaBuffers& buf, int batch, const int32_t
       bool any = false;
       for (int b : finish) {
         active[b] = 0;
-        if (!polish[b]) { hinfo[b] = it > 0 ? it : 1; any = true; }
+        if (polish[b] != 2) { hinfo[b] = it > 0 ? it : 1; any = true; }
       }
       if (any) {
         for (int b : finish) if (hinfo[b]) ZKQ_CUDA_TRY(cudaMemcpyAsync(info + b, &hinfo[b], sizeof(int32_t), cudaMemcpyHostToDevice, st));
@@ -493,7 +502,7 @@ zkq_status oa_refine_t(void* ctx, const OaBuffers& buf, int batch, const int32_t
       const OaProb& q = probs[b];
       // rotate only clusters whose members are still coupled (gap-free measure |s_ij + lambda_j r_ij|);
       // non-orthonormality alone is removed by the r/2 part of E
-      bool need = hst[b].cl_off > tol * (hst[b].anorm > 0 ? hst[b].anorm : 1.0) && hst[b].nclusters > 0 && !polish[b];
+      bool need = hst[b].cl_off > tol * (hst[b].anorm > 0 ? hst[b].anorm : 1.0) && hst[b].nclusters > 0 && polish[b] == 0;
       if (!need) continue;
       for (int c = 0; c < q.n;) {
         int len = hcl_len[q.loff + c];
