@@ -15,8 +15,9 @@
 // about 53 more bits of the small eigenvalues.  E only needs double-double: its entries are of the size of
 // the current error, so their relative accuracy requirement is at most ~106 bits.
 // A problem is converged once every coupling |s_ij + (lambda_i + lambda_j)/2 r_ij| <= 2^-(53W-6) ||A||
-// (E itself can stay at noise / gap for near-degenerate pairs); it then takes one more ordinary iteration
-// and one that only re-orthonormalises (E = R/2), and lambda, X of the following evaluation are reported.
+// (E itself can stay at noise / gap for near-degenerate pairs); after one more ordinary iteration it takes
+// re-orthonormalising steps (E = R/2) until |r_ij| <= 2^-(53W-10), and lambda, X of the following
+// evaluation are reported.
 #include <vector>
 #include <algorithm>
 #include <cstring>
@@ -394,7 +395,7 @@ zkq_status oa_refine_t(void* ctx, const OaBuffers& buf, int batch, const int32_t
     ZKQ_CUDA_TRY(cudaGetLastError());
   }
   const double tol = ldexp(1.0, -(53 * W - 6));
-  std::vector<int> active(batch, 1), polish(batch, 0), iters(batch, 0);
+  std::vector<int> active(batch, 1), polish(batch, 0), iters(batch, 0), orth_steps(batch, 0);
   std::vector<OaStat> hst(batch);
   std::vector<int32_t> hcl_len(le);
   const int p_bits = 53 * W + 6;
@@ -456,13 +457,18 @@ zkq_status oa_refine_t(void* ctx, const OaBuffers& buf, int batch, const int32_t
       hst[b] = ast[a];
       iters[b] = it;
       const double an = ast[a].anorm > 0 ? ast[a].anorm : 1.0;
-      // converged: every coupling (the residual proxy) at the working-precision level; orthonormality only
-      // loosely (near-degenerate noise leaves (noise/gap)^2 in R, removed by the orthonormalising step)
-      bool conv = ast[a].maxNum <= tol * an && ast[a].maxR <= ldexp(1.0, -(53 * W / 3));
-      // polish: 0 iterating; 1 converged, this iteration's update only re-orthonormalises (E = R/2);
-      // 2 report lambda and X of this iteration
+      // converged: every coupling (the residual proxy) at the working-precision level; near-degenerate
+      // noise may leave (noise/gap)^2 in R, which the orthonormalising steps below remove
+      bool conv = ast[a].maxNum <= tol * an;
+      const bool orth_ok = ast[a].maxR <= ldexp(1.0, -(53 * W - 10));
+      // polish: 0 iterating; 1 converged: updates only re-orthonormalise (E = R/2) until R is at working
+      // precision (at most 4 such steps); 2 report lambda and X of this evaluation
       if (polish[b] == 2 || it == max_iter) finish.push_back(b);
-      else { if (polish[b] == 1) polish[b] = 2; else if (conv) polish[b] = 1; upd.push_back(b); }
+      else {
+        if (polish[b] == 1) { if (orth_ok || ++orth_steps[b] >= 4) polish[b] = 2; }
+        else if (conv) polish[b] = 1;
+        upd.push_back(b);
+      }
     }
     if (!finish.empty()) {
       // statistics of finishing problems are in ST at their active index: copy to a per-problem array
