@@ -147,6 +147,25 @@ zkq_status zkq_mw_gemm(zkq_ctx* ctx, int count, const int32_t* m, const int32_t*
 zkq_status zkq_mw_op(int op, int words, int64_t count, const double* a, const double* b, double* out,
                      int on_device, void* stream);
 
+/*
+ * Launch profiler (tracing): when enabled, every kernel launch of the library is bracketed by CUDA events
+ * on its launching stream and device time is accumulated per kernel class (jacobi, rqi, ozaki_scale,
+ * ozaki_slice, ozaki_gemm, ozaki_combine, oa_elementwise, mps, other).  The paper reports only wall
+ * times; this breaks them down for the roofline of each kernel.  Process-wide.
+ *   zkq_profile_classes()        number of classes
+ *   zkq_profile_class_name(c)    name of class c (never NULL)
+ *   zkq_profile_enable(on)       start (1) / stop (0) recording
+ *   zkq_profile_read(ms, n, w, k) waits for the recorded launches, writes per-class milliseconds, launch
+ *                                counts and algorithmic work (flops counted at launch: ozaki_gemm counts
+ *                                2 m (2n) (2k) per kept digit pair; 0 where not counted) for the first k
+ *                                classes, then clears the record
+ * Errors: ZKQ_EINVAL (null arrays, k < 1), ZKQ_ECUDA.
+ */
+int zkq_profile_classes(void);
+const char* zkq_profile_class_name(int cls);
+zkq_status zkq_profile_enable(int on);
+zkq_status zkq_profile_read(double* ms, int64_t* launches, double* work, int nclasses);
+
 #ifdef __cplusplus
 }
 #endif

@@ -63,6 +63,13 @@ def lib():
             L.zkq_rqi_refine.argtypes = [P, I, P, P, P, I, P, P, I, I, P, P, P, P, P]
             L.zkq_mw_gemm.restype = I
             L.zkq_mw_gemm.argtypes = [P, I, P, P, P, P, P, P, I, P, P, I, P, P, I, I, I, P]
+            L.zkq_profile_classes.restype = I
+            L.zkq_profile_class_name.restype = ctypes.c_char_p
+            L.zkq_profile_class_name.argtypes = [I]
+            L.zkq_profile_enable.restype = I
+            L.zkq_profile_enable.argtypes = [I]
+            L.zkq_profile_read.restype = I
+            L.zkq_profile_read.argtypes = [P, P, P, I]
             L.zkq_mw_op.restype = I
             L.zkq_mw_op.argtypes = [I, I, I64, P, P, P, I, P]
             _lib = L
@@ -157,6 +164,19 @@ def zkq_mw_gemm(ctx: Context, m, n, k, opA, A, a_off, wa, B, b_off, wb, C, c_off
 def zkq_mw_op(op: int, words: int, count: int, a, b, out, on_device: bool, stream=None):
     _check(lib().zkq_mw_op(op, words, count, _ptr(a), _ptr(b), _ptr(out), int(bool(on_device)), _stream(stream)),
            "zkq_mw_op")
+
+
+def zkq_profile_enable(on: bool):
+    _check(lib().zkq_profile_enable(int(bool(on))), "zkq_profile_enable")
+
+
+def zkq_profile_read():
+    """{class name: (milliseconds, launches, algorithmic flops)} since the last read."""
+    import numpy as np
+    k = lib().zkq_profile_classes()
+    ms = np.zeros(k); n = np.zeros(k, dtype=np.int64); w = np.zeros(k)
+    _check(lib().zkq_profile_read(ms.ctypes.data, n.ctypes.data, w.ctypes.data, k), "zkq_profile_read")
+    return {lib().zkq_profile_class_name(i).decode(): (float(ms[i]), int(n[i]), float(w[i])) for i in range(k)}
 
 
 # --------------------------------------------------------------------------------------------------

@@ -6,8 +6,11 @@
 #include <new>
 #include "common.cuh"
 #include "mw.cuh"
+#include "prof.cuh"
 
 namespace zkq {
+
+Profiler& profiler() { static Profiler p; return p; }
 
 static thread_local int g_last_cuda = 0;
 void set_last_cuda_error(cudaError_t e) { g_last_cuda = (int)e; }
@@ -225,6 +228,37 @@ zkq_status zkq_mw_gemm(zkq_ctx* ctx, int count, const int32_t* m, const int32_t*
   }
   return mw_gemm_batched(pr.data(), count, wa, wb, wc, p_bits, method, &ctx->oz_ws, &ctx->oz_bytes, &ctx->oz_meta,
                          &ctx->oz_meta_bytes, (cudaStream_t)stream);
+}
+
+static const char* kProfNames[PC_COUNT] = {"jacobi", "rqi", "ozaki_scale", "ozaki_slice", "ozaki_gemm",
+                                           "ozaki_combine", "oa_elementwise", "mps", "other"};
+
+int zkq_profile_classes(void) { return PC_COUNT; }
+
+const char* zkq_profile_class_name(int cls) { return (cls >= 0 && cls < PC_COUNT) ? kProfNames[cls] : "invalid"; }
+
+zkq_status zkq_profile_enable(int on) {
+  Profiler& p = profiler();
+  std::lock_guard<std::mutex> g(p.mu);
+  p.on = on != 0;
+  return ZKQ_OK;
+}
+
+zkq_status zkq_profile_read(double* ms, int64_t* launches, double* work, int nclasses) {
+  if (!ms || !launches || !work || nclasses < 1) return ZKQ_EINVAL;
+  Profiler& p = profiler();
+  std::lock_guard<std::mutex> g(p.mu);
+  for (int i = 0; i < nclasses; ++i) { ms[i] = 0.0; launches[i] = 0; work[i] = 0.0; }
+  for (auto& r : p.recs) {
+    cudaError_t e = cudaEventSynchronize(r.b);
+    if (e != cudaSuccess) { set_last_cuda_error(e); return ZKQ_ECUDA; }
+    float t = 0.f;
+    cudaEventElapsedTime(&t, r.a, r.b);
+    if (r.cls < nclasses) { ms[r.cls] += t; launches[r.cls] += 1; work[r.cls] += r.work; }
+    p.pool.push_back(r.a); p.pool.push_back(r.b);
+  }
+  p.recs.clear();
+  return ZKQ_OK;
 }
 
 }  // extern "C"

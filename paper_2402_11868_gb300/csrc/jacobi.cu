@@ -17,6 +17,7 @@
 // real and positive.
 #include "common.cuh"
 #include "mw.cuh"
+#include "prof.cuh"
 #include <cooperative_groups.h>
 namespace cg = cooperative_groups;
 
@@ -264,6 +265,7 @@ static zkq_status launch_words(const JacobiBatch& jb, int n_small, int n_large, 
   if (n_small > 0) {
     size_t sm = jacobi_smem_bytes(max_small_n);
     ZKQ_CUDA_TRY(cudaFuncSetAttribute(jacobi_smem_kernel<WA>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    ProfScope ps(PC_JACOBI, st);
     jacobi_smem_kernel<WA><<<n_small, 256, sm, st>>>(jb, 0, n_small);
     ZKQ_CUDA_TRY(cudaGetLastError());
   }
@@ -281,6 +283,7 @@ static zkq_status launch_words(const JacobiBatch& jb, int n_small, int n_large, 
     attr[0].id = cudaLaunchAttributeClusterDimension;
     attr[0].val.clusterDim.x = cluster; attr[0].val.clusterDim.y = 1; attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr; cfg.numAttrs = 1;
+    ProfScope ps(PC_JACOBI, st);
     ZKQ_CUDA_TRY(cudaLaunchKernelEx(&cfg, jacobi_global_kernel<WA>, jb, n_small));
   }
   return ZKQ_OK;

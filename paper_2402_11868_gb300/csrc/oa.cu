@@ -27,6 +27,7 @@
 #include "mw.cuh"
 #include "reduce.cuh"
 #include "ozaki.cuh"
+#include "prof.cuh"
 
 namespace zkq {
 
@@ -391,7 +392,7 @@ zkq_status oa_refine_t(void* ctx, const OaBuffers& buf, int batch, const int32_t
   ZKQ_CUDA_TRY(cudaMemsetAsync(info, 0, sizeof(int32_t) * batch, st));
   {
     dim3 g((nmax * nmax + 255) / 256, batch);
-    oa_init_kernel<W><<<g, 256, 0, st>>>(PR, V, X);
+    { ProfScope ps_(PC_OA, st); oa_init_kernel<W><<<g, 256, 0, st>>>(PR, V, X); }
     ZKQ_CUDA_TRY(cudaGetLastError());
   }
   const double tol = ldexp(1.0, -(53 * W - 6));
@@ -431,12 +432,12 @@ zkq_status oa_refine_t(void* ctx, const OaBuffers& buf, int batch, const int32_t
     {
       int mx = 0; for (auto& q : ap) mx = std::max(mx, q.n * q.n);
       dim3 g((mx + 255) / 256, (unsigned)ap.size());
-      oa_lambda_kernel<W><<<(unsigned)ap.size(), 256, 0, st>>>(PRA, Sm, Rm, Lm, CN, ST);
-      oa_coupling_kernel<W><<<g, 256, 0, st>>>(PRA, Sm, Rm, Lm, CN, ST);
-      oa_cluster_kernel<W><<<(unsigned)ap.size(), 32, 0, st>>>(PRA, Lm, CN, CS, CL, ST);
+      { ProfScope ps_(PC_OA, st); oa_lambda_kernel<W><<<(unsigned)ap.size(), 256, 0, st>>>(PRA, Sm, Rm, Lm, CN, ST); }
+      { ProfScope ps_(PC_OA, st); oa_coupling_kernel<W><<<g, 256, 0, st>>>(PRA, Sm, Rm, Lm, CN, ST); }
+      { ProfScope ps_(PC_OA, st); oa_cluster_kernel<W><<<(unsigned)ap.size(), 32, 0, st>>>(PRA, Lm, CN, CS, CL, ST); }
       std::vector<int32_t> oo; for (int b : act) oo.push_back(polish[b] == 1 ? 1 : 0);
       ZKQ_CUDA_TRY(cudaMemcpyAsync(OO, oo.data(), sizeof(int32_t) * oo.size(), cudaMemcpyHostToDevice, st));
-      oa_E_kernel<W><<<g, 256, 0, st>>>(PRA, Sm, Rm, Lm, CS, OO, Em, ST);
+      { ProfScope ps_(PC_OA, st); oa_E_kernel<W><<<g, 256, 0, st>>>(PRA, Sm, Rm, Lm, CS, OO, Em, ST); }
       ZKQ_CUDA_TRY(cudaGetLastError());
     }
     std::vector<OaStat> ast(ap.size());
@@ -477,7 +478,7 @@ zkq_status oa_refine_t(void* ctx, const OaBuffers& buf, int batch, const int32_t
       ZKQ_CUDA_TRY(cudaMemcpyAsync(ST, fst.data(), sizeof(OaStat) * batch, cudaMemcpyHostToDevice, st));
       ZKQ_CUDA_TRY(cudaMemcpyAsync(WH, finish.data(), sizeof(int32_t) * finish.size(), cudaMemcpyHostToDevice, st));
       ZKQ_CUDA_TRY(cudaMemcpyAsync(PR, probs.data(), sizeof(OaProb) * batch, cudaMemcpyHostToDevice, st));
-      oa_output_kernel<W><<<(unsigned)finish.size(), 256, 0, st>>>(PR, WH, X, Pm, Lm, ST, W_out, V_out, err);
+      { ProfScope ps_(PC_OA, st); oa_output_kernel<W><<<(unsigned)finish.size(), 256, 0, st>>>(PR, WH, X, Pm, Lm, ST, W_out, V_out, err); }
       ZKQ_CUDA_TRY(cudaGetLastError());
       std::vector<int32_t> hinfo(batch, 0);
       bool any = false;
@@ -535,7 +536,7 @@ zkq_status oa_refine_t(void* ctx, const OaBuffers& buf, int batch, const int32_t
       s = mw_gemm_batched(p6.data(), (int)p6.size(), W, W, W, p_bits, prod_method, buf.oz_ws, buf.oz_bytes, buf.oz_meta, buf.oz_meta_bytes, st);
       if (s != ZKQ_OK) return s;
       dim3 g((maxl * maxl + 255) / 256, (unsigned)cls.size());
-      oa_cluster_T_kernel<W><<<g, 256, 0, st>>>(PR, CLD, CT, CG, Lm, T);
+      { ProfScope ps_(PC_OA, st); oa_cluster_T_kernel<W><<<g, 256, 0, st>>>(PR, CLD, CT, CG, Lm, T); }
       ZKQ_CUDA_TRY(cudaGetLastError());
       std::vector<int32_t> cn(cls.size()); std::vector<int64_t> co(cls.size());
       for (size_t c = 0; c < cls.size(); ++c) { cn[c] = cls[c].len; co[c] = cls[c].toff; }
@@ -544,7 +545,7 @@ zkq_status oa_refine_t(void* ctx, const OaBuffers& buf, int batch, const int32_t
       // The FP64 eigenvector matrix is unitary only to 2^-53; two Newton-Schulz steps W <- W (3I - W^H W)/2
       // in W-word products make it unitary to working precision, so the rotation does not disturb the
       // orthonormality of X (which would inflate the cluster thresholds of the next iteration).
-      oa_promote_kernel<W><<<g, 256, 0, st>>>(CLD, TV, CT);
+      { ProfScope ps_(PC_OA, st); oa_promote_kernel<W><<<g, 256, 0, st>>>(CLD, TV, CT); }
       ZKQ_CUDA_TRY(cudaGetLastError());
       double* Wcur = CT; double* Wnext = CW;
       for (int ns = 0; ns < 2; ++ns) {
@@ -552,7 +553,7 @@ zkq_status oa_refine_t(void* ctx, const OaBuffers& buf, int batch, const int32_t
         for (auto& c : cls) pg.push_back({c.len, c.len, c.len, 1, Wcur + c.toff * 2 * W, Wcur + c.toff * 2 * W, CG + c.toff * 2 * W, nullptr, 1.0, 0});
         s = mw_gemm_batched(pg.data(), (int)pg.size(), W, W, W, p_bits, prod_method, buf.oz_ws, buf.oz_bytes, buf.oz_meta, buf.oz_meta_bytes, st);
         if (s != ZKQ_OK) return s;
-        oa_ns_kernel<W><<<g, 256, 0, st>>>(CLD, CG);
+        { ProfScope ps_(PC_OA, st); oa_ns_kernel<W><<<g, 256, 0, st>>>(CLD, CG); }
         ZKQ_CUDA_TRY(cudaGetLastError());
         for (auto& c : cls) pw.push_back({c.len, c.len, c.len, 0, Wcur + c.toff * 2 * W, CG + c.toff * 2 * W, Wnext + c.toff * 2 * W, nullptr, 1.0, 0});
         s = mw_gemm_batched(pw.data(), (int)pw.size(), W, W, W, p_bits, prod_method, buf.oz_ws, buf.oz_bytes, buf.oz_meta, buf.oz_meta_bytes, st);
@@ -569,7 +570,7 @@ zkq_status oa_refine_t(void* ctx, const OaBuffers& buf, int batch, const int32_t
       s = mw_gemm_batched(p4.data(), (int)p4.size(), W, W, W, p_bits, prod_method, buf.oz_ws, buf.oz_bytes, buf.oz_meta, buf.oz_meta_bytes, st);
       if (s != ZKQ_OK) return s;
       dim3 g2((nmax * maxl + 255) / 256, (unsigned)cls.size());
-      oa_cluster_copy_kernel<W><<<g2, 256, 0, st>>>(PR, CLD, X, X2);
+      { ProfScope ps_(PC_OA, st); oa_cluster_copy_kernel<W><<<g2, 256, 0, st>>>(PR, CLD, X, X2); }
       ZKQ_CUDA_TRY(cudaGetLastError());
     }
     // X <- X2 for updated problems (swap buffers by copying the updated problems' matrices)

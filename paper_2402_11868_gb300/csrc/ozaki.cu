@@ -16,6 +16,7 @@
 //   Re C = [Re op(A) | Im op(A)] [Re B ; -Im B],  Im C = [Re op(A) | Im op(A)] [Im B ; Re B]   (K' = 2k).
 #include "ozaki.cuh"
 #include "mw.cuh"
+#include "prof.cuh"
 #include <vector>
 #include <algorithm>
 #include <cstring>
@@ -440,6 +441,7 @@ zkq_status mw_gemm_batched(const MwProd* prods, int count, int wa, int wb, int w
     ZKQ_CUDA_TRY(cudaMemcpyAsync(*meta, dp.data(), sizeof(OzProd) * count, cudaMemcpyHostToDevice, st));
     dim3 grid((max_mn + 127) / 128, count);
     const OzProd* d = (const OzProd*)*meta;
+    ProfScope ps(PC_OZ_GEMM, st);
 #define ZKQ_PLAIN(A_, B_, C_) if (wa == A_ && wb == B_ && wc == C_) mw_gemm_plain_kernel<A_, B_, C_><<<grid, 128, 0, st>>>(d);
     ZKQ_PLAIN(1,1,1) ZKQ_PLAIN(1,1,2) ZKQ_PLAIN(1,1,4) ZKQ_PLAIN(1,2,2) ZKQ_PLAIN(1,2,4) ZKQ_PLAIN(1,4,4)
     ZKQ_PLAIN(2,1,2) ZKQ_PLAIN(2,2,2) ZKQ_PLAIN(2,4,4) ZKQ_PLAIN(2,1,4) ZKQ_PLAIN(2,2,4) ZKQ_PLAIN(2,4,2)
@@ -490,6 +492,7 @@ zkq_status mw_gemm_batched(const MwProd* prods, int count, int wa, int wb, int w
   for (auto& o : dp) max_rows = std::max(max_rows, o.m + o.n);
   {
     dim3 g((max_rows + 127) / 128, count);
+    ProfScope ps(PC_OZ_SCALE, st);
 #define ZKQ_SC(A_, B_) if (wa == A_ && wb == B_) oz_scale_kernel<A_, B_><<<g, 128, 0, st>>>(d_p);
     ZKQ_SC(1,1) ZKQ_SC(1,2) ZKQ_SC(1,4) ZKQ_SC(2,1) ZKQ_SC(2,2) ZKQ_SC(2,4) ZKQ_SC(4,1) ZKQ_SC(4,2) ZKQ_SC(4,4)
 #undef ZKQ_SC
@@ -497,6 +500,7 @@ zkq_status mw_gemm_batched(const MwProd* prods, int count, int wa, int wb, int w
   }
   {
     dim3 gA((unsigned)((max_mkp + 255) / 256), count), gB((unsigned)((max_nkp + 255) / 256), count);
+    ProfScope ps(PC_OZ_SLICE, st);
     ZKQ_DISPATCH_W(wa, oz_slice_A_kernel, <<<gA, 256, 0, st>>>(d_p, plan.b, plan.sA));
     ZKQ_DISPATCH_W(wb, oz_slice_B_kernel, <<<gB, 256, 0, st>>>(d_p, plan.b, plan.sB));
     ZKQ_CUDA_TRY(cudaGetLastError());
@@ -504,11 +508,15 @@ zkq_status mw_gemm_batched(const MwProd* prods, int count, int wa, int wb, int w
   {
     size_t sm = (size_t)OZ_STAGES * (OZ_BM + OZ_BN) * 64;
     ZKQ_CUDA_TRY(cudaFuncSetAttribute(oz_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    double flops = 0.0;                        // algorithmic: every kept digit pair, unpadded sizes
+    for (auto& o : dp) flops += 2.0 * plan.npairs * (double)o.m * (2.0 * o.n) * (2.0 * o.k);
+    ProfScope ps(PC_OZ_GEMM, st, flops);
     oz_gemm_kernel<<<(unsigned)tiles.size(), 256, sm, st>>>(d_p, d_t, d_q, plan.npairs, plan.S);
     ZKQ_CUDA_TRY(cudaGetLastError());
   }
   {
     dim3 g((max_mn + 127) / 128, count);
+    ProfScope ps(PC_OZ_COMBINE, st);
     if (wc == 1) oz_combine_kernel<1><<<g, 128, 0, st>>>(d_p, plan.b, plan.S);
     else if (wc == 2) oz_combine_kernel<2><<<g, 128, 0, st>>>(d_p, plan.b, plan.S);
     else oz_combine_kernel<4><<<g, 128, 0, st>>>(d_p, plan.b, plan.S);

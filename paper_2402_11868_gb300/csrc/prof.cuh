@@ -1,0 +1,46 @@
+// Launch profiler: when enabled, every library kernel launch is bracketed by CUDA events recorded on the
+// launching stream, and device time is accumulated per kernel class.  Read after the stream synchronises.
+#pragma once
+#include <cuda_runtime.h>
+#include <vector>
+#include <mutex>
+
+namespace zkq {
+
+enum ProfClass { PC_JACOBI = 0, PC_RQI, PC_OZ_SCALE, PC_OZ_SLICE, PC_OZ_GEMM, PC_OZ_COMBINE, PC_OA, PC_MPS, PC_OTHER, PC_COUNT };
+
+struct Profiler {
+  bool on = false;
+  std::mutex mu;
+  struct Rec { int cls; cudaEvent_t a, b; double work; };
+  std::vector<Rec> recs;
+  std::vector<cudaEvent_t> pool;
+  cudaEvent_t get() {
+    if (!pool.empty()) { cudaEvent_t e = pool.back(); pool.pop_back(); return e; }
+    cudaEvent_t e; cudaEventCreate(&e); return e;
+  }
+};
+Profiler& profiler();
+
+// RAII bracket around one launch
+struct ProfScope {
+  int cls; cudaStream_t st; cudaEvent_t a = nullptr; double work;
+  // work: algorithmic flops of the launch (0 if not counted)
+  ProfScope(int c, cudaStream_t s, double w = 0.0) : cls(c), st(s), work(w) {
+    Profiler& p = profiler();
+    if (!p.on) return;
+    std::lock_guard<std::mutex> g(p.mu);
+    a = p.get();
+    cudaEventRecord(a, st);
+  }
+  ~ProfScope() {
+    if (!a) return;
+    Profiler& p = profiler();
+    std::lock_guard<std::mutex> g(p.mu);
+    cudaEvent_t b = p.get();
+    cudaEventRecord(b, st);
+    p.recs.push_back({cls, a, b, work});
+  }
+};
+
+}  // namespace zkq

@@ -11,6 +11,7 @@
 #include "common.cuh"
 #include "mw.cuh"
 #include "reduce.cuh"
+#include "prof.cuh"
 
 namespace zkq {
 
@@ -236,6 +237,7 @@ template <int W, int WA>
 static zkq_status launch_rqi_t(const RqiBatch& rb, int grid, cudaStream_t st) {
   size_t sm = 256 * sizeof(cmw<W>);
   ZKQ_CUDA_TRY(cudaFuncSetAttribute(rqi_kernel<W, WA>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+  ProfScope ps(PC_RQI, st);
   rqi_kernel<W, WA><<<grid, 256, sm, st>>>(rb);
   ZKQ_CUDA_TRY(cudaGetLastError());
   return ZKQ_OK;
