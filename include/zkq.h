@@ -42,7 +42,8 @@ typedef enum {
   ZKQ_ENOCONV = 3,   /* reserved: a problem did not converge (per-problem detail is in info[]) */
   ZKQ_ETIMEOUT = 4,  /* a bounded device-side wait expired */
   ZKQ_ECUDA = 5,     /* a CUDA runtime call failed; see zkq_last_cuda_error() */
-  ZKQ_EADMIT = 6     /* reserved: request refused by admission control */
+  ZKQ_EADMIT = 6,    /* reserved: request refused by admission control */
+  ZKQ_ETOOBIG = 7    /* the request needs more than the fixed scratch of zkq_eigh_batched_noalloc */
 } zkq_status;
 
 typedef enum { ZKQ_FP64 = 1, ZKQ_DD = 2, ZKQ_QD = 4 } zkq_prec;   /* value = words per real */
@@ -89,6 +90,27 @@ zkq_status zkq_ctx_destroy(zkq_ctx* ctx);
  */
 zkq_status zkq_eigh_batched(zkq_ctx* ctx, int batch, const int32_t* n, const int64_t* a_off,
                             const double* A, int a_words, double* W, double* V, int32_t* info, void* stream);
+
+/*
+ * zkq_eigh_batched_noalloc: zkq_eigh_batched for callers that cannot allocate device memory.  The paper
+ * has no counterpart; it exists for callers such as code running while another part of the process
+ * captures a CUDA graph, hosts that give the library a fixed memory budget, or latency-critical loops
+ * where an allocation could stall on a device-wide synchronisation.
+ * Arguments, layouts, results and errors are those of zkq_eigh_batched on the current device, with
+ * default settings (40 sweeps); no context is needed.  The call allocates nothing: its scratch (batch
+ * metadata and the global-memory copies of A and V for orders above 80, 32 n^2 bytes each) lives in one
+ * file-scope device array of ZKQ_NOALLOC_SCRATCH_BYTES that every GPU which loads the library holds until
+ * the process exits.
+ *   - A batch whose scratch would exceed ZKQ_NOALLOC_SCRATCH_BYTES is rejected with ZKQ_ETOOBIG (e.g. one
+ *     problem of order 1024 needs 32 MiB; orders <= 80 need no scratch beyond ~40 bytes of metadata).
+ *   - The first call on a device looks up the array's device address (cudaGetSymbolAddress) with that
+ *     device current; make that first call before any stream capture.
+ *   - Every call uses the same array and leaves its last contents there: calls that overlap on the GPU
+ *     (different streams, or different host threads, on the same device) race.
+ */
+#define ZKQ_NOALLOC_SCRATCH_BYTES (32u * 1024u * 1024u)
+zkq_status zkq_eigh_batched_noalloc(int batch, const int32_t* n, const int64_t* a_off, const double* A,
+                                    int a_words, double* W, double* V, int32_t* info, void* stream);
 
 /*
  * zkq_rqi_refine: recover the eigenpairs to the target precision from the FP64 ones

@@ -17,7 +17,8 @@ LIB_PATH = os.path.join(_HERE, "libzkq.so")
 _lib = None
 _lock = threading.Lock()
 
-ZKQ_OK, ZKQ_EINVAL, ZKQ_ENOMEM, ZKQ_ENOCONV, ZKQ_ETIMEOUT, ZKQ_ECUDA, ZKQ_EADMIT = range(7)
+ZKQ_OK, ZKQ_EINVAL, ZKQ_ENOMEM, ZKQ_ENOCONV, ZKQ_ETIMEOUT, ZKQ_ECUDA, ZKQ_EADMIT, ZKQ_ETOOBIG = range(8)
+ZKQ_NOALLOC_SCRATCH_BYTES = 32 * 1024 * 1024
 ZKQ_FP64, ZKQ_DD, ZKQ_QD = 1, 2, 4
 ZKQ_PLAIN_RQI, ZKQ_OA_OZAKI, ZKQ_OA_FP64 = 0, 1, 2
 
@@ -59,6 +60,8 @@ def lib():
             L.zkq_ctx_destroy.argtypes = [P]
             L.zkq_eigh_batched.restype = I
             L.zkq_eigh_batched.argtypes = [P, I, P, P, P, I, P, P, P, P]
+            L.zkq_eigh_batched_noalloc.restype = I
+            L.zkq_eigh_batched_noalloc.argtypes = [I, P, P, P, I, P, P, P, P]
             L.zkq_rqi_refine.restype = I
             L.zkq_rqi_refine.argtypes = [P, I, P, P, P, I, P, P, I, I, P, P, P, P, P]
             L.zkq_mw_gemm.restype = I
@@ -142,6 +145,14 @@ def zkq_eigh_batched(ctx: Context, n, a_off, A, a_words, W, V, info, stream=None
     o_arr, o_p = _host_array(a_off, ctypes.c_int64)
     _check(lib().zkq_eigh_batched(ctx.handle, len(n_arr), n_p, o_p, _ptr(A), a_words, _ptr(W), _ptr(V), _ptr(info),
                                   _stream(stream)), "zkq_eigh_batched")
+
+
+def zkq_eigh_batched_noalloc(n, a_off, A, a_words, W, V, info, stream=None):
+    """zkq_eigh_batched on the current device without any device allocation (fixed library scratch)."""
+    n_arr, n_p = _host_array(n, ctypes.c_int32)
+    o_arr, o_p = _host_array(a_off, ctypes.c_int64)
+    _check(lib().zkq_eigh_batched_noalloc(len(n_arr), n_p, o_p, _ptr(A), a_words, _ptr(W), _ptr(V), _ptr(info),
+                                          _stream(stream)), "zkq_eigh_batched_noalloc")
 
 
 def zkq_rqi_refine(ctx: Context, n, a_off, A, a_words, W, V, target_words, method, W_out, V_out, err_est, info,

@@ -76,6 +76,7 @@ const char* zkq_status_string(zkq_status s) {
     case ZKQ_ETIMEOUT: return "ZKQ_ETIMEOUT: bounded device wait expired";
     case ZKQ_ECUDA: return "ZKQ_ECUDA: CUDA runtime error";
     case ZKQ_EADMIT: return "ZKQ_EADMIT: admission refused";
+    case ZKQ_ETOOBIG: return "ZKQ_ETOOBIG: request exceeds the fixed scratch of the no-allocation entry point";
   }
   return "unknown zkq status";
 }
