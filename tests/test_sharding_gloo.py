@@ -1,0 +1,67 @@
+"""Multi-GPU host logic on CPU: the batch shards across ranks by problem (weak scaling, no data-path
+collective); ranks partition by a greedy N^3 balance and gather per-problem results for reporting.
+Runs two gloo ranks on the CPU."""
+from __future__ import annotations
+
+import os
+
+import numpy as np
+import pytest
+import torch.multiprocessing as mp
+
+
+def shard(ns, world):
+    """Greedy longest-processing-time assignment of problems to ranks by N^3 (the Jacobi/OA cost law)."""
+    loads = [0.0] * world
+    owner = [0] * len(ns)
+    for b in sorted(range(len(ns)), key=lambda b: -ns[b] ** 3):
+        r = int(np.argmin(loads))
+        owner[b] = r
+        loads[r] += ns[b] ** 3
+    return owner, loads
+
+
+def _worker(rank, world, port, ns, out_q):
+    import torch
+    import torch.distributed as dist
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    owner, _ = shard(ns, world)
+    mine = [b for b in range(len(ns)) if owner[b] == rank]
+    # stand-in for the per-rank result of the hot path: eigenpairs processed per problem
+    local = torch.zeros(len(ns), dtype=torch.int64)
+    for b in mine:
+        local[b] = ns[b]
+    gathered = [torch.zeros_like(local) for _ in range(world)]
+    dist.all_gather(gathered, local)            # result gather for reporting only
+    t = torch.tensor([float(len(mine))])
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)    # max-over-ranks timing pattern of bench.py
+    if rank == 0:
+        out_q.put((sum(g for g in gathered).tolist(), float(t.item())))
+    dist.destroy_process_group()
+
+
+def test_shard_balance_and_coverage():
+    import workloads as W
+    ns = W.batch_sizes(1)
+    for world in (1, 2, 4, 8):
+        owner, loads = shard(ns, world)
+        assert sorted(set(owner)) == list(range(world))
+        assert max(loads) <= 1.1 * sum(loads) / world + max(n ** 3 for n in ns)
+
+
+def test_two_gloo_ranks_cover_every_problem_once():
+    import workloads as W
+    ns = W.batch_sizes(1, count=64)
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = 29500 + (os.getpid() % 1000)
+    procs = [ctx.Process(target=_worker, args=(r, 2, port, ns, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    total, _ = q.get(timeout=120)
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    assert total == ns                          # each problem processed by exactly one rank
