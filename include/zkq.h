@@ -132,6 +132,43 @@ zkq_status zkq_rqi_refine(zkq_ctx* ctx, int batch, const int32_t* n, const int64
                           int32_t* info, void* stream);
 
 /*
+ * Matrix-product state (Vidal form) resident on the device, and its gate updates (Section 1: an MPS is a
+ * nested Schmidt decomposition evolved without leaving that form, cost O(n g r_max^3); Section 2.1:
+ * diagonalisation at each gate dominates; footnote: Schmidt coefficients ~2^{-(n-1)/2} must survive).
+ * Layout used by download/upload (host arrays): Gamma[l] is row-major (s, alpha, beta) with s in {0,1},
+ * alpha < chi[l-1] (1 for l = 0), beta < chi[l] (1 for l = n-1), complex, `words` words per real,
+ * concatenated over l = 0..n-1; lambda[l] (chi[l] reals of `words` words) concatenated over l = 0..n-2.
+ * Site 0 is the most significant qubit of a basis index.  A two-qubit gate is 4x4 row-major complex in
+ * (i j) x (k m), i the bit of `site`; a one-qubit gate is 2x2.  Gates are host arrays.
+ */
+typedef struct zkq_mps zkq_mps;
+/* |0...0> on n_qubits sites (2 <= n <= 4096), bond dimensions capped at r_max (<= 2048), words 2 or 4.
+ * Allocates per-site capacity min(2^min(l+1, n-l-1), r_max).  Errors: ZKQ_EINVAL, ZKQ_ENOMEM. */
+zkq_status zkq_mps_create(zkq_ctx* ctx, int n_qubits, int r_max, int words, zkq_mps** out);
+zkq_status zkq_mps_destroy(zkq_mps* mps);
+/* current bond dimensions chi[0..n-2] (host) */
+zkq_status zkq_mps_bond_dims(const zkq_mps* mps, int32_t* chi);
+/* copy the state to / from host arrays in the layout above (synchronises the stream) */
+zkq_status zkq_mps_download(const zkq_mps* mps, double* gammas, double* lambdas, void* stream);
+zkq_status zkq_mps_upload(zkq_mps* mps, const int32_t* chi, const double* gammas, const double* lambdas, void* stream);
+/* one-qubit gate U (2x2, host) on `site`: Gamma[site]^i <- sum_k U_ik Gamma[site]^k */
+zkq_status zkq_mps_apply1q(zkq_ctx* ctx, zkq_mps* mps, int site, const double* U, void* stream);
+/*
+ * Two-qubit gate G (4x4, host) on (site, site+1): theta contraction (split products), the Hermitian Gram
+ * matrix of the smaller side (rho = M M^H, ties left), its eigen-decomposition (FP64 Jacobi + refinement
+ * `method`: ZKQ_PLAIN_RQI, ZKQ_OA_OZAKI or ZKQ_OA_FP64, to the state's words), truncation to the Schmidt
+ * values with sigma^2 > trunc_tau * sum sigma^2 (at most r_max), renormalisation sum lambda'^2 = 1, and the
+ * split back into Gamma'[site], lambda'[site], Gamma'[site+1].  Synchronises the stream (the new bond
+ * dimension is decided on the host).
+ *   new_bond (host, may be NULL)          kept Schmidt rank
+ *   discarded_weight (host, may be NULL)  dropped sum sigma^2 over total sum sigma^2 (FP64 estimate)
+ * Errors: ZKQ_EINVAL, ZKQ_ENOMEM, ZKQ_ECUDA; ZKQ_ENOCONV if the eigensolve did not converge (the state is
+ * still updated with the last iterate).
+ */
+zkq_status zkq_mps_apply2q(zkq_ctx* ctx, zkq_mps* mps, int site, const double* G, double trunc_tau, int method,
+                           int32_t* new_bond, double* discarded_weight, void* stream);
+
+/*
  * zkq_mw_gemm: batched multi-word complex products C_i = op(A_i) B_i, the dense products of the refinement
  * step (A X, X^H X, X^H (A X), X E) that recover the precision of the FP64 eigenpairs (Section 2, ZKCM_CUS
  * paragraph).  Method 1 splits both operands into exact 8-bit (7-bit when k > 512) integer digits scaled

@@ -73,6 +73,12 @@ def lib():
             L.zkq_profile_enable.argtypes = [I]
             L.zkq_profile_read.restype = I
             L.zkq_profile_read.argtypes = [P, P, P, I]
+            for nm, args in (("zkq_mps_create", [P, I, I, I, ctypes.POINTER(P)]), ("zkq_mps_destroy", [P]),
+                             ("zkq_mps_bond_dims", [P, P]), ("zkq_mps_download", [P, P, P, P]),
+                             ("zkq_mps_upload", [P, P, P, P, P]), ("zkq_mps_apply1q", [P, P, I, P, P]),
+                             ("zkq_mps_apply2q", [P, P, I, P, ctypes.c_double, I, P, P, P])):
+                getattr(L, nm).restype = I
+                getattr(L, nm).argtypes = args
             L.zkq_mw_op.restype = I
             L.zkq_mw_op.argtypes = [I, I, I64, P, P, P, I, P]
             _lib = L
@@ -188,6 +194,63 @@ def zkq_profile_read():
     ms = np.zeros(k); n = np.zeros(k, dtype=np.int64); w = np.zeros(k)
     _check(lib().zkq_profile_read(ms.ctypes.data, n.ctypes.data, w.ctypes.data, k), "zkq_profile_read")
     return {lib().zkq_profile_class_name(i).decode(): (float(ms[i]), int(n[i]), float(w[i])) for i in range(k)}
+
+
+class MPS:
+    """Device-resident Vidal MPS (|0...0> at creation)."""
+
+    def __init__(self, ctx: Context, n_qubits: int, r_max: int, words: int = 4):
+        h = ctypes.c_void_p()
+        _check(lib().zkq_mps_create(ctx.handle, n_qubits, r_max, words, ctypes.byref(h)), "zkq_mps_create")
+        self.handle, self.ctx, self.n, self.words = h.value, ctx, n_qubits, words
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib().zkq_mps_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def bond_dims(self):
+        import numpy as np
+        chi = np.zeros(self.n - 1, dtype=np.int32)
+        _check(lib().zkq_mps_bond_dims(self.handle, chi.ctypes.data), "zkq_mps_bond_dims")
+        return chi
+
+    def download(self, stream=None):
+        """(chi, gammas (sum 2 chi_l-1 chi_l, 2, w), lambdas (sum chi_l, w)) in the oracle's layout."""
+        import numpy as np
+        chi = self.bond_dims()
+        dims = [1] + list(chi) + [1]
+        ng = sum(2 * dims[l] * dims[l + 1] for l in range(self.n))
+        g = np.zeros((ng, 2, self.words)); lam = np.zeros((max(1, int(chi.sum())), self.words))
+        _check(lib().zkq_mps_download(self.handle, g.ctypes.data, lam.ctypes.data, _stream(stream)), "zkq_mps_download")
+        return chi, g, lam[:int(chi.sum())]
+
+    def upload(self, chi, gammas, lambdas, stream=None):
+        import numpy as np
+        chi = np.ascontiguousarray(chi, dtype=np.int32)
+        g = np.ascontiguousarray(gammas, dtype=np.float64); l = np.ascontiguousarray(lambdas, dtype=np.float64)
+        _check(lib().zkq_mps_upload(self.handle, chi.ctypes.data, g.ctypes.data, l.ctypes.data, _stream(stream)),
+               "zkq_mps_upload")
+
+    def apply1q(self, site, U, stream=None):
+        import numpy as np
+        u = np.ascontiguousarray(U, dtype=np.float64)
+        _check(lib().zkq_mps_apply1q(self.ctx.handle, self.handle, site, u.ctypes.data, _stream(stream)), "zkq_mps_apply1q")
+
+    def apply2q(self, site, G, trunc_tau=0.0, method=ZKQ_OA_OZAKI, stream=None):
+        """Returns (new bond dimension, discarded weight)."""
+        import numpy as np
+        g = np.ascontiguousarray(G, dtype=np.float64)
+        nb = ctypes.c_int32(0); dw = ctypes.c_double(0.0)
+        _check(lib().zkq_mps_apply2q(self.ctx.handle, self.handle, site, g.ctypes.data, float(trunc_tau), method,
+                                     ctypes.byref(nb), ctypes.byref(dw), _stream(stream)), "zkq_mps_apply2q")
+        return nb.value, dw.value
 
 
 # --------------------------------------------------------------------------------------------------

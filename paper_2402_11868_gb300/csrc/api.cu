@@ -51,7 +51,18 @@ struct zkq_ctx {
   size_t oz_bytes = 0;
   void* oz_meta = nullptr;
   size_t oz_meta_bytes = 0;
+  void* mps_ws = nullptr;   // gate-update scratch (theta, rho, split-back)
+  size_t mps_bytes = 0;
 };
+
+namespace zkq {
+OaBuffers ctx_oa_buffers(void* vctx) {
+  zkq_ctx* c = (zkq_ctx*)vctx;
+  return OaBuffers{&c->oa_ws, &c->oa_bytes, &c->oz_ws, &c->oz_bytes, &c->oz_meta, &c->oz_meta_bytes};
+}
+int ctx_oa_max_iter(void* vctx) { return ((zkq_ctx*)vctx)->cfg.oa_max_iter; }
+void** ctx_mps_ws(void* vctx, size_t** bytes) { zkq_ctx* c = (zkq_ctx*)vctx; *bytes = &c->mps_bytes; return &c->mps_ws; }
+}  // namespace zkq
 
 static zkq_status ensure(void** p, size_t* have, size_t need) {
   if (need <= *have) return ZKQ_OK;
@@ -104,7 +115,7 @@ zkq_status zkq_ctx_destroy(zkq_ctx* ctx) {
   if (!ctx) return ZKQ_OK;
   cudaSetDevice(ctx->device);
   cudaDeviceSynchronize();
-  for (void* p : {ctx->ws, ctx->meta, ctx->oa_ws, ctx->oz_ws, ctx->oz_meta}) if (p) cudaFree(p);
+  for (void* p : {ctx->ws, ctx->meta, ctx->oa_ws, ctx->oz_ws, ctx->oz_meta, ctx->mps_ws}) if (p) cudaFree(p);
   delete ctx;
   return ZKQ_OK;
 }
@@ -151,6 +162,38 @@ zkq_status eigh_internal(void* vctx, int batch, const int32_t* n, const int64_t*
                  (double*)((char*)ctx->ws + ws_need), ctx->cfg.max_sweeps};
   return launch_jacobi(jb, a_words, (int)small.size(), (int)large.size(), max_small, max_large, cluster, st);
 }
+zkq_status rqi_refine_internal(void* vctx, int batch, const int32_t* n, const int64_t* a_off, const double* A,
+                               int a_words, const double* W, const double* V, int target_words, double* W_out,
+                               double* V_out, double* err_est, int32_t* info, cudaStream_t st) {
+  zkq_ctx* ctx = (zkq_ctx*)vctx;
+  std::vector<int64_t> w_off(batch);
+  int64_t total = 0; int nmax = 0;
+  for (int b = 0; b < batch; ++b) {
+    if (n[b] < 1 || n[b] > 4096 || a_off[b] < 0) return ZKQ_EINVAL;
+    w_off[b] = total; total += n[b]; nmax = std::max(nmax, n[b]);
+  }
+  std::vector<int32_t> pair_prob(total);
+  for (int b = 0; b < batch; ++b) for (int i = 0; i < n[b]; ++i) pair_prob[w_off[b] + i] = b;
+  size_t m_n = align_up(batch * 4), m_a = align_up(batch * 8), m_w = align_up(batch * 8), m_p = align_up(total * 4), m_c = 256;
+  zkq_status s = ensure(&ctx->meta, &ctx->meta_bytes, m_n + m_a + m_w + m_p + m_c);
+  if (s != ZKQ_OK) return s;
+  int grid = (int)std::min<int64_t>(total, (int64_t)ctx->num_sms);
+  size_t slot = rqi_slot_doubles(nmax, target_words);
+  s = ensure(&ctx->ws, &ctx->ws_bytes, slot * sizeof(double) * grid);
+  if (s != ZKQ_OK) return s;
+  char* mb = (char*)ctx->meta;
+  int32_t* d_n = (int32_t*)mb; int64_t* d_a = (int64_t*)(mb + m_n); int64_t* d_w = (int64_t*)(mb + m_n + m_a);
+  int32_t* d_p = (int32_t*)(mb + m_n + m_a + m_w); int* d_c = (int*)(mb + m_n + m_a + m_w + m_p);
+  ZKQ_CUDA_TRY(cudaMemcpyAsync(d_n, n, batch * 4, cudaMemcpyHostToDevice, st));
+  ZKQ_CUDA_TRY(cudaMemcpyAsync(d_a, a_off, batch * 8, cudaMemcpyHostToDevice, st));
+  ZKQ_CUDA_TRY(cudaMemcpyAsync(d_w, w_off.data(), batch * 8, cudaMemcpyHostToDevice, st));
+  ZKQ_CUDA_TRY(cudaMemcpyAsync(d_p, pair_prob.data(), total * 4, cudaMemcpyHostToDevice, st));
+  ZKQ_CUDA_TRY(cudaMemsetAsync(d_c, 0, sizeof(int), st));
+  ZKQ_CUDA_TRY(cudaMemsetAsync(info, 0, batch * sizeof(int32_t), st));
+  RqiBatch rb{d_n, d_a, d_w, d_p, A, W, V, W_out, V_out, err_est, info, (double*)ctx->ws, (int64_t)slot, total,
+              ctx->cfg.rqi_max_iter, d_c};
+  return launch_rqi(rb, target_words, a_words, grid, st);
+}
 }  // namespace zkq
 
 extern "C" {
@@ -182,33 +225,7 @@ zkq_status zkq_rqi_refine(zkq_ctx* ctx, int batch, const int32_t* n, const int64
     return oa_refine(ctx, ob, batch, n, a_off, A, a_words, V, target_words, W_out, V_out, err_est, info,
                      ctx->cfg.oa_max_iter, method == ZKQ_OA_OZAKI ? 1 : 0, st);
   }
-  std::vector<int64_t> w_off(batch);
-  int64_t total = 0; int nmax = 0;
-  for (int b = 0; b < batch; ++b) {
-    if (n[b] < 1 || n[b] > 4096 || a_off[b] < 0) return ZKQ_EINVAL;
-    w_off[b] = total; total += n[b]; nmax = std::max(nmax, n[b]);
-  }
-  std::vector<int32_t> pair_prob(total);
-  for (int b = 0; b < batch; ++b) for (int i = 0; i < n[b]; ++i) pair_prob[w_off[b] + i] = b;
-  size_t m_n = align_up(batch * 4), m_a = align_up(batch * 8), m_w = align_up(batch * 8), m_p = align_up(total * 4), m_c = 256;
-  zkq_status s = ensure(&ctx->meta, &ctx->meta_bytes, m_n + m_a + m_w + m_p + m_c);
-  if (s != ZKQ_OK) return s;
-  int grid = (int)std::min<int64_t>(total, (int64_t)ctx->num_sms);
-  size_t slot = rqi_slot_doubles(nmax, target_words);
-  s = ensure(&ctx->ws, &ctx->ws_bytes, slot * sizeof(double) * grid);
-  if (s != ZKQ_OK) return s;
-  char* mb = (char*)ctx->meta;
-  int32_t* d_n = (int32_t*)mb; int64_t* d_a = (int64_t*)(mb + m_n); int64_t* d_w = (int64_t*)(mb + m_n + m_a);
-  int32_t* d_p = (int32_t*)(mb + m_n + m_a + m_w); int* d_c = (int*)(mb + m_n + m_a + m_w + m_p);
-  ZKQ_CUDA_TRY(cudaMemcpyAsync(d_n, n, batch * 4, cudaMemcpyHostToDevice, st));
-  ZKQ_CUDA_TRY(cudaMemcpyAsync(d_a, a_off, batch * 8, cudaMemcpyHostToDevice, st));
-  ZKQ_CUDA_TRY(cudaMemcpyAsync(d_w, w_off.data(), batch * 8, cudaMemcpyHostToDevice, st));
-  ZKQ_CUDA_TRY(cudaMemcpyAsync(d_p, pair_prob.data(), total * 4, cudaMemcpyHostToDevice, st));
-  ZKQ_CUDA_TRY(cudaMemsetAsync(d_c, 0, sizeof(int), st));
-  ZKQ_CUDA_TRY(cudaMemsetAsync(info, 0, batch * sizeof(int32_t), st));
-  RqiBatch rb{d_n, d_a, d_w, d_p, A, W, V, W_out, V_out, err_est, info, (double*)ctx->ws, (int64_t)slot, total,
-              ctx->cfg.rqi_max_iter, d_c};
-  return launch_rqi(rb, target_words, a_words, grid, st);
+  return rqi_refine_internal(ctx, batch, n, a_off, A, a_words, W, V, target_words, W_out, V_out, err_est, info, st);
 }
 
 zkq_status zkq_mw_gemm(zkq_ctx* ctx, int count, const int32_t* m, const int32_t* n, const int32_t* k,
