@@ -171,17 +171,19 @@ zkq_status zkq_mps_apply2q(zkq_ctx* ctx, zkq_mps* mps, int site, const double* G
 /*
  * zkq_mw_gemm: batched multi-word complex products C_i = op(A_i) B_i, the dense products of the refinement
  * step (A X, X^H X, X^H (A X), X E) that recover the precision of the FP64 eigenpairs (Section 2, ZKCM_CUS
- * paragraph).  Method 1 splits both operands into exact 8-bit (7-bit when k > 512) integer digits scaled
- * per row / column by powers of two, multiplies digit matrices on the tensor cores with exact fp32
- * accumulation and recombines the integer results exactly (Ozaki, Ogita, Oishi, Rump 2012); method 0
- * computes the same products directly in multi-word arithmetic on the FP64 pipe.
+ * paragraph).  Rows of op(A) and columns of B are scaled by powers of two and truncated to integers.
+ * Method 1 (Chinese-remainder form, Ozaki-Uchino-Imamura): residues modulo ~60 pairwise coprime moduli
+ * <= 256, one exact fp16 tensor-core product per modulus (fp32 accumulation exact below 2^24), exact
+ * reconstruction by the CRT.  Method 2 (digit form, Ozaki-Ogita-Oishi-Rump 2012): 8-bit (7-bit when
+ * k > 512) balanced digits, one exact product per kept digit pair, exact recombination.  Method 0 computes
+ * the same products directly in multi-word arithmetic on the FP64 pipe.
  *   count (>= 0)   number of products; m, n, k, opA (host, int32[count])
  *   opA[i]         0: A_i is m x k (column-major, ld m);  1: A_i is stored k x m (ld k), op(A) = A^H
  *   A, B, C        device arrays; product i uses element offsets a_off[i], b_off[i], c_off[i] (host int64)
  *   wa, wb, wc     words per real of A, B, C (1, 2 or 4); B_i is k x n (ld k), C_i is m x n (ld m)
  *   p_bits         requested accuracy: |C - op(A) B| <= k 2^-p_bits 2^(e_row + f_col) per element, where
  *                  2^e_row <= 8 max|row of op(A)| and 2^f_col <= 8 max|column of B| are the power-of-two
- *                  scales of the split
+ *                  scales of the split (methods 1 and 2)
  *                  (method 1; method 0 rounds in wc-word arithmetic); 1 <= p_bits <= 252
  * Constraints: k <= 2048.  C must not overlap A or B.
  * Errors: ZKQ_EINVAL, ZKQ_ENOMEM, ZKQ_ECUDA.

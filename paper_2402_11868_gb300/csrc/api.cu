@@ -234,7 +234,7 @@ zkq_status zkq_mw_gemm(zkq_ctx* ctx, int count, const int32_t* m, const int32_t*
                        void* stream) {
   if (!ctx || count < 0 || (count > 0 && (!m || !n || !k || !opA || !A || !a_off || !B || !b_off || !C || !c_off)))
     return ZKQ_EINVAL;
-  if (method != 0 && method != 1) return ZKQ_EINVAL;
+  if (method != 0 && method != 1 && method != 2) return ZKQ_EINVAL;
   if (p_bits < 1 || p_bits > 53 * 4 + 40) return ZKQ_EINVAL;
   if (count == 0) return ZKQ_OK;
   ZKQ_CUDA_TRY(cudaSetDevice(ctx->device));

@@ -1,0 +1,31 @@
+// Chinese-remainder form of the split product (Ozaki scheme II: Ozaki, Uchino, Imamura 2024/25).
+// Rows of op(A) and columns of B are scaled by powers of two and truncated to q-bit integers A', B';
+// the exact integer product C' = A' B' is formed from r products of residue matrices modulo pairwise
+// coprime m_i <= 256 (entries |a| <= m_i/2 are exact in fp16, their K-sums are exact in fp32), and C' is
+// reconstructed by the CRT:  C' = (sum_i c_i w_i mod M) taken symmetric,  w_i = (M/m_i) ((M/m_i)^-1 mod m_i).
+// The number of tensor-core products grows linearly with the precision (r ~ (2q + log2 K)/8) instead of
+// quadratically as for digit pairs.
+#pragma once
+#include <cstdint>
+
+namespace zkq {
+
+constexpr int CRT_MAXR = 96;     // moduli
+constexpr int CRT_L = 9;         // 64-bit limbs of M and of the reconstruction sums (576 bits)
+
+struct CrtConst {
+  int r;                         // number of moduli
+  int q;                         // bits of the scaled integers A', B' (|A'| < 2^(q-2))
+  int m[CRT_MAXR];
+  uint8_t pw16[CRT_MAXR][20];    // 2^(16 j) mod m_i, j = 0..19
+  uint64_t w[CRT_MAXR][CRT_L];   // CRT weights
+  uint64_t M[CRT_L];             // product of the moduli
+  uint64_t Mhalf[CRT_L];         // floor(M / 2)
+  double Md;                     // M as a double (upper bits), for quotient estimates
+  int Mexp;                      // M = Md * 2^Mexp with Md in [1, 2)
+};
+
+// host-side construction (moduli, weights); max_kprime decides the modulus bound
+bool crt_build(int max_kprime, int p_out_bits, CrtConst* out);
+
+}  // namespace zkq

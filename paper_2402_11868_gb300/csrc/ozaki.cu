@@ -15,6 +15,7 @@
 // rounded once into the output's double words.  Complex products use the real embedding
 //   Re C = [Re op(A) | Im op(A)] [Re B ; -Im B],  Im C = [Re op(A) | Im op(A)] [Im B ; Re B]   (K' = 2k).
 #include "ozaki.cuh"
+#include "crt.cuh"
 #include "mw.cuh"
 #include "prof.cuh"
 #include <vector>
@@ -381,6 +382,197 @@ __global__ void oz_combine_kernel(const OzProd* __restrict__ P, int b, int S) {
 }
 
 // ------------------------------------------------------------------------------------------------
+// CRT form: residue planes and reconstruction
+template <int L> struct BigL { uint64_t l[L]; };
+
+template <int L> __device__ __forceinline__ void bl_zero(BigL<L>& x) {
+#pragma unroll
+  for (int i = 0; i < L; ++i) x.l[i] = 0;
+}
+// x += c * w (c small, w nonnegative L-limb constant)
+template <int L> __device__ __forceinline__ void bl_add_mul(BigL<L>& x, uint64_t c, const uint64_t* w, int wl) {
+  uint64_t carry = 0;
+#pragma unroll
+  for (int i = 0; i < L; ++i) {
+    uint64_t wi = i < wl ? w[i] : 0;
+    uint64_t lo = wi * c, hi = __umul64hi(wi, c);
+    uint64_t t = x.l[i] + lo; uint64_t c1 = t < x.l[i];
+    uint64_t t2 = t + carry; uint64_t c2 = t2 < t;
+    x.l[i] = t2; carry = hi + c1 + c2;
+  }
+}
+// x -= c * w
+template <int L> __device__ __forceinline__ void bl_sub_mul(BigL<L>& x, uint64_t c, const uint64_t* w, int wl) {
+  uint64_t borrow = 0;
+#pragma unroll
+  for (int i = 0; i < L; ++i) {
+    uint64_t wi = i < wl ? w[i] : 0;
+    uint64_t lo = wi * c, hi = __umul64hi(wi, c);
+    uint64_t t = x.l[i] - lo; uint64_t b1 = x.l[i] < lo;
+    uint64_t t2 = t - borrow; uint64_t b2 = t < borrow;
+    x.l[i] = t2; borrow = hi + b1 + b2;
+  }
+}
+template <int L> __device__ __forceinline__ bool bl_neg(const BigL<L>& x) { return (int64_t)x.l[L - 1] < 0; }
+// compare nonnegative x with constant w (wl limbs): -1, 0, 1
+template <int L> __device__ __forceinline__ int bl_cmp(const BigL<L>& x, const uint64_t* w, int wl) {
+  for (int i = L - 1; i >= 0; --i) {
+    uint64_t wi = i < wl ? w[i] : 0;
+    if (x.l[i] != wi) return x.l[i] > wi ? 1 : -1;
+  }
+  return 0;
+}
+template <int L> __device__ __forceinline__ void bl_negate(BigL<L>& x) {
+  uint64_t c = 1;
+#pragma unroll
+  for (int i = 0; i < L; ++i) { uint64_t v = ~x.l[i] + c; c = (c && v == 0) ? 1 : 0; x.l[i] = v; }
+}
+template <int L> __device__ __forceinline__ int bl_top(const BigL<L>& x) {
+  for (int i = L - 1; i >= 0; --i) if (x.l[i]) return 64 * i + 63 - __clzll(x.l[i]);
+  return -1;
+}
+template <int L> __device__ __forceinline__ int bl_bit(const BigL<L>& x, int i) { return i < 0 ? 0 : (int)((x.l[i >> 6] >> (i & 63)) & 1); }
+// x += sgn * m * 2^sh  (m < 2^63)
+template <int L> __device__ __forceinline__ void bl_add_shifted(BigL<L>& x, uint64_t m, int sh, bool neg) {
+  uint64_t w[L];
+#pragma unroll
+  for (int i = 0; i < L; ++i) w[i] = 0;
+  int li = sh >> 6, bs = sh & 63;
+  if (li < L) w[li] = m << bs;
+  if (bs && li + 1 < L) w[li + 1] = m >> (64 - bs);
+  if (!neg) bl_add_mul<L>(x, 1, w, L); else bl_sub_mul<L>(x, 1, w, L);
+}
+// nearest double of the signed integer R times 2^scale; R -= that value
+template <int L> __device__ double bl_round_off(BigL<L>& R, int scale) {
+  bool ng = bl_neg(R);
+  BigL<L> Mg = R; if (ng) bl_negate(Mg);
+  int tb = bl_top(Mg);
+  if (tb < 0) return 0.0;
+  int lo = tb - 52;
+  uint64_t m;
+  if (lo >= 0) {
+    int li = lo >> 6, bs = lo & 63;
+    m = Mg.l[li] >> bs;
+    if (bs && li + 1 < L) m |= Mg.l[li + 1] << (64 - bs);
+    m &= (1ULL << 53) - 1;
+    int rnd = bl_bit(Mg, lo - 1);
+    bool sticky = false;
+    for (int i = 0; i < ((lo - 1) >> 6) && !sticky; ++i) sticky = Mg.l[i] != 0;
+    if (!sticky && lo - 1 > 0) { int l2 = (lo - 1) >> 6, b2 = (lo - 1) & 63; sticky = (Mg.l[l2] & ((1ULL << b2) - 1)) != 0; }
+    if (rnd && (sticky || (m & 1))) m += 1;
+  } else { m = Mg.l[0]; lo = 0; }
+  bl_add_shifted<L>(R, m, lo, !ng);
+  double v = ldexp((double)m, lo + scale);
+  return ng ? -v : v;
+}
+
+// residues of q-bit scaled integers modulo every m_i, symmetric, written as fp16 planes [r][rows][kp]
+template <int K>
+__device__ __forceinline__ void crt_residues(const double* w, int fix, bool negate, const CrtConst* __restrict__ cc,
+                                             __half* out, size_t plane, size_t e) {
+  Big X; to_fixed<K>(w, fix, negate, X);
+  bool ng = big_neg(X);
+  if (ng) big_negate(X);
+  uint32_t d[20];
+#pragma unroll
+  for (int j = 0; j < 20; ++j) d[j] = (uint32_t)((X.l[j >> 2] >> (16 * (j & 3))) & 0xFFFF);
+  const int r = cc->r;
+  for (int i = 0; i < r; ++i) {
+    const int m = cc->m[i];
+    uint32_t s = 0;
+#pragma unroll
+    for (int j = 0; j < 20; ++j) s += d[j] * (uint32_t)cc->pw16[i][j];
+    int res = (int)(s % (uint32_t)m);
+    if (ng && res) res = m - res;
+    if (res > m / 2) res -= m;
+    out[(size_t)i * plane + e] = __int2half_rn(res);
+  }
+}
+
+template <int WA>
+__global__ void crt_slice_A_kernel(const OzProd* __restrict__ P, const CrtConst* __restrict__ cc) {
+  const OzProd p = P[blockIdx.y];
+  size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  size_t tot = (size_t)p.mp * p.kp;
+  if (e >= tot) return;
+  int i = (int)(e / p.kp), lp = (int)(e % p.kp);
+  const size_t plane = tot;
+  if (i >= p.m || lp >= 2 * p.k) {
+    for (int t = 0; t < cc->r; ++t) p.Ahat[t * plane + e] = __float2half_rn(0.0f);
+    return;
+  }
+  bool im = lp >= p.k;
+  int l = im ? lp - p.k : lp;
+  const double* q = p.opA ? p.A + ((size_t)l + (size_t)i * p.k) * 2 * WA : p.A + ((size_t)i + (size_t)l * p.m) * 2 * WA;
+  crt_residues<WA>(q + (im ? WA : 0), cc->q - p.eA[i], im && p.opA, cc, p.Ahat, plane, e);
+}
+
+template <int WB>
+__global__ void crt_slice_B_kernel(const OzProd* __restrict__ P, const CrtConst* __restrict__ cc) {
+  const OzProd p = P[blockIdx.y];
+  size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  size_t tot = (size_t)p.np2 * p.kp;
+  if (e >= tot) return;
+  int jp = (int)(e / p.kp), lp = (int)(e % p.kp);
+  const size_t plane = tot;
+  if (jp >= 2 * p.n || lp >= 2 * p.k) {
+    for (int t = 0; t < cc->r; ++t) p.Bhat[t * plane + e] = __float2half_rn(0.0f);
+    return;
+  }
+  bool imcol = jp >= p.n;
+  int j = imcol ? jp - p.n : jp;
+  bool lower = lp >= p.k;
+  int l = lower ? lp - p.k : lp;
+  bool use_im = imcol ? !lower : lower;
+  bool negate = !imcol && lower;
+  const double* q = p.B + ((size_t)l + (size_t)j * p.k) * 2 * WB + (use_im ? WB : 0);
+  crt_residues<WB>(q, cc->q - p.eB[j], negate, cc, p.Bhat, plane, e);
+}
+
+// C' = symmetric (sum_i c_i w_i mod M), then value = C' 2^(e_i + f_j - 2q)
+template <int WC>
+__device__ __forceinline__ mw<WC> crt_value(const OzProd& p, const CrtConst* __restrict__ cc, int i, int col, int es) {
+  constexpr int L = CRT_L + 1;
+  BigL<L> S; bl_zero(S);
+  const int r = cc->r;
+  for (int t = 0; t < r; ++t) {
+    int32_t v = p.D[(size_t)t * p.mp * p.np2 + (size_t)i * p.np2 + col];
+    int m = cc->m[t];
+    int c = v % m; if (c < 0) c += m;
+    if (c) bl_add_mul<L>(S, (uint64_t)c, cc->w[t], CRT_L);
+  }
+  // quotient estimate from the top bits, then exact correction into [0, M)
+  int tb = bl_top(S);
+  if (tb >= 0) {
+    int li = tb >> 6;
+    double sd = (double)S.l[li] + (li > 0 ? ldexp((double)S.l[li - 1], -64) : 0.0);
+    double qd = ldexp(sd, 64 * li) / ldexp(cc->Md, cc->Mexp);
+    uint64_t qq = qd > 1.0 ? (uint64_t)qd : 0;
+    if (qq) bl_sub_mul<L>(S, qq, cc->M, CRT_L);
+    for (int it = 0; it < 3 && bl_neg(S); ++it) bl_add_mul<L>(S, 1, cc->M, CRT_L);
+    for (int it = 0; it < 3 && bl_cmp<L>(S, cc->M, CRT_L) >= 0; ++it) bl_sub_mul<L>(S, 1, cc->M, CRT_L);
+    if (bl_cmp<L>(S, cc->Mhalf, CRT_L) > 0) bl_sub_mul<L>(S, 1, cc->M, CRT_L);
+  }
+  mw<WC> out;
+  for (int k = 0; k < WC; ++k) out.x[k] = bl_round_off<L>(S, es - 2 * cc->q);
+  return out;
+}
+
+template <int WC>
+__global__ void crt_combine_kernel(const OzProd* __restrict__ P, const CrtConst* __restrict__ cc) {
+  const OzProd p = P[blockIdx.y];
+  int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= p.m * p.n) return;
+  int i = e % p.m, j = e / p.m;
+  int es = p.eA[i] + p.eB[j];
+  cmw<WC> v = c_make(crt_value<WC>(p, cc, i, j, es), crt_value<WC>(p, cc, i, j + p.n, es));
+  if (p.sgn < 0) v = c_make(mw_neg(v.re), mw_neg(v.im));
+  if (p.base) v = c_add(v, c_load<WC, WC>(p.base, (size_t)e));
+  if (p.base_identity && i == j) v.re = mw_add_d(v.re, 1.0);
+  c_store(p.C, (size_t)e, v);
+}
+
+// ------------------------------------------------------------------------------------------------
 // plain multi-word GEMM on the FP64 pipe (one output element per thread)
 template <int WA, int WB, int WC>
 __global__ void mw_gemm_plain_kernel(const OzProd* __restrict__ P) {
@@ -451,8 +643,19 @@ zkq_status mw_gemm_batched(const MwProd* prods, int count, int wa, int wb, int w
     ZKQ_CUDA_TRY(cudaGetLastError());
     return ZKQ_OK;
   }
-  OzPlan plan = ozaki_plan(max_kp, wa, wb, p_out_bits);
-  std::vector<OzPair> pairs = make_pairs(plan);
+  // method 1: CRT form (default); method 2: digit-pair form
+  const bool crt = (method == 1);
+  CrtConst cc;
+  OzPlan plan;
+  std::vector<OzPair> pairs;
+  if (crt) {
+    if (!crt_build(max_kp, p_out_bits, &cc)) return ZKQ_EINVAL;
+    plan.b = 0; plan.sA = plan.sB = cc.r; plan.S = cc.r - 1; plan.G = 1;
+    for (int i = 0; i < cc.r; ++i) pairs.push_back({(int16_t)(i + 1), (int16_t)(i + 1), (int16_t)i, (int16_t)3});
+  } else {
+    plan = ozaki_plan(max_kp, wa, wb, p_out_bits);
+    pairs = make_pairs(plan);
+  }
   plan.npairs = (int)pairs.size();
   // workspace layout
   size_t off = 0;
@@ -462,7 +665,7 @@ zkq_status mw_gemm_batched(const MwProd* prods, int count, int wa, int wb, int w
     OzProd& o = dp[i];
     oA[i] = off; off += al((size_t)plan.sA * o.mp * o.kp * sizeof(__half));
     oB[i] = off; off += al((size_t)plan.sB * o.np2 * o.kp * sizeof(__half));
-    oD[i] = off; off += al((size_t)(plan.S + 1) * o.mp * o.np2 * sizeof(int32_t));
+    oD[i] = off; off += al((size_t)(crt ? cc.r : plan.S + 1) * o.mp * o.np2 * sizeof(int32_t));
     oe[i] = off; off += al((size_t)(o.m + o.n) * sizeof(int32_t));
     max_mkp = std::max(max_mkp, (size_t)o.mp * o.kp);
     max_nkp = std::max(max_nkp, (size_t)o.np2 * o.kp);
@@ -481,10 +684,13 @@ zkq_status mw_gemm_batched(const MwProd* prods, int count, int wa, int wb, int w
   // biggest problems first (their tiles run longest: K' is larger)
   std::stable_sort(tiles.begin(), tiles.end(), [&](const OzTile& a, const OzTile& c) { return dp[a.prod].kp > dp[c.prod].kp; });
   size_t m_p = al(sizeof(OzProd) * count), m_t = al(sizeof(OzTile) * tiles.size()), m_q = al(sizeof(OzPair) * pairs.size());
-  s = grow(meta, meta_bytes, m_p + m_t + m_q);
+  size_t m_c = crt ? al(sizeof(CrtConst)) : 0;
+  s = grow(meta, meta_bytes, m_p + m_t + m_q + m_c);
   if (s != ZKQ_OK) return s;
   char* mb = (char*)*meta;
   OzProd* d_p = (OzProd*)mb; OzTile* d_t = (OzTile*)(mb + m_p); OzPair* d_q = (OzPair*)(mb + m_p + m_t);
+  CrtConst* d_c = (CrtConst*)(mb + m_p + m_t + m_q);
+  if (crt) ZKQ_CUDA_TRY(cudaMemcpyAsync(d_c, &cc, sizeof(CrtConst), cudaMemcpyHostToDevice, st));
   ZKQ_CUDA_TRY(cudaMemcpyAsync(d_p, dp.data(), sizeof(OzProd) * count, cudaMemcpyHostToDevice, st));
   ZKQ_CUDA_TRY(cudaMemcpyAsync(d_t, tiles.data(), sizeof(OzTile) * tiles.size(), cudaMemcpyHostToDevice, st));
   ZKQ_CUDA_TRY(cudaMemcpyAsync(d_q, pairs.data(), sizeof(OzPair) * pairs.size(), cudaMemcpyHostToDevice, st));
@@ -501,8 +707,13 @@ zkq_status mw_gemm_batched(const MwProd* prods, int count, int wa, int wb, int w
   {
     dim3 gA((unsigned)((max_mkp + 255) / 256), count), gB((unsigned)((max_nkp + 255) / 256), count);
     ProfScope ps(PC_OZ_SLICE, st);
-    ZKQ_DISPATCH_W(wa, oz_slice_A_kernel, <<<gA, 256, 0, st>>>(d_p, plan.b, plan.sA));
-    ZKQ_DISPATCH_W(wb, oz_slice_B_kernel, <<<gB, 256, 0, st>>>(d_p, plan.b, plan.sB));
+    if (crt) {
+      ZKQ_DISPATCH_W(wa, crt_slice_A_kernel, <<<gA, 256, 0, st>>>(d_p, d_c));
+      ZKQ_DISPATCH_W(wb, crt_slice_B_kernel, <<<gB, 256, 0, st>>>(d_p, d_c));
+    } else {
+      ZKQ_DISPATCH_W(wa, oz_slice_A_kernel, <<<gA, 256, 0, st>>>(d_p, plan.b, plan.sA));
+      ZKQ_DISPATCH_W(wb, oz_slice_B_kernel, <<<gB, 256, 0, st>>>(d_p, plan.b, plan.sB));
+    }
     ZKQ_CUDA_TRY(cudaGetLastError());
   }
   {
@@ -517,9 +728,15 @@ zkq_status mw_gemm_batched(const MwProd* prods, int count, int wa, int wb, int w
   {
     dim3 g((max_mn + 127) / 128, count);
     ProfScope ps(PC_OZ_COMBINE, st);
-    if (wc == 1) oz_combine_kernel<1><<<g, 128, 0, st>>>(d_p, plan.b, plan.S);
-    else if (wc == 2) oz_combine_kernel<2><<<g, 128, 0, st>>>(d_p, plan.b, plan.S);
-    else oz_combine_kernel<4><<<g, 128, 0, st>>>(d_p, plan.b, plan.S);
+    if (crt) {
+      if (wc == 1) crt_combine_kernel<1><<<g, 128, 0, st>>>(d_p, d_c);
+      else if (wc == 2) crt_combine_kernel<2><<<g, 128, 0, st>>>(d_p, d_c);
+      else crt_combine_kernel<4><<<g, 128, 0, st>>>(d_p, d_c);
+    } else {
+      if (wc == 1) oz_combine_kernel<1><<<g, 128, 0, st>>>(d_p, plan.b, plan.S);
+      else if (wc == 2) oz_combine_kernel<2><<<g, 128, 0, st>>>(d_p, plan.b, plan.S);
+      else oz_combine_kernel<4><<<g, 128, 0, st>>>(d_p, plan.b, plan.S);
+    }
     ZKQ_CUDA_TRY(cudaGetLastError());
   }
   return ZKQ_OK;

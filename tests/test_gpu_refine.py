@@ -37,7 +37,7 @@ def rand_mw(rng, count, w, spread=6):
 CASES = [(1, 1, 1, 0), (3, 5, 7, 1), (17, 33, 16, 0), (130, 40, 70, 1), (64, 48, 512, 0), (40, 3, 600, 1)]
 
 
-@pytest.mark.parametrize("method", [1, 0])
+@pytest.mark.parametrize("method", [1, 2, 0])
 @pytest.mark.parametrize("wa,wb,wc", [(4, 4, 4), (4, 2, 4), (2, 1, 2), (1, 4, 4)])
 def test_split_products_match_exact(ctx, method, wa, wb, wc):
     import torch
@@ -67,7 +67,7 @@ def test_split_products_match_exact(ctx, method, wa, wb, wc):
         for jj in range(n):
             for ii in range(m):
                 e = ii + jj * m
-                if method == 1:
+                if method in (1, 2):
                     bound = k * 2.0 ** -p_bits * (8 * rowmax[ii]) * (8 * colmax[jj]) * 2
                 else:
                     bound = k * 2.0 ** -(53 * wc - 4) * rowmax[ii] * colmax[jj] * 4
