@@ -3,8 +3,11 @@
 // the exact integer product C' = A' B' is formed from r products of residue matrices modulo pairwise
 // coprime m_i <= 256 (entries |a| <= m_i/2 are exact in fp16, their K-sums are exact in fp32), and C' is
 // reconstructed by the CRT:  C' = (sum_i c_i w_i mod M) taken symmetric,  w_i = (M/m_i) ((M/m_i)^-1 mod m_i).
-// The number of tensor-core products grows linearly with the precision (r ~ (2q + log2 K)/8) instead of
-// quadratically as for digit pairs.
+// Pairwise coprime moduli <= 256 multiply to at most lcm(1..256) ~ 2^369, less than a quad-double product
+// needs, so each scaled integer is split in halves, A' = A_h 2^s + A_l, and the three products
+// A_h B_h, A_h B_l, A_l B_h (each below K 2^(q-2)) are reconstructed by the CRT; A_l B_l is below the
+// requested accuracy and dropped.  3 r ~ 93 exact products per quad-double product instead of ~500 digit
+// pairs.
 #pragma once
 #include <cstdint>
 
@@ -16,6 +19,7 @@ constexpr int CRT_L = 9;         // 64-bit limbs of M and of the reconstruction 
 struct CrtConst {
   int r;                         // number of moduli
   int q;                         // bits of the scaled integers A', B' (|A'| < 2^(q-2))
+  int s;                         // split: A' = A_h 2^s + A_l, 0 <= A_l < 2^s
   int m[CRT_MAXR];
   uint8_t pw16[CRT_MAXR][20];    // 2^(16 j) mod m_i, j = 0..19
   uint64_t w[CRT_MAXR][CRT_L];   // CRT weights

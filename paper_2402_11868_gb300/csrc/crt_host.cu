@@ -3,6 +3,7 @@
 #include <vector>
 #include <cmath>
 #include <cstring>
+#include <algorithm>
 
 namespace zkq {
 
@@ -44,10 +45,11 @@ bool crt_build(int max_kprime, int p_out_bits, CrtConst* out) {
   int lg = 0; while ((1 << lg) < max_kprime) ++lg;
   // modulus bound: K' (m/2)^2 <= 2^24 keeps every residue product sum exact in fp32
   int mb = 256;
-  while ((long long)max_kprime * (mb / 2) * (mb / 2) > (1LL << 24)) mb /= 2;
-  if (mb < 16) return false;
+  if ((long long)max_kprime * (mb / 2) * (mb / 2) > (1LL << 24)) return false;   // K' > 1024: digit form
   const int q = p_out_bits + lg + 4;           // |A'|,|B'| < 2^(q-2); truncation error 2^-q of the scale
-  const double need = 2.0 * (q - 2) + lg + 2;  // log2 M > log2(2 K' 2^(2(q-2)))
+  const int s = (q - 2 + 1) / 2;               // halves: |A_h| <= 2^(q-2-s), 0 <= A_l < 2^s
+  const int hb = std::max(q - 2 - s, s);       // each half below 2^hb
+  const double need = 2.0 * hb + lg + 2;       // log2 M > log2(2 K' 2^(2 hb))
   std::vector<int> ms;
   double bits = 0.0;
   for (int c = mb; c >= 3 && bits < need; --c) {
@@ -60,6 +62,7 @@ bool crt_build(int max_kprime, int p_out_bits, CrtConst* out) {
   if (bits < need || (int)ms.size() > CRT_MAXR || bits + 16 > 64.0 * CRT_L - 2) return false;
   out->r = (int)ms.size();
   out->q = q;
+  out->s = s;
   Limbs M{1};
   for (int m : ms) mul_small(M, (uint32_t)m);
   to64(M, out->M);

@@ -467,10 +467,9 @@ template <int L> __device__ double bl_round_off(BigL<L>& R, int scale) {
 }
 
 // residues of q-bit scaled integers modulo every m_i, symmetric, written as fp16 planes [r][rows][kp]
-template <int K>
-__device__ __forceinline__ void crt_residues(const double* w, int fix, bool negate, const CrtConst* __restrict__ cc,
-                                             __half* out, size_t plane, size_t e) {
-  Big X; to_fixed<K>(w, fix, negate, X);
+// symmetric residues of the signed integer X modulo every m_i into planes [plane0 + i]
+__device__ __forceinline__ void crt_emit(Big X, const CrtConst* __restrict__ cc, __half* out, size_t plane, size_t e,
+                                         int plane0) {
   bool ng = big_neg(X);
   if (ng) big_negate(X);
   uint32_t d[20];
@@ -485,8 +484,33 @@ __device__ __forceinline__ void crt_residues(const double* w, int fix, bool nega
     int res = (int)(s % (uint32_t)m);
     if (ng && res) res = m - res;
     if (res > m / 2) res -= m;
-    out[(size_t)i * plane + e] = __int2half_rn(res);
+    out[(size_t)(plane0 + i) * plane + e] = __int2half_rn(res);
   }
+}
+// q-bit scaled integer X = A_h 2^s + A_l: residues of A_h into planes [0, r), of A_l into [r, 2r)
+template <int K>
+__device__ __forceinline__ void crt_residues(const double* w, int fix, bool negate, const CrtConst* __restrict__ cc,
+                                             __half* out, size_t plane, size_t e) {
+  Big X; to_fixed<K>(w, fix, negate, X);
+  const int s = cc->s;
+  Big lo = X;                                  // low s bits (two's complement residue, nonnegative)
+  for (int i = 0; i < 5; ++i) {
+    int b0 = 64 * i;
+    if (b0 >= s) lo.l[i] = 0;
+    else if (b0 + 64 > s) lo.l[i] &= (s - b0 == 64) ? ~0ULL : ((1ULL << (s - b0)) - 1);
+  }
+  Big hi;                                      // floor(X / 2^s): arithmetic shift
+  {
+    int ls = s >> 6, bs = s & 63;
+    for (int i = 0; i < 5; ++i) {
+      int src = i + ls;
+      uint64_t a = src < 5 ? X.l[src] : (big_neg(X) ? ~0ULL : 0ULL);
+      uint64_t b = src + 1 < 5 ? X.l[src + 1] : (big_neg(X) ? ~0ULL : 0ULL);
+      hi.l[i] = bs ? ((a >> bs) | (b << (64 - bs))) : a;
+    }
+  }
+  crt_emit(hi, cc, out, plane, e, 0);
+  crt_emit(lo, cc, out, plane, e, cc->r);
 }
 
 template <int WA>
@@ -498,7 +522,7 @@ __global__ void crt_slice_A_kernel(const OzProd* __restrict__ P, const CrtConst*
   int i = (int)(e / p.kp), lp = (int)(e % p.kp);
   const size_t plane = tot;
   if (i >= p.m || lp >= 2 * p.k) {
-    for (int t = 0; t < cc->r; ++t) p.Ahat[t * plane + e] = __float2half_rn(0.0f);
+    for (int t = 0; t < 2 * cc->r; ++t) p.Ahat[t * plane + e] = __float2half_rn(0.0f);
     return;
   }
   bool im = lp >= p.k;
@@ -516,7 +540,7 @@ __global__ void crt_slice_B_kernel(const OzProd* __restrict__ P, const CrtConst*
   int jp = (int)(e / p.kp), lp = (int)(e % p.kp);
   const size_t plane = tot;
   if (jp >= 2 * p.n || lp >= 2 * p.k) {
-    for (int t = 0; t < cc->r; ++t) p.Bhat[t * plane + e] = __float2half_rn(0.0f);
+    for (int t = 0; t < 2 * cc->r; ++t) p.Bhat[t * plane + e] = __float2half_rn(0.0f);
     return;
   }
   bool imcol = jp >= p.n;
@@ -529,32 +553,66 @@ __global__ void crt_slice_B_kernel(const OzProd* __restrict__ P, const CrtConst*
   crt_residues<WB>(q, cc->q - p.eB[j], negate, cc, p.Bhat, plane, e);
 }
 
-// C' = symmetric (sum_i c_i w_i mod M), then value = C' 2^(e_i + f_j - 2q)
-template <int WC>
-__device__ __forceinline__ mw<WC> crt_value(const OzProd& p, const CrtConst* __restrict__ cc, int i, int col, int es) {
-  constexpr int L = CRT_L + 1;
-  BigL<L> S; bl_zero(S);
+// symmetric (sum_i c_i w_i mod M) of the residues stored at levels [lev0, lev0 + r)
+template <int L>
+__device__ __forceinline__ void crt_reconstruct(const OzProd& p, const CrtConst* __restrict__ cc, int i, int col, int lev0,
+                                                BigL<L>& S) {
+  bl_zero(S);
   const int r = cc->r;
   for (int t = 0; t < r; ++t) {
-    int32_t v = p.D[(size_t)t * p.mp * p.np2 + (size_t)i * p.np2 + col];
+    int32_t v = p.D[(size_t)(lev0 + t) * p.mp * p.np2 + (size_t)i * p.np2 + col];
     int m = cc->m[t];
     int c = v % m; if (c < 0) c += m;
     if (c) bl_add_mul<L>(S, (uint64_t)c, cc->w[t], CRT_L);
   }
-  // quotient estimate from the top bits, then exact correction into [0, M)
   int tb = bl_top(S);
-  if (tb >= 0) {
-    int li = tb >> 6;
-    double sd = (double)S.l[li] + (li > 0 ? ldexp((double)S.l[li - 1], -64) : 0.0);
-    double qd = ldexp(sd, 64 * li) / ldexp(cc->Md, cc->Mexp);
-    uint64_t qq = qd > 1.0 ? (uint64_t)qd : 0;
-    if (qq) bl_sub_mul<L>(S, qq, cc->M, CRT_L);
-    for (int it = 0; it < 3 && bl_neg(S); ++it) bl_add_mul<L>(S, 1, cc->M, CRT_L);
-    for (int it = 0; it < 3 && bl_cmp<L>(S, cc->M, CRT_L) >= 0; ++it) bl_sub_mul<L>(S, 1, cc->M, CRT_L);
-    if (bl_cmp<L>(S, cc->Mhalf, CRT_L) > 0) bl_sub_mul<L>(S, 1, cc->M, CRT_L);
+  if (tb < 0) return;
+  int li = tb >> 6;
+  double sd = (double)S.l[li] + (li > 0 ? ldexp((double)S.l[li - 1], -64) : 0.0);
+  double qd = ldexp(sd, 64 * li) / ldexp(cc->Md, cc->Mexp);      // quotient estimate (< 2^14)
+  uint64_t qq = qd > 1.0 ? (uint64_t)qd : 0;
+  if (qq) bl_sub_mul<L>(S, qq, cc->M, CRT_L);
+  for (int it = 0; it < 3 && bl_neg(S); ++it) bl_add_mul<L>(S, 1, cc->M, CRT_L);
+  for (int it = 0; it < 3 && bl_cmp<L>(S, cc->M, CRT_L) >= 0; ++it) bl_sub_mul<L>(S, 1, cc->M, CRT_L);
+  if (bl_cmp<L>(S, cc->Mhalf, CRT_L) > 0) bl_sub_mul<L>(S, 1, cc->M, CRT_L);
+}
+
+// C' = C_hh 2^(2s) + (C_hl + C_lh) 2^s, value = C' 2^(e_i + f_j - 2q)
+template <int WC>
+__device__ __forceinline__ mw<WC> crt_value(const OzProd& p, const CrtConst* __restrict__ cc, int i, int col, int es) {
+  constexpr int L = CRT_L + 1;
+  const int r = cc->r, s = cc->s;
+  BigL<L> T, U;
+  crt_reconstruct<L>(p, cc, i, col, 0, T);          // A_h B_h
+  // shift T left by 2s (T stays far below 2^(64 L - 1))
+  {
+    BigL<L> Z; bl_zero(Z);
+    int sh = 2 * s, ls = sh >> 6, bs = sh & 63;
+    for (int k = L - 1; k >= 0; --k) {
+      int src = k - ls;
+      uint64_t a = src >= 0 ? T.l[src] : 0, b = (src - 1 >= 0) ? T.l[src - 1] : 0;
+      if (src >= 0) Z.l[k] = bs ? ((a << bs) | (b >> (64 - bs))) : a;
+      else Z.l[k] = 0;
+    }
+    T = Z;                                          // a left shift keeps the two's complement sign
   }
+  BigL<L> H1, H2;
+  crt_reconstruct<L>(p, cc, i, col, r, H1);         // A_h B_l
+  crt_reconstruct<L>(p, cc, i, col, 2 * r, H2);     // A_l B_h
+  // U = (H1 + H2) 2^s
+  {
+    uint64_t c = 0;
+    for (int k = 0; k < L; ++k) { uint64_t a = H1.l[k], t = a + H2.l[k]; uint64_t c1 = t < a; uint64_t t2 = t + c; c = c1 | (t2 < t); H1.l[k] = t2; }
+    int ls = s >> 6, bs = s & 63;
+    for (int k = L - 1; k >= 0; --k) {
+      int src = k - ls;
+      uint64_t a = src >= 0 ? H1.l[src] : 0, b = (src - 1 >= 0) ? H1.l[src - 1] : 0;
+      U.l[k] = src >= 0 ? (bs ? ((a << bs) | (b >> (64 - bs))) : a) : 0;
+    }
+  }
+  bl_add_mul<L>(T, 1, U.l, L);
   mw<WC> out;
-  for (int k = 0; k < WC; ++k) out.x[k] = bl_round_off<L>(S, es - 2 * cc->q);
+  for (int k = 0; k < WC; ++k) out.x[k] = bl_round_off<L>(T, es - 2 * cc->q);
   return out;
 }
 
@@ -644,14 +702,18 @@ zkq_status mw_gemm_batched(const MwProd* prods, int count, int wa, int wb, int w
     return ZKQ_OK;
   }
   // method 1: CRT form (default); method 2: digit-pair form
-  const bool crt = (method == 1);
   CrtConst cc;
   OzPlan plan;
   std::vector<OzPair> pairs;
+  bool crt = (method == 1) && crt_build(max_kp, p_out_bits, &cc);   // K' > 1024: digit form
   if (crt) {
-    if (!crt_build(max_kp, p_out_bits, &cc)) return ZKQ_EINVAL;
-    plan.b = 0; plan.sA = plan.sB = cc.r; plan.S = cc.r - 1; plan.G = 1;
-    for (int i = 0; i < cc.r; ++i) pairs.push_back({(int16_t)(i + 1), (int16_t)(i + 1), (int16_t)i, (int16_t)3});
+    // planes: [0, r) high halves, [r, 2r) low halves; levels: hh i, hl r + i, lh 2r + i
+    plan.b = 0; plan.sA = plan.sB = 2 * cc.r; plan.S = 3 * cc.r - 1; plan.G = 1;
+    for (int i = 0; i < cc.r; ++i) {
+      pairs.push_back({(int16_t)(i + 1), (int16_t)(i + 1), (int16_t)i, (int16_t)3});
+      pairs.push_back({(int16_t)(i + 1), (int16_t)(cc.r + i + 1), (int16_t)(cc.r + i), (int16_t)3});
+      pairs.push_back({(int16_t)(cc.r + i + 1), (int16_t)(i + 1), (int16_t)(2 * cc.r + i), (int16_t)3});
+    }
   } else {
     plan = ozaki_plan(max_kp, wa, wb, p_out_bits);
     pairs = make_pairs(plan);
@@ -665,7 +727,7 @@ zkq_status mw_gemm_batched(const MwProd* prods, int count, int wa, int wb, int w
     OzProd& o = dp[i];
     oA[i] = off; off += al((size_t)plan.sA * o.mp * o.kp * sizeof(__half));
     oB[i] = off; off += al((size_t)plan.sB * o.np2 * o.kp * sizeof(__half));
-    oD[i] = off; off += al((size_t)(crt ? cc.r : plan.S + 1) * o.mp * o.np2 * sizeof(int32_t));
+    oD[i] = off; off += al((size_t)(crt ? 3 * cc.r : plan.S + 1) * o.mp * o.np2 * sizeof(int32_t));
     oe[i] = off; off += al((size_t)(o.m + o.n) * sizeof(int32_t));
     max_mkp = std::max(max_mkp, (size_t)o.mp * o.kp);
     max_nkp = std::max(max_nkp, (size_t)o.np2 * o.kp);
