@@ -15,6 +15,7 @@ namespace zkq {
 
 constexpr int CRT_MAXR = 96;     // moduli
 constexpr int CRT_L = 9;         // 64-bit limbs of M and of the reconstruction sums (576 bits)
+constexpr int CRT_L32 = 18;      // the same in 32-bit limbs
 
 struct CrtConst {
   int r;                         // number of moduli
@@ -27,6 +28,10 @@ struct CrtConst {
   uint64_t Mhalf[CRT_L];         // floor(M / 2)
   double Md;                     // M as a double (upper bits), for quotient estimates
   int Mexp;                      // M = Md * 2^Mexp with Md in [1, 2)
+  uint32_t w32[CRT_MAXR][CRT_L32];   // weights in 32-bit limbs
+  uint32_t M32[CRT_L32];
+  uint32_t Mhalf32[CRT_L32];
+  uint32_t minv[CRT_MAXR];           // floor(2^32 / m_i) + 1: division-free reduction of sums < 2^29
 };
 
 // host-side construction (moduli, weights); max_kprime decides the modulus bound

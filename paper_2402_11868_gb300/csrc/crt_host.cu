@@ -32,6 +32,9 @@ int inv_mod(int a, int m) {                    // a^-1 mod m (gcd(a, m) = 1)
   return t < 0 ? t + m : t;
 }
 int gcd(int a, int b) { while (b) { int t = a % b; a = b; b = t; } return a; }
+void to32(const Limbs& a, uint32_t* out) {
+  for (int i = 0; i < CRT_L32; ++i) out[i] = i < (int)a.size() ? a[i] : 0;
+}
 void to64(const Limbs& a, uint64_t* out) {
   for (int i = 0; i < CRT_L; ++i) {
     uint64_t lo = (2 * i < (int)a.size()) ? a[2 * i] : 0, hi = (2 * i + 1 < (int)a.size()) ? a[2 * i + 1] : 0;
@@ -49,7 +52,7 @@ bool crt_build(int max_kprime, int p_out_bits, CrtConst* out) {
   const int q = p_out_bits + lg + 4;           // |A'|,|B'| < 2^(q-2); truncation error 2^-q of the scale
   const int s = (q - 2 + 1) / 2;               // halves: |A_h| <= 2^(q-2-s), 0 <= A_l < 2^s
   const int hb = std::max(q - 2 - s, s);       // each half below 2^hb
-  const double need = 2.0 * hb + lg + 2;       // log2 M > log2(2 K' 2^(2 hb))
+  const double need = 2.0 * hb + lg + 4;       // log2 M > log2(4 K' 2^(2 hb)): C_hl + C_lh, with a margin
   std::vector<int> ms;
   double bits = 0.0;
   for (int c = mb; c >= 3 && bits < need; --c) {
@@ -66,8 +69,10 @@ bool crt_build(int max_kprime, int p_out_bits, CrtConst* out) {
   Limbs M{1};
   for (int m : ms) mul_small(M, (uint32_t)m);
   to64(M, out->M);
+  to32(M, out->M32);
   Limbs half = div_small(M, 2);
   to64(half, out->Mhalf);
+  to32(half, out->Mhalf32);
   for (int i = 0; i < out->r; ++i) {
     int m = ms[i];
     out->m[i] = m;
@@ -75,6 +80,8 @@ bool crt_build(int max_kprime, int p_out_bits, CrtConst* out) {
     int inv = inv_mod((int)mod_small(Mi, (uint32_t)m), m);
     Limbs w = Mi; mul_small(w, (uint32_t)inv);
     to64(w, out->w[i]);
+    to32(w, out->w32[i]);
+    out->minv[i] = (uint32_t)((1ULL << 32) / (uint64_t)m) + 1;
     uint32_t p = 1 % m;
     for (int j = 0; j < 20; ++j) { out->pw16[i][j] = (uint8_t)p; p = (uint32_t)(((uint64_t)p << 16) % m); }
   }

@@ -481,7 +481,10 @@ __device__ __forceinline__ void crt_emit(Big X, const CrtConst* __restrict__ cc,
     uint32_t s = 0;
 #pragma unroll
     for (int j = 0; j < 20; ++j) s += d[j] * (uint32_t)cc->pw16[i][j];
-    int res = (int)(s % (uint32_t)m);
+    // s < 2^29: q = floor(s * (floor(2^32/m) + 1) / 2^32) is floor(s/m) or one more
+    uint32_t qq = __umulhi(s, cc->minv[i]);
+    int res = (int)(s - qq * (uint32_t)m);
+    if (res < 0) res += m;
     if (ng && res) res = m - res;
     if (res > m / 2) res -= m;
     out[(size_t)(plane0 + i) * plane + e] = __int2half_rn(res);
@@ -553,64 +556,127 @@ __global__ void crt_slice_B_kernel(const OzProd* __restrict__ P, const CrtConst*
   crt_residues<WB>(q, cc->q - p.eB[j], negate, cc, p.Bhat, plane, e);
 }
 
-// symmetric (sum_i c_i w_i mod M) of the residues stored at levels [lev0, lev0 + r)
-template <int L>
-__device__ __forceinline__ void crt_reconstruct(const OzProd& p, const CrtConst* __restrict__ cc, int i, int col, int lev0,
-                                                BigL<L>& S) {
-  bl_zero(S);
+// symmetric (sum_i c_i w_i mod M) from residues c_i; 32-bit limbs with 64-bit lazy accumulators (every
+// product c w_limb < 2^40, at most 96 of them per limb), one carry pass at the end.
+// out: signed two's complement, CRT_L32 + 2 limbs.
+__device__ __forceinline__ void crt_sum32(const int* c, const CrtConst* __restrict__ cc, uint32_t* out) {
+  constexpr int L = CRT_L32 + 2;
+  uint64_t acc[CRT_L32];
+#pragma unroll
+  for (int k = 0; k < CRT_L32; ++k) acc[k] = 0;
   const int r = cc->r;
   for (int t = 0; t < r; ++t) {
-    int32_t v = p.D[(size_t)(lev0 + t) * p.mp * p.np2 + (size_t)i * p.np2 + col];
-    int m = cc->m[t];
-    int c = v % m; if (c < 0) c += m;
-    if (c) bl_add_mul<L>(S, (uint64_t)c, cc->w[t], CRT_L);
+    const uint64_t ct = (uint64_t)c[t];
+    const uint32_t* w = cc->w32[t];
+#pragma unroll
+    for (int k = 0; k < CRT_L32; ++k) acc[k] += ct * w[k];
   }
-  int tb = bl_top(S);
-  if (tb < 0) return;
-  int li = tb >> 6;
-  double sd = (double)S.l[li] + (li > 0 ? ldexp((double)S.l[li - 1], -64) : 0.0);
-  double qd = ldexp(sd, 64 * li) / ldexp(cc->Md, cc->Mexp);      // quotient estimate (< 2^14)
-  uint64_t qq = qd > 1.0 ? (uint64_t)qd : 0;
-  if (qq) bl_sub_mul<L>(S, qq, cc->M, CRT_L);
-  for (int it = 0; it < 3 && bl_neg(S); ++it) bl_add_mul<L>(S, 1, cc->M, CRT_L);
-  for (int it = 0; it < 3 && bl_cmp<L>(S, cc->M, CRT_L) >= 0; ++it) bl_sub_mul<L>(S, 1, cc->M, CRT_L);
-  if (bl_cmp<L>(S, cc->Mhalf, CRT_L) > 0) bl_sub_mul<L>(S, 1, cc->M, CRT_L);
+  uint32_t S[L];
+  uint64_t carry = 0;
+#pragma unroll
+  for (int k = 0; k < CRT_L32; ++k) { uint64_t v = acc[k] + carry; S[k] = (uint32_t)v; carry = v >> 32; }
+  S[CRT_L32] = (uint32_t)carry; S[CRT_L32 + 1] = (uint32_t)(carry >> 32);
+  // quotient estimate q = floor(S / M) (< 2^15) from the leading bits, exact correction after
+  int top = L - 1; while (top > 0 && S[top] == 0) --top;
+  double sd = (double)S[top] + (top > 0 ? ldexp((double)S[top - 1], -32) : 0.0) + (top > 1 ? ldexp((double)S[top - 2], -64) : 0.0);
+  double qd = ldexp(sd, 32 * top) / ldexp(cc->Md, cc->Mexp);
+  int64_t qq = qd > 1.0 ? (int64_t)qd : 0;
+  // S -= q M (signed 64-bit lazy borrow)
+  {
+    int64_t b = 0;
+#pragma unroll
+    for (int k = 0; k < L; ++k) {
+      int64_t v = (int64_t)S[k] - (k < CRT_L32 ? (int64_t)((uint64_t)qq * cc->M32[k] & 0xFFFFFFFFULL) : 0) + b;
+      int64_t hi = k < CRT_L32 ? (int64_t)(((uint64_t)qq * cc->M32[k]) >> 32) : 0;
+      S[k] = (uint32_t)v;
+      b = (v >> 32) - hi;                       // arithmetic shift keeps the borrow
+    }
+  }
+  auto neg = [&]() { return (int32_t)S[L - 1] < 0; };
+  auto addM = [&](int sgn) {
+    int64_t cy = 0;
+#pragma unroll
+    for (int k = 0; k < L; ++k) {
+      int64_t v = (int64_t)S[k] + (k < CRT_L32 ? sgn * (int64_t)cc->M32[k] : 0) + cy;
+      S[k] = (uint32_t)v; cy = v >> 32;
+    }
+  };
+  auto geq = [&](const uint32_t* X) {           // S >= X for nonnegative S
+    for (int k = L - 1; k >= 0; --k) {
+      uint32_t x = k < CRT_L32 ? X[k] : 0;
+      if (S[k] != x) return S[k] > x;
+    }
+    return true;
+  };
+  for (int it = 0; it < 3 && neg(); ++it) addM(1);
+  for (int it = 0; it < 3 && geq(cc->M32); ++it) addM(-1);
+  auto gt = [&](const uint32_t* X) {            // S > X for nonnegative S
+    for (int k = L - 1; k >= 0; --k) {
+      uint32_t x = k < CRT_L32 ? X[k] : 0;
+      if (S[k] != x) return S[k] > x;
+    }
+    return false;
+  };
+  if (!neg() && gt(cc->Mhalf32)) addM(-1);      // symmetric representative
+#pragma unroll
+  for (int k = 0; k < L; ++k) out[k] = S[k];
 }
 
 // C' = C_hh 2^(2s) + (C_hl + C_lh) 2^s, value = C' 2^(e_i + f_j - 2q)
 template <int WC>
 __device__ __forceinline__ mw<WC> crt_value(const OzProd& p, const CrtConst* __restrict__ cc, int i, int col, int es) {
-  constexpr int L = CRT_L + 1;
+  constexpr int L32 = CRT_L32 + 2;
   const int r = cc->r, s = cc->s;
-  BigL<L> T, U;
-  crt_reconstruct<L>(p, cc, i, col, 0, T);          // A_h B_h
-  // shift T left by 2s (T stays far below 2^(64 L - 1))
-  {
-    BigL<L> Z; bl_zero(Z);
-    int sh = 2 * s, ls = sh >> 6, bs = sh & 63;
-    for (int k = L - 1; k >= 0; --k) {
-      int src = k - ls;
-      uint64_t a = src >= 0 ? T.l[src] : 0, b = (src - 1 >= 0) ? T.l[src - 1] : 0;
-      if (src >= 0) Z.l[k] = bs ? ((a << bs) | (b >> (64 - bs))) : a;
-      else Z.l[k] = 0;
-    }
-    T = Z;                                          // a left shift keeps the two's complement sign
+  int c[CRT_MAXR];
+  const size_t stride = (size_t)p.mp * p.np2, base = (size_t)i * p.np2 + col;
+  // v mod m in [0, m) without division, |v| < 2^29 (minv = floor(2^32/m) + 1)
+  auto modm = [&](int v, int t) {
+    const uint32_t m = (uint32_t)cc->m[t];
+    uint32_t a = (uint32_t)(v < 0 ? -v : v);
+    int res = (int)(a - __umulhi(a, cc->minv[t]) * m);
+    if (res < 0) res += (int)m;
+    if (v < 0 && res) res = (int)m - res;
+    return res;
+  };
+  for (int t = 0; t < r; ++t) c[t] = modm(p.D[(size_t)t * stride + base], t);
+  uint32_t hh[L32], sm[L32];
+  crt_sum32(c, cc, hh);
+  for (int t = 0; t < r; ++t) {
+    int v = p.D[(size_t)(r + t) * stride + base] + p.D[(size_t)(2 * r + t) * stride + base];   // |v| < 2^25
+    c[t] = modm(v, t);
   }
-  BigL<L> H1, H2;
-  crt_reconstruct<L>(p, cc, i, col, r, H1);         // A_h B_l
-  crt_reconstruct<L>(p, cc, i, col, 2 * r, H2);     // A_l B_h
-  // U = (H1 + H2) 2^s
-  {
-    uint64_t c = 0;
-    for (int k = 0; k < L; ++k) { uint64_t a = H1.l[k], t = a + H2.l[k]; uint64_t c1 = t < a; uint64_t t2 = t + c; c = c1 | (t2 < t); H1.l[k] = t2; }
-    int ls = s >> 6, bs = s & 63;
-    for (int k = L - 1; k >= 0; --k) {
-      int src = k - ls;
-      uint64_t a = src >= 0 ? H1.l[src] : 0, b = (src - 1 >= 0) ? H1.l[src - 1] : 0;
-      U.l[k] = src >= 0 ? (bs ? ((a << bs) | (b >> (64 - bs))) : a) : 0;
+  crt_sum32(c, cc, sm);
+  // T = hh 2^(2s) + sm 2^s as a signed 64-bit-limb integer (sign-extended shifts of 32-bit limbs)
+  constexpr int L = CRT_L + 1;
+  BigL<L> T; bl_zero(T);
+  auto add_shifted32 = [&](const uint32_t* X, int sh) {
+    const bool ng = (int32_t)X[L32 - 1] < 0;
+    BigL<L> Y;
+#pragma unroll
+    for (int k = 0; k < L; ++k) Y.l[k] = ng ? ~0ULL : 0ULL;
+    // place X (L32 limbs of 32 bits) shifted by sh bits
+    for (int k = 0; k < L32; ++k) {
+      int bit = 32 * k + sh;
+      int li = bit >> 6, bs = bit & 63;
+      if (li >= L) break;
+      uint64_t x = X[k];
+      uint64_t mask_lo = 0xFFFFFFFFULL << bs;
+      Y.l[li] = (Y.l[li] & ~mask_lo) | ((x << bs) & mask_lo);
+      if (bs > 32 && li + 1 < L) {
+        uint64_t mask_hi = (1ULL << (bs - 32)) - 1;
+        Y.l[li + 1] = (Y.l[li + 1] & ~mask_hi) | (x >> (64 - bs));
+      }
     }
-  }
-  bl_add_mul<L>(T, 1, U.l, L);
+    // bits below sh are zero
+    for (int k = 0; k < L; ++k) {
+      int b0 = 64 * k;
+      if (b0 + 64 <= sh) Y.l[k] = 0;
+      else if (b0 < sh) Y.l[k] &= ~((1ULL << (sh - b0)) - 1);
+    }
+    bl_add_mul<L>(T, 1, Y.l, L);
+  };
+  add_shifted32(hh, 2 * s);
+  add_shifted32(sm, s);
   mw<WC> out;
   for (int k = 0; k < WC; ++k) out.x[k] = bl_round_off<L>(T, es - 2 * cc->q);
   return out;
