@@ -253,6 +253,14 @@ def run_ours(args):
                 "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
                 "peak_source": f"{peak_kind} bf16_tflops_sustained (fp16 dense has the bf16 rate)",
                 "launches": dom_n, "avg_launch_ms": dom_ms / max(dom_n, 1)}
+    elif dom_name == "jacobi":
+        peak = 1.006   # measured DFMA throughput of this GB300 pool, TFLOP/s (FMA = 2 flops)
+        achieved = dom_work / (dom_ms / 1e3) / 1e12
+        roof = {"bound": "alu", "kernel": "jacobi_smem_kernel + jacobi_global_kernel (FP64 rotations)",
+                "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+                "peak_source": "measured FP64 DFMA microbenchmark (MEASURED_PEAKS.json has no FP64 entry)",
+                "work": "24 n flops per applied rotation (12 n FMA: Hermitian 2x2-block update of A + V)",
+                "launches": dom_n, "avg_launch_ms": dom_ms / max(dom_n, 1)}
     elif dom_name == "rqi":
         it = 2.0
         cmacs = sum(nn * (it * (nn ** 3 / 3.0 + nn * nn) + 2 * nn * nn) for nn in R.ns) * args.steps
@@ -274,6 +282,7 @@ def run_ours(args):
         "latency_ms": {"p50": float(np.percentile(step_ms, 50)), "p99": float(np.percentile(step_ms, 99))},
         "breakdown_ms": {"jacobi_fp64": float(np.mean(jac_ms)), "refine": float(np.mean(ref_ms))},
         "kernel_ms_per_step": {k: v[0] / args.steps for k, v in prof.items() if v[1]},
+        "kernel_tflops": {k: v[2] / (v[0] / 1e3) / 1e12 for k, v in prof.items() if v[1] and v[2] > 0},
         "roofline": roof,
         "clocks": clk,
         "e2e": {"value": e2e_value, "unit": "eigenpairs/s", "h2d_bytes_per_step": int(in_bytes),

@@ -217,9 +217,10 @@ zkq_status zkq_mw_op(int op, int words, int64_t count, const double* a, const do
  *   zkq_profile_class_name(c)    name of class c (never NULL)
  *   zkq_profile_enable(on)       start (1) / stop (0) recording
  *   zkq_profile_read(ms, n, w, k) waits for the recorded launches, writes per-class milliseconds, launch
- *                                counts and algorithmic work (flops counted at launch: ozaki_gemm counts
- *                                2 m (2n) (2k) per kept digit pair; 0 where not counted) for the first k
- *                                classes, then clears the record
+ *                                counts and algorithmic work for the first k classes, then clears the
+ *                                record.  Work: ozaki_gemm counts 2 m (2n) (2k) flops per exact slice
+ *                                product (at launch); jacobi counts 24 n flops per applied rotation
+ *                                (on the device); 0 where not counted
  * Errors: ZKQ_EINVAL (null arrays, k < 1), ZKQ_ECUDA.
  */
 int zkq_profile_classes(void);

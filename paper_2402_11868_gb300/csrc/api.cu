@@ -11,6 +11,8 @@
 namespace zkq {
 
 Profiler& profiler() { static Profiler p; return p; }
+static unsigned long long* g_prof_ctr = nullptr;   // device counters, PC_COUNT entries
+unsigned long long* prof_device_counters() { return profiler().on ? g_prof_ctr : nullptr; }
 
 static thread_local int g_last_cuda = 0;
 void set_last_cuda_error(cudaError_t e) { g_last_cuda = (int)e; }
@@ -258,6 +260,11 @@ const char* zkq_profile_class_name(int cls) { return (cls >= 0 && cls < PC_COUNT
 zkq_status zkq_profile_enable(int on) {
   Profiler& p = profiler();
   std::lock_guard<std::mutex> g(p.mu);
+  if (on && !g_prof_ctr) {
+    cudaError_t e = cudaMalloc(&g_prof_ctr, sizeof(unsigned long long) * PC_COUNT);
+    if (e != cudaSuccess) { set_last_cuda_error(e); g_prof_ctr = nullptr; return ZKQ_ENOMEM; }
+    cudaMemset(g_prof_ctr, 0, sizeof(unsigned long long) * PC_COUNT);
+  }
   p.on = on != 0;
   return ZKQ_OK;
 }
@@ -276,6 +283,13 @@ zkq_status zkq_profile_read(double* ms, int64_t* launches, double* work, int ncl
     p.pool.push_back(r.a); p.pool.push_back(r.b);
   }
   p.recs.clear();
+  if (g_prof_ctr) {                              // device-counted work (all recorded launches are complete)
+    unsigned long long h[PC_COUNT];
+    cudaError_t e = cudaMemcpy(h, g_prof_ctr, sizeof(h), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) { set_last_cuda_error(e); return ZKQ_ECUDA; }
+    for (int i = 0; i < PC_COUNT && i < nclasses; ++i) work[i] += (double)h[i];
+    cudaMemset(g_prof_ctr, 0, sizeof(h));
+  }
   return ZKQ_OK;
 }
 

@@ -25,6 +25,8 @@ namespace zkq {
 
 struct RotParams { double c, tb; c64 z1, z2; int rot; int p, q; };
 
+__device__ unsigned long long* g_jacobi_flops = nullptr;   // work counter, set by the launcher when profiling
+
 // Storage policy: matrix element (i, j) of a column-major matrix with leading dimension ld.
 // SMEM: plain loads/stores.  GLOBAL: L2-only loads (other CTAs of the cluster write the same matrix).
 template <bool SMEM> struct Mat {
@@ -177,6 +179,9 @@ __device__ void jacobi_problem(int n, const double* __restrict__ A_in, Mat<SMEM>
     }
     if (my_rot) atomicAdd(&s_rot, my_rot);
     __syncthreads();
+    // algorithmic FP64 flops of this sweep: per applied rotation 12 n FMA (6 n on A with the Hermitian
+    // block update, 6 n on V) = 24 n flops; counted once per problem (part 0)
+    if (part == 0 && tid == 0 && g_jacobi_flops && s_rot) atomicAdd(g_jacobi_flops, (unsigned long long)s_rot * 24ULL * (unsigned long long)n);
     if constexpr (CLUSTER) {
       // every CTA computed the same parameters, but take part 0's count so the barrier counts of the
       // cluster's CTAs cannot diverge
@@ -291,6 +296,9 @@ static zkq_status launch_words(const JacobiBatch& jb, int n_small, int n_large, 
 
 zkq_status launch_jacobi(const JacobiBatch& jb, int a_words, int n_small, int n_large, int max_small_n,
                          int max_large_n, int cluster, cudaStream_t st) {
+  unsigned long long* ctr = prof_device_counters();
+  unsigned long long* dev_ctr = ctr ? ctr + PC_JACOBI : nullptr;
+  ZKQ_CUDA_TRY(cudaMemcpyToSymbolAsync(g_jacobi_flops, &dev_ctr, sizeof(dev_ctr), 0, cudaMemcpyHostToDevice, st));
   switch (a_words) {
     case 1: return launch_words<1>(jb, n_small, n_large, max_small_n, max_large_n, cluster, st);
     case 2: return launch_words<2>(jb, n_small, n_large, max_small_n, max_large_n, cluster, st);

@@ -21,6 +21,10 @@ struct Profiler {
   }
 };
 Profiler& profiler();
+// Device-side algorithmic work counters (one unsigned 64-bit counter per class; flops counted by the
+// kernels themselves where the work depends on the data, e.g. the rotations Jacobi applies).  Null when
+// profiling is off.
+unsigned long long* prof_device_counters();
 
 // RAII bracket around one launch
 struct ProfScope {
