@@ -194,6 +194,17 @@ zkq_status zkq_mw_gemm(zkq_ctx* ctx, int count, const int32_t* m, const int32_t*
                        void* stream);
 
 /*
+ * Slice-GEMM kernel selection for the split products (process-wide): 1 = tcgen05 kernel (5th-generation
+ * tensor cores, accumulators in tensor memory; default), 0 = warp-level mma.sync kernel.  Both compute
+ * identical exact integer slice products.
+ * zkq_check_device_waits: ZKQ_ETIMEOUT if a bounded device-side wait of the tcgen05 kernel expired since
+ * the last check (synchronises the device), else ZKQ_OK.
+ */
+zkq_status zkq_set_gemm_kernel(int which);
+int zkq_get_gemm_kernel(void);
+zkq_status zkq_check_device_waits(void);
+
+/*
  * zkq_mw_op: element-wise multi-word arithmetic, the building block of every refinement step
  * (the paper's multiple-precision numbers, Section 1; here double-double / quad-double made of FP64
  * error-free transformations).  Diagnostic entry point used to check the arithmetic.

@@ -79,6 +79,10 @@ def lib():
                              ("zkq_mps_apply2q", [P, P, I, P, ctypes.c_double, I, P, P, P])):
                 getattr(L, nm).restype = I
                 getattr(L, nm).argtypes = args
+            L.zkq_set_gemm_kernel.restype = I
+            L.zkq_set_gemm_kernel.argtypes = [I]
+            L.zkq_get_gemm_kernel.restype = I
+            L.zkq_check_device_waits.restype = I
             L.zkq_mw_op.restype = I
             L.zkq_mw_op.argtypes = [I, I, I64, P, P, P, I, P]
             _lib = L
@@ -181,6 +185,18 @@ def zkq_mw_gemm(ctx: Context, m, n, k, opA, A, a_off, wa, B, b_off, wb, C, c_off
 def zkq_mw_op(op: int, words: int, count: int, a, b, out, on_device: bool, stream=None):
     _check(lib().zkq_mw_op(op, words, count, _ptr(a), _ptr(b), _ptr(out), int(bool(on_device)), _stream(stream)),
            "zkq_mw_op")
+
+
+def zkq_set_gemm_kernel(which: int):
+    _check(lib().zkq_set_gemm_kernel(which), "zkq_set_gemm_kernel")
+
+
+def zkq_get_gemm_kernel() -> int:
+    return lib().zkq_get_gemm_kernel()
+
+
+def zkq_check_device_waits():
+    _check(lib().zkq_check_device_waits(), "zkq_check_device_waits")
 
 
 def zkq_profile_enable(on: bool):

@@ -34,6 +34,9 @@ zkq_status oa_refine(void* ctx, const OaBuffers& buf, int batch, const int32_t* 
                      const double* A, int wa, const double* V, int W, double* W_out, double* V_out, double* err,
                      int32_t* info, int max_iter, int prod_method, cudaStream_t st);
 
+int gemm_kernel_get();
+void gemm_kernel_set(int k);
+bool gemm_kernel_error();
 }  // namespace zkq
 #include "ozaki.cuh"
 
@@ -246,9 +249,20 @@ zkq_status zkq_mw_gemm(zkq_ctx* ctx, int count, const int32_t* m, const int32_t*
       return ZKQ_EINVAL;
     pr[i] = {m[i], n[i], k[i], opA[i], A + a_off[i] * 2 * wa, B + b_off[i] * 2 * wb, C + c_off[i] * 2 * wc, nullptr, 1.0, 0};
   }
-  return mw_gemm_batched(pr.data(), count, wa, wb, wc, p_bits, method, &ctx->oz_ws, &ctx->oz_bytes, &ctx->oz_meta,
-                         &ctx->oz_meta_bytes, (cudaStream_t)stream);
+  zkq_status s = mw_gemm_batched(pr.data(), count, wa, wb, wc, p_bits, method, &ctx->oz_ws, &ctx->oz_bytes,
+                                 &ctx->oz_meta, &ctx->oz_meta_bytes, (cudaStream_t)stream);
+  return s;
 }
+
+zkq_status zkq_set_gemm_kernel(int which) {
+  if (which != 0 && which != 1) return ZKQ_EINVAL;
+  gemm_kernel_set(which);
+  return ZKQ_OK;
+}
+
+int zkq_get_gemm_kernel(void) { return gemm_kernel_get(); }
+
+zkq_status zkq_check_device_waits(void) { return gemm_kernel_error() ? ZKQ_ETIMEOUT : ZKQ_OK; }
 
 static const char* kProfNames[PC_COUNT] = {"jacobi", "rqi", "ozaki_scale", "ozaki_slice", "ozaki_gemm",
                                            "ozaki_combine", "oa_elementwise", "mps", "other"};

@@ -15,6 +15,7 @@
 // rounded once into the output's double words.  Complex products use the real embedding
 //   Re C = [Re op(A) | Im op(A)] [Re B ; -Im B],  Im C = [Re op(A) | Im op(A)] [Im B ; Re B]   (K' = 2k).
 #include "ozaki.cuh"
+#include "oz_tc.cuh"
 #include "crt.cuh"
 #include "mw.cuh"
 #include "prof.cuh"
@@ -244,6 +245,10 @@ __global__ void oz_slice_B_kernel(const OzProd* __restrict__ P, int b, int sB) {
 constexpr int OZ_BM = 128, OZ_BN = 128, OZ_BK = 32, OZ_STAGES = 3;
 
 struct OzTile { int prod, ti, tj; };
+
+// slice-GEMM kernel: 0 mma.sync (legacy warp-level path), 1 tcgen05 (tensor memory accumulators)
+static int g_gemm_kernel = 1;
+static int* g_oz_err = nullptr;              // device flag raised by a bounded wait that expired
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 __device__ __forceinline__ void cp_async16(uint32_t dst, const void* src) {
@@ -747,7 +752,7 @@ zkq_status mw_gemm_batched(const MwProd* prods, int count, int wa, int wb, int w
     o.A = q.A; o.B = q.B; o.C = q.C; o.base = q.base; o.sgn = q.sgn; o.base_identity = q.base_identity;
     o.mp = (q.m + OZ_BM - 1) / OZ_BM * OZ_BM;
     o.np2 = (2 * q.n + OZ_BN - 1) / OZ_BN * OZ_BN;
-    o.kp = (2 * q.k + OZ_BK - 1) / OZ_BK * OZ_BK;
+    o.kp = (2 * q.k + 63) / 64 * 64;            // multiple of both kernels' K step
     max_kp = std::max(max_kp, 2 * q.k);
     max_mn = std::max(max_mn, q.m * q.n);
   }
@@ -846,11 +851,21 @@ zkq_status mw_gemm_batched(const MwProd* prods, int count, int wa, int wb, int w
   }
   {
     size_t sm = (size_t)OZ_STAGES * (OZ_BM + OZ_BN) * 64;
-    ZKQ_CUDA_TRY(cudaFuncSetAttribute(oz_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    if (g_gemm_kernel != 1)
+      ZKQ_CUDA_TRY(cudaFuncSetAttribute(oz_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
     double flops = 0.0;                        // algorithmic: every kept digit pair, unpadded sizes
     for (auto& o : dp) flops += 2.0 * plan.npairs * (double)o.m * (2.0 * o.n) * (2.0 * o.k);
     ProfScope ps(PC_OZ_GEMM, st, flops);
-    oz_gemm_kernel<<<(unsigned)tiles.size(), 256, sm, st>>>(d_p, d_t, d_q, plan.npairs, plan.S);
+    if (g_gemm_kernel == 1) {
+      if (!g_oz_err) {
+        ZKQ_CUDA_TRY(cudaMalloc(&g_oz_err, sizeof(int)));
+        ZKQ_CUDA_TRY(cudaMemset(g_oz_err, 0, sizeof(int)));
+      }
+      zkq_status ls = launch_oz_tc(d_p, d_t, (int)tiles.size(), d_q, plan.npairs, g_oz_err, st);
+      if (ls != ZKQ_OK) return ls;
+    } else {
+      oz_gemm_kernel<<<(unsigned)tiles.size(), 256, sm, st>>>(d_p, d_t, d_q, plan.npairs, plan.S);
+    }
     ZKQ_CUDA_TRY(cudaGetLastError());
   }
   {
@@ -868,6 +883,17 @@ zkq_status mw_gemm_batched(const MwProd* prods, int count, int wa, int wb, int w
     ZKQ_CUDA_TRY(cudaGetLastError());
   }
   return ZKQ_OK;
+}
+
+int gemm_kernel_get() { return g_gemm_kernel; }
+void gemm_kernel_set(int k) { g_gemm_kernel = k; }
+// reads and clears the expired-wait flag of the tcgen05 kernel (synchronous)
+bool gemm_kernel_error() {
+  if (!g_oz_err) return false;
+  int h = 0;
+  cudaMemcpy(&h, g_oz_err, sizeof(int), cudaMemcpyDeviceToHost);
+  if (h) cudaMemset(g_oz_err, 0, sizeof(int));
+  return h != 0;
 }
 
 }  // namespace zkq

@@ -37,11 +37,15 @@ def rand_mw(rng, count, w, spread=6):
 CASES = [(1, 1, 1, 0), (3, 5, 7, 1), (17, 33, 16, 0), (130, 40, 70, 1), (64, 48, 512, 0), (40, 3, 600, 1)]
 
 
+@pytest.mark.parametrize("kernel", [1, 0])
 @pytest.mark.parametrize("method", [1, 2, 0])
 @pytest.mark.parametrize("wa,wb,wc", [(4, 4, 4), (4, 2, 4), (2, 1, 2), (1, 4, 4)])
-def test_split_products_match_exact(ctx, method, wa, wb, wc):
+def test_split_products_match_exact(ctx, method, wa, wb, wc, kernel):
     import torch
     import paper_2402_11868_gb300 as Z
+    if method == 0 and kernel == 0:
+        pytest.skip("method 0 does not use the slice-GEMM kernels")
+    Z.zkq_set_gemm_kernel(kernel)
     rng = np.random.default_rng(1000 * wa + 100 * wb + 10 * wc + method)
     As, Bs, ms, ns, ks, ops = [], [], [], [], [], []
     for (m, n, k, op) in CASES:
@@ -56,6 +60,8 @@ def test_split_products_match_exact(ctx, method, wa, wb, wc):
     p_bits = 53 * wc + 6
     Z.zkq_mw_gemm(ctx, ms, ns, ks, ops, dA, a_off, wa, dB, b_off, wb, dC, c_off, wc, p_bits, method)
     torch.cuda.synchronize()
+    Z.zkq_check_device_waits()
+    Z.zkq_set_gemm_kernel(1)
     Ch = dC.cpu().numpy()
     for i, (m, n, k, op) in enumerate(CASES):
         ref = oracle.matmul(As[i], Bs[i], m, n, k, opA=op)
