@@ -259,7 +259,7 @@ def run_ours(args):
         roof = {"bound": "alu", "kernel": "jacobi_smem_kernel + jacobi_global_kernel (FP64 rotations)",
                 "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
                 "peak_source": "measured FP64 DFMA microbenchmark (MEASURED_PEAKS.json has no FP64 entry)",
-                "work": "24 n flops per applied rotation (12 n FMA: Hermitian 2x2-block update of A + V)",
+                "work": "48 n flops per applied rotation (24 n FMA: Hermitian 2x2-block update of A 12 n + V 12 n)",
                 "launches": dom_n, "avg_launch_ms": dom_ms / max(dom_n, 1)}
     elif dom_name == "rqi":
         it = 2.0

@@ -230,7 +230,7 @@ zkq_status zkq_mw_op(int op, int words, int64_t count, const double* a, const do
  *   zkq_profile_read(ms, n, w, k) waits for the recorded launches, writes per-class milliseconds, launch
  *                                counts and algorithmic work for the first k classes, then clears the
  *                                record.  Work: ozaki_gemm counts 2 m (2n) (2k) flops per exact slice
- *                                product (at launch); jacobi counts 24 n flops per applied rotation
+ *                                product (at launch); jacobi counts 48 n flops per applied rotation
  *                                (on the device); 0 where not counted
  * Errors: ZKQ_EINVAL (null arrays, k < 1), ZKQ_ECUDA.
  */

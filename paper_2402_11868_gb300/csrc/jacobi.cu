@@ -179,9 +179,9 @@ __device__ void jacobi_problem(int n, const double* __restrict__ A_in, Mat<SMEM>
     }
     if (my_rot) atomicAdd(&s_rot, my_rot);
     __syncthreads();
-    // algorithmic FP64 flops of this sweep: per applied rotation 12 n FMA (6 n on A with the Hermitian
-    // block update, 6 n on V) = 24 n flops; counted once per problem (part 0)
-    if (part == 0 && tid == 0 && g_jacobi_flops && s_rot) atomicAdd(g_jacobi_flops, (unsigned long long)s_rot * 24ULL * (unsigned long long)n);
+    // algorithmic FP64 flops of this sweep: per applied rotation 24 n FMA (12 n on A: a round's n/2
+    // rotations update n^2/8 2x2 blocks at 48 FMA each; 12 n on V) = 48 n flops; counted once per problem
+    if (part == 0 && tid == 0 && g_jacobi_flops && s_rot) atomicAdd(g_jacobi_flops, (unsigned long long)s_rot * 48ULL * (unsigned long long)n);
     if constexpr (CLUSTER) {
       // every CTA computed the same parameters, but take part 0's count so the barrier counts of the
       // cluster's CTAs cannot diverge
