@@ -259,12 +259,14 @@ class MPS:
         u = np.ascontiguousarray(U, dtype=np.float64)
         _check(lib().zkq_mps_apply1q(self.ctx.handle, self.handle, site, u.ctypes.data, _stream(stream)), "zkq_mps_apply1q")
 
-    def apply2q(self, site, G, trunc_tau=0.0, method=ZKQ_OA_OZAKI, stream=None):
-        """Returns (new bond dimension, discarded weight)."""
+    def apply2q(self, site, G, trunc_tau=0.0, method=ZKQ_OA_OZAKI, stream=None, ctx=None):
+        """Returns (new bond dimension, discarded weight).  `ctx` (default: the creating context) supplies
+        the workspace; concurrent updates must use different contexts."""
         import numpy as np
         g = np.ascontiguousarray(G, dtype=np.float64)
         nb = ctypes.c_int32(0); dw = ctypes.c_double(0.0)
-        _check(lib().zkq_mps_apply2q(self.ctx.handle, self.handle, site, g.ctypes.data, float(trunc_tau), method,
+        c = (ctx or self.ctx).handle
+        _check(lib().zkq_mps_apply2q(c, self.handle, site, g.ctypes.data, float(trunc_tau), method,
                                      ctypes.byref(nb), ctypes.byref(dw), _stream(stream)), "zkq_mps_apply2q")
         return nb.value, dw.value
 
