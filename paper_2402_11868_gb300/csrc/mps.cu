@@ -350,6 +350,7 @@ static zkq_status apply2q_t(zkq_ctx* ctx, zkq_mps* m, int l, const double* G, do
   }
   // rho = M M^H (op(A) = (M^H)^H with A = MH stored C x R, B = MH) or M^H M (A = M stored R x C, B = M)
   MwProd pg = left ? MwProd{R, R, C, 1, MH, MH, Rho, nullptr, 1.0, 0} : MwProd{C, C, R, 1, M, M, Rho, nullptr, 1.0, 0};
+  pg.hermitian = 1;
   s = mw_gemm_batched(&pg, 1, W, W, W, p_bits, 1, ob.oz_ws, ob.oz_bytes, ob.oz_meta, ob.oz_meta_bytes, st);
   if (s != ZKQ_OK) return s;
   // eigen-decomposition of rho (descending), refined to W words

@@ -86,7 +86,8 @@ __device__ __forceinline__ void atomic_max_nonneg(double* a, double v) {
 // column norms ||num_{:,c}||^2, max |num| and max |r|.
 template <int W>
 __global__ void oa_coupling_kernel(const OaProb* __restrict__ pr, const double* __restrict__ S, const double* __restrict__ R,
-                                   const double* __restrict__ lam, double* __restrict__ colnum, OaStat* __restrict__ st) {
+                                   const double* __restrict__ lam, double* __restrict__ colnum, double* __restrict__ NUM,
+                                   OaStat* __restrict__ st) {
   const OaProb p = pr[blockIdx.y];
   int e = blockIdx.x * blockDim.x + threadIdx.x;
   double cpl = 0.0, rmag = 0.0;
@@ -94,13 +95,16 @@ __global__ void oa_coupling_kernel(const OaProb* __restrict__ pr, const double* 
     const int n = p.n, i = e % n, j = e / n;
     cmw<W> r = c_load<W, W>(R + p.xoff * 2 * W, e);
     rmag = hypot(r.re.x[0], r.im.x[0]);
+    cmw<2> num2 = c_zero<2>();
     if (i != j) {
       cmw<W> sv = c_load<W, W>(S + p.xoff * 2 * W, e);
       mw<W> hs = mw_mul_d(mw_add(mw_load<W, W>(lam + p.loff * W, i), mw_load<W, W>(lam + p.loff * W, j)), 0.5);
-      cmw<W> num = c_add(sv, c_scale(r, hs));
+      cmw<W> num = c_add(sv, c_scale(r, hs));       // cancellation-sensitive: working precision
       cpl = hypot(num.re.x[0], num.im.x[0]);
       if (cpl > 0) atomicAdd(&colnum[p.loff + j], cpl * cpl);
+      num2 = c_make(mw_from_words<2, W>(num.re.x), mw_from_words<2, W>(num.im.x));
     }
+    c_store(NUM + p.xoff * 2 * 2, e, num2);
   }
   for (int o = 16; o > 0; o >>= 1) {
     cpl = fmax(cpl, __shfl_down_sync(0xffffffffu, cpl, o));
@@ -159,7 +163,7 @@ __global__ void oa_cluster_kernel(const OaProb* __restrict__ pr, const double* _
 // E + E^H = R holds to rounding even where the computed S carries noise / gap for near-degenerate pairs;
 // that noise then only rotates inside the pair's span.
 template <int W>
-__global__ void oa_E_kernel(const OaProb* __restrict__ pr, const double* __restrict__ S, const double* __restrict__ R,
+__global__ void oa_E_kernel(const OaProb* __restrict__ pr, const double* __restrict__ NUM, const double* __restrict__ R,
                             const double* __restrict__ lam, const int32_t* __restrict__ cl_start,
                             const int32_t* __restrict__ orth_only, double* __restrict__ E, OaStat* __restrict__ st) {
   const OaProb p = pr[blockIdx.y];
@@ -179,17 +183,15 @@ __global__ void oa_E_kernel(const OaProb* __restrict__ pr, const double* __restr
       out.im = mw_zero<2>();
       rmag = fabs(r.re.x[0]);
     } else {
-      cmw<W> s = c_load<W, W>(S + p.xoff * 2 * W, eu);
-      mw<W> la = mw_load<W, W>(lam + p.loff * W, a), lb = mw_load<W, W>(lam + p.loff * W, b);
-      mw<W> hsum = mw_mul_d(mw_add(la, lb), 0.5);
-      cmw<W> num = c_add(s, c_scale(r, hsum));                // coupling (gap-free)
-      cpl = hypot(num.re.x[0], num.im.x[0]);
+      // coupling num_ab (gap-free), evaluated in working precision by the coupling pass, kept as DD
+      cmw<2> n2 = c_load<2, 2>(NUM + p.xoff * 2 * 2, eu);
+      cpl = hypot(n2.re.x[0], n2.im.x[0]);
       cmw<2> k = c_zero<2>();
       if (cl_start[p.loff + a] == cl_start[p.loff + b]) {
         incl = cpl;
       } else if (!no_rot) {
+        mw<W> la = mw_load<W, W>(lam + p.loff * W, a), lb = mw_load<W, W>(lam + p.loff * W, b);
         mw<W> den = mw_sub(lb, la);
-        cmw<2> n2 = c_make(mw_from_words<2, W>(num.re.x), mw_from_words<2, W>(num.im.x));
         k = c_scale(n2, mw_recip(mw_from_words<2, W>(den.x)));
       }
       cmw<2> half_r = c_scale_d(r2, 0.5);
@@ -217,18 +219,28 @@ struct OaCluster { int prob; int start; int len; int64_t toff; int64_t woff; };
 // CT = X_J^H A X_J and CG = X_J^H X_J (W words, len x len at toff) were formed by split products from the
 // updated X, so the components of X_J outside the cluster are second order and do not blur the small
 // splittings; mu = mean of the current lambdas over J.
+// mu of every cluster (one thread per cluster)
+template <int W>
+__global__ void oa_cluster_mu_kernel(const OaProb* __restrict__ pr, const OaCluster* __restrict__ cl, int ncl,
+                                     const double* __restrict__ lam, double* __restrict__ MU) {
+  int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= ncl) return;
+  const OaCluster c = cl[k];
+  const OaProb p = pr[c.prob];
+  mw<W> mu = mw_zero<W>();
+  for (int q = 0; q < c.len; ++q) mu = mw_add(mu, mw_load<W, W>(lam + p.loff * W, c.start + q));
+  mw_store(MU, k, mw_mul_d(mu, 1.0 / c.len));
+}
+
 template <int W>
 __global__ void oa_cluster_T_kernel(const OaProb* __restrict__ pr, const OaCluster* __restrict__ cl,
                                     const double* __restrict__ CT, const double* __restrict__ CG,
-                                    const double* __restrict__ lam, double* __restrict__ T) {
+                                    const double* __restrict__ MU, double* __restrict__ T) {
   const OaCluster c = cl[blockIdx.y];
-  const OaProb p = pr[c.prob];
   int e = blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= c.len * c.len) return;
   int a = e % c.len, b = e / c.len;
-  mw<W> mu = mw_zero<W>();
-  for (int q = 0; q < c.len; ++q) mu = mw_add(mu, mw_load<W, W>(lam + p.loff * W, c.start + q));
-  mu = mw_mul_d(mu, 1.0 / c.len);
+  const mw<W> mu = mw_load<W, W>(MU, blockIdx.y);
   cmw<W> t = c_load<W, W>(CT + c.toff * 2 * W, e);
   cmw<W> g = c_load<W, W>(CG + c.toff * 2 * W, e);
   t = c_sub(t, c_scale(g, mu));
@@ -375,6 +387,8 @@ zkq_status oa_refine_t(void* ctx, const OaBuffers& buf, int batch, const int32_t
   size_t oCT = take(mat), oCG = take(mat), oCW = take(mat);   // cluster blocks X_J^H A X_J, X_J^H X_J; rotation
   size_t oCN = take((size_t)le * sizeof(double));              // column coupling norms
   size_t oOO = take(sizeof(int32_t) * batch);                  // per active problem: orthonormalise only
+  size_t oMU = take((size_t)le * W * sizeof(double));           // cluster means
+  size_t oNUM = take((size_t)xe * 2 * 2 * sizeof(double));      // couplings (double-double)
   zkq_status s = grow_buf(buf.ws, buf.ws_bytes, off);
   if (s != ZKQ_OK) return s;
   char* base = (char*)*buf.ws;
@@ -388,6 +402,8 @@ zkq_status oa_refine_t(void* ctx, const OaBuffers& buf, int batch, const int32_t
   double *CT = (double*)(base + oCT), *CG = (double*)(base + oCG), *CW = (double*)(base + oCW);
   double* CN = (double*)(base + oCN);
   int32_t* OO = (int32_t*)(base + oOO);
+  double* MUb = (double*)(base + oMU);
+  double* NUM = (double*)(base + oNUM);
   ZKQ_CUDA_TRY(cudaMemcpyAsync(PR, probs.data(), sizeof(OaProb) * batch, cudaMemcpyHostToDevice, st));
   ZKQ_CUDA_TRY(cudaMemsetAsync(info, 0, sizeof(int32_t) * batch, st));
   {
@@ -416,8 +432,11 @@ zkq_status oa_refine_t(void* ctx, const OaBuffers& buf, int batch, const int32_t
     for (int b : act) {
       const OaProb& q = probs[b];
       double* Xb = X + q.xoff * 2 * W;
-      p2.push_back({q.n, q.n, q.n, 1, Xb, Pm + q.xoff * 2 * W, Sm + q.xoff * 2 * W, nullptr, 1.0, 0});
-      p2.push_back({q.n, q.n, q.n, 1, Xb, Xb, Rm + q.xoff * 2 * W, nullptr, -1.0, 1});
+      MwProd ps_{q.n, q.n, q.n, 1, Xb, Pm + q.xoff * 2 * W, Sm + q.xoff * 2 * W, nullptr, 1.0, 0};
+      MwProd pr_{q.n, q.n, q.n, 1, Xb, Xb, Rm + q.xoff * 2 * W, nullptr, -1.0, 1};
+      ps_.hermitian = 1; pr_.hermitian = 1;        // S = X^H A X and R = I - X^H X are Hermitian
+      p2.push_back(ps_);
+      p2.push_back(pr_);
     }
     s = mw_gemm_batched(p2.data(), (int)p2.size(), W, W, W, p_bits, prod_method, buf.oz_ws, buf.oz_bytes, buf.oz_meta, buf.oz_meta_bytes, st);
     if (s != ZKQ_OK) return s;
@@ -433,11 +452,11 @@ zkq_status oa_refine_t(void* ctx, const OaBuffers& buf, int batch, const int32_t
       int mx = 0; for (auto& q : ap) mx = std::max(mx, q.n * q.n);
       dim3 g((mx + 255) / 256, (unsigned)ap.size());
       { ProfScope ps_(PC_OA, st); oa_lambda_kernel<W><<<(unsigned)ap.size(), 256, 0, st>>>(PRA, Sm, Rm, Lm, CN, ST); }
-      { ProfScope ps_(PC_OA, st); oa_coupling_kernel<W><<<g, 256, 0, st>>>(PRA, Sm, Rm, Lm, CN, ST); }
+      { ProfScope ps_(PC_OA, st); oa_coupling_kernel<W><<<g, 256, 0, st>>>(PRA, Sm, Rm, Lm, CN, NUM, ST); }
       { ProfScope ps_(PC_OA, st); oa_cluster_kernel<W><<<(unsigned)ap.size(), 32, 0, st>>>(PRA, Lm, CN, CS, CL, ST); }
       std::vector<int32_t> oo; for (int b : act) oo.push_back(polish[b] == 1 ? 1 : 0);
       ZKQ_CUDA_TRY(cudaMemcpyAsync(OO, oo.data(), sizeof(int32_t) * oo.size(), cudaMemcpyHostToDevice, st));
-      { ProfScope ps_(PC_OA, st); oa_E_kernel<W><<<g, 256, 0, st>>>(PRA, Sm, Rm, Lm, CS, OO, Em, ST); }
+      { ProfScope ps_(PC_OA, st); oa_E_kernel<W><<<g, 256, 0, st>>>(PRA, NUM, Rm, Lm, CS, OO, Em, ST); }
       ZKQ_CUDA_TRY(cudaGetLastError());
     }
     std::vector<OaStat> ast(ap.size());
@@ -528,15 +547,19 @@ zkq_status oa_refine_t(void* ctx, const OaBuffers& buf, int batch, const int32_t
         double* XJ = X2 + (q.xoff + (int64_t)c.start * q.n) * 2 * W;
         double* QJ = Pm + (q.xoff + (int64_t)c.start * q.n) * 2 * W;
         p5.push_back({q.n, c.len, q.n, 0, A + q.a_off * 2 * wa, XJ, QJ, nullptr, 1.0, 0});
-        p6.push_back({c.len, c.len, q.n, 1, XJ, QJ, CT + c.toff * 2 * W, nullptr, 1.0, 0});
-        p6.push_back({c.len, c.len, q.n, 1, XJ, XJ, CG + c.toff * 2 * W, nullptr, 1.0, 0});
+        MwProd pt_{c.len, c.len, q.n, 1, XJ, QJ, CT + c.toff * 2 * W, nullptr, 1.0, 0};
+        MwProd pg_{c.len, c.len, q.n, 1, XJ, XJ, CG + c.toff * 2 * W, nullptr, 1.0, 0};
+        pt_.hermitian = 1; pg_.hermitian = 1;
+        p6.push_back(pt_);
+        p6.push_back(pg_);
       }
       s = mw_gemm_batched(p5.data(), (int)p5.size(), wa, W, W, p_bits, prod_method, buf.oz_ws, buf.oz_bytes, buf.oz_meta, buf.oz_meta_bytes, st);
       if (s != ZKQ_OK) return s;
       s = mw_gemm_batched(p6.data(), (int)p6.size(), W, W, W, p_bits, prod_method, buf.oz_ws, buf.oz_bytes, buf.oz_meta, buf.oz_meta_bytes, st);
       if (s != ZKQ_OK) return s;
       dim3 g((maxl * maxl + 255) / 256, (unsigned)cls.size());
-      { ProfScope ps_(PC_OA, st); oa_cluster_T_kernel<W><<<g, 256, 0, st>>>(PR, CLD, CT, CG, Lm, T); }
+      { ProfScope ps_(PC_OA, st); oa_cluster_mu_kernel<W><<<(unsigned)((cls.size() + 127) / 128), 128, 0, st>>>(PR, CLD, (int)cls.size(), Lm, MUb); }
+      { ProfScope ps_(PC_OA, st); oa_cluster_T_kernel<W><<<g, 256, 0, st>>>(PR, CLD, CT, CG, MUb, T); }
       ZKQ_CUDA_TRY(cudaGetLastError());
       std::vector<int32_t> cn(cls.size()); std::vector<int64_t> co(cls.size());
       for (size_t c = 0; c < cls.size(); ++c) { cn[c] = cls[c].len; co[c] = cls[c].toff; }
@@ -550,7 +573,11 @@ zkq_status oa_refine_t(void* ctx, const OaBuffers& buf, int batch, const int32_t
       double* Wcur = CT; double* Wnext = CW;
       for (int ns = 0; ns < 2; ++ns) {
         std::vector<MwProd> pg, pw;
-        for (auto& c : cls) pg.push_back({c.len, c.len, c.len, 1, Wcur + c.toff * 2 * W, Wcur + c.toff * 2 * W, CG + c.toff * 2 * W, nullptr, 1.0, 0});
+        for (auto& c : cls) {
+          MwProd g_{c.len, c.len, c.len, 1, Wcur + c.toff * 2 * W, Wcur + c.toff * 2 * W, CG + c.toff * 2 * W, nullptr, 1.0, 0};
+          g_.hermitian = 1;
+          pg.push_back(g_);
+        }
         s = mw_gemm_batched(pg.data(), (int)pg.size(), W, W, W, p_bits, prod_method, buf.oz_ws, buf.oz_bytes, buf.oz_meta, buf.oz_meta_bytes, st);
         if (s != ZKQ_OK) return s;
         { ProfScope ps_(PC_OA, st); oa_ns_kernel<W><<<g, 256, 0, st>>>(CLD, CG); }

@@ -179,6 +179,7 @@ __global__ void oz_scale_kernel(const OzProd* __restrict__ P) {
   const OzProd p = P[blockIdx.y];
   int r = blockIdx.x * blockDim.x + threadIdx.x;
   if (r < p.m) {
+    if (!p.sliceA) return;
     double mx = 0.0;
     for (int l = 0; l < p.k; ++l) {
       const double* q = p.opA ? p.A + ((size_t)l + (size_t)r * p.k) * 2 * WA : p.A + ((size_t)r + (size_t)l * p.m) * 2 * WA;
@@ -186,6 +187,7 @@ __global__ void oz_scale_kernel(const OzProd* __restrict__ P) {
     }
     p.eA[r] = mx > 0 ? ilogb(mx) + 3 : 0;
   } else if (r < p.m + p.n) {
+    if (!p.sliceB) return;
     int j = r - p.m;
     double mx = 0.0;
     for (int l = 0; l < p.k; ++l) {
@@ -199,6 +201,7 @@ __global__ void oz_scale_kernel(const OzProd* __restrict__ P) {
 template <int WA>
 __global__ void oz_slice_A_kernel(const OzProd* __restrict__ P, int b, int sA) {
   const OzProd p = P[blockIdx.y];
+  if (!p.sliceA) return;
   size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   size_t tot = (size_t)p.mp * p.kp;
   if (e >= tot) return;
@@ -219,6 +222,7 @@ __global__ void oz_slice_A_kernel(const OzProd* __restrict__ P, int b, int sA) {
 template <int WB>
 __global__ void oz_slice_B_kernel(const OzProd* __restrict__ P, int b, int sB) {
   const OzProd p = P[blockIdx.y];
+  if (!p.sliceB) return;
   size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   size_t tot = (size_t)p.np2 * p.kp;
   if (e >= tot) return;
@@ -378,12 +382,15 @@ __global__ void oz_combine_kernel(const OzProd* __restrict__ P, int b, int S) {
   int e = blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= p.m * p.n) return;
   int i = e % p.m, j = e / p.m;
+  if (p.hermitian && i > j) return;
   int es = p.eA[i] + p.eB[j];
   cmw<WC> v = c_make(combine_value<WC>(p, i, j, es, b, S), combine_value<WC>(p, i, j + p.n, es, b, S));
   if (p.sgn < 0) v = c_make(mw_neg(v.re), mw_neg(v.im));
   if (p.base) v = c_add(v, c_load<WC, WC>(p.base, (size_t)e));
   if (p.base_identity && i == j) v.re = mw_add_d(v.re, 1.0);
+  if (p.hermitian && i == j) v.im = mw_zero<WC>();
   c_store(p.C, (size_t)e, v);
+  if (p.hermitian && i < j) c_store(p.C, (size_t)j + (size_t)i * p.m, c_conj(v));
 }
 
 // ------------------------------------------------------------------------------------------------
@@ -524,6 +531,7 @@ __device__ __forceinline__ void crt_residues(const double* w, int fix, bool nega
 template <int WA>
 __global__ void crt_slice_A_kernel(const OzProd* __restrict__ P, const CrtConst* __restrict__ cc) {
   const OzProd p = P[blockIdx.y];
+  if (!p.sliceA) return;
   size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   size_t tot = (size_t)p.mp * p.kp;
   if (e >= tot) return;
@@ -542,6 +550,7 @@ __global__ void crt_slice_A_kernel(const OzProd* __restrict__ P, const CrtConst*
 template <int WB>
 __global__ void crt_slice_B_kernel(const OzProd* __restrict__ P, const CrtConst* __restrict__ cc) {
   const OzProd p = P[blockIdx.y];
+  if (!p.sliceB) return;
   size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   size_t tot = (size_t)p.np2 * p.kp;
   if (e >= tot) return;
@@ -693,12 +702,15 @@ __global__ void crt_combine_kernel(const OzProd* __restrict__ P, const CrtConst*
   int e = blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= p.m * p.n) return;
   int i = e % p.m, j = e / p.m;
+  if (p.hermitian && i > j) return;            // written by the (j, i) thread
   int es = p.eA[i] + p.eB[j];
   cmw<WC> v = c_make(crt_value<WC>(p, cc, i, j, es), crt_value<WC>(p, cc, i, j + p.n, es));
   if (p.sgn < 0) v = c_make(mw_neg(v.re), mw_neg(v.im));
   if (p.base) v = c_add(v, c_load<WC, WC>(p.base, (size_t)e));
   if (p.base_identity && i == j) v.re = mw_add_d(v.re, 1.0);
+  if (p.hermitian && i == j) v.im = mw_zero<WC>();
   c_store(p.C, (size_t)e, v);
+  if (p.hermitian && i < j) c_store(p.C, (size_t)j + (size_t)i * p.m, c_conj(v));
 }
 
 // ------------------------------------------------------------------------------------------------
@@ -750,6 +762,8 @@ zkq_status mw_gemm_batched(const MwProd* prods, int count, int wa, int wb, int w
     std::memset(&o, 0, sizeof(o));
     o.m = q.m; o.n = q.n; o.k = q.k; o.opA = q.opA;
     o.A = q.A; o.B = q.B; o.C = q.C; o.base = q.base; o.sgn = q.sgn; o.base_identity = q.base_identity;
+    o.hermitian = (q.hermitian && q.m == q.n) ? 1 : 0;
+    o.sliceA = o.sliceB = 1;
     o.mp = (q.m + OZ_BM - 1) / OZ_BM * OZ_BM;
     o.np2 = (2 * q.n + OZ_BN - 1) / OZ_BN * OZ_BN;
     o.kp = (2 * q.k + 63) / 64 * 64;            // multiple of both kernels' K step
@@ -794,10 +808,22 @@ zkq_status mw_gemm_batched(const MwProd* prods, int count, int wa, int wb, int w
   size_t off = 0;
   std::vector<size_t> oA(count), oB(count), oD(count), oe(count);
   size_t max_mkp = 0, max_nkp = 0;
+  // operands shared by several products of the batch (same matrix, same role) are split once
+  std::vector<int> srcA(count), srcB(count);
+  for (int i = 0; i < count; ++i) {
+    srcA[i] = i; srcB[i] = i;
+    for (int j = 0; j < i; ++j) {
+      const OzProd &a = dp[i], &b = dp[j];
+      if (srcA[i] == i && srcA[j] == j && a.A == b.A && a.opA == b.opA && a.m == b.m && a.k == b.k) srcA[i] = j;
+      if (srcB[i] == i && srcB[j] == j && a.B == b.B && a.n == b.n && a.k == b.k) srcB[i] = j;
+    }
+    if (srcA[i] != i) dp[i].sliceA = 0;
+    if (srcB[i] != i) dp[i].sliceB = 0;
+  }
   for (int i = 0; i < count; ++i) {
     OzProd& o = dp[i];
-    oA[i] = off; off += al((size_t)plan.sA * o.mp * o.kp * sizeof(__half));
-    oB[i] = off; off += al((size_t)plan.sB * o.np2 * o.kp * sizeof(__half));
+    oA[i] = off; if (o.sliceA) off += al((size_t)plan.sA * o.mp * o.kp * sizeof(__half));
+    oB[i] = off; if (o.sliceB) off += al((size_t)plan.sB * o.np2 * o.kp * sizeof(__half));
     oD[i] = off; off += al((size_t)(crt ? 3 * cc.r : plan.S + 1) * o.mp * o.np2 * sizeof(int32_t));
     oe[i] = off; off += al((size_t)(o.m + o.n) * sizeof(int32_t));
     max_mkp = std::max(max_mkp, (size_t)o.mp * o.kp);
@@ -811,8 +837,22 @@ zkq_status mw_gemm_batched(const MwProd* prods, int count, int wa, int wb, int w
     OzProd& o = dp[i];
     o.Ahat = (__half*)(base + oA[i]); o.Bhat = (__half*)(base + oB[i]);
     o.D = (int32_t*)(base + oD[i]); o.eA = (int32_t*)(base + oe[i]); o.eB = o.eA + o.m;
+  }
+  for (int i = 0; i < count; ++i) {                // shared operands point at the first product's planes
+    OzProd& o = dp[i];
+    if (!o.sliceA) { o.Ahat = dp[srcA[i]].Ahat; o.eA = dp[srcA[i]].eA; }
+    if (!o.sliceB) { o.Bhat = dp[srcB[i]].Bhat; o.eB = dp[srcB[i]].eB; }
     for (int ti = 0; ti < o.mp / OZ_BM; ++ti)
-      for (int tj = 0; tj < o.np2 / OZ_BN; ++tj) tiles.push_back({i, ti, tj});
+      for (int tj = 0; tj < o.np2 / OZ_BN; ++tj) {
+        if (o.hermitian) {
+          // keep the tile if one of its columns j (re block: j', im block: j' - n) reaches row ti*BM
+          int c0 = tj * OZ_BN, c1 = std::min(c0 + OZ_BN, 2 * o.n), jmax = -1;
+          if (c0 < o.n) jmax = std::max(jmax, std::min(c1, o.n) - 1);
+          if (c1 > o.n) jmax = std::max(jmax, c1 - 1 - o.n);
+          if (jmax < ti * OZ_BM) continue;
+        }
+        tiles.push_back({i, ti, tj});
+      }
   }
   // biggest problems first (their tiles run longest: K' is larger)
   std::stable_sort(tiles.begin(), tiles.end(), [&](const OzTile& a, const OzTile& c) { return dp[a.prod].kp > dp[c.prod].kp; });

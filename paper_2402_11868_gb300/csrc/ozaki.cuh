@@ -15,6 +15,8 @@ struct MwProd {
   int m, n, k, opA;
   const double* A; const double* B; double* C; const double* base;
   double sgn; int base_identity;
+  int hermitian = 0;             // C is Hermitian (m == n): only tiles touching i <= j are computed and the
+                                 // lower triangle is written as the conjugate of the upper one
 };
 
 // device-side layout of one product inside the Ozaki workspace
@@ -27,6 +29,8 @@ struct OzProd {
   int32_t* D;                    // [S+1][mp][np2] (levels 2..S used)
   int32_t* eA;                   // row exponents of op(A) (m)
   int32_t* eB;                   // column exponents of B (n)
+  int hermitian;
+  int sliceA, sliceB;            // 0: the planes are shared with an earlier product of the batch
 };
 
 struct OzPair { int16_t t, u; int16_t level; int16_t flags; };   // flags: 1 chunk end, 2 level end
