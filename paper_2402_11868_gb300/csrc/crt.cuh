@@ -32,7 +32,22 @@ struct CrtConst {
   uint32_t M32[CRT_L32];
   uint32_t Mhalf32[CRT_L32];
   uint32_t minv[CRT_MAXR];           // floor(2^32 / m_i) + 1: division-free reduction of sums < 2^29
+  int l32;                           // 32-bit limbs that hold M with 16 bits of headroom (<= CRT_L32)
+  int hdig;                          // 16-bit digits that hold a split half (|A_h|, A_l < 2^(16 hdig))
+  int tbits;                         // bits (with sign) of the reconstructed C' = A' B', bounded by K' 2^(2q-4)
 };
+
+// v mod m in [0, m) for |v| < 2^29 without division: minv = floor(2^32 / m) + 1 makes
+// umulhi(|v|, minv) equal to floor(|v| / m) or one more
+#ifdef __CUDACC__
+__device__ __forceinline__ uint32_t crt_mod(int v, uint32_t m, uint32_t minv) {
+  const uint32_t a = (uint32_t)(v < 0 ? -v : v);
+  int res = (int)(a - __umulhi(a, minv) * m);
+  if (res < 0) res += (int)m;
+  if (v < 0 && res) res = (int)m - res;
+  return (uint32_t)res;
+}
+#endif
 
 // host-side construction (moduli, weights); max_kprime decides the modulus bound
 bool crt_build(int max_kprime, int p_out_bits, CrtConst* out);

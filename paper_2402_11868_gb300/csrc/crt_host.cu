@@ -85,6 +85,12 @@ bool crt_build(int max_kprime, int p_out_bits, CrtConst* out) {
     uint32_t p = 1 % m;
     for (int j = 0; j < 20; ++j) { out->pw16[i][j] = (uint8_t)p; p = (uint32_t)(((uint64_t)p << 16) % m); }
   }
+  out->l32 = (int)std::ceil((bits + 16.0) / 32.0);
+  if (out->l32 > CRT_L32) return false;
+  out->hdig = (std::max(q - 2 - s, s) + 1 + 15) / 16;
+  if (out->hdig > 20) return false;
+  out->tbits = 2 * q - 4 + lg + 2;
+  if (out->tbits > 64 * (CRT_L + 1) - 1) return false;
   // M as double * 2^exp (from its top 64 bits)
   int top = CRT_L - 1; while (top > 0 && out->M[top] == 0) --top;
   double v = (double)out->M[top] + (top > 0 ? std::ldexp((double)out->M[top - 1], -64) : 0.0);

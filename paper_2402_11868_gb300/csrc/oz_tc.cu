@@ -1,6 +1,7 @@
 // tcgen05 slice GEMM (see oz_tc.cuh).
 #include "oz_tc.cuh"
 #include "common.cuh"
+#include "crt.cuh"
 
 namespace zkq {
 
@@ -53,7 +54,8 @@ __device__ __forceinline__ void cp_async16_tc(uint32_t dst, const void* src) {
 __device__ __forceinline__ int sw128(int row, int chunk) { return row * 128 + ((chunk ^ (row & 7)) << 4); }
 
 __global__ void __launch_bounds__(128, 1) oz_tc_kernel(const OzProd* __restrict__ P, const OzTile* __restrict__ tiles,
-                                                       const OzPair* __restrict__ pairs, int npairs, int* err) {
+                                                       const OzPair* __restrict__ pairs, int npairs,
+                                                       const CrtConst* __restrict__ cc, int* err) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   // 1024-byte aligned carve-out for the swizzled stages
   unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
@@ -174,12 +176,29 @@ __global__ void __launch_bounds__(128, 1) oz_tc_kernel(const OzProd* __restrict_
       if (pr.flags & 2) {
         // row = tile row of this thread (TMEM lane), 128 consecutive columns
         const int r = tl.ti * TC_BM + warp * 32 + lane;
-        int32_t* D = p.D + (size_t)pr.level * p.mp * p.np2 + (size_t)r * p.np2 + (size_t)tl.tj * TC_BN;
+        const size_t off = (size_t)pr.level * p.mp * p.np2 + (size_t)r * p.np2 + (size_t)tl.tj * TC_BN;
+        if (cc) {
+          // CRT form: residues modulo the level's modulus, one byte each
+          const int t = pr.level % cc->r;
+          const uint32_t m = (uint32_t)cc->m[t], minv = cc->minv[t];
+          uint8_t* D8 = reinterpret_cast<uint8_t*>(p.D) + off;
 #pragma unroll
-        for (int j = 0; j < TC_BN; j += 4) {
-          *reinterpret_cast<int4*>(D + j) = make_int4(dacc[j], dacc[j + 1], dacc[j + 2], dacc[j + 3]);
-          dacc[j] = dacc[j + 1] = dacc[j + 2] = dacc[j + 3] = 0;
+          for (int j = 0; j < TC_BN; j += 16) {
+            uint32_t w[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+              w[q] = crt_mod(dacc[j + 4 * q], m, minv) | (crt_mod(dacc[j + 4 * q + 1], m, minv) << 8) |
+                     (crt_mod(dacc[j + 4 * q + 2], m, minv) << 16) | (crt_mod(dacc[j + 4 * q + 3], m, minv) << 24);
+            *reinterpret_cast<uint4*>(D8 + j) = make_uint4(w[0], w[1], w[2], w[3]);
+          }
+        } else {
+          int32_t* D = p.D + off;
+#pragma unroll
+          for (int j = 0; j < TC_BN; j += 4)
+            *reinterpret_cast<int4*>(D + j) = make_int4(dacc[j], dacc[j + 1], dacc[j + 2], dacc[j + 3]);
         }
+#pragma unroll
+        for (int j = 0; j < TC_BN; ++j) dacc[j] = 0;
       }
       __syncthreads();          // the accumulator is free again before the next pair's first MMA
     }
@@ -203,11 +222,11 @@ __global__ void __launch_bounds__(128, 1) oz_tc_kernel(const OzProd* __restrict_
 
 size_t oz_tc_smem_bytes() { return (size_t)TC_STAGES * (TC_BM + TC_BN) * 128 + 1024; }
 
-zkq_status launch_oz_tc(const OzProd* d_p, const OzTile* d_t, int ntiles, const OzPair* d_q, int npairs, int* d_err,
-                        cudaStream_t st) {
+zkq_status launch_oz_tc(const OzProd* d_p, const OzTile* d_t, int ntiles, const OzPair* d_q, int npairs,
+                        const CrtConst* d_c, int* d_err, cudaStream_t st) {
   size_t sm = oz_tc_smem_bytes();
   ZKQ_CUDA_TRY(cudaFuncSetAttribute(oz_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-  oz_tc_kernel<<<ntiles, 128, sm, st>>>(d_p, d_t, d_q, npairs, d_err);
+  oz_tc_kernel<<<ntiles, 128, sm, st>>>(d_p, d_t, d_q, npairs, d_c, d_err);
   ZKQ_CUDA_TRY(cudaGetLastError());
   return ZKQ_OK;
 }

@@ -261,7 +261,8 @@ __device__ __forceinline__ void cp_async16(uint32_t dst, const void* src) {
 __device__ __forceinline__ int swz(int row, int chunk) { return row * 64 + ((chunk ^ ((row >> 1) & 3)) << 4); }
 
 __global__ void __launch_bounds__(256) oz_gemm_kernel(const OzProd* __restrict__ P, const OzTile* __restrict__ tiles,
-                                                      const OzPair* __restrict__ pairs, int npairs, int S) {
+                                                      const OzPair* __restrict__ pairs, int npairs, int S,
+                                                      const CrtConst* __restrict__ cc) {
   extern __shared__ __align__(128) unsigned char smem[];
   const OzTile tl = tiles[blockIdx.x];
   const OzProd p = P[tl.prod];
@@ -346,15 +347,26 @@ __global__ void __launch_bounds__(256) oz_gemm_kernel(const OzProd* __restrict__
             for (int c = 0; c < 4; ++c) { dacc[a][b2][c] += __float2int_rn(acc[a][b2][c]); acc[a][b2][c] = 0.f; }
       }
       if (pr.flags & 2) {
-        int32_t* D = p.D + (size_t)pr.level * p.mp * p.np2;
+        const size_t po = (size_t)pr.level * p.mp * p.np2;
+        uint32_t m = 0, minv = 0;
+        if (cc) { const int t = pr.level % cc->r; m = (uint32_t)cc->m[t]; minv = cc->minv[t]; }
 #pragma unroll
         for (int mi = 0; mi < 4; ++mi)
 #pragma unroll
           for (int ni = 0; ni < 4; ++ni) {
             int r = tl.ti * OZ_BM + wm * 64 + mi * 16 + (lane >> 2);
             int c = tl.tj * OZ_BN + wn * 32 + ni * 8 + (lane & 3) * 2;
-            *reinterpret_cast<int2*>(D + (size_t)r * p.np2 + c) = make_int2(dacc[mi][ni][0], dacc[mi][ni][1]);
-            *reinterpret_cast<int2*>(D + (size_t)(r + 8) * p.np2 + c) = make_int2(dacc[mi][ni][2], dacc[mi][ni][3]);
+            if (cc) {                            // CRT form: residues, one byte each
+              uint8_t* D8 = reinterpret_cast<uint8_t*>(p.D) + po;
+              *reinterpret_cast<uchar2*>(D8 + (size_t)r * p.np2 + c) =
+                  make_uchar2((uint8_t)crt_mod(dacc[mi][ni][0], m, minv), (uint8_t)crt_mod(dacc[mi][ni][1], m, minv));
+              *reinterpret_cast<uchar2*>(D8 + (size_t)(r + 8) * p.np2 + c) =
+                  make_uchar2((uint8_t)crt_mod(dacc[mi][ni][2], m, minv), (uint8_t)crt_mod(dacc[mi][ni][3], m, minv));
+            } else {
+              int32_t* D = p.D + po;
+              *reinterpret_cast<int2*>(D + (size_t)r * p.np2 + c) = make_int2(dacc[mi][ni][0], dacc[mi][ni][1]);
+              *reinterpret_cast<int2*>(D + (size_t)(r + 8) * p.np2 + c) = make_int2(dacc[mi][ni][2], dacc[mi][ni][3]);
+            }
             dacc[mi][ni][0] = dacc[mi][ni][1] = dacc[mi][ni][2] = dacc[mi][ni][3] = 0;
           }
       }
@@ -379,9 +391,10 @@ __device__ __forceinline__ mw<WC> combine_value(const OzProd& p, int i, int col,
 template <int WC>
 __global__ void oz_combine_kernel(const OzProd* __restrict__ P, int b, int S) {
   const OzProd p = P[blockIdx.y];
-  int e = blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= p.m * p.n) return;
-  int i = e % p.m, j = e / p.m;
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= p.m * p.n) return;
+  const int j = t % p.n, i = t / p.n;          // columns fastest: the planes are row-major [i][col]
+  const size_t e = (size_t)i + (size_t)j * p.m;
   if (p.hermitian && i > j) return;
   int es = p.eA[i] + p.eB[j];
   cmw<WC> v = c_make(combine_value<WC>(p, i, j, es, b, S), combine_value<WC>(p, i, j + p.n, es, b, S));
@@ -478,37 +491,16 @@ template <int L> __device__ double bl_round_off(BigL<L>& R, int scale) {
   return ng ? -v : v;
 }
 
-// residues of q-bit scaled integers modulo every m_i, symmetric, written as fp16 planes [r][rows][kp]
-// symmetric residues of the signed integer X modulo every m_i into planes [plane0 + i]
-__device__ __forceinline__ void crt_emit(Big X, const CrtConst* __restrict__ cc, __half* out, size_t plane, size_t e,
-                                         int plane0) {
-  bool ng = big_neg(X);
-  if (ng) big_negate(X);
-  uint32_t d[20];
-#pragma unroll
-  for (int j = 0; j < 20; ++j) d[j] = (uint32_t)((X.l[j >> 2] >> (16 * (j & 3))) & 0xFFFF);
-  const int r = cc->r;
-  for (int i = 0; i < r; ++i) {
-    const int m = cc->m[i];
-    uint32_t s = 0;
-#pragma unroll
-    for (int j = 0; j < 20; ++j) s += d[j] * (uint32_t)cc->pw16[i][j];
-    // s < 2^29: q = floor(s * (floor(2^32/m) + 1) / 2^32) is floor(s/m) or one more
-    uint32_t qq = __umulhi(s, cc->minv[i]);
-    int res = (int)(s - qq * (uint32_t)m);
-    if (res < 0) res += m;
-    if (ng && res) res = m - res;
-    if (res > m / 2) res -= m;
-    out[(size_t)(plane0 + i) * plane + e] = __int2half_rn(res);
-  }
-}
-// q-bit scaled integer X = A_h 2^s + A_l: residues of A_h into planes [0, r), of A_l into [r, 2r)
-template <int K>
-__device__ __forceinline__ void crt_residues(const double* w, int fix, bool negate, const CrtConst* __restrict__ cc,
-                                             __half* out, size_t plane, size_t e) {
-  Big X; to_fixed<K>(w, fix, negate, X);
-  const int s = cc->s;
+// Residue planes of the CRT form.  X (q-bit scaled integer of one operand entry) = A_h 2^s + A_l with
+// 0 <= A_l < 2^s; the symmetric residues of A_h and A_l modulo every m_i are written as fp16 planes
+// [i][rows][kp] and [r + i][rows][kp].  A half below 2^(16 HD) is a sum of HD 16-bit digits d_j, and
+// A mod m = sum_j d_j (2^(16 j) mod m) mod m with the digit sum below 2^29.
+struct CrtHalves { uint32_t dh[20], dl[20]; bool nh; };
+
+template <int HD>
+__device__ __forceinline__ void crt_halves(const Big& X, int s, CrtHalves& o) {
   Big lo = X;                                  // low s bits (two's complement residue, nonnegative)
+#pragma unroll
   for (int i = 0; i < 5; ++i) {
     int b0 = 64 * i;
     if (b0 >= s) lo.l[i] = 0;
@@ -516,71 +508,139 @@ __device__ __forceinline__ void crt_residues(const double* w, int fix, bool nega
   }
   Big hi;                                      // floor(X / 2^s): arithmetic shift
   {
-    int ls = s >> 6, bs = s & 63;
+    const int ls = s >> 6, bs = s & 63;
+    const uint64_t sx = big_neg(X) ? ~0ULL : 0ULL;
+#pragma unroll
     for (int i = 0; i < 5; ++i) {
       int src = i + ls;
-      uint64_t a = src < 5 ? X.l[src] : (big_neg(X) ? ~0ULL : 0ULL);
-      uint64_t b = src + 1 < 5 ? X.l[src + 1] : (big_neg(X) ? ~0ULL : 0ULL);
+      uint64_t a = src < 5 ? X.l[src] : sx;
+      uint64_t b = src + 1 < 5 ? X.l[src + 1] : sx;
       hi.l[i] = bs ? ((a >> bs) | (b << (64 - bs))) : a;
     }
   }
-  crt_emit(hi, cc, out, plane, e, 0);
-  crt_emit(lo, cc, out, plane, e, cc->r);
+  o.nh = big_neg(hi);
+  if (o.nh) big_negate(hi);
+#pragma unroll
+  for (int j = 0; j < HD; ++j) {
+    o.dh[j] = (uint32_t)((hi.l[j >> 2] >> (16 * (j & 3))) & 0xFFFF);
+    o.dl[j] = (uint32_t)((lo.l[j >> 2] >> (16 * (j & 3))) & 0xFFFF);
+  }
 }
 
-template <int WA>
+// symmetric residue of sign * (digit sum) modulo m as fp16
+__device__ __forceinline__ __half crt_sym(uint32_t sum, bool neg, uint32_t m, uint32_t minv) {
+  int res = (int)(sum - __umulhi(sum, minv) * m);
+  if (res < 0) res += (int)m;
+  if (neg && res) res = (int)m - res;
+  if (res > (int)(m >> 1)) res -= (int)m;
+  return __int2half_rn(res);
+}
+
+// per-modulus constants in shared memory: [m, minv, pw_0 .. pw_{HD-1}] for every modulus
+template <int HD>
+__device__ __forceinline__ void crt_stage_consts(const CrtConst* __restrict__ cc, uint32_t* sc) {
+  const int r = cc->r;
+  for (int x = threadIdx.x; x < r * (HD + 2); x += blockDim.x) {
+    const int i = x / (HD + 2), k = x % (HD + 2);
+    sc[x] = k == 0 ? (uint32_t)cc->m[i] : (k == 1 ? cc->minv[i] : (uint32_t)cc->pw16[i][k - 2]);
+  }
+  __syncthreads();
+}
+
+// residues of two neighbouring entries (e0, e0 + 1 of every plane) from their halves
+template <int HD>
+__device__ __forceinline__ void crt_emit2(const CrtHalves& a, const CrtHalves& b, int r, const uint32_t* sc,
+                                          __half* out, size_t plane, size_t e0) {
+  for (int i = 0; i < r; ++i) {
+    const uint32_t* c = sc + i * (HD + 2);
+    const uint32_t m = c[0], minv = c[1];
+    uint32_t ha = 0, la = 0, hb = 0, lb = 0;
+#pragma unroll
+    for (int j = 0; j < HD; ++j) {
+      const uint32_t pw = c[2 + j];
+      ha += a.dh[j] * pw; la += a.dl[j] * pw; hb += b.dh[j] * pw; lb += b.dl[j] * pw;
+    }
+    *reinterpret_cast<__half2*>(out + (size_t)i * plane + e0) =
+        __halves2half2(crt_sym(ha, a.nh, m, minv), crt_sym(hb, b.nh, m, minv));
+    *reinterpret_cast<__half2*>(out + (size_t)(r + i) * plane + e0) =
+        __halves2half2(crt_sym(la, false, m, minv), crt_sym(lb, false, m, minv));
+  }
+}
+
+// A planes: two neighbouring K' entries of one row of op(A) per thread (kp is even)
+template <int WA, int HD>
 __global__ void crt_slice_A_kernel(const OzProd* __restrict__ P, const CrtConst* __restrict__ cc) {
+  __shared__ uint32_t sc[CRT_MAXR * (HD + 2)];
   const OzProd p = P[blockIdx.y];
   if (!p.sliceA) return;
-  size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-  size_t tot = (size_t)p.mp * p.kp;
-  if (e >= tot) return;
-  int i = (int)(e / p.kp), lp = (int)(e % p.kp);
-  const size_t plane = tot;
+  crt_stage_consts<HD>(cc, sc);
+  const size_t e0 = 2 * ((size_t)blockIdx.x * blockDim.x + threadIdx.x);
+  const size_t tot = (size_t)p.mp * p.kp;
+  if (e0 >= tot) return;
+  const int i = (int)(e0 / p.kp), lp = (int)(e0 % p.kp);
+  const int r = cc->r;
   if (i >= p.m || lp >= 2 * p.k) {
-    for (int t = 0; t < 2 * cc->r; ++t) p.Ahat[t * plane + e] = __float2half_rn(0.0f);
+    for (int t = 0; t < 2 * r; ++t) *reinterpret_cast<__half2*>(p.Ahat + t * tot + e0) = __float2half2_rn(0.0f);
     return;
   }
-  bool im = lp >= p.k;
-  int l = im ? lp - p.k : lp;
-  const double* q = p.opA ? p.A + ((size_t)l + (size_t)i * p.k) * 2 * WA : p.A + ((size_t)i + (size_t)l * p.m) * 2 * WA;
-  crt_residues<WA>(q + (im ? WA : 0), cc->q - p.eA[i], im && p.opA, cc, p.Ahat, plane, e);
+  CrtHalves h[2];
+#pragma unroll
+  for (int u = 0; u < 2; ++u) {
+    const bool im = lp + u >= p.k;
+    const int l = im ? lp + u - p.k : lp + u;
+    const double* q = p.opA ? p.A + ((size_t)l + (size_t)i * p.k) * 2 * WA : p.A + ((size_t)i + (size_t)l * p.m) * 2 * WA;
+    Big X; to_fixed<WA>(q + (im ? WA : 0), cc->q - p.eA[i], im && p.opA, X);
+    crt_halves<HD>(X, cc->s, h[u]);
+  }
+  crt_emit2<HD>(h[0], h[1], r, sc, p.Ahat, tot, e0);
 }
 
-template <int WB>
+// B planes: column j' of [Re | Im] output, rows [Re; Im] of K' (real embedding of the complex product)
+template <int WB, int HD>
 __global__ void crt_slice_B_kernel(const OzProd* __restrict__ P, const CrtConst* __restrict__ cc) {
+  __shared__ uint32_t sc[CRT_MAXR * (HD + 2)];
   const OzProd p = P[blockIdx.y];
   if (!p.sliceB) return;
-  size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-  size_t tot = (size_t)p.np2 * p.kp;
-  if (e >= tot) return;
-  int jp = (int)(e / p.kp), lp = (int)(e % p.kp);
-  const size_t plane = tot;
+  crt_stage_consts<HD>(cc, sc);
+  const size_t e0 = 2 * ((size_t)blockIdx.x * blockDim.x + threadIdx.x);
+  const size_t tot = (size_t)p.np2 * p.kp;
+  if (e0 >= tot) return;
+  const int jp = (int)(e0 / p.kp), lp = (int)(e0 % p.kp);
+  const int r = cc->r;
   if (jp >= 2 * p.n || lp >= 2 * p.k) {
-    for (int t = 0; t < 2 * cc->r; ++t) p.Bhat[t * plane + e] = __float2half_rn(0.0f);
+    for (int t = 0; t < 2 * r; ++t) *reinterpret_cast<__half2*>(p.Bhat + t * tot + e0) = __float2half2_rn(0.0f);
     return;
   }
-  bool imcol = jp >= p.n;
-  int j = imcol ? jp - p.n : jp;
-  bool lower = lp >= p.k;
-  int l = lower ? lp - p.k : lp;
-  bool use_im = imcol ? !lower : lower;
-  bool negate = !imcol && lower;
-  const double* q = p.B + ((size_t)l + (size_t)j * p.k) * 2 * WB + (use_im ? WB : 0);
-  crt_residues<WB>(q, cc->q - p.eB[j], negate, cc, p.Bhat, plane, e);
+  const bool imcol = jp >= p.n;
+  const int j = imcol ? jp - p.n : jp;
+  CrtHalves h[2];
+#pragma unroll
+  for (int u = 0; u < 2; ++u) {
+    const bool lower = lp + u >= p.k;
+    const int l = lower ? lp + u - p.k : lp + u;
+    const bool use_im = imcol ? !lower : lower;
+    const bool negate = !imcol && lower;
+    const double* q = p.B + ((size_t)l + (size_t)j * p.k) * 2 * WB + (use_im ? WB : 0);
+    Big X; to_fixed<WB>(q, cc->q - p.eB[j], negate, X);
+    crt_halves<HD>(X, cc->s, h[u]);
+  }
+  crt_emit2<HD>(h[0], h[1], r, sc, p.Bhat, tot, e0);
 }
 
 // symmetric (sum_i c_i w_i mod M) from residues c_i; 32-bit limbs with 64-bit lazy accumulators (every
 // product c w_limb < 2^40, at most 96 of them per limb), one carry pass at the end.
 // out: signed two's complement, CRT_L32 + 2 limbs.
-__device__ __forceinline__ void crt_sum32(const int* c, const CrtConst* __restrict__ cc, uint32_t* out) {
-  constexpr int L = CRT_L32 + 2;
+// residue(t) yields c_t in [0, m_t).
+template <int LW, typename Res>   // LW: 32-bit limbs of M (>= cc->l32); the output has LW + 2 limbs
+__device__ __forceinline__ void crt_sum32(Res&& residue, const CrtConst* __restrict__ cc, uint32_t* out) {
+  constexpr int L = LW + 2;
+  constexpr int CRT_L32 = LW;
   uint64_t acc[CRT_L32];
 #pragma unroll
   for (int k = 0; k < CRT_L32; ++k) acc[k] = 0;
   const int r = cc->r;
   for (int t = 0; t < r; ++t) {
-    const uint64_t ct = (uint64_t)c[t];
+    const uint64_t ct = (uint64_t)residue(t);
     const uint32_t* w = cc->w32[t];
 #pragma unroll
     for (int k = 0; k < CRT_L32; ++k) acc[k] += ct * w[k];
@@ -636,32 +696,21 @@ __device__ __forceinline__ void crt_sum32(const int* c, const CrtConst* __restri
   for (int k = 0; k < L; ++k) out[k] = S[k];
 }
 
-// C' = C_hh 2^(2s) + (C_hl + C_lh) 2^s, value = C' 2^(e_i + f_j - 2q)
-template <int WC>
+// C' = C_hh 2^(2s) + (C_hl + C_lh) 2^s, value = C' 2^(e_i + f_j - 2q); LT 64-bit limbs hold C' (tbits)
+template <int WC, int LW, int LT>
 __device__ __forceinline__ mw<WC> crt_value(const OzProd& p, const CrtConst* __restrict__ cc, int i, int col, int es) {
-  constexpr int L32 = CRT_L32 + 2;
+  constexpr int L32 = LW + 2;
   const int r = cc->r, s = cc->s;
-  int c[CRT_MAXR];
-  const size_t stride = (size_t)p.mp * p.np2, base = (size_t)i * p.np2 + col;
-  // v mod m in [0, m) without division, |v| < 2^29 (minv = floor(2^32/m) + 1)
-  auto modm = [&](int v, int t) {
-    const uint32_t m = (uint32_t)cc->m[t];
-    uint32_t a = (uint32_t)(v < 0 ? -v : v);
-    int res = (int)(a - __umulhi(a, cc->minv[t]) * m);
-    if (res < 0) res += (int)m;
-    if (v < 0 && res) res = (int)m - res;
-    return res;
-  };
-  for (int t = 0; t < r; ++t) c[t] = modm(p.D[(size_t)t * stride + base], t);
+  const size_t stride = (size_t)p.mp * p.np2;
+  const uint8_t* D8 = reinterpret_cast<const uint8_t*>(p.D) + (size_t)i * p.np2 + col;   // residues in [0, m_t)
   uint32_t hh[L32], sm[L32];
-  crt_sum32(c, cc, hh);
-  for (int t = 0; t < r; ++t) {
-    int v = p.D[(size_t)(r + t) * stride + base] + p.D[(size_t)(2 * r + t) * stride + base];   // |v| < 2^25
-    c[t] = modm(v, t);
-  }
-  crt_sum32(c, cc, sm);
+  crt_sum32<LW>([&](int t) { return (int)__ldg(D8 + (size_t)t * stride); }, cc, hh);
+  crt_sum32<LW>([&](int t) {
+    const int v = (int)__ldg(D8 + (size_t)(r + t) * stride) + (int)__ldg(D8 + (size_t)(2 * r + t) * stride);
+    return v >= cc->m[t] ? v - cc->m[t] : v;
+  }, cc, sm);
   // T = hh 2^(2s) + sm 2^s as a signed 64-bit-limb integer (sign-extended shifts of 32-bit limbs)
-  constexpr int L = CRT_L + 1;
+  constexpr int L = LT;
   BigL<L> T; bl_zero(T);
   auto add_shifted32 = [&](const uint32_t* X, int sh) {
     const bool ng = (int32_t)X[L32 - 1] < 0;
@@ -696,15 +745,16 @@ __device__ __forceinline__ mw<WC> crt_value(const OzProd& p, const CrtConst* __r
   return out;
 }
 
-template <int WC>
+template <int WC, int LW, int LT>
 __global__ void crt_combine_kernel(const OzProd* __restrict__ P, const CrtConst* __restrict__ cc) {
   const OzProd p = P[blockIdx.y];
-  int e = blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= p.m * p.n) return;
-  int i = e % p.m, j = e / p.m;
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= p.m * p.n) return;
+  const int j = t % p.n, i = t / p.n;          // columns fastest: the planes are row-major [i][col]
+  const size_t e = (size_t)i + (size_t)j * p.m;
   if (p.hermitian && i > j) return;            // written by the (j, i) thread
   int es = p.eA[i] + p.eB[j];
-  cmw<WC> v = c_make(crt_value<WC>(p, cc, i, j, es), crt_value<WC>(p, cc, i, j + p.n, es));
+  cmw<WC> v = c_make(crt_value<WC, LW, LT>(p, cc, i, j, es), crt_value<WC, LW, LT>(p, cc, i, j + p.n, es));
   if (p.sgn < 0) v = c_make(mw_neg(v.re), mw_neg(v.im));
   if (p.base) v = c_add(v, c_load<WC, WC>(p.base, (size_t)e));
   if (p.base_identity && i == j) v.re = mw_add_d(v.re, 1.0);
@@ -824,7 +874,7 @@ zkq_status mw_gemm_batched(const MwProd* prods, int count, int wa, int wb, int w
     OzProd& o = dp[i];
     oA[i] = off; if (o.sliceA) off += al((size_t)plan.sA * o.mp * o.kp * sizeof(__half));
     oB[i] = off; if (o.sliceB) off += al((size_t)plan.sB * o.np2 * o.kp * sizeof(__half));
-    oD[i] = off; off += al((size_t)(crt ? 3 * cc.r : plan.S + 1) * o.mp * o.np2 * sizeof(int32_t));
+    oD[i] = off; off += al(crt ? (size_t)3 * cc.r * o.mp * o.np2 : (size_t)(plan.S + 1) * o.mp * o.np2 * sizeof(int32_t));
     oe[i] = off; off += al((size_t)(o.m + o.n) * sizeof(int32_t));
     max_mkp = std::max(max_mkp, (size_t)o.mp * o.kp);
     max_nkp = std::max(max_nkp, (size_t)o.np2 * o.kp);
@@ -881,8 +931,17 @@ zkq_status mw_gemm_batched(const MwProd* prods, int count, int wa, int wb, int w
     dim3 gA((unsigned)((max_mkp + 255) / 256), count), gB((unsigned)((max_nkp + 255) / 256), count);
     ProfScope ps(PC_OZ_SLICE, st);
     if (crt) {
-      ZKQ_DISPATCH_W(wa, crt_slice_A_kernel, <<<gA, 256, 0, st>>>(d_p, d_c));
-      ZKQ_DISPATCH_W(wb, crt_slice_B_kernel, <<<gB, 256, 0, st>>>(d_p, d_c));
+      // two entries per thread; digits per half: 5 (double-double-sized products), 8 (quad-double), 20
+      dim3 gA2((unsigned)((max_mkp / 2 + 255) / 256), count), gB2((unsigned)((max_nkp / 2 + 255) / 256), count);
+#define ZKQ_CRT_SLICE(HD) \
+      if (wa == 1) crt_slice_A_kernel<1, HD><<<gA2, 256, 0, st>>>(d_p, d_c); \
+      else if (wa == 2) crt_slice_A_kernel<2, HD><<<gA2, 256, 0, st>>>(d_p, d_c); \
+      else crt_slice_A_kernel<4, HD><<<gA2, 256, 0, st>>>(d_p, d_c); \
+      if (wb == 1) crt_slice_B_kernel<1, HD><<<gB2, 256, 0, st>>>(d_p, d_c); \
+      else if (wb == 2) crt_slice_B_kernel<2, HD><<<gB2, 256, 0, st>>>(d_p, d_c); \
+      else crt_slice_B_kernel<4, HD><<<gB2, 256, 0, st>>>(d_p, d_c);
+      if (cc.hdig <= 5) { ZKQ_CRT_SLICE(5) } else if (cc.hdig <= 8) { ZKQ_CRT_SLICE(8) } else { ZKQ_CRT_SLICE(20) }
+#undef ZKQ_CRT_SLICE
     } else {
       ZKQ_DISPATCH_W(wa, oz_slice_A_kernel, <<<gA, 256, 0, st>>>(d_p, plan.b, plan.sA));
       ZKQ_DISPATCH_W(wb, oz_slice_B_kernel, <<<gB, 256, 0, st>>>(d_p, plan.b, plan.sB));
@@ -901,10 +960,10 @@ zkq_status mw_gemm_batched(const MwProd* prods, int count, int wa, int wb, int w
         ZKQ_CUDA_TRY(cudaMalloc(&g_oz_err, sizeof(int)));
         ZKQ_CUDA_TRY(cudaMemset(g_oz_err, 0, sizeof(int)));
       }
-      zkq_status ls = launch_oz_tc(d_p, d_t, (int)tiles.size(), d_q, plan.npairs, g_oz_err, st);
+      zkq_status ls = launch_oz_tc(d_p, d_t, (int)tiles.size(), d_q, plan.npairs, crt ? d_c : nullptr, g_oz_err, st);
       if (ls != ZKQ_OK) return ls;
     } else {
-      oz_gemm_kernel<<<(unsigned)tiles.size(), 256, sm, st>>>(d_p, d_t, d_q, plan.npairs, plan.S);
+      oz_gemm_kernel<<<(unsigned)tiles.size(), 256, sm, st>>>(d_p, d_t, d_q, plan.npairs, plan.S, crt ? d_c : nullptr);
     }
     ZKQ_CUDA_TRY(cudaGetLastError());
   }
@@ -912,9 +971,16 @@ zkq_status mw_gemm_batched(const MwProd* prods, int count, int wa, int wb, int w
     dim3 g((max_mn + 127) / 128, count);
     ProfScope ps(PC_OZ_COMBINE, st);
     if (crt) {
-      if (wc == 1) crt_combine_kernel<1><<<g, 128, 0, st>>>(d_p, d_c);
-      else if (wc == 2) crt_combine_kernel<2><<<g, 128, 0, st>>>(d_p, d_c);
-      else crt_combine_kernel<4><<<g, 128, 0, st>>>(d_p, d_c);
+      // limbs sized to M and C': double-double-sized products (M < 2^176, C' < 2^320), quad-double-sized
+      // (M < 2^272, C' < 2^512), else the largest
+#define ZKQ_CRT_COMB(LW, LT) \
+      if (wc == 1) crt_combine_kernel<1, LW, LT><<<g, 128, 0, st>>>(d_p, d_c); \
+      else if (wc == 2) crt_combine_kernel<2, LW, LT><<<g, 128, 0, st>>>(d_p, d_c); \
+      else crt_combine_kernel<4, LW, LT><<<g, 128, 0, st>>>(d_p, d_c);
+      if (cc.l32 <= 6 && cc.tbits <= 5 * 64 - 1) { ZKQ_CRT_COMB(6, 5) }
+      else if (cc.l32 <= 9 && cc.tbits <= 8 * 64 - 1) { ZKQ_CRT_COMB(9, 8) }
+      else { ZKQ_CRT_COMB(18, CRT_L + 1) }
+#undef ZKQ_CRT_COMB
     } else {
       if (wc == 1) oz_combine_kernel<1><<<g, 128, 0, st>>>(d_p, plan.b, plan.S);
       else if (wc == 2) oz_combine_kernel<2><<<g, 128, 0, st>>>(d_p, plan.b, plan.S);

@@ -26,7 +26,8 @@ struct OzProd {
   const double* A; const double* B; double* C; const double* base; double sgn; int base_identity;
   __half* Ahat;                  // [sA][mp][kp]
   __half* Bhat;                  // [sB][np2][kp]
-  int32_t* D;                    // [S+1][mp][np2] (levels 2..S used)
+  int32_t* D;                    // digit form: int32 [S+1][mp][np2] (levels 2..S used);
+                                 // CRT form: uint8 residues [3r][mp][np2] (cast), reduced in the GEMM epilogue
   int32_t* eA;                   // row exponents of op(A) (m)
   int32_t* eB;                   // column exponents of B (n)
   int hermitian;

@@ -36,7 +36,7 @@ def eig_footprint(n: int, a_words: int, target: int) -> int:
     kp = -(-2 * n // 64) * 64
     mp = -(-n // 128) * 128
     np2 = -(-2 * n // 128) * 128
-    scratch = 4 * (2 * 64 * (mp + np2) * kp * 2 + 3 * 32 * mp * np2 * 4)  # residue planes + level sums
+    scratch = 4 * (2 * 34 * (mp + np2) * kp * 2 + 3 * 34 * mp * np2)  # fp16 residue planes + uint8 GEMM residues
     return int(inputs + outputs + refine + scratch)
 
 
