@@ -10,6 +10,11 @@ Workloads (seeded, synthetic; see workloads/):
                    quad-double input; chosen path: Ogita-Aishima refinement with Ozaki split products
                    on tensor cores (default)
   single128_plain  one 128x128 problem, lambda_k = 2^-0.3(k-1), quad-double input, plain RQI path
+  brickwork40      MPS simulation of a 40-qubit brickwork circuit of Haar two-qubit gates (r_max = 256,
+                   quad-double, truncation 2^-200): one step = one layer of gates on disjoint bonds; the
+                   state keeps evolving, so the timed layers follow the warm-up layers (bond dimensions grow)
+  serve            continuous-batching engine under Poisson arrivals at 0.7x saturation: eigensolves (DD/QD,
+                   N <= 256) and gate updates on four MPS simulations; per-type p50/p99 latency
 The plain RQI path cannot resolve eigenvalues below the FP64 floor (2^-53 ||A||), so the same-accuracy
 comparison of the two paths is reported on single128 (both paths), beside the batch number.
 
@@ -46,7 +51,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="batch256_qd", choices=["batch256_qd", "single128_plain"])
+    ap.add_argument("--workload", default="batch256_qd", choices=["batch256_qd", "single128_plain", "brickwork40", "serve"])
     ap.add_argument("--count", type=int, default=256, help="problems in the batch workload")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-compare", action="store_true", help="skip the single128 chosen-vs-plain comparison")
@@ -242,36 +247,7 @@ def run_ours(args):
         e1.synchronize()
         e2e_ms.append(e0.elapsed_time(e1))
     e2e_value = R.pairs / (float(np.mean(e2e_ms)) / 1e3)
-    # dominant kernel class by device time in the timed region
-    peaks, peak_kind = measured_peaks()
-    dom = max(prof.items(), key=lambda kv: kv[1][0])
-    dom_name, (dom_ms, dom_n, dom_work) = dom
-    if dom_name == "ozaki_gemm":
-        peak = peaks.get("bf16_tflops_sustained", 1700.0)   # fp16 dense = bf16 dense rate
-        achieved = dom_work / (dom_ms / 1e3) / 1e12
-        roof = {"bound": "tensor", "kernel": "oz_gemm_kernel (mma.sync f16->f32 digit slices)", "achieved": achieved,
-                "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
-                "peak_source": f"{peak_kind} bf16_tflops_sustained (fp16 dense has the bf16 rate)",
-                "launches": dom_n, "avg_launch_ms": dom_ms / max(dom_n, 1)}
-    elif dom_name == "jacobi":
-        peak = 1.006   # measured DFMA throughput of this GB300 pool, TFLOP/s (FMA = 2 flops)
-        achieved = dom_work / (dom_ms / 1e3) / 1e12
-        roof = {"bound": "alu", "kernel": "jacobi_smem_kernel + jacobi_global_kernel (FP64 rotations)",
-                "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
-                "peak_source": "measured FP64 DFMA microbenchmark (MEASURED_PEAKS.json has no FP64 entry)",
-                "work": "48 n flops per applied rotation (24 n FMA: Hermitian 2x2-block update of A 12 n + V 12 n)",
-                "launches": dom_n, "avg_launch_ms": dom_ms / max(dom_n, 1)}
-    elif dom_name == "rqi":
-        it = 2.0
-        cmacs = sum(nn * (it * (nn ** 3 / 3.0 + nn * nn) + 2 * nn * nn) for nn in R.ns) * args.steps
-        achieved = cmacs * QD_CMAC_INSTR / (dom_ms / 1e3) / 1e12
-        roof = {"bound": "alu", "kernel": "rqi_kernel<4,4>", "achieved": achieved, "peak": FP64_INSTR_PEAK / 1e12,
-                "unit": "TFLOP/s", "frac": achieved / (FP64_INSTR_PEAK / 1e12), "traffic": None,
-                "peak_source": "measured DFMA issue rate (FP64 instructions/s, one op per DADD/DMUL/DFMA)",
-                "launches": dom_n, "avg_launch_ms": dom_ms / max(dom_n, 1)}
-    else:
-        roof = {"bound": "alu", "kernel": dom_name, "achieved": None, "peak": FP64_INSTR_PEAK / 1e12, "unit": "TFLOP/s",
-                "frac": None, "traffic": None, "launches": dom_n, "avg_launch_ms": dom_ms / max(dom_n, 1)}
+    roof = roofline(Z, prof, R.ns, args.steps)
     out = {
         "metric": METRIC, "value": value, "unit": "eigenpairs/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
@@ -324,6 +300,226 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+def roofline(Z, prof, ns, steps):
+    """Roofline object of the dominant kernel class (by device time in the timed region)."""
+    peaks, peak_kind = measured_peaks()
+    dom_name, (dom_ms, dom_n, dom_work) = max(prof.items(), key=lambda kv: kv[1][0])
+    base = {"launches": dom_n, "avg_launch_ms": dom_ms / max(dom_n, 1), "traffic": None}
+    if dom_name == "ozaki_gemm":
+        peak = peaks.get("bf16_tflops_sustained", 1700.0)   # fp16 dense = bf16 dense rate
+        achieved = dom_work / (dom_ms / 1e3) / 1e12
+        kern = ("oz_tc_kernel (tcgen05.mma kind::f16, TMEM accumulators)" if Z.zkq_get_gemm_kernel() == 1
+                else "oz_gemm_kernel (mma.sync f16->f32)")
+        return dict(base, bound="tensor", kernel=kern, achieved=achieved, peak=peak, unit="TFLOP/s",
+                    frac=achieved / peak, peak_source=f"{peak_kind} bf16_tflops_sustained (fp16 dense has the bf16 rate)",
+                    work="2 m (2n) (2k) flops per kept slice pair, unpadded sizes")
+    if dom_name in ("jacobi", "jacobi_cluster"):
+        peak = 1.006   # measured DFMA throughput of this GB300 pool, TFLOP/s (FMA = 2 flops)
+        achieved = dom_work / (dom_ms / 1e3) / 1e12
+        what = "FP64 eigensolve of the inputs" if dom_name == "jacobi" else "FP64 eigensolves of the refinement's cluster blocks"
+        return dict(base, bound="alu", kernel=f"jacobi_smem/global/grid_kernel ({what})",
+                    achieved=achieved, peak=peak, unit="TFLOP/s", frac=achieved / peak,
+                    peak_source="measured FP64 DFMA microbenchmark (MEASURED_PEAKS.json has no FP64 entry)",
+                    work="48 n flops per applied rotation (24 n FMA: Hermitian 2x2-block update of A 12 n + V 12 n)")
+    if dom_name == "rqi":
+        it = 2.0
+        cmacs = sum(nn * (it * (nn ** 3 / 3.0 + nn * nn) + 2 * nn * nn) for nn in ns) * steps
+        achieved = cmacs * QD_CMAC_INSTR / (dom_ms / 1e3) / 1e12
+        return dict(base, bound="alu", kernel="rqi_kernel<4,4>", achieved=achieved, peak=FP64_INSTR_PEAK / 1e12,
+                    unit="TFLOP/s", frac=achieved / (FP64_INSTR_PEAK / 1e12),
+                    peak_source="measured DFMA issue rate (FP64 instructions/s, one op per DADD/DMUL/DFMA)")
+    return dict(base, bound="alu", kernel=dom_name, achieved=None, peak=FP64_INSTR_PEAK / 1e12, unit="TFLOP/s",
+                frac=None)
+
+
+def run_brickwork(args):
+    """Two-qubit gate updates of a device-resident quad-double MPS (40 qubits, r_max 256): theta
+    contraction, Gram eigensolve (FP64 Jacobi + refinement), truncation and split back per gate."""
+    import torch
+    import paper_2402_11868_gb300 as Z
+    import workloads as W
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    n, r_max, words, tau = 40, 256, 4, 2.0 ** -200
+    layers = args.warmup + args.steps
+    gates, idx = [], 0                           # per layer: [(site, G)] on disjoint bonds
+    for t in range(layers):
+        layer = []
+        for s_ in range(t % 2, n - 1, 2):
+            layer.append((s_, W.haar_gate(3 + rank, idx, words)))
+            idx += 1
+        gates.append(layer)
+    ctx = Z.Context(local)
+    mps = Z.MPS(ctx, n, r_max=r_max, words=words)
+    stream = torch.cuda.Stream(device=dev)
+    for t in range(args.warmup):
+        for site, G in gates[t]:
+            mps.apply2q(site, G, trunc_tau=tau, stream=stream)
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    Z.zkq_profile_enable(True)
+    Z.zkq_profile_read()
+    if world > 1:
+        dist.barrier()
+    step_ms, ngates, rho_pairs, disc = [], 0, 0, 0.0
+    t_wall = time.perf_counter()
+    for t in range(args.warmup, layers):
+        e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for site, G in gates[t]:
+            chi = mps.bond_dims()
+            a = 1 if site == 0 else int(chi[site - 1])
+            d = 1 if site + 1 == n - 1 else int(chi[site + 1])
+            rho_pairs += 2 * min(a, d)
+            _, dw = mps.apply2q(site, G, trunc_tau=tau, stream=stream)
+            disc += dw
+            ngates += 1
+        e1.record(stream)
+        e1.synchronize()
+        step_ms.append(e0.elapsed_time(e1))
+    wall = time.perf_counter() - t_wall
+    torch.cuda.synchronize()
+    prof = Z.zkq_profile_read()
+    Z.zkq_profile_enable(False)
+    clk = clocks.stop()
+    total_ms = float(sum(step_ms))
+    if world > 1:
+        tt = torch.tensor([total_ms, wall], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        total_ms, wall = float(tt[0].item()), float(tt[1].item())
+    chi = mps.bond_dims()
+    out = {
+        "metric": "two-qubit gate updates/sec of a quad-double MPS (n=40, r_max=256)",
+        "value": ngates * world / (total_ms / 1e3), "unit": "gates/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "brickwork40", "desc": "40-qubit brickwork of Haar 4x4 gates, r_max 256, QD, tau 2^-200",
+                   "gates_timed": ngates, "layers_timed": args.steps, "max_bond_after": int(chi.max()),
+                   "discarded_weight": disc},
+        "eigenpairs_per_s": rho_pairs * world / (total_ms / 1e3),
+        "latency_ms": {"p50_layer": float(np.percentile(step_ms, 50)), "p99_layer": float(np.percentile(step_ms, 99)),
+                       "per_gate": total_ms / max(ngates, 1)},
+        "kernel_ms_per_step": {k: v[0] / args.steps for k, v in prof.items() if v[1]},
+        "roofline": roofline(Z, prof, [], args.steps),
+        "clocks": clk,
+        "e2e": {"value": ngates * world / wall, "unit": "gates/s",
+                "h2d_bytes_per_step": int(16 * 2 * words * 8 * ngates / args.steps),
+                "d2h_bytes_per_step": int(12 * ngates / args.steps)},
+        "gpu_launches": int(sum(v[1] for v in prof.values())),
+    }
+    mps.close()
+    ctx.close()
+    if rank == 0:
+        print(json.dumps(out))
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def run_serve(args):
+    """Continuous-batching request loop (paper_2402_11868_gb300.serve.Engine) under an open Poisson load:
+    eigensolve requests (double-double and quad-double, N <= 256 from the batch distribution) and two-qubit
+    gate requests on device-resident MPS simulations.  The arrival rate is 0.7x the throughput measured
+    with all warm-up requests submitted at once."""
+    import torch
+    import paper_2402_11868_gb300 as Z
+    import workloads as W
+    from paper_2402_11868_gb300.serve import Engine
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    per_step = 16
+    rng = np.random.default_rng(4 + rank)
+    eng = Engine(device=local, hbm_budget=96 << 30, slots=2, max_batch=32)
+    sims = []                                     # (sid, n, words, next gate index)
+    for n_q, r_max, words in ((24, 32, 4), (32, 64, 2), (40, 32, 4), (48, 64, 2)):
+        sims.append([eng.create_simulation(n_q, r_max, words), n_q, words, 0])
+    total_req = (args.warmup + args.steps) * per_step
+    sizes = [min(s, 256) for s in W.batch_sizes(4 + rank, total_req)]
+    kinds = rng.random(total_req) < 0.5            # True: eigensolve, False: gate
+    precs = rng.random(total_req) < 0.5            # True: quad-double eigensolve
+    which_sim = rng.integers(0, len(sims), total_req)
+    reqs = []
+    for i in range(total_req):
+        if kinds[i]:
+            cfg = 2 if precs[i] else 1
+            p = W.config_batch(cfg, seed=4 + rank, count=1, sizes=[sizes[i]])[0]
+            reqs.append(("eig", p, 4 if cfg == 2 else 2))
+        else:
+            sm = sims[int(which_sim[i])]
+            sid, n_q, words, g = sm
+            layer, k = divmod(g, (n_q - 1 + 1) // 2)
+            sites = list(range(layer % 2, n_q - 1, 2))
+            site = sites[k % len(sites)]
+            sm[3] += 1
+            reqs.append(("gate", (sid, site, W.haar_gate(5 + rank, g + 1000 * sid, words)), words))
+
+    def submit(r):
+        if r[0] == "eig":
+            return eng.submit_eig(r[1].A, r[1].n, r[2])
+        sid, site, G = r[1]
+        return eng.submit_gate(sid, site, G, 2.0 ** -(53 * r[2] - 12))
+
+    # saturation: the warm-up requests all at once
+    warm = reqs[:args.warmup * per_step]
+    t0 = time.perf_counter()
+    hs = [submit(r) for r in warm]
+    for h in hs:
+        h.done.wait(600)
+    cap = len(warm) / (time.perf_counter() - t0)
+    eng.completed.clear()
+    # open loop at 0.7x saturation
+    rate = 0.7 * cap
+    clocks = ClockSampler(local)
+    clocks.start()
+    timed = reqs[args.warmup * per_step:]
+    gaps = rng.exponential(1.0 / rate, len(timed))
+    t0 = time.perf_counter()
+    hs, t_next = [], t0
+    for r, gp in zip(timed, gaps):
+        t_next += gp
+        dt = t_next - time.perf_counter()
+        if dt > 0:
+            time.sleep(dt)
+        hs.append((r, submit(r)))
+    for _, h in hs:
+        h.done.wait(600)
+    wall = time.perf_counter() - t0
+    clk = clocks.stop()
+    errors = [h.error for _, h in hs if h.error]
+    lat = {}
+    for (r, h) in hs:
+        key = f"{r[0]}_{'qd' if r[2] == 4 else 'dd'}"
+        lat.setdefault(key, []).append(1e3 * (h.t_done - h.t_arrive))
+    stats = {k: {"count": len(v), "p50_ms": float(np.percentile(v, 50)), "p99_ms": float(np.percentile(v, 99))}
+             for k, v in sorted(lat.items())}
+    eig_pairs = sum(r[1].n for r, h in hs if r[0] == "eig" and not h.error)
+    ngates = sum(1 for r, h in hs if r[0] == "gate" and not h.error)
+    all_lat = [x for v in lat.values() for x in v]
+    out = {
+        "metric": "serving: eigenpairs/s and p50/p99 request latency at 0.7x saturation (Poisson arrivals)",
+        "value": eig_pairs / wall, "unit": "eigenpairs/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * wall / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "serve", "requests_timed": len(timed), "arrival_rate_per_s": rate,
+                   "saturated_requests_per_s": cap, "simulations": [(s[1], s[2]) for s in sims],
+                   "eig_sizes": "N from the batch distribution, capped at 256", "errors": len(errors)},
+        "latency_ms": {"p50": float(np.percentile(all_lat, 50)), "p99": float(np.percentile(all_lat, 99)),
+                       "by_type": stats},
+        "gates_per_s": ngates / wall,
+        "clocks": clk,
+        "e2e": {"value": eig_pairs / wall, "unit": "eigenpairs/s",
+                "h2d_bytes_per_step": int(sum(r[1].A.nbytes for r, _ in hs if r[0] == "eig") / args.steps),
+                "d2h_bytes_per_step": int(sum(r[1].n * r[2] * 8 * (1 + 2 * r[1].n) for r, _ in hs if r[0] == "eig") / args.steps)},
+    }
+    eng.close()
+    if rank == 0:
+        print(json.dumps(out))
+
+
 def run_reference(args):
     """The oracle, as it stands, on the host cores: a bounded sample of the same workload per step."""
     rank, world, _ = dist_env()
@@ -358,4 +554,11 @@ def run_reference(args):
 
 if __name__ == "__main__":
     a = parse()
-    run_reference(a) if a.impl == "reference" else run_ours(a)
+    if a.impl == "reference":
+        run_reference(a)
+    elif a.workload == "brickwork40":
+        run_brickwork(a)
+    elif a.workload == "serve":
+        run_serve(a)
+    else:
+        run_ours(a)

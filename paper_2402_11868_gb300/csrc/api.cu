@@ -7,6 +7,7 @@
 #include "common.cuh"
 #include "mw.cuh"
 #include "prof.cuh"
+#include "internal.cuh"
 
 namespace zkq {
 
@@ -17,26 +18,6 @@ unsigned long long* prof_device_counters() { return profiler().on ? g_prof_ctr :
 static thread_local int g_last_cuda = 0;
 void set_last_cuda_error(cudaError_t e) { g_last_cuda = (int)e; }
 
-struct JacobiBatch { const int32_t* n; const int64_t* a_off; const int64_t* w_off; const int32_t* order;
-  const double* A; double* W; double* V; int32_t* info; double* ws; const int64_t* ws_off; double* red; int max_sweeps; };
-zkq_status launch_jacobi(const JacobiBatch& jb, int a_words, int n_small, int n_large, int max_small_n,
-                         int max_large_n, int cluster, cudaStream_t st);
-size_t jacobi_smem_bytes(int n);
-
-struct RqiBatch { const int32_t* n; const int64_t* a_off; const int64_t* w_off; const int32_t* pair_prob;
-  const double* A; const double* W; const double* V; double* W_out; double* V_out; double* err; int32_t* info;
-  double* ws; int64_t ws_stride; int64_t total_pairs; int max_iter; int* counter; };
-zkq_status launch_rqi(const RqiBatch& rb, int W, int WA, int grid, cudaStream_t st);
-size_t rqi_slot_doubles(int nmax, int W);
-
-struct OaBuffers { void** ws; size_t* ws_bytes; void** oz_ws; size_t* oz_bytes; void** oz_meta; size_t* oz_meta_bytes; };
-zkq_status oa_refine(void* ctx, const OaBuffers& buf, int batch, const int32_t* n, const int64_t* a_off,
-                     const double* A, int wa, const double* V, int W, double* W_out, double* V_out, double* err,
-                     int32_t* info, int max_iter, int prod_method, cudaStream_t st);
-
-int gemm_kernel_get();
-void gemm_kernel_set(int k);
-bool gemm_kernel_error();
 }  // namespace zkq
 #include "ozaki.cuh"
 
@@ -58,13 +39,15 @@ struct zkq_ctx {
   size_t oz_meta_bytes = 0;
   void* mps_ws = nullptr;   // gate-update scratch (theta, rho, split-back)
   size_t mps_bytes = 0;
+  HostStage stage;          // pinned staging of metadata uploads and statistics read-back
 };
 
 namespace zkq {
 OaBuffers ctx_oa_buffers(void* vctx) {
   zkq_ctx* c = (zkq_ctx*)vctx;
-  return OaBuffers{&c->oa_ws, &c->oa_bytes, &c->oz_ws, &c->oz_bytes, &c->oz_meta, &c->oz_meta_bytes};
+  return OaBuffers{&c->oa_ws, &c->oa_bytes, &c->oz_ws, &c->oz_bytes, &c->oz_meta, &c->oz_meta_bytes, &c->stage};
 }
+HostStage* ctx_stage(void* vctx) { return &((zkq_ctx*)vctx)->stage; }
 int ctx_oa_max_iter(void* vctx) { return ((zkq_ctx*)vctx)->cfg.oa_max_iter; }
 void** ctx_mps_ws(void* vctx, size_t** bytes) { zkq_ctx* c = (zkq_ctx*)vctx; *bytes = &c->mps_bytes; return &c->mps_ws; }
 }  // namespace zkq
@@ -131,7 +114,7 @@ static constexpr int kSmallMax = 80;
 
 namespace zkq {
 zkq_status eigh_internal(void* vctx, int batch, const int32_t* n, const int64_t* a_off, const double* A, int a_words,
-                         double* W, double* V, int32_t* info, cudaStream_t st) {
+                         double* W, double* V, int32_t* info, cudaStream_t st, int prof_class) {
   zkq_ctx* ctx = (zkq_ctx*)vctx;
   std::vector<int64_t> w_off(batch), ws_off(batch, 0);
   std::vector<int32_t> small, large;
@@ -144,28 +127,42 @@ zkq_status eigh_internal(void* vctx, int batch, const int32_t* n, const int64_t*
   }
   std::sort(large.begin(), large.end(), [&](int a, int c) { return n[a] > n[c] || (n[a] == n[c] && a < c); });
   for (int b : large) { ws_off[b] = (int64_t)(ws_need / sizeof(double)); ws_need += align_up((size_t)n[b] * n[b] * 4 * sizeof(double)); }
+  // few large problems: one at a time on a cooperative grid instead of a cluster each (a cluster of at
+  // most 16 CTAs would leave most SMs idle)
+  int cluster = ctx->cfg.jacobi_cluster;
+  if (cluster <= 0) cluster = max_large <= 128 ? 2 : (max_large <= 256 ? 4 : 8);
+  if (cluster > 16) cluster = 16;
+  int grid_blocks = 0;
+  if (!large.empty() && (int)large.size() * cluster * 2 <= ctx->num_sms) {
+    const int per_sm = jacobi_grid_max_blocks(max_large, a_words);
+    grid_blocks = std::min(std::min(ctx->num_sms, std::max(8, max_large / 4)), per_sm * ctx->num_sms);
+  }
   size_t red_bytes = align_up((size_t)64 * std::max<size_t>(1, large.size()) * sizeof(double));
+  red_bytes = std::max(red_bytes, align_up((size_t)(2 * grid_blocks + 64) * sizeof(double)));
+  const size_t gb_bytes = align_up(sizeof(GridBar));
   std::vector<int32_t> order(small); order.insert(order.end(), large.begin(), large.end());
   // metadata: n, a_off, w_off, order, ws_off
   size_t m_n = align_up(batch * 4), m_a = align_up(batch * 8), m_w = align_up(batch * 8), m_o = align_up(batch * 4), m_s = align_up(batch * 8);
   zkq_status s = ensure(&ctx->meta, &ctx->meta_bytes, m_n + m_a + m_w + m_o + m_s);
   if (s != ZKQ_OK) return s;
-  s = ensure(&ctx->ws, &ctx->ws_bytes, ws_need + red_bytes);
+  s = ensure(&ctx->ws, &ctx->ws_bytes, ws_need + red_bytes + gb_bytes);
   if (s != ZKQ_OK) return s;
   char* mb = (char*)ctx->meta;
   int32_t* d_n = (int32_t*)mb; int64_t* d_a = (int64_t*)(mb + m_n); int64_t* d_w = (int64_t*)(mb + m_n + m_a);
   int32_t* d_o = (int32_t*)(mb + m_n + m_a + m_w); int64_t* d_s = (int64_t*)(mb + m_n + m_a + m_w + m_o);
-  ZKQ_CUDA_TRY(cudaMemcpyAsync(d_n, n, batch * 4, cudaMemcpyHostToDevice, st));
-  ZKQ_CUDA_TRY(cudaMemcpyAsync(d_a, a_off, batch * 8, cudaMemcpyHostToDevice, st));
-  ZKQ_CUDA_TRY(cudaMemcpyAsync(d_w, w_off.data(), batch * 8, cudaMemcpyHostToDevice, st));
-  ZKQ_CUDA_TRY(cudaMemcpyAsync(d_o, order.data(), batch * 4, cudaMemcpyHostToDevice, st));
-  ZKQ_CUDA_TRY(cudaMemcpyAsync(d_s, ws_off.data(), batch * 8, cudaMemcpyHostToDevice, st));
-  int cluster = ctx->cfg.jacobi_cluster;
-  if (cluster <= 0) cluster = max_large <= 128 ? 2 : (max_large <= 256 ? 4 : 8);
-  if (cluster > 16) cluster = 16;
+  HostStage& hs = ctx->stage;
+  hs.add(d_n, n, batch * 4);
+  hs.add(d_a, a_off, batch * 8);
+  hs.add(d_w, w_off.data(), batch * 8);
+  hs.add(d_o, order.data(), batch * 4);
+  hs.add(d_s, ws_off.data(), batch * 8);
+  ZKQ_CUDA_TRY(hs.flush(st));
+  unsigned long long* ctr = prof_device_counters();
   JacobiBatch jb{d_n, d_a, d_w, d_o, A, W, V, info, (double*)ctx->ws, d_s,
-                 (double*)((char*)ctx->ws + ws_need), ctx->cfg.max_sweeps};
-  return launch_jacobi(jb, a_words, (int)small.size(), (int)large.size(), max_small, max_large, cluster, st);
+                 (double*)((char*)ctx->ws + ws_need), ctx->cfg.max_sweeps, ctr ? ctr + prof_class : nullptr, prof_class};
+  GridBar* gb = (GridBar*)((char*)ctx->ws + ws_need + red_bytes);
+  return launch_jacobi(jb, a_words, (int)small.size(), (int)large.size(), max_small, max_large, cluster, grid_blocks,
+                       gb, st);
 }
 zkq_status rqi_refine_internal(void* vctx, int batch, const int32_t* n, const int64_t* a_off, const double* A,
                                int a_words, const double* W, const double* V, int target_words, double* W_out,
@@ -189,10 +186,12 @@ zkq_status rqi_refine_internal(void* vctx, int batch, const int32_t* n, const in
   char* mb = (char*)ctx->meta;
   int32_t* d_n = (int32_t*)mb; int64_t* d_a = (int64_t*)(mb + m_n); int64_t* d_w = (int64_t*)(mb + m_n + m_a);
   int32_t* d_p = (int32_t*)(mb + m_n + m_a + m_w); int* d_c = (int*)(mb + m_n + m_a + m_w + m_p);
-  ZKQ_CUDA_TRY(cudaMemcpyAsync(d_n, n, batch * 4, cudaMemcpyHostToDevice, st));
-  ZKQ_CUDA_TRY(cudaMemcpyAsync(d_a, a_off, batch * 8, cudaMemcpyHostToDevice, st));
-  ZKQ_CUDA_TRY(cudaMemcpyAsync(d_w, w_off.data(), batch * 8, cudaMemcpyHostToDevice, st));
-  ZKQ_CUDA_TRY(cudaMemcpyAsync(d_p, pair_prob.data(), total * 4, cudaMemcpyHostToDevice, st));
+  HostStage& hs = ctx->stage;
+  hs.add(d_n, n, batch * 4);
+  hs.add(d_a, a_off, batch * 8);
+  hs.add(d_w, w_off.data(), batch * 8);
+  hs.add(d_p, pair_prob.data(), total * 4);
+  ZKQ_CUDA_TRY(hs.flush(st));
   ZKQ_CUDA_TRY(cudaMemsetAsync(d_c, 0, sizeof(int), st));
   ZKQ_CUDA_TRY(cudaMemsetAsync(info, 0, batch * sizeof(int32_t), st));
   RqiBatch rb{d_n, d_a, d_w, d_p, A, W, V, W_out, V_out, err_est, info, (double*)ctx->ws, (int64_t)slot, total,
@@ -226,7 +225,7 @@ zkq_status zkq_rqi_refine(zkq_ctx* ctx, int batch, const int32_t* n, const int64
   cudaStream_t st = (cudaStream_t)stream;
   if (method != ZKQ_PLAIN_RQI) {
     for (int b = 0; b < batch; ++b) if (n[b] < 1 || n[b] > 2048 || a_off[b] < 0) return ZKQ_EINVAL;
-    OaBuffers ob{&ctx->oa_ws, &ctx->oa_bytes, &ctx->oz_ws, &ctx->oz_bytes, &ctx->oz_meta, &ctx->oz_meta_bytes};
+    OaBuffers ob{&ctx->oa_ws, &ctx->oa_bytes, &ctx->oz_ws, &ctx->oz_bytes, &ctx->oz_meta, &ctx->oz_meta_bytes, &ctx->stage};
     return oa_refine(ctx, ob, batch, n, a_off, A, a_words, V, target_words, W_out, V_out, err_est, info,
                      ctx->cfg.oa_max_iter, method == ZKQ_OA_OZAKI ? 1 : 0, st);
   }
@@ -250,7 +249,7 @@ zkq_status zkq_mw_gemm(zkq_ctx* ctx, int count, const int32_t* m, const int32_t*
     pr[i] = {m[i], n[i], k[i], opA[i], A + a_off[i] * 2 * wa, B + b_off[i] * 2 * wb, C + c_off[i] * 2 * wc, nullptr, 1.0, 0};
   }
   zkq_status s = mw_gemm_batched(pr.data(), count, wa, wb, wc, p_bits, method, &ctx->oz_ws, &ctx->oz_bytes,
-                                 &ctx->oz_meta, &ctx->oz_meta_bytes, (cudaStream_t)stream);
+                                 &ctx->oz_meta, &ctx->oz_meta_bytes, (cudaStream_t)stream, &ctx->stage);
   return s;
 }
 
@@ -265,7 +264,7 @@ int zkq_get_gemm_kernel(void) { return gemm_kernel_get(); }
 zkq_status zkq_check_device_waits(void) { return gemm_kernel_error() ? ZKQ_ETIMEOUT : ZKQ_OK; }
 
 static const char* kProfNames[PC_COUNT] = {"jacobi", "rqi", "ozaki_scale", "ozaki_slice", "ozaki_gemm",
-                                           "ozaki_combine", "oa_elementwise", "mps", "other"};
+                                           "ozaki_combine", "oa_elementwise", "mps", "other", "jacobi_cluster"};
 
 int zkq_profile_classes(void) { return PC_COUNT; }
 

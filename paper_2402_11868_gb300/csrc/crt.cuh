@@ -35,6 +35,7 @@ struct CrtConst {
   int l32;                           // 32-bit limbs that hold M with 16 bits of headroom (<= CRT_L32)
   int hdig;                          // 16-bit digits that hold a split half (|A_h|, A_l < 2^(16 hdig))
   int tbits;                         // bits (with sign) of the reconstructed C' = A' B', bounded by K' 2^(2q-4)
+  double Mrcp;                       // 1 / Md (quotient estimates by multiplication)
 };
 
 // v mod m in [0, m) for |v| < 2^29 without division: minv = floor(2^32 / m) + 1 makes

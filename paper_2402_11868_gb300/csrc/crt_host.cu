@@ -96,6 +96,7 @@ bool crt_build(int max_kprime, int p_out_bits, CrtConst* out) {
   double v = (double)out->M[top] + (top > 0 ? std::ldexp((double)out->M[top - 1], -64) : 0.0);
   int e = 0; double fr = std::frexp(v, &e);   // v = fr 2^e, fr in [0.5,1)
   out->Md = fr * 2.0; out->Mexp = e - 1 + 64 * top;
+  out->Mrcp = 1.0 / out->Md;
   return true;
 }
 

@@ -1,0 +1,98 @@
+// Declarations shared by the library's translation units: launch descriptors of the batched kernels,
+// internal entry points reused across stages, and the pinned host staging ring of a context.
+#pragma once
+#include <cstdint>
+#include <cstddef>
+#include <deque>
+#include <vector>
+#include <cuda_runtime.h>
+#include "common.cuh"
+
+namespace zkq {
+
+// ---- pinned host staging -------------------------------------------------------------------------
+// The small per-call uploads (batch metadata, tile and pair lists, CRT constants) and the per-iteration
+// statistics read-back go through one pinned ring per context: copies from pageable memory may wait for
+// the stream to drain, copies from pinned memory stay asynchronous, so the host prepares the next launch
+// while the device works.  A region is handed out again only after the event recorded behind the copy
+// that read (or wrote) it has completed.  A context, and so its ring, is used by one host thread at a time.
+class HostStage {
+ public:
+  HostStage() = default;
+  HostStage(const HostStage&) = delete;
+  HostStage& operator=(const HostStage&) = delete;
+  ~HostStage();
+  // H2D copy of `bytes` from pageable `src` to device `dst`, ordered on `st`
+  cudaError_t upload(void* dst, const void* src, size_t bytes, cudaStream_t st);
+  // D2H copy of `bytes` from device `src` to `dst`; waits for `st` (the caller reads the data next)
+  cudaError_t download_sync(void* dst, const void* src, size_t bytes, cudaStream_t st);
+  // several uploads through one pinned region and one event: add() the pieces (copied at once), then flush()
+  void add(void* dst, const void* src, size_t bytes);
+  cudaError_t flush(cudaStream_t st);
+ private:
+  struct Span { size_t lo, hi; cudaEvent_t ev; };
+  struct Piece { void* dst; size_t off, bytes; };
+  char* buf_ = nullptr;
+  size_t cap_ = 0, head_ = 0;
+  std::deque<Span> inflight_;
+  std::vector<cudaEvent_t> free_ev_;
+  std::vector<char> pend_;                            // pieces collected by add() before flush()
+  std::vector<Piece> pieces_;
+  cudaError_t reserve(size_t bytes, size_t* off);
+  cudaError_t fence(size_t lo, size_t hi, cudaStream_t st);
+};
+
+// ---- FP64 Jacobi ---------------------------------------------------------------------------------
+struct JacobiBatch {
+  const int32_t* n; const int64_t* a_off; const int64_t* w_off; const int32_t* order;
+  const double* A; double* W; double* V; int32_t* info; double* ws; const int64_t* ws_off; double* red;
+  int max_sweeps;
+  unsigned long long* flops;     // device counter of applied-rotation flops (null: not counted)
+  int prof_class;                // profiler class of the launches
+};
+// grid barrier state of the cooperative Jacobi launch (zeroed before each launch)
+struct GridBar { unsigned count; unsigned gen; int abort; int pad; };
+// small problems: one CTA each; large problems: a cluster of `cluster` CTAs each, or, when grid_blocks > 0,
+// one problem at a time on a cooperative grid of grid_blocks CTAs (few large problems)
+zkq_status launch_jacobi(const JacobiBatch& jb, int a_words, int n_small, int n_large, int max_small_n,
+                         int max_large_n, int cluster, int grid_blocks, GridBar* gb, cudaStream_t st);
+size_t jacobi_smem_bytes(int n);
+int jacobi_grid_max_blocks(int max_large_n, int a_words);   // co-resident blocks per SM of the grid kernel
+
+// ---- plain RQI -----------------------------------------------------------------------------------
+struct RqiBatch {
+  const int32_t* n; const int64_t* a_off; const int64_t* w_off; const int32_t* pair_prob;
+  const double* A; const double* W; const double* V;
+  double* W_out; double* V_out; double* err; int32_t* info;
+  double* ws; int64_t ws_stride; int64_t total_pairs; int max_iter; int* counter;
+};
+zkq_status launch_rqi(const RqiBatch& rb, int W, int WA, int grid, cudaStream_t st);
+size_t rqi_slot_doubles(int nmax, int W);
+
+// ---- refinement ----------------------------------------------------------------------------------
+struct OaBuffers {
+  void** ws; size_t* ws_bytes; void** oz_ws; size_t* oz_bytes; void** oz_meta; size_t* oz_meta_bytes;
+  HostStage* stage;
+};
+zkq_status oa_refine(void* ctx, const OaBuffers& buf, int batch, const int32_t* n, const int64_t* a_off,
+                     const double* A, int wa, const double* V, int W, double* W_out, double* V_out, double* err,
+                     int32_t* info, int max_iter, int prod_method, cudaStream_t st);
+
+// ---- context internals ---------------------------------------------------------------------------
+// prof_class: profiler class of the launches (0 = PC_JACOBI; the refinement's cluster solves use their own)
+zkq_status eigh_internal(void* ctx, int batch, const int32_t* n, const int64_t* a_off, const double* A, int a_words,
+                         double* W, double* V, int32_t* info, cudaStream_t st, int prof_class = 0);
+zkq_status rqi_refine_internal(void* ctx, int batch, const int32_t* n, const int64_t* a_off, const double* A,
+                               int a_words, const double* W, const double* V, int target_words, double* W_out,
+                               double* V_out, double* err_est, int32_t* info, cudaStream_t st);
+OaBuffers ctx_oa_buffers(void* ctx);
+int ctx_oa_max_iter(void* ctx);
+void** ctx_mps_ws(void* ctx, size_t** bytes);
+HostStage* ctx_stage(void* ctx);
+
+// ---- split-product GEMM kernel choice --------------------------------------------------------------
+int gemm_kernel_get();
+void gemm_kernel_set(int k);
+bool gemm_kernel_error();
+
+}  // namespace zkq

@@ -18,6 +18,7 @@
 #include "common.cuh"
 #include "mw.cuh"
 #include "prof.cuh"
+#include "internal.cuh"
 #include <cooperative_groups.h>
 namespace cg = cooperative_groups;
 
@@ -25,7 +26,6 @@ namespace zkq {
 
 struct RotParams { double c, tb; c64 z1, z2; int rot; int p, q; };
 
-__device__ unsigned long long* g_jacobi_flops = nullptr;   // work counter, set by the launcher when profiling
 
 // Storage policy: matrix element (i, j) of a column-major matrix with leading dimension ld.
 // SMEM: plain loads/stores.  GLOBAL: L2-only loads (other CTAs of the cluster write the same matrix).
@@ -42,15 +42,43 @@ template <bool SMEM> struct Mat {
   }
 };
 
-// One problem, processed by `nparts` cooperating CTAs (part = rank in the cluster; 1 CTA if nparts = 1).
+// One problem, processed by `nparts` cooperating CTAs: a thread-block cluster (SYNC 1), the whole grid of
+// a cooperative launch (SYNC 2), or a single CTA (SYNC 0, nparts = 1).
 __device__ __forceinline__ void cluster_barrier() { __threadfence(); cg::this_cluster().sync(); }
 
-template <bool SMEM, bool CLUSTER, int WA>
+// Grid barrier of a cooperative launch (all blocks co-resident): arrival counter + generation number.  The
+// wait is bounded; on expiry the barrier raises gb->abort, after which no barrier waits any more, so every
+// block runs its remaining (bounded) loops to the end and the problem reports failure.
+__device__ __forceinline__ void grid_barrier(GridBar* gb, unsigned nblocks) {
+  __syncthreads();
+  if (threadIdx.x == 0 && !*(volatile int*)&gb->abort) {
+    __threadfence();
+    const unsigned g = *(volatile unsigned*)&gb->gen;
+    if (atomicAdd(&gb->count, 1u) == nblocks - 1) {
+      atomicExch(&gb->count, 0u);
+      __threadfence();
+      atomicAdd(&gb->gen, 1u);
+    } else {
+      for (int it = 0; *(volatile unsigned*)&gb->gen == g; ++it) {
+        if (it > (1 << 22)) { atomicExch(&gb->abort, 1); break; }
+        __nanosleep(64);
+      }
+    }
+    __threadfence();
+  }
+  __syncthreads();
+}
+
+template <bool SMEM, int SYNC, int WA>
 __device__ void jacobi_problem(int n, const double* __restrict__ A_in, Mat<SMEM> A, Mat<SMEM> V,
-                               RotParams* rp, double* red, int max_sweeps,
+                               RotParams* rp, double* red, int max_sweeps, unsigned long long* flops,
                                double* __restrict__ W_out, double* __restrict__ V_out, int32_t* info,
-                               int part, int nparts) {
-  auto sync = [] { if constexpr (CLUSTER) cluster_barrier(); else __syncthreads(); };
+                               int part, int nparts, GridBar* gb = nullptr) {
+  auto sync = [&] {
+    if constexpr (SYNC == 1) cluster_barrier();
+    else if constexpr (SYNC == 2) grid_barrier(gb, (unsigned)nparts);
+    else __syncthreads();
+  };
   const int tid = threadIdx.x, nth = blockDim.x;
   const int gtid = part * nth + tid, gnth = nparts * nth;
   const int m = n + (n & 1);               // even number of players; index n is a dummy when n is odd
@@ -181,10 +209,10 @@ __device__ void jacobi_problem(int n, const double* __restrict__ A_in, Mat<SMEM>
     __syncthreads();
     // algorithmic FP64 flops of this sweep: per applied rotation 24 n FMA (12 n on A: a round's n/2
     // rotations update n^2/8 2x2 blocks at 48 FMA each; 12 n on V) = 48 n flops; counted once per problem
-    if (part == 0 && tid == 0 && g_jacobi_flops && s_rot) atomicAdd(g_jacobi_flops, (unsigned long long)s_rot * 48ULL * (unsigned long long)n);
-    if constexpr (CLUSTER) {
+    if (part == 0 && tid == 0 && flops && s_rot) atomicAdd(flops, (unsigned long long)s_rot * 48ULL * (unsigned long long)n);
+    if constexpr (SYNC != 0) {
       // every CTA computed the same parameters, but take part 0's count so the barrier counts of the
-      // cluster's CTAs cannot diverge
+      // cooperating CTAs cannot diverge
       if (tid == 0) red[nparts + part] = (double)s_rot;
       sync();
       converged = (__ldcg(red + nparts) == 0.0);
@@ -216,14 +244,12 @@ __device__ void jacobi_problem(int n, const double* __restrict__ A_in, Mat<SMEM>
       V_out[((size_t)r + (size_t)rank * n) * 2 + 1] = v.im;
     }
   }
-  if (part == 0 && tid == 0) *info = converged ? 0 : sweep;
+  if (part == 0 && tid == 0) {
+    bool failed = false;
+    if constexpr (SYNC == 2) failed = *(volatile int*)&gb->abort != 0;
+    *info = failed ? -1 : (converged ? 0 : sweep);
+  }
 }
-
-struct JacobiBatch {
-  const int32_t* n; const int64_t* a_off; const int64_t* w_off; const int32_t* order;
-  const double* A; double* W; double* V; int32_t* info; double* ws; const int64_t* ws_off; double* red;
-  int max_sweeps;
-};
 
 // small problems: matrix and eigenvectors in shared memory, one CTA per problem
 template <int WA>
@@ -237,7 +263,7 @@ __global__ void __launch_bounds__(256) jacobi_smem_kernel(JacobiBatch jb, int fi
   c64* sV = sA + (size_t)ld * n;
   RotParams* rp = reinterpret_cast<RotParams*>(sV + (size_t)ld * n);
   Mat<true> A{sA, ld}, V{sV, ld};
-  jacobi_problem<true, false, WA>(n, jb.A + jb.a_off[b] * 2 * WA, A, V, rp, nullptr, jb.max_sweeps,
+  jacobi_problem<true, 0, WA>(n, jb.A + jb.a_off[b] * 2 * WA, A, V, rp, nullptr, jb.max_sweeps, jb.flops,
                                   jb.W + jb.w_off[b], jb.V + jb.a_off[b] * 2, jb.info + b, 0, 1);
 }
 
@@ -255,24 +281,53 @@ __global__ void __launch_bounds__(256) jacobi_global_kernel(JacobiBatch jb, int 
   Mat<false> A{reinterpret_cast<c64*>(wsA), n}, V{reinterpret_cast<c64*>(wsV), n};
   double* red = jb.red + (size_t)64 * (blockIdx.x / nparts);   // 2 * cluster (<= 32) entries used
   if (nparts > 1)
-    jacobi_problem<false, true, WA>(n, jb.A + jb.a_off[b] * 2 * WA, A, V, rp, red, jb.max_sweeps,
+    jacobi_problem<false, 1, WA>(n, jb.A + jb.a_off[b] * 2 * WA, A, V, rp, red, jb.max_sweeps, jb.flops,
                                     jb.W + jb.w_off[b], jb.V + jb.a_off[b] * 2, jb.info + b, part, nparts);
   else
-    jacobi_problem<false, false, WA>(n, jb.A + jb.a_off[b] * 2 * WA, A, V, rp, red, jb.max_sweeps,
+    jacobi_problem<false, 0, WA>(n, jb.A + jb.a_off[b] * 2 * WA, A, V, rp, red, jb.max_sweeps, jb.flops,
                                      jb.W + jb.w_off[b], jb.V + jb.a_off[b] * 2, jb.info + b, 0, 1);
+}
+
+// few large problems: every block of a cooperative launch works on one problem at a time, in turn
+template <int WA>
+__global__ void __launch_bounds__(256) jacobi_grid_kernel(JacobiBatch jb, int first, int count, GridBar* gb) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  RotParams* rp = reinterpret_cast<RotParams*>(smem);
+  for (int q = 0; q < count; ++q) {
+    const int b = jb.order[first + q];
+    const int n = jb.n[b];
+    double* wsA = jb.ws + jb.ws_off[b];
+    double* wsV = wsA + (size_t)n * n * 2;
+    Mat<false> A{reinterpret_cast<c64*>(wsA), n}, V{reinterpret_cast<c64*>(wsV), n};
+    jacobi_problem<false, 2, WA>(n, jb.A + jb.a_off[b] * 2 * WA, A, V, rp, jb.red, jb.max_sweeps, jb.flops,
+                                 jb.W + jb.w_off[b], jb.V + jb.a_off[b] * 2, jb.info + b, (int)blockIdx.x,
+                                 (int)gridDim.x, gb);
+    grid_barrier(gb, gridDim.x);     // the reduction slots are reused by the next problem
+  }
 }
 
 size_t jacobi_smem_bytes(int n) { return (size_t)2 * (n + 1) * n * sizeof(c64) + (size_t)(n / 2 + 1) * sizeof(RotParams); }
 
 template <int WA>
 static zkq_status launch_words(const JacobiBatch& jb, int n_small, int n_large, int max_small_n, int max_large_n,
-                               int cluster, cudaStream_t st) {
+                               int cluster, int grid_blocks, GridBar* gb, cudaStream_t st) {
   if (n_small > 0) {
     size_t sm = jacobi_smem_bytes(max_small_n);
     ZKQ_CUDA_TRY(cudaFuncSetAttribute(jacobi_smem_kernel<WA>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-    ProfScope ps(PC_JACOBI, st);
+    ProfScope ps(jb.prof_class, st);
     jacobi_smem_kernel<WA><<<n_small, 256, sm, st>>>(jb, 0, n_small);
     ZKQ_CUDA_TRY(cudaGetLastError());
+  }
+  if (n_large > 0 && grid_blocks > 0) {
+    size_t sm = (size_t)(max_large_n / 2 + 1) * sizeof(RotParams);
+    ZKQ_CUDA_TRY(cudaFuncSetAttribute(jacobi_grid_kernel<WA>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    ZKQ_CUDA_TRY(cudaMemsetAsync(gb, 0, sizeof(GridBar), st));
+    JacobiBatch jbc = jb;
+    int first = n_small, count = n_large;
+    void* args[] = {&jbc, &first, &count, &gb};
+    ProfScope ps(jb.prof_class, st);
+    ZKQ_CUDA_TRY(cudaLaunchCooperativeKernel((const void*)jacobi_grid_kernel<WA>, dim3(grid_blocks), dim3(256), args, sm, st));
+    return ZKQ_OK;
   }
   if (n_large > 0) {
     size_t sm = (size_t)(max_large_n / 2 + 1) * sizeof(RotParams);
@@ -288,23 +343,31 @@ static zkq_status launch_words(const JacobiBatch& jb, int n_small, int n_large, 
     attr[0].id = cudaLaunchAttributeClusterDimension;
     attr[0].val.clusterDim.x = cluster; attr[0].val.clusterDim.y = 1; attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr; cfg.numAttrs = 1;
-    ProfScope ps(PC_JACOBI, st);
+    ProfScope ps(jb.prof_class, st);
     ZKQ_CUDA_TRY(cudaLaunchKernelEx(&cfg, jacobi_global_kernel<WA>, jb, n_small));
   }
   return ZKQ_OK;
 }
 
 zkq_status launch_jacobi(const JacobiBatch& jb, int a_words, int n_small, int n_large, int max_small_n,
-                         int max_large_n, int cluster, cudaStream_t st) {
-  unsigned long long* ctr = prof_device_counters();
-  unsigned long long* dev_ctr = ctr ? ctr + PC_JACOBI : nullptr;
-  ZKQ_CUDA_TRY(cudaMemcpyToSymbolAsync(g_jacobi_flops, &dev_ctr, sizeof(dev_ctr), 0, cudaMemcpyHostToDevice, st));
+                         int max_large_n, int cluster, int grid_blocks, GridBar* gb, cudaStream_t st) {
   switch (a_words) {
-    case 1: return launch_words<1>(jb, n_small, n_large, max_small_n, max_large_n, cluster, st);
-    case 2: return launch_words<2>(jb, n_small, n_large, max_small_n, max_large_n, cluster, st);
-    case 4: return launch_words<4>(jb, n_small, n_large, max_small_n, max_large_n, cluster, st);
+    case 1: return launch_words<1>(jb, n_small, n_large, max_small_n, max_large_n, cluster, grid_blocks, gb, st);
+    case 2: return launch_words<2>(jb, n_small, n_large, max_small_n, max_large_n, cluster, grid_blocks, gb, st);
+    case 4: return launch_words<4>(jb, n_small, n_large, max_small_n, max_large_n, cluster, grid_blocks, gb, st);
     default: return ZKQ_EINVAL;
   }
+}
+
+int jacobi_grid_max_blocks(int max_large_n, int a_words) {
+  size_t sm = (size_t)(max_large_n / 2 + 1) * sizeof(RotParams);
+  int per_sm = 0;
+  cudaError_t e = cudaSuccess;
+  if (a_words == 1) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, jacobi_grid_kernel<1>, 256, sm);
+  else if (a_words == 2) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, jacobi_grid_kernel<2>, 256, sm);
+  else e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, jacobi_grid_kernel<4>, 256, sm);
+  if (e != cudaSuccess) { set_last_cuda_error(e); return 0; }
+  return per_sm;
 }
 
 }  // namespace zkq

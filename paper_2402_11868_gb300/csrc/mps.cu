@@ -21,21 +21,10 @@
 #include "mw.cuh"
 #include "ozaki.cuh"
 #include "prof.cuh"
+#include "internal.cuh"
 
 namespace zkq {
 
-zkq_status eigh_internal(void* ctx, int batch, const int32_t* n, const int64_t* a_off, const double* A, int a_words,
-                         double* W, double* V, int32_t* info, cudaStream_t st);
-struct OaBuffers { void** ws; size_t* ws_bytes; void** oz_ws; size_t* oz_bytes; void** oz_meta; size_t* oz_meta_bytes; };
-zkq_status oa_refine(void* ctx, const OaBuffers& buf, int batch, const int32_t* n, const int64_t* a_off,
-                     const double* A, int wa, const double* V, int W, double* W_out, double* V_out, double* err,
-                     int32_t* info, int max_iter, int prod_method, cudaStream_t st);
-zkq_status rqi_refine_internal(void* ctx, int batch, const int32_t* n, const int64_t* a_off, const double* A,
-                               int a_words, const double* W, const double* V, int target_words, double* W_out,
-                               double* V_out, double* err_est, int32_t* info, cudaStream_t st);
-OaBuffers ctx_oa_buffers(void* ctx);
-int ctx_oa_max_iter(void* ctx);
-void** ctx_mps_ws(void* ctx, size_t** bytes);
 
 // ------------------------------------------------------------------------------------------------------
 // kernels (one thread per element)
@@ -340,7 +329,7 @@ static zkq_status apply2q_t(zkq_ctx* ctx, zkq_mps* m, int l, const double* G, do
     for (int mm = 0; mm < 2; ++mm)
       pr.push_back({a, d, c, 0, Mc + (size_t)k * a * c * E, Nc + (size_t)mm * c * d * E,
                     T + (size_t)(2 * k + mm) * a * d * E, nullptr, 1.0, 0});
-  zkq_status s = mw_gemm_batched(pr.data(), 4, W, W, W, p_bits, 1, ob.oz_ws, ob.oz_bytes, ob.oz_meta, ob.oz_meta_bytes, st);
+  zkq_status s = mw_gemm_batched(pr.data(), 4, W, W, W, p_bits, 1, ob.oz_ws, ob.oz_bytes, ob.oz_meta, ob.oz_meta_bytes, st, ob.stage);
   if (s != ZKQ_OK) return s;
   {
     ProfScope ps(PC_MPS, st);
@@ -351,7 +340,7 @@ static zkq_status apply2q_t(zkq_ctx* ctx, zkq_mps* m, int l, const double* G, do
   // rho = M M^H (op(A) = (M^H)^H with A = MH stored C x R, B = MH) or M^H M (A = M stored R x C, B = M)
   MwProd pg = left ? MwProd{R, R, C, 1, MH, MH, Rho, nullptr, 1.0, 0} : MwProd{C, C, R, 1, M, M, Rho, nullptr, 1.0, 0};
   pg.hermitian = 1;
-  s = mw_gemm_batched(&pg, 1, W, W, W, p_bits, 1, ob.oz_ws, ob.oz_bytes, ob.oz_meta, ob.oz_meta_bytes, st);
+  s = mw_gemm_batched(&pg, 1, W, W, W, p_bits, 1, ob.oz_ws, ob.oz_bytes, ob.oz_meta, ob.oz_meta_bytes, st, ob.stage);
   if (s != ZKQ_OK) return s;
   // eigen-decomposition of rho (descending), refined to W words
   int32_t nn = g; int64_t zero = 0;
@@ -384,7 +373,7 @@ static zkq_status apply2q_t(zkq_ctx* ctx, zkq_mps* m, int l, const double* G, do
   if (left) {
     // Z = U^H M  (chi x C): op(A) = U^H with A = U stored R x chi
     MwProd pz{chi, C, R, 1, Vq, M, Y, nullptr, 1.0, 0};
-    s = mw_gemm_batched(&pz, 1, W, W, W, p_bits, 1, ob.oz_ws, ob.oz_bytes, ob.oz_meta, ob.oz_meta_bytes, st);
+    s = mw_gemm_batched(&pz, 1, W, W, W, p_bits, 1, ob.oz_ws, ob.oz_bytes, ob.oz_meta, ob.oz_meta_bytes, st, ob.stage);
     if (s != ZKQ_OK) return s;
     ProfScope ps(PC_MPS, st);
     mps_split_left_kernel<W><<<blocks<W>(2 * (size_t)a * chi), 256, 0, st>>>(Vq, a, chi, lamL, nullptr, m->gamma[l]);
@@ -392,7 +381,7 @@ static zkq_status apply2q_t(zkq_ctx* ctx, zkq_mps* m, int l, const double* G, do
   } else {
     // Y = M V (R x chi)
     MwProd py{R, chi, C, 0, M, Vq, Y, nullptr, 1.0, 0};
-    s = mw_gemm_batched(&py, 1, W, W, W, p_bits, 1, ob.oz_ws, ob.oz_bytes, ob.oz_meta, ob.oz_meta_bytes, st);
+    s = mw_gemm_batched(&py, 1, W, W, W, p_bits, 1, ob.oz_ws, ob.oz_bytes, ob.oz_meta, ob.oz_meta_bytes, st, ob.stage);
     if (s != ZKQ_OK) return s;
     ProfScope ps(PC_MPS, st);
     mps_split_left_kernel<W><<<blocks<W>(2 * (size_t)a * chi), 256, 0, st>>>(Y, a, chi, lamL, Sig, m->gamma[l]);

@@ -10,13 +10,7 @@
 #include <vector>
 #include <algorithm>
 #include "common.cuh"
-
-namespace zkq {
-struct JacobiBatch { const int32_t* n; const int64_t* a_off; const int64_t* w_off; const int32_t* order;
-  const double* A; double* W; double* V; int32_t* info; double* ws; const int64_t* ws_off; double* red; int max_sweeps; };
-zkq_status launch_jacobi(const JacobiBatch& jb, int a_words, int n_small, int n_large, int max_small_n,
-                         int max_large_n, int cluster, cudaStream_t st);
-}  // namespace zkq
+#include "internal.cuh"
 
 using namespace zkq;
 
@@ -90,6 +84,6 @@ extern "C" zkq_status zkq_eigh_batched_noalloc(int batch, const int32_t* n, cons
   int cluster = max_large <= 128 ? 2 : (max_large <= 256 ? 4 : 8);
   JacobiBatch jb{(const int32_t*)(base + o_n), (const int64_t*)(base + o_a), (const int64_t*)(base + o_w),
                  (const int32_t*)(base + o_o), A, W, V, info, (double*)(base + o_ws), (const int64_t*)(base + o_s),
-                 (double*)(base + o_red), 40};
-  return launch_jacobi(jb, a_words, (int)small.size(), (int)large.size(), max_small, max_large, cluster, st);
+                 (double*)(base + o_red), 40, nullptr, 0};
+  return launch_jacobi(jb, a_words, (int)small.size(), (int)large.size(), max_small, max_large, cluster, 0, nullptr, st);
 }

@@ -28,6 +28,7 @@
 #include "reduce.cuh"
 #include "ozaki.cuh"
 #include "prof.cuh"
+#include "internal.cuh"
 
 namespace zkq {
 
@@ -117,12 +118,17 @@ __global__ void oa_coupling_kernel(const OaProb* __restrict__ pr, const double* 
 }
 
 // clusters: consecutive columns c, c+1 stay together while
-//   |lambda_c - lambda_{c+1}| <= delta_c = 2 (||num_{:,c}|| + ||num_{:,c+1}||) + 2^-(53W/2+4) max(|lambda_c|, |lambda_{c+1}|),
+//   |lambda_c - lambda_{c+1}| <= delta_c = g (||num_{:,c}|| + ||num_{:,c+1}||) + 2^-(53W/2+4) max(|lambda_c|, |lambda_{c+1}|),
 // a local version of the Ogita-Aishima threshold: the couplings bound the eigenvalue errors of the two
 // columns, so a non-orthonormality confined to tiny-eigenvalue columns cannot merge the whole spectrum.
+// The margin g = 128 keeps every rotation k = num / gap outside the clusters below 1/128: the first-order
+// update X + X K then leaves non-orthonormality k^H k < 2^-14, and the iteration stays in its quadratic
+// regime (with g = 2, k reached 1/4 and the first iterations made little progress).
 // The relative floor keeps pairs closer than ~2^-(53W/2) apart together: for them the computed coupling
 // (noise ~2^-53W |lambda|) over the gap would give rotations k whose second-order term k^H k exceeds the
 // working precision; the cluster step (exactly unitary rotation) separates them instead.
+constexpr double kClusterMargin = 128.0;
+
 template <int W>
 __global__ void oa_cluster_kernel(const OaProb* __restrict__ pr, const double* __restrict__ lam,
                                   const double* __restrict__ colnum, int32_t* __restrict__ cl_start,
@@ -139,7 +145,7 @@ __global__ void oa_cluster_kernel(const OaProb* __restrict__ pr, const double* _
     if (!brk) {
       mw<W> a = mw_load<W, W>(lb, i - 1), b = mw_load<W, W>(lb, i);
       double gap = fabs(mw_sub(a, b).x[0]);
-      double d = 2.0 * (sqrt(colnum[p.loff + i - 1]) + sqrt(colnum[p.loff + i])) +
+      double d = kClusterMargin * (sqrt(colnum[p.loff + i - 1]) + sqrt(colnum[p.loff + i])) +
                  floor_rel * fmax(fabs(a.x[0]), fabs(b.x[0]));
       dmax = fmax(dmax, d);
       brk = gap > d;
@@ -335,10 +341,6 @@ __global__ void __launch_bounds__(256) oa_output_kernel(const OaProb* __restrict
 }
 
 // --------------------------------------------------------------------------------------------------
-struct OaBuffers { void** ws; size_t* ws_bytes; void** oz_ws; size_t* oz_bytes; void** oz_meta; size_t* oz_meta_bytes; };
-
-zkq_status eigh_internal(void* ctx, int batch, const int32_t* n, const int64_t* a_off, const double* A, int a_words,
-                         double* W, double* V, int32_t* info, cudaStream_t st);
 
 static size_t alg(size_t x) { return (x + 255) & ~(size_t)255; }
 
@@ -404,7 +406,8 @@ zkq_status oa_refine_t(void* ctx, const OaBuffers& buf, int batch, const int32_t
   int32_t* OO = (int32_t*)(base + oOO);
   double* MUb = (double*)(base + oMU);
   double* NUM = (double*)(base + oNUM);
-  ZKQ_CUDA_TRY(cudaMemcpyAsync(PR, probs.data(), sizeof(OaProb) * batch, cudaMemcpyHostToDevice, st));
+  HostStage& hs = *buf.stage;
+  ZKQ_CUDA_TRY(hs.upload(PR, probs.data(), sizeof(OaProb) * batch, st));
   ZKQ_CUDA_TRY(cudaMemsetAsync(info, 0, sizeof(int32_t) * batch, st));
   {
     dim3 g((nmax * nmax + 255) / 256, batch);
@@ -421,13 +424,16 @@ zkq_status oa_refine_t(void* ctx, const OaBuffers& buf, int batch, const int32_t
     for (int b = 0; b < batch; ++b) if (active[b]) act.push_back(b);
     if (act.empty()) break;
     // P = A X ; S = X^H P ; R = I - X^H X
+    // re-orthonormalising steps (polish 1) need R only: their lambda and couplings are not used, and the
+    // final evaluation (polish 2) forms P and S again
     std::vector<MwProd> p1, p2;
     for (int b : act) {
+      if (polish[b] == 1) continue;
       const OaProb& q = probs[b];
       double* Xb = X + q.xoff * 2 * W;
       p1.push_back({q.n, q.n, q.n, 0, A + q.a_off * 2 * wa, Xb, Pm + q.xoff * 2 * W, nullptr, 1.0, 0});
     }
-    s = mw_gemm_batched(p1.data(), (int)p1.size(), wa, W, W, p_bits, prod_method, buf.oz_ws, buf.oz_bytes, buf.oz_meta, buf.oz_meta_bytes, st);
+    s = mw_gemm_batched(p1.data(), (int)p1.size(), wa, W, W, p_bits, prod_method, buf.oz_ws, buf.oz_bytes, buf.oz_meta, buf.oz_meta_bytes, st, buf.stage);
     if (s != ZKQ_OK) return s;
     for (int b : act) {
       const OaProb& q = probs[b];
@@ -435,34 +441,34 @@ zkq_status oa_refine_t(void* ctx, const OaBuffers& buf, int batch, const int32_t
       MwProd ps_{q.n, q.n, q.n, 1, Xb, Pm + q.xoff * 2 * W, Sm + q.xoff * 2 * W, nullptr, 1.0, 0};
       MwProd pr_{q.n, q.n, q.n, 1, Xb, Xb, Rm + q.xoff * 2 * W, nullptr, -1.0, 1};
       ps_.hermitian = 1; pr_.hermitian = 1;        // S = X^H A X and R = I - X^H X are Hermitian
-      p2.push_back(ps_);
+      if (polish[b] != 1) p2.push_back(ps_);
       p2.push_back(pr_);
     }
-    s = mw_gemm_batched(p2.data(), (int)p2.size(), W, W, W, p_bits, prod_method, buf.oz_ws, buf.oz_bytes, buf.oz_meta, buf.oz_meta_bytes, st);
+    s = mw_gemm_batched(p2.data(), (int)p2.size(), W, W, W, p_bits, prod_method, buf.oz_ws, buf.oz_bytes, buf.oz_meta, buf.oz_meta_bytes, st, buf.stage);
     if (s != ZKQ_OK) return s;
     // statistics for every problem (inactive ones keep their last values: recompute is harmless but skipped)
     std::vector<OaProb> ap; for (int b : act) ap.push_back(probs[b]);
     OaProb* APR = PR;   // the stats/E kernels index PR by the active list
     std::vector<int32_t> actv(act.begin(), act.end());
-    ZKQ_CUDA_TRY(cudaMemcpyAsync(WH, actv.data(), sizeof(int32_t) * actv.size(), cudaMemcpyHostToDevice, st));
+    std::vector<int32_t> oo; for (int b : act) oo.push_back(polish[b] == 1 ? 1 : 0);
     // pack the active problems' descriptors at the front of a scratch copy
     OaProb* PRA = (OaProb*)(base + oCLD);   // reuse: cluster list is built after these kernels
-    ZKQ_CUDA_TRY(cudaMemcpyAsync(PRA, ap.data(), sizeof(OaProb) * ap.size(), cudaMemcpyHostToDevice, st));
+    hs.add(WH, actv.data(), sizeof(int32_t) * actv.size());
+    hs.add(PRA, ap.data(), sizeof(OaProb) * ap.size());
+    hs.add(OO, oo.data(), sizeof(int32_t) * oo.size());
+    ZKQ_CUDA_TRY(hs.flush(st));
     {
       int mx = 0; for (auto& q : ap) mx = std::max(mx, q.n * q.n);
       dim3 g((mx + 255) / 256, (unsigned)ap.size());
       { ProfScope ps_(PC_OA, st); oa_lambda_kernel<W><<<(unsigned)ap.size(), 256, 0, st>>>(PRA, Sm, Rm, Lm, CN, ST); }
       { ProfScope ps_(PC_OA, st); oa_coupling_kernel<W><<<g, 256, 0, st>>>(PRA, Sm, Rm, Lm, CN, NUM, ST); }
       { ProfScope ps_(PC_OA, st); oa_cluster_kernel<W><<<(unsigned)ap.size(), 32, 0, st>>>(PRA, Lm, CN, CS, CL, ST); }
-      std::vector<int32_t> oo; for (int b : act) oo.push_back(polish[b] == 1 ? 1 : 0);
-      ZKQ_CUDA_TRY(cudaMemcpyAsync(OO, oo.data(), sizeof(int32_t) * oo.size(), cudaMemcpyHostToDevice, st));
       { ProfScope ps_(PC_OA, st); oa_E_kernel<W><<<g, 256, 0, st>>>(PRA, NUM, Rm, Lm, CS, OO, Em, ST); }
       ZKQ_CUDA_TRY(cudaGetLastError());
     }
     std::vector<OaStat> ast(ap.size());
-    ZKQ_CUDA_TRY(cudaMemcpyAsync(ast.data(), ST, sizeof(OaStat) * ap.size(), cudaMemcpyDeviceToHost, st));
-    ZKQ_CUDA_TRY(cudaMemcpyAsync(hcl_len.data(), CL, sizeof(int32_t) * le, cudaMemcpyDeviceToHost, st));
-    ZKQ_CUDA_TRY(cudaStreamSynchronize(st));
+    ZKQ_CUDA_TRY(hs.download_sync(ast.data(), ST, sizeof(OaStat) * ap.size(), st));
+    ZKQ_CUDA_TRY(hs.download_sync(hcl_len.data(), CL, sizeof(int32_t) * le, st));
     (void)APR;
     if (debug_log()) {
       for (size_t a = 0; a < act.size(); ++a)
@@ -494,9 +500,10 @@ zkq_status oa_refine_t(void* ctx, const OaBuffers& buf, int batch, const int32_t
       // statistics of finishing problems are in ST at their active index: copy to a per-problem array
       std::vector<OaStat> fst(batch);
       for (size_t a = 0; a < act.size(); ++a) fst[act[a]] = ast[a];
-      ZKQ_CUDA_TRY(cudaMemcpyAsync(ST, fst.data(), sizeof(OaStat) * batch, cudaMemcpyHostToDevice, st));
-      ZKQ_CUDA_TRY(cudaMemcpyAsync(WH, finish.data(), sizeof(int32_t) * finish.size(), cudaMemcpyHostToDevice, st));
-      ZKQ_CUDA_TRY(cudaMemcpyAsync(PR, probs.data(), sizeof(OaProb) * batch, cudaMemcpyHostToDevice, st));
+      hs.add(ST, fst.data(), sizeof(OaStat) * batch);
+      hs.add(WH, finish.data(), sizeof(int32_t) * finish.size());
+      hs.add(PR, probs.data(), sizeof(OaProb) * batch);
+      ZKQ_CUDA_TRY(hs.flush(st));
       { ProfScope ps_(PC_OA, st); oa_output_kernel<W><<<(unsigned)finish.size(), 256, 0, st>>>(PR, WH, X, Pm, Lm, ST, W_out, V_out, err); }
       ZKQ_CUDA_TRY(cudaGetLastError());
       std::vector<int32_t> hinfo(batch, 0);
@@ -506,8 +513,8 @@ zkq_status oa_refine_t(void* ctx, const OaBuffers& buf, int batch, const int32_t
         if (polish[b] != 2) { hinfo[b] = it > 0 ? it : 1; any = true; }
       }
       if (any) {
-        for (int b : finish) if (hinfo[b]) ZKQ_CUDA_TRY(cudaMemcpyAsync(info + b, &hinfo[b], sizeof(int32_t), cudaMemcpyHostToDevice, st));
-        ZKQ_CUDA_TRY(cudaStreamSynchronize(st));
+        for (int b : finish) if (hinfo[b]) hs.add(info + b, &hinfo[b], sizeof(int32_t));
+        ZKQ_CUDA_TRY(hs.flush(st));
       }
     }
     if (upd.empty()) continue;
@@ -519,7 +526,7 @@ zkq_status oa_refine_t(void* ctx, const OaBuffers& buf, int batch, const int32_t
       p3.push_back({q.n, q.n, q.n, 0, Xb, Em + q.xoff * 2 * 2, X2 + q.xoff * 2 * W, Xb, 1.0, 0});
     }
     // E is indexed by the active order in the E kernel: it wrote at each problem's own xoff, so p3 is direct
-    s = mw_gemm_batched(p3.data(), (int)p3.size(), W, 2, W, p_bits, prod_method, buf.oz_ws, buf.oz_bytes, buf.oz_meta, buf.oz_meta_bytes, st);
+    s = mw_gemm_batched(p3.data(), (int)p3.size(), W, 2, W, p_bits, prod_method, buf.oz_ws, buf.oz_bytes, buf.oz_meta, buf.oz_meta_bytes, st, buf.stage);
     if (s != ZKQ_OK) return s;
     // clusters that still need separation
     std::vector<OaCluster> cls;
@@ -538,8 +545,9 @@ zkq_status oa_refine_t(void* ctx, const OaBuffers& buf, int batch, const int32_t
     }
     if (!cls.empty()) {
       int maxl = 0; for (auto& c : cls) maxl = std::max(maxl, c.len);
-      ZKQ_CUDA_TRY(cudaMemcpyAsync(PR, probs.data(), sizeof(OaProb) * batch, cudaMemcpyHostToDevice, st));
-      ZKQ_CUDA_TRY(cudaMemcpyAsync(CLD, cls.data(), sizeof(OaCluster) * cls.size(), cudaMemcpyHostToDevice, st));
+      hs.add(PR, probs.data(), sizeof(OaProb) * batch);
+      hs.add(CLD, cls.data(), sizeof(OaCluster) * cls.size());
+      ZKQ_CUDA_TRY(hs.flush(st));
       // Q_J = A X2_J (into the P buffer's cluster columns), then CT = X2_J^H Q_J, CG = X2_J^H X2_J
       std::vector<MwProd> p5, p6;
       for (auto& c : cls) {
@@ -553,9 +561,9 @@ zkq_status oa_refine_t(void* ctx, const OaBuffers& buf, int batch, const int32_t
         p6.push_back(pt_);
         p6.push_back(pg_);
       }
-      s = mw_gemm_batched(p5.data(), (int)p5.size(), wa, W, W, p_bits, prod_method, buf.oz_ws, buf.oz_bytes, buf.oz_meta, buf.oz_meta_bytes, st);
+      s = mw_gemm_batched(p5.data(), (int)p5.size(), wa, W, W, p_bits, prod_method, buf.oz_ws, buf.oz_bytes, buf.oz_meta, buf.oz_meta_bytes, st, buf.stage);
       if (s != ZKQ_OK) return s;
-      s = mw_gemm_batched(p6.data(), (int)p6.size(), W, W, W, p_bits, prod_method, buf.oz_ws, buf.oz_bytes, buf.oz_meta, buf.oz_meta_bytes, st);
+      s = mw_gemm_batched(p6.data(), (int)p6.size(), W, W, W, p_bits, prod_method, buf.oz_ws, buf.oz_bytes, buf.oz_meta, buf.oz_meta_bytes, st, buf.stage);
       if (s != ZKQ_OK) return s;
       dim3 g((maxl * maxl + 255) / 256, (unsigned)cls.size());
       { ProfScope ps_(PC_OA, st); oa_cluster_mu_kernel<W><<<(unsigned)((cls.size() + 127) / 128), 128, 0, st>>>(PR, CLD, (int)cls.size(), Lm, MUb); }
@@ -563,7 +571,7 @@ zkq_status oa_refine_t(void* ctx, const OaBuffers& buf, int batch, const int32_t
       ZKQ_CUDA_TRY(cudaGetLastError());
       std::vector<int32_t> cn(cls.size()); std::vector<int64_t> co(cls.size());
       for (size_t c = 0; c < cls.size(); ++c) { cn[c] = cls[c].len; co[c] = cls[c].toff; }
-      s = eigh_internal(ctx, (int)cls.size(), cn.data(), co.data(), T, 1, TW, TV, TI, st);
+      s = eigh_internal(ctx, (int)cls.size(), cn.data(), co.data(), T, 1, TW, TV, TI, st, PC_JACOBI_CLUSTER);
       if (s != ZKQ_OK) return s;
       // The FP64 eigenvector matrix is unitary only to 2^-53; two Newton-Schulz steps W <- W (3I - W^H W)/2
       // in W-word products make it unitary to working precision, so the rotation does not disturb the
@@ -578,12 +586,12 @@ zkq_status oa_refine_t(void* ctx, const OaBuffers& buf, int batch, const int32_t
           g_.hermitian = 1;
           pg.push_back(g_);
         }
-        s = mw_gemm_batched(pg.data(), (int)pg.size(), W, W, W, p_bits, prod_method, buf.oz_ws, buf.oz_bytes, buf.oz_meta, buf.oz_meta_bytes, st);
+        s = mw_gemm_batched(pg.data(), (int)pg.size(), W, W, W, p_bits, prod_method, buf.oz_ws, buf.oz_bytes, buf.oz_meta, buf.oz_meta_bytes, st, buf.stage);
         if (s != ZKQ_OK) return s;
         { ProfScope ps_(PC_OA, st); oa_ns_kernel<W><<<g, 256, 0, st>>>(CLD, CG); }
         ZKQ_CUDA_TRY(cudaGetLastError());
         for (auto& c : cls) pw.push_back({c.len, c.len, c.len, 0, Wcur + c.toff * 2 * W, CG + c.toff * 2 * W, Wnext + c.toff * 2 * W, nullptr, 1.0, 0});
-        s = mw_gemm_batched(pw.data(), (int)pw.size(), W, W, W, p_bits, prod_method, buf.oz_ws, buf.oz_bytes, buf.oz_meta, buf.oz_meta_bytes, st);
+        s = mw_gemm_batched(pw.data(), (int)pw.size(), W, W, W, p_bits, prod_method, buf.oz_ws, buf.oz_bytes, buf.oz_meta, buf.oz_meta_bytes, st, buf.stage);
         if (s != ZKQ_OK) return s;
         std::swap(Wcur, Wnext);
       }
@@ -594,18 +602,14 @@ zkq_status oa_refine_t(void* ctx, const OaBuffers& buf, int batch, const int32_t
         p4.push_back({q.n, c.len, c.len, 0, X2 + (q.xoff + (int64_t)c.start * q.n) * 2 * W, Wcur + c.toff * 2 * W,
                       X + (q.xoff + (int64_t)c.start * q.n) * 2 * W, nullptr, 1.0, 0});
       }
-      s = mw_gemm_batched(p4.data(), (int)p4.size(), W, W, W, p_bits, prod_method, buf.oz_ws, buf.oz_bytes, buf.oz_meta, buf.oz_meta_bytes, st);
+      s = mw_gemm_batched(p4.data(), (int)p4.size(), W, W, W, p_bits, prod_method, buf.oz_ws, buf.oz_bytes, buf.oz_meta, buf.oz_meta_bytes, st, buf.stage);
       if (s != ZKQ_OK) return s;
       dim3 g2((nmax * maxl + 255) / 256, (unsigned)cls.size());
       { ProfScope ps_(PC_OA, st); oa_cluster_copy_kernel<W><<<g2, 256, 0, st>>>(PR, CLD, X, X2); }
       ZKQ_CUDA_TRY(cudaGetLastError());
     }
-    // X <- X2 for updated problems (swap buffers by copying the updated problems' matrices)
-    for (int b : upd) {
-      const OaProb& q = probs[b];
-      ZKQ_CUDA_TRY(cudaMemcpyAsync(X + q.xoff * 2 * W, X2 + q.xoff * 2 * W, (size_t)q.n * q.n * 2 * W * sizeof(double),
-                                   cudaMemcpyDeviceToDevice, st));
-    }
+    // X <- X2: every active problem was either finished (its output is written) or updated into X2
+    std::swap(X, X2);
   }
   return ZKQ_OK;
 }

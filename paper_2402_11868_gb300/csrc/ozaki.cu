@@ -19,6 +19,7 @@
 #include "crt.cuh"
 #include "mw.cuh"
 #include "prof.cuh"
+#include "internal.cuh"
 #include <vector>
 #include <algorithm>
 #include <cstring>
@@ -467,6 +468,10 @@ template <int L> __device__ __forceinline__ void bl_add_shifted(BigL<L>& x, uint
   if (bs && li + 1 < L) w[li + 1] = m >> (64 - bs);
   if (!neg) bl_add_mul<L>(x, 1, w, L); else bl_sub_mul<L>(x, 1, w, L);
 }
+// 2^e as a double for |e| <= 1022 (exponent field), else by ldexp
+__device__ __forceinline__ double pow2i(int e) {
+  return (e >= -1022 && e <= 1023) ? __longlong_as_double((long long)(e + 1023) << 52) : ldexp(1.0, e);
+}
 // nearest double of the signed integer R times 2^scale; R -= that value
 template <int L> __device__ double bl_round_off(BigL<L>& R, int scale) {
   bool ng = bl_neg(R);
@@ -487,7 +492,8 @@ template <int L> __device__ double bl_round_off(BigL<L>& R, int scale) {
     if (rnd && (sticky || (m & 1))) m += 1;
   } else { m = Mg.l[0]; lo = 0; }
   bl_add_shifted<L>(R, m, lo, !ng);
-  double v = ldexp((double)m, lo + scale);
+  const int ev = lo + scale;                     // m < 2^54: the product is exact unless it underflows
+  double v = (ev >= -1022 && ev <= 1023) ? (double)m * pow2i(ev) : ldexp((double)m, ev);
   return ng ? -v : v;
 }
 
@@ -652,9 +658,10 @@ __device__ __forceinline__ void crt_sum32(Res&& residue, const CrtConst* __restr
   S[CRT_L32] = (uint32_t)carry; S[CRT_L32 + 1] = (uint32_t)(carry >> 32);
   // quotient estimate q = floor(S / M) (< 2^15) from the leading bits, exact correction after
   int top = L - 1; while (top > 0 && S[top] == 0) --top;
-  double sd = (double)S[top] + (top > 0 ? ldexp((double)S[top - 1], -32) : 0.0) + (top > 1 ? ldexp((double)S[top - 2], -64) : 0.0);
-  double qd = ldexp(sd, 32 * top) / ldexp(cc->Md, cc->Mexp);
-  int64_t qq = qd > 1.0 ? (int64_t)qd : 0;
+  double sd = (double)S[top] + (top > 0 ? (double)S[top - 1] * 0x1p-32 : 0.0) + (top > 1 ? (double)S[top - 2] * 0x1p-64 : 0.0);
+  const int qe = 32 * top - cc->Mexp;            // S / M ~ sd Mrcp 2^qe
+  double qd = qe < -60 ? 0.0 : (qe > 60 ? 1e30 : sd * cc->Mrcp * pow2i(qe));
+  int64_t qq = qd > 1.0 ? (int64_t)fmin(qd, 1e18) : 0;
   // S -= q M (signed 64-bit lazy borrow)
   {
     int64_t b = 0;
@@ -800,7 +807,14 @@ static zkq_status grow(void** p, size_t* have, size_t need) {
   do { if ((w) == 1) { F<1> __VA_ARGS__; } else if ((w) == 2) { F<2> __VA_ARGS__; } else { F<4> __VA_ARGS__; } } while (0)
 
 zkq_status mw_gemm_batched(const MwProd* prods, int count, int wa, int wb, int wc, int p_out_bits, int method,
-                           void** ws, size_t* ws_bytes, void** meta, size_t* meta_bytes, cudaStream_t st) {
+                           void** ws, size_t* ws_bytes, void** meta, size_t* meta_bytes, cudaStream_t st,
+                           HostStage* stage) {
+  // uploads of the batch description: pinned ring when available, else plain copies
+  auto up = [&](void* dst, const void* src, size_t bytes) -> cudaError_t {
+    if (stage) { stage->add(dst, src, bytes); return cudaSuccess; }
+    return cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, st);
+  };
+  auto up_done = [&]() -> cudaError_t { return stage ? stage->flush(st) : cudaSuccess; };
   if (count <= 0) return ZKQ_OK;
   for (int w : {wa, wb, wc}) if (w != 1 && w != 2 && w != 4) return ZKQ_EINVAL;
   std::vector<OzProd> dp(count);
@@ -823,7 +837,8 @@ zkq_status mw_gemm_batched(const MwProd* prods, int count, int wa, int wb, int w
   if (method == 0) {
     zkq_status s = grow(meta, meta_bytes, al(sizeof(OzProd) * count));
     if (s != ZKQ_OK) return s;
-    ZKQ_CUDA_TRY(cudaMemcpyAsync(*meta, dp.data(), sizeof(OzProd) * count, cudaMemcpyHostToDevice, st));
+    ZKQ_CUDA_TRY(up(*meta, dp.data(), sizeof(OzProd) * count));
+    ZKQ_CUDA_TRY(up_done());
     dim3 grid((max_mn + 127) / 128, count);
     const OzProd* d = (const OzProd*)*meta;
     ProfScope ps(PC_OZ_GEMM, st);
@@ -913,10 +928,11 @@ zkq_status mw_gemm_batched(const MwProd* prods, int count, int wa, int wb, int w
   char* mb = (char*)*meta;
   OzProd* d_p = (OzProd*)mb; OzTile* d_t = (OzTile*)(mb + m_p); OzPair* d_q = (OzPair*)(mb + m_p + m_t);
   CrtConst* d_c = (CrtConst*)(mb + m_p + m_t + m_q);
-  if (crt) ZKQ_CUDA_TRY(cudaMemcpyAsync(d_c, &cc, sizeof(CrtConst), cudaMemcpyHostToDevice, st));
-  ZKQ_CUDA_TRY(cudaMemcpyAsync(d_p, dp.data(), sizeof(OzProd) * count, cudaMemcpyHostToDevice, st));
-  ZKQ_CUDA_TRY(cudaMemcpyAsync(d_t, tiles.data(), sizeof(OzTile) * tiles.size(), cudaMemcpyHostToDevice, st));
-  ZKQ_CUDA_TRY(cudaMemcpyAsync(d_q, pairs.data(), sizeof(OzPair) * pairs.size(), cudaMemcpyHostToDevice, st));
+  if (crt) ZKQ_CUDA_TRY(up(d_c, &cc, sizeof(CrtConst)));
+  ZKQ_CUDA_TRY(up(d_p, dp.data(), sizeof(OzProd) * count));
+  ZKQ_CUDA_TRY(up(d_t, tiles.data(), sizeof(OzTile) * tiles.size()));
+  ZKQ_CUDA_TRY(up(d_q, pairs.data(), sizeof(OzPair) * pairs.size()));
+  ZKQ_CUDA_TRY(up_done());
   int max_rows = 0;
   for (auto& o : dp) max_rows = std::max(max_rows, o.m + o.n);
   {

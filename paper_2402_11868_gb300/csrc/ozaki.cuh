@@ -45,9 +45,12 @@ struct OzPlan {
 
 OzPlan ozaki_plan(int max_kprime, int wa, int wb, int p_out_bits);
 
-// Run a batch of products (all with the same word counts and output precision).  method 1: Ozaki
-// tensor-core slices; method 0: plain multi-word GEMM on the FP64 pipe.
+class HostStage;
+// Run a batch of products (all with the same word counts and output precision).  method 1: CRT residue
+// products on the tensor cores (digit form when K' > 1024); method 2: digit form; method 0: plain
+// multi-word GEMM on the FP64 pipe.  Metadata goes up through `stage` (pinned) when it is given.
 zkq_status mw_gemm_batched(const MwProd* prods, int count, int wa, int wb, int wc, int p_out_bits, int method,
-                           void** ws, size_t* ws_bytes, void** meta, size_t* meta_bytes, cudaStream_t st);
+                           void** ws, size_t* ws_bytes, void** meta, size_t* meta_bytes, cudaStream_t st,
+                           HostStage* stage);
 
 }  // namespace zkq

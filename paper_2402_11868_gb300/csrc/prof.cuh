@@ -7,7 +7,10 @@
 
 namespace zkq {
 
-enum ProfClass { PC_JACOBI = 0, PC_RQI, PC_OZ_SCALE, PC_OZ_SLICE, PC_OZ_GEMM, PC_OZ_COMBINE, PC_OA, PC_MPS, PC_OTHER, PC_COUNT };
+// PC_JACOBI: the FP64 eigensolve of the inputs; PC_JACOBI_CLUSTER: the same kernels on the refinement's
+// cluster blocks
+enum ProfClass { PC_JACOBI = 0, PC_RQI, PC_OZ_SCALE, PC_OZ_SLICE, PC_OZ_GEMM, PC_OZ_COMBINE, PC_OA, PC_MPS, PC_OTHER,
+                 PC_JACOBI_CLUSTER, PC_COUNT };
 
 struct Profiler {
   bool on = false;

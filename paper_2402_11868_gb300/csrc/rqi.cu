@@ -12,15 +12,10 @@
 #include "mw.cuh"
 #include "reduce.cuh"
 #include "prof.cuh"
+#include "internal.cuh"
 
 namespace zkq {
 
-struct RqiBatch {
-  const int32_t* n; const int64_t* a_off; const int64_t* w_off; const int32_t* pair_prob;
-  const double* A; const double* W; const double* V;
-  double* W_out; double* V_out; double* err; int32_t* info;
-  double* ws; int64_t ws_stride; int64_t total_pairs; int max_iter; int* counter;
-};
 
 // Convergence: the computed residual cannot drop below the rounding floor ~ n 2^(-53W) ||A||, so the
 // iteration counts as converged at 16 n 2^(-53W) ||A|| and then takes one more (cubically convergent)
