@@ -85,12 +85,22 @@ __device__ __forceinline__ void atomic_max_nonneg(double* a, double v) {
 // couplings num_ij = s_ij + (lambda_i + lambda_j)/2 r_ij (i != j): first-order insensitive to the
 // non-orthonormality of X, (lambda_i - lambda_j)/2 times the rotation error of the pair.  Accumulates
 // column norms ||num_{:,c}||^2, max |num| and max |r|.
+// The column sums go through shared memory first (a block of 256 consecutive elements touches at most
+// 256/n + 2 columns), then one global atomic per touched column.
 template <int W>
-__global__ void oa_coupling_kernel(const OaProb* __restrict__ pr, const double* __restrict__ S, const double* __restrict__ R,
-                                   const double* __restrict__ lam, double* __restrict__ colnum, double* __restrict__ NUM,
-                                   OaStat* __restrict__ st) {
+__global__ void __launch_bounds__(256) oa_coupling_kernel(const OaProb* __restrict__ pr, const double* __restrict__ S,
+                                                          const double* __restrict__ R, const double* __restrict__ lam,
+                                                          double* __restrict__ colnum, double* __restrict__ NUM,
+                                                          OaStat* __restrict__ st) {
+  __shared__ double csum[258];
   const OaProb p = pr[blockIdx.y];
-  int e = blockIdx.x * blockDim.x + threadIdx.x;
+  const int e0 = blockIdx.x * blockDim.x;
+  if (e0 >= p.n * p.n) return;                         // whole block past this problem
+  const int j0 = e0 / p.n;
+  const int jn = min(p.n - 1, (e0 + (int)blockDim.x - 1) / p.n) - j0 + 1;   // columns touched (<= 258)
+  for (int t = threadIdx.x; t < jn; t += blockDim.x) csum[t] = 0.0;
+  __syncthreads();
+  int e = e0 + threadIdx.x;
   double cpl = 0.0, rmag = 0.0;
   if (e < p.n * p.n) {
     const int n = p.n, i = e % n, j = e / n;
@@ -102,11 +112,14 @@ __global__ void oa_coupling_kernel(const OaProb* __restrict__ pr, const double* 
       mw<W> hs = mw_mul_d(mw_add(mw_load<W, W>(lam + p.loff * W, i), mw_load<W, W>(lam + p.loff * W, j)), 0.5);
       cmw<W> num = c_add(sv, c_scale(r, hs));       // cancellation-sensitive: working precision
       cpl = hypot(num.re.x[0], num.im.x[0]);
-      if (cpl > 0) atomicAdd(&colnum[p.loff + j], cpl * cpl);
+      if (cpl > 0) atomicAdd(&csum[j - j0], cpl * cpl);
       num2 = c_make(mw_from_words<2, W>(num.re.x), mw_from_words<2, W>(num.im.x));
     }
     c_store(NUM + p.xoff * 2 * 2, e, num2);
   }
+  __syncthreads();
+  for (int t = threadIdx.x; t < jn; t += blockDim.x)
+    if (csum[t] > 0) atomicAdd(&colnum[p.loff + j0 + t], csum[t]);
   for (int o = 16; o > 0; o >>= 1) {
     cpl = fmax(cpl, __shfl_down_sync(0xffffffffu, cpl, o));
     rmag = fmax(rmag, __shfl_down_sync(0xffffffffu, rmag, o));
@@ -296,47 +309,59 @@ __device__ __forceinline__ bool mw_greater(const mw<W>& a, const mw<W>& b) {
   return d.x[0] > 0.0;
 }
 
+// One warp per output column c (8 per block): rank of lambda_c (descending, ties by index), residual
+// estimate ||P_c - lambda_c X_c|| / ||A|| (the residual in W words, its norm in double), and X_c with its
+// first largest-modulus component made real and positive, written to column `rank`.  Lanes stride the
+// rows, so the column reads and writes are coalesced.
 template <int W>
 __global__ void __launch_bounds__(256) oa_output_kernel(const OaProb* __restrict__ pr, const int32_t* __restrict__ which,
                                                         const double* __restrict__ X, const double* __restrict__ P,
                                                         const double* __restrict__ lam, const OaStat* __restrict__ st,
                                                         double* __restrict__ W_out, double* __restrict__ V_out,
                                                         double* __restrict__ err) {
-  const int b = which[blockIdx.x];
+  const int b = which[blockIdx.y];
   const OaProb p = pr[b];
   const int n = p.n;
+  const int lane = threadIdx.x & 31;
+  const int c = blockIdx.x * 8 + (threadIdx.x >> 5);
+  if (c >= n) return;                                  // whole warps leave
   const double* lb = lam + p.loff * W;
   const double anorm = fmax(st[b].anorm, 1e-300);
-  for (int c = threadIdx.x; c < n; c += blockDim.x) {
-    mw<W> lc = mw_load<W, W>(lb, c);
-    int rank = 0;
-    for (int d = 0; d < n; ++d) {
-      if (d == c) continue;
-      mw<W> ld = mw_load<W, W>(lb, d);
-      mw<W> df = mw_sub(ld, lc);
-      rank += (df.x[0] > 0.0) || (df.x[0] == 0.0 && d < c);
-    }
+  const mw<W> lc = mw_load<W, W>(lb, c);
+  int rank = 0;
+  for (int d = lane; d < n; d += 32) {
+    if (d == c) continue;
+    mw<W> df = mw_sub(mw_load<W, W>(lb, d), lc);
+    rank += (df.x[0] > 0.0) || (df.x[0] == 0.0 && d < c);
+  }
+  const double* xc = X + (p.xoff + (size_t)c * n) * 2 * W;
+  const double* pc = P + (p.xoff + (size_t)c * n) * 2 * W;
+  int best = n; double bm = -1.0, rr = 0.0;
+  for (int r = lane; r < n; r += 32) {
+    const double m2 = xc[r * 2 * W] * xc[r * 2 * W] + xc[r * 2 * W + W] * xc[r * 2 * W + W];
+    if (m2 > bm) { bm = m2; best = r; }                // rows ascend per lane: the first largest
+    cmw<W> res = c_sub(c_load<W, W>(pc, r), c_scale(c_load<W, W>(xc, r), lc));
+    rr += res.re.x[0] * res.re.x[0] + res.im.x[0] * res.im.x[0];
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    rank += __shfl_xor_sync(0xffffffffu, rank, o);
+    rr += __shfl_xor_sync(0xffffffffu, rr, o);
+    const double obm = __shfl_xor_sync(0xffffffffu, bm, o);
+    const int obest = __shfl_xor_sync(0xffffffffu, best, o);
+    if (obm > bm || (obm == bm && obest < best)) { bm = obm; best = obest; }
+  }
+  if (lane == 0) {
     mw_store(W_out, p.loff + rank, lc);
-    const double* xc = X + (p.xoff + (size_t)c * n) * 2 * W;
-    const double* pc = P + (p.xoff + (size_t)c * n) * 2 * W;
-    int best = 0; double bm = -1.0;
-    mw<W> rr = mw_zero<W>();
-    for (int r = 0; r < n; ++r) {
-      double m2 = xc[r * 2 * W] * xc[r * 2 * W] + xc[r * 2 * W + W] * xc[r * 2 * W + W];
-      if (m2 > bm) { bm = m2; best = r; }
-      cmw<W> res = c_sub(c_load<W, W>(pc, r), c_scale(c_load<W, W>(xc, r), lc));
-      rr = mw_add(rr, c_abs2(res));
-    }
-    err[p.loff + rank] = sqrt(fmax(rr.x[0], 0.0)) / anorm;
-    cmw<W> xb = c_load<W, W>(xc, best);
-    mw<W> mag = mw_sqrt(c_abs2(xb));
-    cmw<W> ph = c_make(mw_div(xb.re, mag), mw_neg(mw_div(xb.im, mag)));
-    double* vo = V_out + (p.a_off + (size_t)rank * n) * 2 * W;
-    for (int r = 0; r < n; ++r) {
-      cmw<W> v = c_mul(c_load<W, W>(xc, r), ph);
-      if (r == best) v.im = mw_zero<W>();
-      c_store(vo, r, v);
-    }
+    err[p.loff + rank] = sqrt(rr) / anorm;
+  }
+  const cmw<W> xb = c_load<W, W>(xc, best);
+  const mw<W> mag = mw_sqrt(c_abs2(xb));
+  const cmw<W> ph = c_make(mw_div(xb.re, mag), mw_neg(mw_div(xb.im, mag)));
+  double* vo = V_out + (p.a_off + (size_t)rank * n) * 2 * W;
+  for (int r = lane; r < n; r += 32) {
+    cmw<W> v = c_mul(c_load<W, W>(xc, r), ph);
+    if (r == best) v.im = mw_zero<W>();
+    c_store(vo, r, v);
   }
 }
 
@@ -504,7 +529,10 @@ zkq_status oa_refine_t(void* ctx, const OaBuffers& buf, int batch, const int32_t
       hs.add(WH, finish.data(), sizeof(int32_t) * finish.size());
       hs.add(PR, probs.data(), sizeof(OaProb) * batch);
       ZKQ_CUDA_TRY(hs.flush(st));
-      { ProfScope ps_(PC_OA, st); oa_output_kernel<W><<<(unsigned)finish.size(), 256, 0, st>>>(PR, WH, X, Pm, Lm, ST, W_out, V_out, err); }
+      {
+        ProfScope ps_(PC_OA, st);
+        oa_output_kernel<W><<<dim3((unsigned)((nmax + 7) / 8), (unsigned)finish.size()), 256, 0, st>>>(PR, WH, X, Pm, Lm, ST, W_out, V_out, err);
+      }
       ZKQ_CUDA_TRY(cudaGetLastError());
       std::vector<int32_t> hinfo(batch, 0);
       bool any = false;

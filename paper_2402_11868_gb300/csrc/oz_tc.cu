@@ -53,16 +53,88 @@ __device__ __forceinline__ void cp_async16_tc(uint32_t dst, const void* src) {
 // 128-byte swizzle: 16-byte chunk c of row r lives at r*128 + ((c ^ (r & 7)) * 16)
 __device__ __forceinline__ int sw128(int row, int chunk) { return row * 128 + ((chunk ^ (row & 7)) << 4); }
 
-__global__ void __launch_bounds__(128, 1) oz_tc_kernel(const OzProd* __restrict__ P, const OzTile* __restrict__ tiles,
-                                                       const OzPair* __restrict__ pairs, int npairs,
-                                                       const CrtConst* __restrict__ cc, int* err) {
+// One 32-column chunk of the accumulator in TMEM (columns col0 .. col0 + 31 of buffer at tmem_col) added to
+// the running level sums; at a level end the chunk is stored (int32, or CRT residues as bytes) and cleared.
+template <int C>
+__device__ __forceinline__ void tc_epilogue_chunk(int32_t (&dacc)[TC_BN], uint32_t tmem_lane_col, bool level_end,
+                                                  const OzProd& p, const OzTile& tl, int level,
+                                                  const CrtConst* __restrict__ cc, int warp, int lane) {
+  uint32_t v[32];
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+               "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];\n"
+               : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+                 "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]),
+                 "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]),
+                 "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+               : "r"(tmem_lane_col + (uint32_t)(32 * C)));
+  asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::);
+#pragma unroll
+  for (int j = 0; j < 32; ++j) dacc[32 * C + j] += __float2int_rn(__uint_as_float(v[j]));
+  if (!level_end) return;
+  // row = tile row of this thread (TMEM lane), columns 32 C .. 32 C + 31 of the tile
+  const int r = tl.ti * TC_BM + warp * 32 + lane;
+  const size_t off = (size_t)level * p.mp * p.np2 + (size_t)r * p.np2 + (size_t)tl.tj * TC_BN + 32 * C;
+  if (cc) {
+    // CRT form: residues modulo the level's modulus, one byte each
+    const int t = level % cc->r;
+    const uint32_t m = (uint32_t)cc->m[t], minv = cc->minv[t];
+    uint8_t* D8 = reinterpret_cast<uint8_t*>(p.D) + off;
+#pragma unroll
+    for (int j = 0; j < 32; j += 16) {
+      uint32_t w[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int b = 32 * C + j + 4 * q;
+        w[q] = crt_mod(dacc[b], m, minv) | (crt_mod(dacc[b + 1], m, minv) << 8) |
+               (crt_mod(dacc[b + 2], m, minv) << 16) | (crt_mod(dacc[b + 3], m, minv) << 24);
+      }
+      *reinterpret_cast<uint4*>(D8 + j) = make_uint4(w[0], w[1], w[2], w[3]);
+    }
+  } else {
+    int32_t* D = p.D + off;
+#pragma unroll
+    for (int j = 0; j < 32; j += 4)
+      *reinterpret_cast<int4*>(D + j) = make_int4(dacc[32 * C + j], dacc[32 * C + j + 1], dacc[32 * C + j + 2], dacc[32 * C + j + 3]);
+  }
+#pragma unroll
+  for (int j = 0; j < 32; ++j) dacc[32 * C + j] = 0;
+}
+
+// bounded wait that also gives up once another role raised the CTA's abort flag
+__device__ __forceinline__ bool mbar_wait_ab(uint64_t* b, uint32_t par, volatile int* abort_flag) {
+  uint32_t addr = tc_smem_u32(b);
+  for (int it = 0; it < (1 << 24); ++it) {
+    uint32_t ok;
+    asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+                 : "=r"(ok) : "r"(addr), "r"(par));
+    if (ok) return true;
+    if ((it & 1023) == 1023 && *abort_flag) return false;
+  }
+  return false;
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* b) {
+  asm volatile("{\n .reg .b64 st;\n mbarrier.arrive.shared::cta.b64 st, [%0];\n}\n" :: "r"(tc_smem_u32(b)));
+}
+
+// Warp roles (7 warps): 0-3 epilogue (warp w reads TMEM lanes 32w..32w+31 = tile rows), 4-5 producers
+// (cp.async of the A and B stage tiles), 6 MMA issue (one lane).  Barriers:
+//   full[s]   stage s loaded (64 producer arrivals, each after its copies completed and were fenced
+//             for the async proxy)              -> MMA
+//   empty[s]  the MMAs reading stage s are done (tcgen05.commit)            -> producers
+//   accf[b]   accumulator b holds a finished group (tcgen05.commit)         -> epilogue
+//   acce[b]   accumulator b was read out (128 epilogue arrivals)            -> MMA
+// The k-th completion of a barrier is waited for with parity k & 1.
+constexpr int TC_THREADS = 224;
+constexpr int TC_PRODUCERS = 64;
+
+__global__ void __launch_bounds__(TC_THREADS, 1) oz_tc_kernel(const OzProd* __restrict__ P, const OzTile* __restrict__ tiles,
+                                                              const OzPair* __restrict__ pairs, int npairs,
+                                                              const CrtConst* __restrict__ cc, int* err) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
-  // 1024-byte aligned carve-out for the swizzled stages
   unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   unsigned char* sA = smem;                                         // STAGES x 16 KB
   unsigned char* sB = smem + TC_STAGES * TC_BM * 128;               // STAGES x 16 KB
-  __shared__ __align__(8) uint64_t bar_stage[TC_STAGES];
-  __shared__ __align__(8) uint64_t bar_acc;
+  __shared__ __align__(8) uint64_t full[TC_STAGES], empty[TC_STAGES], accf[2], acce[2], fin;
   __shared__ uint32_t tmem_base;
   __shared__ int abort_flag;
 
@@ -71,152 +143,129 @@ __global__ void __launch_bounds__(128, 1) oz_tc_kernel(const OzProd* __restrict_
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int nk = p.kp / TC_BK;
   const int total = npairs * nk;
-  const size_t planeA = (size_t)p.mp * p.kp, planeB = (size_t)p.np2 * p.kp;
-  const __half* Abase = p.Ahat + (size_t)tl.ti * TC_BM * p.kp;
-  const __half* Bbase = p.Bhat + (size_t)tl.tj * TC_BN * p.kp;
+  volatile int* abort_v = &abort_flag;
 
   if (tid == 0) {
-    for (int s = 0; s < TC_STAGES; ++s) mbar_init(&bar_stage[s], 1);
-    mbar_init(&bar_acc, 1);
+    for (int s = 0; s < TC_STAGES; ++s) { mbar_init(&full[s], TC_PRODUCERS); mbar_init(&empty[s], 1); }
+    for (int b = 0; b < 2; ++b) { mbar_init(&accf[b], 1); mbar_init(&acce[b], 128); }
+    mbar_init(&fin, 1);
     abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;\n" ::);
   }
-  if (warp == 0) {
+  if (warp == 0) {                      // two accumulators: 2 x TC_BN columns
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n"
-                 :: "r"(tc_smem_u32(&tmem_base)), "r"(TC_BN));
+                 :: "r"(tc_smem_u32(&tmem_base)), "r"(2 * TC_BN));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::);
   }
   asm volatile("tcgen05.fence::before_thread_sync;\n" ::);
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;\n" ::);
   const uint32_t tmem = tmem_base;
+  auto fail = [&]() { atomicExch(err, 1); *abort_v = 1; };
 
-  auto load = [&](int step) {
-    if (step < total) {
+  if (warp >= 4 && warp < 6) {
+    // ---------------- producers ----------------
+    const int ptid = tid - 128;                                     // 0 .. 63
+    const size_t planeA = (size_t)p.mp * p.kp, planeB = (size_t)p.np2 * p.kp;
+    const __half* Abase = p.Ahat + (size_t)tl.ti * TC_BM * p.kp;
+    const __half* Bbase = p.Bhat + (size_t)tl.tj * TC_BN * p.kp;
+    constexpr int LAG = TC_STAGES - 2;                              // stages whose copies may still be in flight
+    for (int step = 0; step < total; ++step) {
+      const int s = step % TC_STAGES;
+      if (step >= TC_STAGES && !mbar_wait_ab(&empty[s], ((step / TC_STAGES) - 1) & 1, abort_v)) { fail(); break; }
       const OzPair pr = pairs[step / nk];
-      const int kt = step % nk, stage = step % TC_STAGES;
+      const int kt = step % nk;
       const __half* a = Abase + (size_t)(pr.t - 1) * planeA + (size_t)kt * TC_BK;
       const __half* b = Bbase + (size_t)(pr.u - 1) * planeB + (size_t)kt * TC_BK;
-      const uint32_t da = tc_smem_u32(sA + stage * TC_BM * 128), db = tc_smem_u32(sB + stage * TC_BN * 128);
-      for (int c = tid; c < TC_BM * 8; c += 128) {
-        int row = c >> 3, ch = c & 7;
+      const uint32_t da = tc_smem_u32(sA + s * TC_BM * 128), db = tc_smem_u32(sB + s * TC_BN * 128);
+      for (int c = ptid; c < TC_BM * 8; c += TC_PRODUCERS) {
+        const int row = c >> 3, ch = c & 7;
         cp_async16_tc(da + sw128(row, ch), a + (size_t)row * p.kp + ch * 8);
         cp_async16_tc(db + sw128(row, ch), b + (size_t)row * p.kp + ch * 8);
       }
-    }
-    asm volatile("cp.async.commit_group;\n" ::);
-  };
-
-  int32_t dacc[TC_BN];
-#pragma unroll
-  for (int j = 0; j < TC_BN; ++j) dacc[j] = 0;
-  uint32_t stage_phase = 0;       // bit s: parity to wait for on bar_stage[s]
-  uint32_t acc_phase = 0;
-  const uint32_t idesc = instr_desc();
-  bool first_of_chunk = true;
-
-  for (int s = 0; s < TC_STAGES - 1; ++s) load(s);
-
-  for (int step = 0; step < total; ++step) {
-    const int stage = step % TC_STAGES;
-    asm volatile("cp.async.wait_group %0;\n" :: "n"(TC_STAGES - 2));
-    asm volatile("fence.proxy.async.shared::cta;\n" ::);     // cp.async writes -> visible to the tensor core
-    __syncthreads();
-    if (abort_flag) break;
-    if (tid == 0) {
-      asm volatile("tcgen05.fence::after_thread_sync;\n" ::);
-      const uint32_t a0 = tc_smem_u32(sA + stage * TC_BM * 128), b0 = tc_smem_u32(sB + stage * TC_BN * 128);
-#pragma unroll
-      for (int k = 0; k < TC_BK / 16; ++k) {
-        uint64_t ad = smem_desc(a0 + 32 * k), bd = smem_desc(b0 + 32 * k);
-        uint32_t acc = (first_of_chunk && k == 0) ? 0u : 1u;
-        asm volatile("{\n .reg .pred p;\n setp.ne.u32 p, %4, 0;\n"
-                     " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n"
-                     :: "r"(tmem), "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
+      asm volatile("cp.async.commit_group;\n" ::);
+      if (step >= LAG) {
+        asm volatile("cp.async.wait_group %0;\n" :: "n"(LAG));
+        asm volatile("fence.proxy.async.shared::cta;\n" ::);       // cp.async writes -> visible to the tensor core
+        mbar_arrive(&full[(step - LAG) % TC_STAGES]);
       }
-      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n"
-                   :: "r"(tc_smem_u32(&bar_stage[stage])));
     }
-    first_of_chunk = false;
-    // refill the buffer consumed one step earlier once its MMAs are done
-    const int next = step + TC_STAGES - 1;
-    if (step >= 1) {
-      const int ps = (step - 1) % TC_STAGES;
-      if (!mbar_wait(&bar_stage[ps], (stage_phase >> ps) & 1)) { atomicExch(err, 1); abort_flag = 1; }
-      stage_phase ^= 1u << ps;
-    }
-    load(next);
-    if (step % nk == nk - 1) {
-      const OzPair pr = pairs[step / nk];
-      if (pr.flags & 1) {
-        if (tid == 0)
-          asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n"
-                       :: "r"(tc_smem_u32(&bar_acc)));
-        if (!mbar_wait(&bar_acc, acc_phase)) { atomicExch(err, 1); abort_flag = 1; }
-        acc_phase ^= 1u;
+    asm volatile("cp.async.wait_group 0;\n" ::);
+    asm volatile("fence.proxy.async.shared::cta;\n" ::);
+    if (!*abort_v)
+      for (int step = (total > LAG ? total - LAG : 0); step < total; ++step) mbar_arrive(&full[step % TC_STAGES]);
+  } else if (warp == 6) {
+    // ---------------- MMA issue ----------------
+    if (lane == 0) {
+      const uint32_t idesc = instr_desc();
+      int grp = 0;
+      bool first = true;
+      for (int step = 0; step < total; ++step) {
+        const int s = step % TC_STAGES;
+        const int buf = grp & 1;
+        if (!mbar_wait_ab(&full[s], (step / TC_STAGES) & 1, abort_v)) { fail(); break; }
+        if (first && grp >= 2 && !mbar_wait_ab(&acce[buf], ((grp >> 1) - 1) & 1, abort_v)) { fail(); break; }
+        asm volatile("fence.proxy.async.shared::cta;\n" ::);
         asm volatile("tcgen05.fence::after_thread_sync;\n" ::);
+        const uint32_t a0 = tc_smem_u32(sA + s * TC_BM * 128), b0 = tc_smem_u32(sB + s * TC_BN * 128);
+        const uint32_t dcol = tmem + (uint32_t)(buf * TC_BN);
 #pragma unroll
-        for (int cb = 0; cb < TC_BN; cb += 32) {
-          uint32_t v[32];
-          const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)cb;
-          asm volatile("tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-                       "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];\n"
-                       : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
-                         "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]),
-                         "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]),
-                         "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
-                       : "r"(taddr));
-          asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::);
-#pragma unroll
-          for (int j = 0; j < 32; ++j) dacc[cb + j] += __float2int_rn(__uint_as_float(v[j]));
+        for (int k = 0; k < TC_BK / 16; ++k) {
+          uint64_t ad = smem_desc(a0 + 32 * k), bd = smem_desc(b0 + 32 * k);
+          uint32_t acc = (first && k == 0) ? 0u : 1u;
+          asm volatile("{\n .reg .pred p;\n setp.ne.u32 p, %4, 0;\n"
+                       " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n"
+                       :: "r"(dcol), "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
         }
-        asm volatile("tcgen05.fence::before_thread_sync;\n" ::);
-        first_of_chunk = true;
-      }
-      if (pr.flags & 2) {
-        // row = tile row of this thread (TMEM lane), 128 consecutive columns
-        const int r = tl.ti * TC_BM + warp * 32 + lane;
-        const size_t off = (size_t)pr.level * p.mp * p.np2 + (size_t)r * p.np2 + (size_t)tl.tj * TC_BN;
-        if (cc) {
-          // CRT form: residues modulo the level's modulus, one byte each
-          const int t = pr.level % cc->r;
-          const uint32_t m = (uint32_t)cc->m[t], minv = cc->minv[t];
-          uint8_t* D8 = reinterpret_cast<uint8_t*>(p.D) + off;
-#pragma unroll
-          for (int j = 0; j < TC_BN; j += 16) {
-            uint32_t w[4];
-#pragma unroll
-            for (int q = 0; q < 4; ++q)
-              w[q] = crt_mod(dacc[j + 4 * q], m, minv) | (crt_mod(dacc[j + 4 * q + 1], m, minv) << 8) |
-                     (crt_mod(dacc[j + 4 * q + 2], m, minv) << 16) | (crt_mod(dacc[j + 4 * q + 3], m, minv) << 24);
-            *reinterpret_cast<uint4*>(D8 + j) = make_uint4(w[0], w[1], w[2], w[3]);
-          }
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n"
+                     :: "r"(tc_smem_u32(&empty[s])));
+        const OzPair pr = pairs[step / nk];
+        if ((step % nk == nk - 1) && (pr.flags & 1)) {
+          asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n"
+                       :: "r"(tc_smem_u32(&accf[buf])));
+          ++grp; first = true;
         } else {
-          int32_t* D = p.D + off;
-#pragma unroll
-          for (int j = 0; j < TC_BN; j += 4)
-            *reinterpret_cast<int4*>(D + j) = make_int4(dacc[j], dacc[j + 1], dacc[j + 2], dacc[j + 3]);
+          first = false;
         }
-#pragma unroll
-        for (int j = 0; j < TC_BN; ++j) dacc[j] = 0;
       }
-      __syncthreads();          // the accumulator is free again before the next pair's first MMA
+      // completion of every MMA issued (also after an abort) before tensor memory is released
+      if (total > 0)
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n"
+                     :: "r"(tc_smem_u32(&fin)));
+    }
+  } else if (warp < 4) {
+    // ---------------- epilogue ----------------
+    int32_t dacc[TC_BN];
+#pragma unroll
+    for (int j = 0; j < TC_BN; ++j) dacc[j] = 0;
+    int grp = 0;
+    const uint32_t lane_base = tmem + ((uint32_t)(warp * 32) << 16);
+    for (int pi = 0; pi < npairs; ++pi) {
+      const OzPair pr = pairs[pi];
+      if (!(pr.flags & 1)) continue;                 // the group goes on
+      const int buf = grp & 1;
+      // warp-uniform decision: the TMEM loads below are warp-collective
+      const bool ok = __all_sync(0xffffffffu, mbar_wait_ab(&accf[buf], (grp >> 1) & 1, abort_v));
+      if (!ok) { fail(); break; }
+      asm volatile("tcgen05.fence::after_thread_sync;\n" ::);
+      const uint32_t tcol = lane_base + (uint32_t)(buf * TC_BN);
+      const bool lev = (pr.flags & 2) != 0;
+      tc_epilogue_chunk<0>(dacc, tcol, lev, p, tl, pr.level, cc, warp, lane);
+      tc_epilogue_chunk<1>(dacc, tcol, lev, p, tl, pr.level, cc, warp, lane);
+      tc_epilogue_chunk<2>(dacc, tcol, lev, p, tl, pr.level, cc, warp, lane);
+      tc_epilogue_chunk<3>(dacc, tcol, lev, p, tl, pr.level, cc, warp, lane);
+      asm volatile("tcgen05.fence::before_thread_sync;\n" ::);
+      mbar_arrive(&acce[buf]);
+      ++grp;
     }
   }
-  asm volatile("cp.async.wait_group 0;\n" ::);
-  // drain: make sure no MMA is in flight before releasing tensor memory
-  if (tid == 0 && total > 0 && !abort_flag) {
-    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n"
-                 :: "r"(tc_smem_u32(&bar_acc)));
-  }
-  if (total > 0 && !abort_flag) {
-    if (!mbar_wait(&bar_acc, acc_phase)) { if (tid == 0) atomicExch(err, 1); }
-  }
+  __syncthreads();
+  if (total > 0 && !mbar_wait(&fin, 0) && tid == 0) atomicExch(err, 1);
   asm volatile("tcgen05.fence::before_thread_sync;\n" ::);
   __syncthreads();
   if (warp == 0) {
     asm volatile("tcgen05.fence::after_thread_sync;\n" ::);
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" :: "r"(tmem), "r"(TC_BN));
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" :: "r"(tmem), "r"(2 * TC_BN));
   }
 }
 
@@ -226,7 +275,7 @@ zkq_status launch_oz_tc(const OzProd* d_p, const OzTile* d_t, int ntiles, const 
                         const CrtConst* d_c, int* d_err, cudaStream_t st) {
   size_t sm = oz_tc_smem_bytes();
   ZKQ_CUDA_TRY(cudaFuncSetAttribute(oz_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-  oz_tc_kernel<<<ntiles, 128, sm, st>>>(d_p, d_t, d_q, npairs, d_c, d_err);
+  oz_tc_kernel<<<ntiles, TC_THREADS, sm, st>>>(d_p, d_t, d_q, npairs, d_c, d_err);
   ZKQ_CUDA_TRY(cudaGetLastError());
   return ZKQ_OK;
 }

@@ -2,11 +2,13 @@
 // tensor memory).  Same contract as oz_gemm_kernel: for every tile, a stream of slice pairs (t, u) whose
 // exact integer products are accumulated per chunk, flushed to int32 and stored per level.
 //
-// CTA: 128 threads (4 warps), tile 128 rows x 128 columns, K staged 64 halves (one 128-byte swizzle atom)
-// per step in STAGES shared-memory buffers filled with cp.async.  Thread 0 issues four K=16 MMAs per step
-// and commits them to the step's mbarrier; at the end of each slice pair the accumulator is read back with
-// tcgen05.ld (warp w owns TMEM lanes 32w..32w+31 = tile rows), converted to int32 and added / stored
-// (CRT form: stored as residues modulo the level's modulus, one byte per entry).
+// CTA: 7 warps in three roles, tile 128 rows x 128 columns, K staged 64 halves (one 128-byte swizzle
+// atom) per step in STAGES shared-memory buffers.  Two producer warps fill the stages with cp.async; one
+// lane issues four K=16 MMAs per stage; four epilogue warps read finished accumulators back with
+// tcgen05.ld (warp w owns TMEM lanes 32w..32w+31 = tile rows), convert them to int32 and add / store them
+// (CRT form: residues modulo the level's modulus, one byte per entry).  Two accumulators (2 x 128 TMEM
+// columns) alternate between accumulation groups, so the epilogue of one group overlaps the MMAs of the
+// next.  The roles hand stages and accumulators to one another through mbarriers.
 // Every mbarrier wait is bounded; on expiry the kernel raises *err and leaves.
 #pragma once
 #include <cstdint>
@@ -14,7 +16,7 @@
 
 namespace zkq {
 
-constexpr int TC_BM = 128, TC_BN = 128, TC_BK = 64, TC_STAGES = 4;
+constexpr int TC_BM = 128, TC_BN = 128, TC_BK = 64, TC_STAGES = 6;
 
 struct OzTile;
 struct CrtConst;

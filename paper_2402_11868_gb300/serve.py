@@ -53,7 +53,7 @@ def mps_footprint(n_qubits: int, r_max: int, words: int) -> int:
     return int(tot + eig_footprint(g, words, words) + 16 * g * g * 2 * words * 8)
 
 
-@dataclass
+@dataclass(eq=False)
 class Request:
     kind: str                      # "eig" or "gate"
     sim: int
