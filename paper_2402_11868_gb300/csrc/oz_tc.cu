@@ -5,7 +5,6 @@
 
 namespace zkq {
 
-struct OzTile { int prod, ti, tj; };
 
 __device__ __forceinline__ uint32_t tc_smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -36,13 +35,13 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t saddr) {
   d |= (uint64_t)2 << 61;                           // swizzle mode: 128B
   return d;
 }
-// instruction descriptor, kind::f16: D f32, A/B f16, both K-major, N = 128, M = 128
-__device__ __forceinline__ uint32_t instr_desc() {
+// instruction descriptor, kind::f16: D f32, A/B f16, both K-major, M = 128, N = bn
+__device__ __forceinline__ uint32_t instr_desc(int bn) {
   uint32_t d = 0;
   d |= 1u << 4;                                     // D format f32
   d |= 0u << 7;                                     // A format f16
   d |= 0u << 10;                                    // B format f16
-  d |= (uint32_t)(TC_BN >> 3) << 17;                // N >> 3
+  d |= (uint32_t)(bn >> 3) << 17;                   // N >> 3
   d |= (uint32_t)(TC_BM >> 4) << 24;                // M >> 4
   return d;
 }
@@ -100,6 +99,32 @@ __device__ __forceinline__ void tc_epilogue_chunk(int32_t (&dacc)[TC_BN], uint32
   for (int j = 0; j < 32; ++j) dacc[32 * C + j] = 0;
 }
 
+// CRT form without running sums (every accumulation group is one level): chunk `c` (32 columns) of the
+// accumulator converted to residues modulo the level's modulus and stored, one byte each
+__device__ __forceinline__ void tc_store_residue_chunk(uint32_t tmem_addr, const OzProd& p, size_t off,
+                                                       uint32_t m, uint32_t minv) {
+  uint32_t v[32];
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+               "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];\n"
+               : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+                 "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]),
+                 "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]),
+                 "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+               : "r"(tmem_addr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::);
+  uint32_t w[8];
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
+    uint32_t x = 0;
+#pragma unroll
+    for (int b = 0; b < 4; ++b) x |= crt_mod(__float2int_rn(__uint_as_float(v[4 * q + b])), m, minv) << (8 * b);
+    w[q] = x;
+  }
+  uint8_t* D8 = reinterpret_cast<uint8_t*>(p.D) + off;
+  *reinterpret_cast<uint4*>(D8) = make_uint4(w[0], w[1], w[2], w[3]);
+  *reinterpret_cast<uint4*>(D8 + 16) = make_uint4(w[4], w[5], w[6], w[7]);
+}
+
 // bounded wait that also gives up once another role raised the CTA's abort flag
 __device__ __forceinline__ bool mbar_wait_ab(uint64_t* b, uint32_t par, volatile int* abort_flag) {
   uint32_t addr = tc_smem_u32(b);
@@ -127,34 +152,43 @@ __device__ __forceinline__ void mbar_arrive(uint64_t* b) {
 constexpr int TC_THREADS = 224;
 constexpr int TC_PRODUCERS = 64;
 
+// BN: the widest tile (stage and accumulator sizes); a tile's own width is 128 w columns.  ACC: running
+// level sums across accumulation groups (digit form, BN = 128), else every group is one CRT level stored
+// as residues.
+template <int BN, bool ACC>
 __global__ void __launch_bounds__(TC_THREADS, 1) oz_tc_kernel(const OzProd* __restrict__ P, const OzTile* __restrict__ tiles,
-                                                              const OzPair* __restrict__ pairs, int npairs,
+                                                              const OzPair* __restrict__ gpairs, int npairs,
                                                               const CrtConst* __restrict__ cc, int* err) {
+  constexpr int S_ = tc_stages(BN);
+  static_assert(!ACC || BN == TC_BN, "running sums are kept for 128-column tiles");
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-  unsigned char* sA = smem;                                         // STAGES x 16 KB
-  unsigned char* sB = smem + TC_STAGES * TC_BM * 128;               // STAGES x 16 KB
-  __shared__ __align__(8) uint64_t full[TC_STAGES], empty[TC_STAGES], accf[2], acce[2], fin;
+  unsigned char* sA = smem;                                         // S_ x 16 KB
+  unsigned char* sB = smem + S_ * TC_BM * 128;                      // S_ x BN x 128 B
+  OzPair* pairs = reinterpret_cast<OzPair*>(sB + S_ * BN * 128);    // the pair list, read every step
+  __shared__ __align__(8) uint64_t full[S_], empty[S_], accf[2], acce[2], fin;
   __shared__ uint32_t tmem_base;
   __shared__ int abort_flag;
 
   const OzTile tl = tiles[blockIdx.x];
   const OzProd p = P[tl.prod];
+  const int bn = ACC ? TC_BN : min(BN, 128 * tl.w);                // this tile's width
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int nk = p.kp / TC_BK;
   const int total = npairs * nk;
   volatile int* abort_v = &abort_flag;
 
+  for (int i = tid; i < npairs; i += TC_THREADS) pairs[i] = gpairs[i];
   if (tid == 0) {
-    for (int s = 0; s < TC_STAGES; ++s) { mbar_init(&full[s], TC_PRODUCERS); mbar_init(&empty[s], 1); }
+    for (int s = 0; s < S_; ++s) { mbar_init(&full[s], TC_PRODUCERS); mbar_init(&empty[s], 1); }
     for (int b = 0; b < 2; ++b) { mbar_init(&accf[b], 1); mbar_init(&acce[b], 128); }
     mbar_init(&fin, 1);
     abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;\n" ::);
   }
-  if (warp == 0) {                      // two accumulators: 2 x TC_BN columns
+  if (warp == 0) {                      // two accumulators: 2 x BN columns
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n"
-                 :: "r"(tc_smem_u32(&tmem_base)), "r"(2 * TC_BN));
+                 :: "r"(tc_smem_u32(&tmem_base)), "r"(2 * BN));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::);
   }
   asm volatile("tcgen05.fence::before_thread_sync;\n" ::);
@@ -168,47 +202,50 @@ __global__ void __launch_bounds__(TC_THREADS, 1) oz_tc_kernel(const OzProd* __re
     const int ptid = tid - 128;                                     // 0 .. 63
     const size_t planeA = (size_t)p.mp * p.kp, planeB = (size_t)p.np2 * p.kp;
     const __half* Abase = p.Ahat + (size_t)tl.ti * TC_BM * p.kp;
-    const __half* Bbase = p.Bhat + (size_t)tl.tj * TC_BN * p.kp;
-    constexpr int LAG = TC_STAGES - 2;                              // stages whose copies may still be in flight
+    const __half* Bbase = p.Bhat + (size_t)tl.tj * TC_BN * p.kp;      // tj counts 128-column units
+    constexpr int LAG = S_ - 2;                                     // stages whose copies may still be in flight
     for (int step = 0; step < total; ++step) {
-      const int s = step % TC_STAGES;
-      if (step >= TC_STAGES && !mbar_wait_ab(&empty[s], ((step / TC_STAGES) - 1) & 1, abort_v)) { fail(); break; }
+      const int s = step % S_;
+      if (step >= S_ && !mbar_wait_ab(&empty[s], ((step / S_) - 1) & 1, abort_v)) { fail(); break; }
       const OzPair pr = pairs[step / nk];
       const int kt = step % nk;
       const __half* a = Abase + (size_t)(pr.t - 1) * planeA + (size_t)kt * TC_BK;
       const __half* b = Bbase + (size_t)(pr.u - 1) * planeB + (size_t)kt * TC_BK;
-      const uint32_t da = tc_smem_u32(sA + s * TC_BM * 128), db = tc_smem_u32(sB + s * TC_BN * 128);
+      const uint32_t da = tc_smem_u32(sA + s * TC_BM * 128), db = tc_smem_u32(sB + s * BN * 128);
       for (int c = ptid; c < TC_BM * 8; c += TC_PRODUCERS) {
         const int row = c >> 3, ch = c & 7;
         cp_async16_tc(da + sw128(row, ch), a + (size_t)row * p.kp + ch * 8);
+      }
+      for (int c = ptid; c < bn * 8; c += TC_PRODUCERS) {
+        const int row = c >> 3, ch = c & 7;
         cp_async16_tc(db + sw128(row, ch), b + (size_t)row * p.kp + ch * 8);
       }
       asm volatile("cp.async.commit_group;\n" ::);
       if (step >= LAG) {
         asm volatile("cp.async.wait_group %0;\n" :: "n"(LAG));
         asm volatile("fence.proxy.async.shared::cta;\n" ::);       // cp.async writes -> visible to the tensor core
-        mbar_arrive(&full[(step - LAG) % TC_STAGES]);
+        mbar_arrive(&full[(step - LAG) % S_]);
       }
     }
     asm volatile("cp.async.wait_group 0;\n" ::);
     asm volatile("fence.proxy.async.shared::cta;\n" ::);
     if (!*abort_v)
-      for (int step = (total > LAG ? total - LAG : 0); step < total; ++step) mbar_arrive(&full[step % TC_STAGES]);
+      for (int step = (total > LAG ? total - LAG : 0); step < total; ++step) mbar_arrive(&full[step % S_]);
   } else if (warp == 6) {
     // ---------------- MMA issue ----------------
     if (lane == 0) {
-      const uint32_t idesc = instr_desc();
+      const uint32_t idesc = instr_desc(bn);
       int grp = 0;
       bool first = true;
       for (int step = 0; step < total; ++step) {
-        const int s = step % TC_STAGES;
+        const int s = step % S_;
         const int buf = grp & 1;
-        if (!mbar_wait_ab(&full[s], (step / TC_STAGES) & 1, abort_v)) { fail(); break; }
+        if (!mbar_wait_ab(&full[s], (step / S_) & 1, abort_v)) { fail(); break; }
         if (first && grp >= 2 && !mbar_wait_ab(&acce[buf], ((grp >> 1) - 1) & 1, abort_v)) { fail(); break; }
         asm volatile("fence.proxy.async.shared::cta;\n" ::);
         asm volatile("tcgen05.fence::after_thread_sync;\n" ::);
-        const uint32_t a0 = tc_smem_u32(sA + s * TC_BM * 128), b0 = tc_smem_u32(sB + s * TC_BN * 128);
-        const uint32_t dcol = tmem + (uint32_t)(buf * TC_BN);
+        const uint32_t a0 = tc_smem_u32(sA + s * TC_BM * 128), b0 = tc_smem_u32(sB + s * BN * 128);
+        const uint32_t dcol = tmem + (uint32_t)(buf * BN);
 #pragma unroll
         for (int k = 0; k < TC_BK / 16; ++k) {
           uint64_t ad = smem_desc(a0 + 32 * k), bd = smem_desc(b0 + 32 * k);
@@ -233,8 +270,30 @@ __global__ void __launch_bounds__(TC_THREADS, 1) oz_tc_kernel(const OzProd* __re
         asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n"
                      :: "r"(tc_smem_u32(&fin)));
     }
+  } else if (warp < 4 && !ACC) {
+    // ---------------- epilogue: CRT residues, one level per group ----------------
+    int grp = 0;
+    const uint32_t lane_base = tmem + ((uint32_t)(warp * 32) << 16);
+    const int r = tl.ti * TC_BM + warp * 32 + lane;
+    for (int pi = 0; pi < npairs; ++pi) {
+      const OzPair pr = pairs[pi];
+      if (!(pr.flags & 1)) continue;
+      const int buf = grp & 1;
+      const bool ok = __all_sync(0xffffffffu, mbar_wait_ab(&accf[buf], (grp >> 1) & 1, abort_v));
+      if (!ok) { fail(); break; }
+      asm volatile("tcgen05.fence::after_thread_sync;\n" ::);
+      const int t = pr.level % cc->r;
+      const uint32_t m = (uint32_t)cc->m[t], minv = cc->minv[t];
+      const size_t off = (size_t)pr.level * p.mp * p.np2 + (size_t)r * p.np2 + (size_t)tl.tj * TC_BN;
+#pragma unroll 1
+      for (int c = 0; c < bn / 32; ++c)
+        tc_store_residue_chunk(lane_base + (uint32_t)(buf * BN + 32 * c), p, off + 32 * c, m, minv);
+      asm volatile("tcgen05.fence::before_thread_sync;\n" ::);
+      mbar_arrive(&acce[buf]);
+      ++grp;
+    }
   } else if (warp < 4) {
-    // ---------------- epilogue ----------------
+    // ---------------- epilogue: running level sums ----------------
     int32_t dacc[TC_BN];
 #pragma unroll
     for (int j = 0; j < TC_BN; ++j) dacc[j] = 0;
@@ -265,19 +324,30 @@ __global__ void __launch_bounds__(TC_THREADS, 1) oz_tc_kernel(const OzProd* __re
   __syncthreads();
   if (warp == 0) {
     asm volatile("tcgen05.fence::after_thread_sync;\n" ::);
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" :: "r"(tmem), "r"(2 * TC_BN));
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" :: "r"(tmem), "r"(2 * BN));
   }
 }
 
-size_t oz_tc_smem_bytes() { return (size_t)TC_STAGES * (TC_BM + TC_BN) * 128 + 1024; }
+size_t oz_tc_smem_bytes(int bn, int npairs) {
+  return (size_t)tc_stages(bn) * (TC_BM + bn) * 128 + 1024 + (size_t)npairs * sizeof(OzPair);
+}
+
+template <int BN, bool ACC>
+static zkq_status launch_t(const OzProd* d_p, const OzTile* d_t, int ntiles, const OzPair* d_q, int npairs,
+                           const CrtConst* d_c, int* d_err, cudaStream_t st) {
+  size_t sm = oz_tc_smem_bytes(BN, npairs);
+  if (sm > 227 * 1024) return ZKQ_EINVAL;        // pair lists of this length do not occur (<= 3 x 96 or ~600)
+  ZKQ_CUDA_TRY(cudaFuncSetAttribute(oz_tc_kernel<BN, ACC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+  oz_tc_kernel<BN, ACC><<<ntiles, TC_THREADS, sm, st>>>(d_p, d_t, d_q, npairs, d_c, d_err);
+  ZKQ_CUDA_TRY(cudaGetLastError());
+  return ZKQ_OK;
+}
 
 zkq_status launch_oz_tc(const OzProd* d_p, const OzTile* d_t, int ntiles, const OzPair* d_q, int npairs,
                         const CrtConst* d_c, int* d_err, cudaStream_t st) {
-  size_t sm = oz_tc_smem_bytes();
-  ZKQ_CUDA_TRY(cudaFuncSetAttribute(oz_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-  oz_tc_kernel<<<ntiles, TC_THREADS, sm, st>>>(d_p, d_t, d_q, npairs, d_c, d_err);
-  ZKQ_CUDA_TRY(cudaGetLastError());
-  return ZKQ_OK;
+  if (ntiles <= 0) return ZKQ_OK;
+  if (!d_c) return launch_t<TC_BN, true>(d_p, d_t, ntiles, d_q, npairs, d_c, d_err, st);
+  return launch_t<256, false>(d_p, d_t, ntiles, d_q, npairs, d_c, d_err, st);
 }
 
 }  // namespace zkq

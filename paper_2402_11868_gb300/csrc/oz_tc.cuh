@@ -16,12 +16,14 @@
 
 namespace zkq {
 
-constexpr int TC_BM = 128, TC_BN = 128, TC_BK = 64, TC_STAGES = 6;
+constexpr int TC_BM = 128, TC_BN = 128, TC_BK = 64;
+// stages per tile width: 6 x 32 KB (128 columns) or 4 x 48 KB (256 columns)
+__host__ __device__ constexpr int tc_stages(int bn) { return bn == 256 ? 4 : 6; }
 
-struct OzTile;
 struct CrtConst;
-size_t oz_tc_smem_bytes();
-// d_c: CRT constants (the levels are stored as uint8 residues) or null (int32 levels, digit form)
+size_t oz_tc_smem_bytes(int bn, int npairs);
+// d_c: CRT constants (the levels are stored as uint8 residues; tiles 128 or 256 columns wide) or null
+// (int32 levels, digit form; 128-column tiles only).
 zkq_status launch_oz_tc(const OzProd* d_p, const OzTile* d_t, int ntiles, const OzPair* d_q, int npairs,
                         const CrtConst* d_c, int* d_err, cudaStream_t st);
 

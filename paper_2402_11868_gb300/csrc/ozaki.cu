@@ -249,7 +249,6 @@ __global__ void oz_slice_B_kernel(const OzProd* __restrict__ P, int b, int sB) {
 // slice GEMM: fp16 x fp16 -> fp32 (exact), mma.sync m16n8k16, CTA tile 128 x 128 x 32, 8 warps (2 x 4)
 constexpr int OZ_BM = 128, OZ_BN = 128, OZ_BK = 32, OZ_STAGES = 3;
 
-struct OzTile { int prod, ti, tj; };
 
 // slice-GEMM kernel: 0 mma.sync (legacy warp-level path), 1 tcgen05 (tensor memory accumulators)
 static int g_gemm_kernel = 1;
@@ -897,7 +896,8 @@ zkq_status mw_gemm_batched(const MwProd* prods, int count, int wa, int wb, int w
   zkq_status s = grow(ws, ws_bytes, off);
   if (s != ZKQ_OK) return s;
   char* base = (char*)*ws;
-  std::vector<OzTile> tiles;
+  std::vector<OzTile> tiles, wide;                 // wide: 256-column tiles (CRT form on the tcgen05 kernel)
+  const bool use_wide = crt && g_gemm_kernel == 1;
   for (int i = 0; i < count; ++i) {
     OzProd& o = dp[i];
     o.Ahat = (__half*)(base + oA[i]); o.Bhat = (__half*)(base + oB[i]);
@@ -907,21 +907,36 @@ zkq_status mw_gemm_batched(const MwProd* prods, int count, int wa, int wb, int w
     OzProd& o = dp[i];
     if (!o.sliceA) { o.Ahat = dp[srcA[i]].Ahat; o.eA = dp[srcA[i]].eA; }
     if (!o.sliceB) { o.Bhat = dp[srcB[i]].Bhat; o.eB = dp[srcB[i]].eB; }
-    for (int ti = 0; ti < o.mp / OZ_BM; ++ti)
-      for (int tj = 0; tj < o.np2 / OZ_BN; ++tj) {
-        if (o.hermitian) {
-          // keep the tile if one of its columns j (re block: j', im block: j' - n) reaches row ti*BM
-          int c0 = tj * OZ_BN, c1 = std::min(c0 + OZ_BN, 2 * o.n), jmax = -1;
-          if (c0 < o.n) jmax = std::max(jmax, std::min(c1, o.n) - 1);
-          if (c1 > o.n) jmax = std::max(jmax, c1 - 1 - o.n);
-          if (jmax < ti * OZ_BM) continue;
+    // a Hermitian output keeps a tile if one of its columns j (re block: j', im block: j' - n) reaches
+    // row ti*BM
+    auto needed = [&](int ti, int c0, int width) {
+      if (!o.hermitian) return true;
+      int c1 = std::min(c0 + width, 2 * o.n), jmax = -1;
+      if (c0 < o.n) jmax = std::max(jmax, std::min(c1, o.n) - 1);
+      if (c1 > o.n) jmax = std::max(jmax, c1 - 1 - o.n);
+      return jmax >= ti * OZ_BM;
+    };
+    for (int ti = 0; ti < o.mp / OZ_BM; ++ti) {
+      const int units = o.np2 / OZ_BN;
+      for (int tj = 0; tj < units;) {
+        if (use_wide && tj + 1 < units) {
+          if (needed(ti, tj * OZ_BN, 2 * OZ_BN)) wide.push_back({i, ti, tj, 2});
+          tj += 2;
+        } else {
+          if (needed(ti, tj * OZ_BN, OZ_BN)) tiles.push_back({i, ti, tj, 1});
+          tj += 1;
         }
-        tiles.push_back({i, ti, tj});
       }
+    }
   }
   // biggest problems first (their tiles run longest: K' is larger)
-  std::stable_sort(tiles.begin(), tiles.end(), [&](const OzTile& a, const OzTile& c) { return dp[a.prod].kp > dp[c.prod].kp; });
-  size_t m_p = al(sizeof(OzProd) * count), m_t = al(sizeof(OzTile) * tiles.size()), m_q = al(sizeof(OzPair) * pairs.size());
+  // one list: longest tiles first (K', then width), so the tail of the launch is short tiles
+  tiles.insert(tiles.end(), wide.begin(), wide.end());
+  std::stable_sort(tiles.begin(), tiles.end(), [&](const OzTile& a, const OzTile& c) {
+    const long wa_ = (long)dp[a.prod].kp * a.w, wc_ = (long)dp[c.prod].kp * c.w;
+    return wa_ > wc_;
+  });
+  size_t m_p = al(sizeof(OzProd) * count), m_t = al(sizeof(OzTile) * std::max<size_t>(1, tiles.size())), m_q = al(sizeof(OzPair) * pairs.size());
   size_t m_c = crt ? al(sizeof(CrtConst)) : 0;
   s = grow(meta, meta_bytes, m_p + m_t + m_q + m_c);
   if (s != ZKQ_OK) return s;

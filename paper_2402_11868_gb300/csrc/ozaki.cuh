@@ -36,6 +36,9 @@ struct OzProd {
 
 struct OzPair { int16_t t, u; int16_t level; int16_t flags; };   // flags: 1 chunk end, 2 level end
 
+// one output tile: rows 128 ti.., columns 128 tj.. of product `prod`, w x 128 columns wide (w = 1 or 2)
+struct OzTile { int prod, ti, tj, w; };
+
 struct OzPlan {
   int b;            // digit width (bits)
   int sA, sB, S;    // digit counts and the highest level kept
