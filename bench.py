@@ -300,6 +300,21 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+def recorded_traffic(kernel_source):
+    """DRAM bytes per launch from the committed ncu summary of the kernel, when the summary was taken of the
+    kernel source as it is now (its sha256 matches); else None."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", "jacobi_global_traffic.txt")
+    try:
+        fields = dict(l.split(":", 1) for l in open(path) if ":" in l)
+        src = open(os.path.join(ROOT, kernel_source), "rb").read()
+        if fields.get("source_sha256", "").strip() != hashlib.sha256(src).hexdigest():
+            return None
+        return int(fields["dram_bytes_per_launch"].strip())
+    except Exception:
+        return None
+
+
 def roofline(Z, prof, ns, steps):
     """Roofline object of the dominant kernel class (by device time in the timed region)."""
     peaks, peak_kind = measured_peaks()
@@ -317,6 +332,9 @@ def roofline(Z, prof, ns, steps):
         peak = 1.006   # measured DFMA throughput of this GB300 pool, TFLOP/s (FMA = 2 flops)
         achieved = dom_work / (dom_ms / 1e3) / 1e12
         what = "FP64 eigensolve of the inputs" if dom_name == "jacobi" else "FP64 eigensolves of the refinement's cluster blocks"
+        if dom_name == "jacobi":   # the batch's large problems: one jacobi_global_kernel launch per step
+            base["traffic"] = recorded_traffic("paper_2402_11868_gb300/csrc/jacobi.cu")
+            base["traffic_kernel"] = "jacobi_global_kernel<4> (DRAM read + write per launch, ncu)"
         return dict(base, bound="alu", kernel=f"jacobi_smem/global/grid_kernel ({what})",
                     achieved=achieved, peak=peak, unit="TFLOP/s", frac=achieved / peak,
                     peak_source="measured FP64 DFMA microbenchmark (MEASURED_PEAKS.json has no FP64 entry)",

@@ -132,6 +132,47 @@ zkq_status zkq_rqi_refine(zkq_ctx* ctx, int batch, const int32_t* n, const int64
                           int32_t* info, void* stream);
 
 /*
+ * zkq_autotune_jacobi: measure the cluster width (CTAs per problem: 2, 4, 8 or 16) of the batched FP64
+ * Jacobi for each order in sizes[0..nsizes) (81 .. 2048) and keep the fastest in the context's table; from
+ * then on the context's eigensolves (zkq_eigh_batched, the refinement's cluster blocks, plans created
+ * afterwards) take the width of the first table order >= their largest order (else the last entry), unless
+ * zkq_config.jacobi_cluster fixes one.  The results do not depend on the width.  Each order is timed on a
+ * synthetic batch of one Hermitian problem per SM (a_words words per real), reps timed runs after one
+ * warm-up per width; the call allocates that batch and synchronises the device.
+ *   best (host)   out: int32[nsizes], the chosen widths
+ * Errors: ZKQ_EINVAL, ZKQ_ENOMEM, ZKQ_ECUDA (the table is unchanged then).
+ */
+zkq_status zkq_autotune_jacobi(zkq_ctx* ctx, int nsizes, const int32_t* sizes, int a_words, int reps, int32_t* best);
+
+/*
+ * Plans: a fixed-shape batch of the FP64 eigensolve (zkq_eigh_batched) followed, optionally, by plain RQI
+ * refinement (zkq_rqi_refine with ZKQ_PLAIN_RQI) -- the batched diagonalisation of Section 2.1 repeated on
+ * batches of one shape.  zkq_plan_create lays the batch out, allocates the plan's own device metadata and
+ * workspace and uploads the metadata once (it synchronises the context's device); zkq_plan_execute then
+ * only enqueues kernels and stream-ordered memsets (no allocation, no host copy, no synchronisation), so it
+ * can be captured into a CUDA graph; zkq_plan_execute_graph does that capture at its first call for the
+ * given buffers and replays the graph afterwards (a call with other buffers captures again).
+ *   n, a_off (host)   as for zkq_eigh_batched; copied
+ *   a_words           1, 2 or 4
+ *   target_words      0 (eigensolve only), 2 or 4 (plain RQI to that precision)
+ * Execute arguments have the layouts of zkq_eigh_batched (A, W, V, info) and zkq_rqi_refine (W_out, V_out,
+ * err_est, rinfo); the refinement ones are ignored (may be NULL) when target_words is 0.  The caller owns
+ * every buffer; a plan is used by one host thread at a time; calls that overlap on the GPU race on the
+ * plan's workspace.  zkq_plan_execute_graph needs a stream other than the legacy default stream and
+ * profiling (zkq_profile_enable) off.
+ * Errors: ZKQ_EINVAL, ZKQ_ENOMEM, ZKQ_ECUDA.
+ */
+typedef struct zkq_plan zkq_plan;
+zkq_status zkq_plan_create(zkq_ctx* ctx, int batch, const int32_t* n, const int64_t* a_off, int a_words,
+                           int target_words, zkq_plan** out);
+zkq_status zkq_plan_execute(zkq_plan* plan, const double* A, double* W, double* V, int32_t* info, double* W_out,
+                            double* V_out, double* err_est, int32_t* rinfo, void* stream);
+zkq_status zkq_plan_execute_graph(zkq_plan* plan, const double* A, double* W, double* V, int32_t* info,
+                                  double* W_out, double* V_out, double* err_est, int32_t* rinfo, void* stream);
+/* Frees the plan (synchronises its device first).  NULL is accepted. */
+zkq_status zkq_plan_destroy(zkq_plan* plan);
+
+/*
  * Matrix-product state (Vidal form) resident on the device, and its gate updates (Section 1: an MPS is a
  * nested Schmidt decomposition evolved without leaving that form, cost O(n g r_max^3); Section 2.1:
  * diagonalisation at each gate dominates; footnote: Schmidt coefficients ~2^{-(n-1)/2} must survive).

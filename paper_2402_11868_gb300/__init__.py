@@ -79,6 +79,15 @@ def lib():
                              ("zkq_mps_apply2q", [P, P, I, P, ctypes.c_double, I, P, P, P])):
                 getattr(L, nm).restype = I
                 getattr(L, nm).argtypes = args
+            L.zkq_autotune_jacobi.restype = I
+            L.zkq_autotune_jacobi.argtypes = [P, I, P, I, I, P]
+            L.zkq_plan_create.restype = I
+            L.zkq_plan_create.argtypes = [P, I, P, P, I, I, ctypes.POINTER(P)]
+            for nm in ("zkq_plan_execute", "zkq_plan_execute_graph"):
+                getattr(L, nm).restype = I
+                getattr(L, nm).argtypes = [P, P, P, P, P, P, P, P, P, P]
+            L.zkq_plan_destroy.restype = I
+            L.zkq_plan_destroy.argtypes = [P]
             L.zkq_set_gemm_kernel.restype = I
             L.zkq_set_gemm_kernel.argtypes = [I]
             L.zkq_get_gemm_kernel.restype = I
@@ -131,6 +140,15 @@ class Context:
         _check(lib().zkq_ctx_create(ctypes.byref(h), ctypes.byref(cfg)), "zkq_ctx_create")
         self.handle = h.value
         self.device = device
+
+    def autotune_jacobi(self, sizes, a_words: int = 4, reps: int = 2):
+        """Measure the Jacobi cluster width per order (zkq_autotune_jacobi); returns the chosen widths."""
+        import numpy as np
+        sz, sp = _host_array(sizes, ctypes.c_int32)
+        best = np.zeros(len(sz), dtype=np.int32)
+        _check(lib().zkq_autotune_jacobi(self.handle, len(sz), sp, a_words, reps, best.ctypes.data),
+               "zkq_autotune_jacobi")
+        return [int(x) for x in best]
 
     def close(self):
         if getattr(self, "handle", None):
@@ -210,6 +228,39 @@ def zkq_profile_read():
     ms = np.zeros(k); n = np.zeros(k, dtype=np.int64); w = np.zeros(k)
     _check(lib().zkq_profile_read(ms.ctypes.data, n.ctypes.data, w.ctypes.data, k), "zkq_profile_read")
     return {lib().zkq_profile_class_name(i).decode(): (float(ms[i]), int(n[i]), float(w[i])) for i in range(k)}
+
+
+class Plan:
+    """Fixed-shape batch: FP64 eigensolve, then plain RQI to `target_words` (0: eigensolve only).  execute()
+    only enqueues kernels; execute_graph() replays a CUDA graph captured for the same buffers."""
+
+    def __init__(self, ctx: Context, n, a_off, a_words: int, target_words: int = 0):
+        n_arr, n_p = _host_array(n, ctypes.c_int32)
+        o_arr, o_p = _host_array(a_off, ctypes.c_int64)
+        h = ctypes.c_void_p()
+        _check(lib().zkq_plan_create(ctx.handle, len(n_arr), n_p, o_p, a_words, target_words, ctypes.byref(h)),
+               "zkq_plan_create")
+        self.handle, self.ctx = h.value, ctx
+
+    def execute(self, A, W, V, info, W_out=None, V_out=None, err_est=None, rinfo=None, stream=None):
+        _check(lib().zkq_plan_execute(self.handle, _ptr(A), _ptr(W), _ptr(V), _ptr(info), _ptr(W_out), _ptr(V_out),
+                                      _ptr(err_est), _ptr(rinfo), _stream(stream)), "zkq_plan_execute")
+
+    def execute_graph(self, A, W, V, info, W_out=None, V_out=None, err_est=None, rinfo=None, stream=None):
+        _check(lib().zkq_plan_execute_graph(self.handle, _ptr(A), _ptr(W), _ptr(V), _ptr(info), _ptr(W_out),
+                                            _ptr(V_out), _ptr(err_est), _ptr(rinfo), _stream(stream)),
+               "zkq_plan_execute_graph")
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib().zkq_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class MPS:

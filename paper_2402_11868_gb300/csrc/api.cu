@@ -40,6 +40,7 @@ struct zkq_ctx {
   void* mps_ws = nullptr;   // gate-update scratch (theta, rho, split-back)
   size_t mps_bytes = 0;
   HostStage stage;          // pinned staging of metadata uploads and statistics read-back
+  JacobiTune jacobi_tune;   // cluster widths measured by zkq_autotune_jacobi (empty: built-in choice)
 };
 
 namespace zkq {
@@ -48,6 +49,11 @@ OaBuffers ctx_oa_buffers(void* vctx) {
   return OaBuffers{&c->oa_ws, &c->oa_bytes, &c->oz_ws, &c->oz_bytes, &c->oz_meta, &c->oz_meta_bytes, &c->stage};
 }
 HostStage* ctx_stage(void* vctx) { return &((zkq_ctx*)vctx)->stage; }
+int ctx_num_sms(void* vctx) { return ((zkq_ctx*)vctx)->num_sms; }
+JacobiTune* ctx_jacobi_tune(void* vctx) { return &((zkq_ctx*)vctx)->jacobi_tune; }
+int ctx_device(void* vctx) { return ((zkq_ctx*)vctx)->device; }
+const zkq_config& ctx_config(void* vctx) { return ((zkq_ctx*)vctx)->cfg; }
+zkq_config& ctx_config_mut(void* vctx) { return ((zkq_ctx*)vctx)->cfg; }
 int ctx_oa_max_iter(void* vctx) { return ((zkq_ctx*)vctx)->cfg.oa_max_iter; }
 void** ctx_mps_ws(void* vctx, size_t** bytes) { zkq_ctx* c = (zkq_ctx*)vctx; *bytes = &c->mps_bytes; return &c->mps_ws; }
 }  // namespace zkq
@@ -62,7 +68,6 @@ static zkq_status ensure(void** p, size_t* have, size_t need) {
   return ZKQ_OK;
 }
 
-static size_t align_up(size_t x, size_t a = 256) { return (x + a - 1) / a * a; }
 
 extern "C" {
 
@@ -108,7 +113,6 @@ zkq_status zkq_ctx_destroy(zkq_ctx* ctx) {
   return ZKQ_OK;
 }
 
-static constexpr int kSmallMax = 80;
 
 }  // extern "C"
 
@@ -116,87 +120,32 @@ namespace zkq {
 zkq_status eigh_internal(void* vctx, int batch, const int32_t* n, const int64_t* a_off, const double* A, int a_words,
                          double* W, double* V, int32_t* info, cudaStream_t st, int prof_class) {
   zkq_ctx* ctx = (zkq_ctx*)vctx;
-  std::vector<int64_t> w_off(batch), ws_off(batch, 0);
-  std::vector<int32_t> small, large;
-  int64_t acc = 0; size_t ws_need = 0; int max_small = 0, max_large = 0;
-  for (int b = 0; b < batch; ++b) {
-    if (n[b] < 1 || n[b] > 4096 || a_off[b] < 0) return ZKQ_EINVAL;
-    w_off[b] = acc; acc += n[b];
-    if (n[b] <= kSmallMax) { small.push_back(b); max_small = std::max(max_small, n[b]); }
-    else { large.push_back(b); max_large = std::max(max_large, n[b]); }
-  }
-  std::sort(large.begin(), large.end(), [&](int a, int c) { return n[a] > n[c] || (n[a] == n[c] && a < c); });
-  for (int b : large) { ws_off[b] = (int64_t)(ws_need / sizeof(double)); ws_need += align_up((size_t)n[b] * n[b] * 4 * sizeof(double)); }
-  // few large problems: one at a time on a cooperative grid instead of a cluster each (a cluster of at
-  // most 16 CTAs would leave most SMs idle)
-  int cluster = ctx->cfg.jacobi_cluster;
-  if (cluster <= 0) cluster = max_large <= 128 ? 2 : (max_large <= 256 ? 4 : 8);
-  if (cluster > 16) cluster = 16;
-  int grid_blocks = 0;
-  if (!large.empty() && (int)large.size() * cluster * 2 <= ctx->num_sms) {
-    const int per_sm = jacobi_grid_max_blocks(max_large, a_words);
-    grid_blocks = std::min(std::min(ctx->num_sms, std::max(8, max_large / 4)), per_sm * ctx->num_sms);
-  }
-  size_t red_bytes = align_up((size_t)64 * std::max<size_t>(1, large.size()) * sizeof(double));
-  red_bytes = std::max(red_bytes, align_up((size_t)(2 * grid_blocks + 64) * sizeof(double)));
-  const size_t gb_bytes = align_up(sizeof(GridBar));
-  std::vector<int32_t> order(small); order.insert(order.end(), large.begin(), large.end());
-  // metadata: n, a_off, w_off, order, ws_off
-  size_t m_n = align_up(batch * 4), m_a = align_up(batch * 8), m_w = align_up(batch * 8), m_o = align_up(batch * 4), m_s = align_up(batch * 8);
-  zkq_status s = ensure(&ctx->meta, &ctx->meta_bytes, m_n + m_a + m_w + m_o + m_s);
+  EighLayout L;
+  zkq_status s = eigh_layout(batch, n, a_off, a_words, ctx->cfg.jacobi_cluster, ctx->num_sms, &L, &ctx->jacobi_tune);
   if (s != ZKQ_OK) return s;
-  s = ensure(&ctx->ws, &ctx->ws_bytes, ws_need + red_bytes + gb_bytes);
+  s = ensure(&ctx->meta, &ctx->meta_bytes, L.meta_bytes());
   if (s != ZKQ_OK) return s;
-  char* mb = (char*)ctx->meta;
-  int32_t* d_n = (int32_t*)mb; int64_t* d_a = (int64_t*)(mb + m_n); int64_t* d_w = (int64_t*)(mb + m_n + m_a);
-  int32_t* d_o = (int32_t*)(mb + m_n + m_a + m_w); int64_t* d_s = (int64_t*)(mb + m_n + m_a + m_w + m_o);
-  HostStage& hs = ctx->stage;
-  hs.add(d_n, n, batch * 4);
-  hs.add(d_a, a_off, batch * 8);
-  hs.add(d_w, w_off.data(), batch * 8);
-  hs.add(d_o, order.data(), batch * 4);
-  hs.add(d_s, ws_off.data(), batch * 8);
-  ZKQ_CUDA_TRY(hs.flush(st));
-  unsigned long long* ctr = prof_device_counters();
-  JacobiBatch jb{d_n, d_a, d_w, d_o, A, W, V, info, (double*)ctx->ws, d_s,
-                 (double*)((char*)ctx->ws + ws_need), ctx->cfg.max_sweeps, ctr ? ctr + prof_class : nullptr, prof_class};
-  GridBar* gb = (GridBar*)((char*)ctx->ws + ws_need + red_bytes);
-  return launch_jacobi(jb, a_words, (int)small.size(), (int)large.size(), max_small, max_large, cluster, grid_blocks,
-                       gb, st);
+  s = ensure(&ctx->ws, &ctx->ws_bytes, L.ws_bytes());
+  if (s != ZKQ_OK) return s;
+  s = eigh_upload(L, ctx->meta, ctx->stage, st);
+  if (s != ZKQ_OK) return s;
+  return eigh_launch(L, ctx->meta, ctx->ws, A, a_words, W, V, info, ctx->cfg.max_sweeps, prof_class, st);
 }
 zkq_status rqi_refine_internal(void* vctx, int batch, const int32_t* n, const int64_t* a_off, const double* A,
                                int a_words, const double* W, const double* V, int target_words, double* W_out,
                                double* V_out, double* err_est, int32_t* info, cudaStream_t st) {
   zkq_ctx* ctx = (zkq_ctx*)vctx;
-  std::vector<int64_t> w_off(batch);
-  int64_t total = 0; int nmax = 0;
-  for (int b = 0; b < batch; ++b) {
-    if (n[b] < 1 || n[b] > 4096 || a_off[b] < 0) return ZKQ_EINVAL;
-    w_off[b] = total; total += n[b]; nmax = std::max(nmax, n[b]);
-  }
-  std::vector<int32_t> pair_prob(total);
-  for (int b = 0; b < batch; ++b) for (int i = 0; i < n[b]; ++i) pair_prob[w_off[b] + i] = b;
-  size_t m_n = align_up(batch * 4), m_a = align_up(batch * 8), m_w = align_up(batch * 8), m_p = align_up(total * 4), m_c = 256;
-  zkq_status s = ensure(&ctx->meta, &ctx->meta_bytes, m_n + m_a + m_w + m_p + m_c);
+  RqiLayout L;
+  zkq_status s = rqi_layout(batch, n, a_off, target_words, ctx->num_sms, &L);
   if (s != ZKQ_OK) return s;
-  int grid = (int)std::min<int64_t>(total, (int64_t)ctx->num_sms);
-  size_t slot = rqi_slot_doubles(nmax, target_words);
-  s = ensure(&ctx->ws, &ctx->ws_bytes, slot * sizeof(double) * grid);
+  s = ensure(&ctx->meta, &ctx->meta_bytes, L.meta_bytes());
   if (s != ZKQ_OK) return s;
-  char* mb = (char*)ctx->meta;
-  int32_t* d_n = (int32_t*)mb; int64_t* d_a = (int64_t*)(mb + m_n); int64_t* d_w = (int64_t*)(mb + m_n + m_a);
-  int32_t* d_p = (int32_t*)(mb + m_n + m_a + m_w); int* d_c = (int*)(mb + m_n + m_a + m_w + m_p);
-  HostStage& hs = ctx->stage;
-  hs.add(d_n, n, batch * 4);
-  hs.add(d_a, a_off, batch * 8);
-  hs.add(d_w, w_off.data(), batch * 8);
-  hs.add(d_p, pair_prob.data(), total * 4);
-  ZKQ_CUDA_TRY(hs.flush(st));
-  ZKQ_CUDA_TRY(cudaMemsetAsync(d_c, 0, sizeof(int), st));
-  ZKQ_CUDA_TRY(cudaMemsetAsync(info, 0, batch * sizeof(int32_t), st));
-  RqiBatch rb{d_n, d_a, d_w, d_p, A, W, V, W_out, V_out, err_est, info, (double*)ctx->ws, (int64_t)slot, total,
-              ctx->cfg.rqi_max_iter, d_c};
-  return launch_rqi(rb, target_words, a_words, grid, st);
+  s = ensure(&ctx->ws, &ctx->ws_bytes, L.ws_bytes());
+  if (s != ZKQ_OK) return s;
+  s = rqi_upload(L, ctx->meta, ctx->stage, st);
+  if (s != ZKQ_OK) return s;
+  return rqi_launch(L, ctx->meta, ctx->ws, A, a_words, W, V, target_words, W_out, V_out, err_est, info,
+                    ctx->cfg.rqi_max_iter, st);
 }
 }  // namespace zkq
 

@@ -5,6 +5,7 @@
 #include <cstddef>
 #include <deque>
 #include <vector>
+#include <utility>
 #include <cuda_runtime.h>
 #include "common.cuh"
 
@@ -52,10 +53,13 @@ struct JacobiBatch {
 };
 // grid barrier state of the cooperative Jacobi launch (zeroed before each launch)
 struct GridBar { unsigned count; unsigned gen; int abort; int pad; };
-// small problems: one CTA each; large problems: a cluster of `cluster` CTAs each, or, when grid_blocks > 0,
-// one problem at a time on a cooperative grid of grid_blocks CTAs (few large problems)
+// small problems: one CTA each; large problems: a cluster of `cluster` CTAs each, or, when grid_blocks > 0
+// (few large problems), a cooperative grid of grid_blocks CTAs split into one group per large problem:
+// blocks grp_start[q] .. grp_start[q+1]-1 (device array, n_large + 1 entries), barrier gb[q], reduction
+// slots red + q red_stride
 zkq_status launch_jacobi(const JacobiBatch& jb, int a_words, int n_small, int n_large, int max_small_n,
-                         int max_large_n, int cluster, int grid_blocks, GridBar* gb, cudaStream_t st);
+                         int max_large_n, int cluster, int grid_blocks, GridBar* gb, const int32_t* grp_start,
+                         int red_stride, cudaStream_t st);
 size_t jacobi_smem_bytes(int n);
 int jacobi_grid_max_blocks(int max_large_n, int a_words);   // co-resident blocks per SM of the grid kernel
 
@@ -78,6 +82,43 @@ zkq_status oa_refine(void* ctx, const OaBuffers& buf, int batch, const int32_t* 
                      const double* A, int wa, const double* V, int W, double* W_out, double* V_out, double* err,
                      int32_t* info, int max_iter, int prod_method, cudaStream_t st);
 
+// ---- batch layouts (layout.cu) -----------------------------------------------------------------------
+// FP64 eigensolve: device metadata [n | a_off | w_off | order | ws_off | block groups] (meta_bytes) and
+// workspace [large-problem copies of A and V | reduction slots | grid barriers] (ws_bytes)
+struct EighLayout {
+  int batch = 0, n_small = 0, n_large = 0, max_small = 0, max_large = 0, cluster = 2, grid_blocks = 0, red_stride = 0;
+  std::vector<int32_t> n, order, grp;
+  std::vector<int64_t> a_off, w_off, ws_off;
+  size_t ws_need = 0, red_bytes = 0, gb_bytes = 0;
+  size_t meta_bytes() const;
+  size_t ws_bytes() const;
+};
+// cluster width of the large problems: cfg_cluster if > 0, else the tuning table's entry for the largest
+// order (tune: (order, width) pairs by increasing order, from zkq_autotune_jacobi; the first entry whose
+// order is >= the largest order, else the last), else 2 / 4 / 8 for largest orders <= 128 / 256 / above
+using JacobiTune = std::vector<std::pair<int, int>>;
+zkq_status eigh_layout(int batch, const int32_t* n, const int64_t* a_off, int a_words, int cfg_cluster, int num_sms,
+                       EighLayout* L, const JacobiTune* tune = nullptr);
+zkq_status eigh_upload(const EighLayout& L, void* meta, HostStage& hs, cudaStream_t st);
+zkq_status eigh_launch(const EighLayout& L, const void* meta, void* ws, const double* A, int a_words, double* W,
+                       double* V, int32_t* info, int max_sweeps, int prof_class, cudaStream_t st);
+// plain RQI: device metadata [n | a_off | w_off | eigenpair -> problem | work counter], workspace grid slots
+struct RqiLayout {
+  int batch = 0, grid = 0;
+  int64_t total = 0;
+  size_t slot = 0;
+  std::vector<int32_t> n, pair_prob;
+  std::vector<int64_t> a_off, w_off;
+  size_t meta_bytes() const;
+  size_t ws_bytes() const;
+};
+zkq_status rqi_layout(int batch, const int32_t* n, const int64_t* a_off, int target_words, int num_sms, RqiLayout* L);
+zkq_status rqi_upload(const RqiLayout& L, void* meta, HostStage& hs, cudaStream_t st);
+// also clears the work counter and info (stream-ordered memsets)
+zkq_status rqi_launch(const RqiLayout& L, const void* meta, void* ws, const double* A, int a_words, const double* W,
+                      const double* V, int target_words, double* W_out, double* V_out, double* err, int32_t* info,
+                      int max_iter, cudaStream_t st);
+
 // ---- context internals ---------------------------------------------------------------------------
 // prof_class: profiler class of the launches (0 = PC_JACOBI; the refinement's cluster solves use their own)
 zkq_status eigh_internal(void* ctx, int batch, const int32_t* n, const int64_t* a_off, const double* A, int a_words,
@@ -89,6 +130,7 @@ OaBuffers ctx_oa_buffers(void* ctx);
 int ctx_oa_max_iter(void* ctx);
 void** ctx_mps_ws(void* ctx, size_t** bytes);
 HostStage* ctx_stage(void* ctx);
+JacobiTune* ctx_jacobi_tune(void* ctx);
 
 // ---- split-product GEMM kernel choice --------------------------------------------------------------
 int gemm_kernel_get();

@@ -288,50 +288,52 @@ __global__ void __launch_bounds__(256) jacobi_global_kernel(JacobiBatch jb, int 
                                      jb.W + jb.w_off[b], jb.V + jb.a_off[b] * 2, jb.info + b, 0, 1);
 }
 
-// few large problems: every block of a cooperative launch works on one problem at a time, in turn
+// few large problems: a cooperative launch whose blocks form one group per problem, blocks
+// grp_start[q] .. grp_start[q+1]-1 for problem q, each group with its own barrier and reduction slots
 template <int WA>
-__global__ void __launch_bounds__(256) jacobi_grid_kernel(JacobiBatch jb, int first, int count, GridBar* gb) {
+__global__ void __launch_bounds__(256) jacobi_grid_kernel(JacobiBatch jb, int first, int count, GridBar* gb,
+                                                          const int32_t* __restrict__ grp_start, int red_stride) {
   extern __shared__ __align__(16) unsigned char smem[];
   RotParams* rp = reinterpret_cast<RotParams*>(smem);
-  for (int q = 0; q < count; ++q) {
-    const int b = jb.order[first + q];
-    const int n = jb.n[b];
-    double* wsA = jb.ws + jb.ws_off[b];
-    double* wsV = wsA + (size_t)n * n * 2;
-    Mat<false> A{reinterpret_cast<c64*>(wsA), n}, V{reinterpret_cast<c64*>(wsV), n};
-    jacobi_problem<false, 2, WA>(n, jb.A + jb.a_off[b] * 2 * WA, A, V, rp, jb.red, jb.max_sweeps, jb.flops,
-                                 jb.W + jb.w_off[b], jb.V + jb.a_off[b] * 2, jb.info + b, (int)blockIdx.x,
-                                 (int)gridDim.x, gb);
-    grid_barrier(gb, gridDim.x);     // the reduction slots are reused by the next problem
-  }
+  int q = 0;
+  while (q + 1 < count && (int)blockIdx.x >= grp_start[q + 1]) ++q;
+  const int part = (int)blockIdx.x - grp_start[q], nparts = grp_start[q + 1] - grp_start[q];
+  const int b = jb.order[first + q];
+  const int n = jb.n[b];
+  double* wsA = jb.ws + jb.ws_off[b];
+  double* wsV = wsA + (size_t)n * n * 2;
+  Mat<false> A{reinterpret_cast<c64*>(wsA), n}, V{reinterpret_cast<c64*>(wsV), n};
+  jacobi_problem<false, 2, WA>(n, jb.A + jb.a_off[b] * 2 * WA, A, V, rp, jb.red + (size_t)q * red_stride, jb.max_sweeps,
+                               jb.flops, jb.W + jb.w_off[b], jb.V + jb.a_off[b] * 2, jb.info + b, part, nparts, gb + q);
 }
 
 size_t jacobi_smem_bytes(int n) { return (size_t)2 * (n + 1) * n * sizeof(c64) + (size_t)(n / 2 + 1) * sizeof(RotParams); }
 
 template <int WA>
 static zkq_status launch_words(const JacobiBatch& jb, int n_small, int n_large, int max_small_n, int max_large_n,
-                               int cluster, int grid_blocks, GridBar* gb, cudaStream_t st) {
+                               int cluster, int grid_blocks, GridBar* gb, const int32_t* grp_start, int red_stride,
+                               cudaStream_t st) {
   if (n_small > 0) {
     size_t sm = jacobi_smem_bytes(max_small_n);
-    ZKQ_CUDA_TRY(cudaFuncSetAttribute(jacobi_smem_kernel<WA>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    ZKQ_CUDA_TRY(smem_limit_max<jacobi_smem_kernel<WA>>());
     ProfScope ps(jb.prof_class, st);
     jacobi_smem_kernel<WA><<<n_small, 256, sm, st>>>(jb, 0, n_small);
     ZKQ_CUDA_TRY(cudaGetLastError());
   }
   if (n_large > 0 && grid_blocks > 0) {
     size_t sm = (size_t)(max_large_n / 2 + 1) * sizeof(RotParams);
-    ZKQ_CUDA_TRY(cudaFuncSetAttribute(jacobi_grid_kernel<WA>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-    ZKQ_CUDA_TRY(cudaMemsetAsync(gb, 0, sizeof(GridBar), st));
+    ZKQ_CUDA_TRY(smem_limit_max<jacobi_grid_kernel<WA>>());
+    ZKQ_CUDA_TRY(cudaMemsetAsync(gb, 0, sizeof(GridBar) * n_large, st));
     JacobiBatch jbc = jb;
     int first = n_small, count = n_large;
-    void* args[] = {&jbc, &first, &count, &gb};
+    void* args[] = {&jbc, &first, &count, &gb, &grp_start, &red_stride};
     ProfScope ps(jb.prof_class, st);
     ZKQ_CUDA_TRY(cudaLaunchCooperativeKernel((const void*)jacobi_grid_kernel<WA>, dim3(grid_blocks), dim3(256), args, sm, st));
     return ZKQ_OK;
   }
   if (n_large > 0) {
     size_t sm = (size_t)(max_large_n / 2 + 1) * sizeof(RotParams);
-    ZKQ_CUDA_TRY(cudaFuncSetAttribute(jacobi_global_kernel<WA>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    ZKQ_CUDA_TRY(smem_limit_max<jacobi_global_kernel<WA>>());
     if (cluster > 8)
       ZKQ_CUDA_TRY(cudaFuncSetAttribute(jacobi_global_kernel<WA>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
     cudaLaunchConfig_t cfg = {};
@@ -350,11 +352,12 @@ static zkq_status launch_words(const JacobiBatch& jb, int n_small, int n_large, 
 }
 
 zkq_status launch_jacobi(const JacobiBatch& jb, int a_words, int n_small, int n_large, int max_small_n,
-                         int max_large_n, int cluster, int grid_blocks, GridBar* gb, cudaStream_t st) {
+                         int max_large_n, int cluster, int grid_blocks, GridBar* gb, const int32_t* grp_start,
+                         int red_stride, cudaStream_t st) {
   switch (a_words) {
-    case 1: return launch_words<1>(jb, n_small, n_large, max_small_n, max_large_n, cluster, grid_blocks, gb, st);
-    case 2: return launch_words<2>(jb, n_small, n_large, max_small_n, max_large_n, cluster, grid_blocks, gb, st);
-    case 4: return launch_words<4>(jb, n_small, n_large, max_small_n, max_large_n, cluster, grid_blocks, gb, st);
+    case 1: return launch_words<1>(jb, n_small, n_large, max_small_n, max_large_n, cluster, grid_blocks, gb, grp_start, red_stride, st);
+    case 2: return launch_words<2>(jb, n_small, n_large, max_small_n, max_large_n, cluster, grid_blocks, gb, grp_start, red_stride, st);
+    case 4: return launch_words<4>(jb, n_small, n_large, max_small_n, max_large_n, cluster, grid_blocks, gb, grp_start, red_stride, st);
     default: return ZKQ_EINVAL;
   }
 }

@@ -85,5 +85,5 @@ extern "C" zkq_status zkq_eigh_batched_noalloc(int batch, const int32_t* n, cons
   JacobiBatch jb{(const int32_t*)(base + o_n), (const int64_t*)(base + o_a), (const int64_t*)(base + o_w),
                  (const int32_t*)(base + o_o), A, W, V, info, (double*)(base + o_ws), (const int64_t*)(base + o_s),
                  (double*)(base + o_red), 40, nullptr, 0};
-  return launch_jacobi(jb, a_words, (int)small.size(), (int)large.size(), max_small, max_large, cluster, 0, nullptr, st);
+  return launch_jacobi(jb, a_words, (int)small.size(), (int)large.size(), max_small, max_large, cluster, 0, nullptr, nullptr, 0, st);
 }

@@ -337,7 +337,7 @@ static zkq_status launch_t(const OzProd* d_p, const OzTile* d_t, int ntiles, con
                            const CrtConst* d_c, int* d_err, cudaStream_t st) {
   size_t sm = oz_tc_smem_bytes(BN, npairs);
   if (sm > 227 * 1024) return ZKQ_EINVAL;        // pair lists of this length do not occur (<= 3 x 96 or ~600)
-  ZKQ_CUDA_TRY(cudaFuncSetAttribute(oz_tc_kernel<BN, ACC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+  ZKQ_CUDA_TRY((smem_limit_max<oz_tc_kernel<BN, ACC>>()));
   oz_tc_kernel<BN, ACC><<<ntiles, TC_THREADS, sm, st>>>(d_p, d_t, d_q, npairs, d_c, d_err);
   ZKQ_CUDA_TRY(cudaGetLastError());
   return ZKQ_OK;

@@ -21,6 +21,7 @@
 #include "prof.cuh"
 #include "internal.cuh"
 #include <vector>
+#include <mutex>
 #include <algorithm>
 #include <cstring>
 
@@ -982,14 +983,18 @@ zkq_status mw_gemm_batched(const MwProd* prods, int count, int wa, int wb, int w
   {
     size_t sm = (size_t)OZ_STAGES * (OZ_BM + OZ_BN) * 64;
     if (g_gemm_kernel != 1)
-      ZKQ_CUDA_TRY(cudaFuncSetAttribute(oz_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+      ZKQ_CUDA_TRY(smem_limit_max<oz_gemm_kernel>());
     double flops = 0.0;                        // algorithmic: every kept digit pair, unpadded sizes
     for (auto& o : dp) flops += 2.0 * plan.npairs * (double)o.m * (2.0 * o.n) * (2.0 * o.k);
     ProfScope ps(PC_OZ_GEMM, st, flops);
     if (g_gemm_kernel == 1) {
-      if (!g_oz_err) {
-        ZKQ_CUDA_TRY(cudaMalloc(&g_oz_err, sizeof(int)));
-        ZKQ_CUDA_TRY(cudaMemset(g_oz_err, 0, sizeof(int)));
+      {
+        static std::mutex mu;                          // contexts on several host threads share the flag
+        std::lock_guard<std::mutex> g(mu);
+        if (!g_oz_err) {
+          ZKQ_CUDA_TRY(cudaMalloc(&g_oz_err, sizeof(int)));
+          ZKQ_CUDA_TRY(cudaMemset(g_oz_err, 0, sizeof(int)));
+        }
       }
       zkq_status ls = launch_oz_tc(d_p, d_t, (int)tiles.size(), d_q, plan.npairs, crt ? d_c : nullptr, g_oz_err, st);
       if (ls != ZKQ_OK) return ls;

@@ -231,7 +231,7 @@ __global__ void __launch_bounds__(256) rqi_kernel(RqiBatch rb) {
 template <int W, int WA>
 static zkq_status launch_rqi_t(const RqiBatch& rb, int grid, cudaStream_t st) {
   size_t sm = 256 * sizeof(cmw<W>);
-  ZKQ_CUDA_TRY(cudaFuncSetAttribute(rqi_kernel<W, WA>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+  ZKQ_CUDA_TRY((smem_limit_max<rqi_kernel<W, WA>>()));
   ProfScope ps(PC_RQI, st);
   rqi_kernel<W, WA><<<grid, 256, sm, st>>>(rb);
   ZKQ_CUDA_TRY(cudaGetLastError());

@@ -1,6 +1,9 @@
 // Pinned host staging ring (see internal.cuh).
 #include <cstring>
 #include <algorithm>
+#include <mutex>
+#include <set>
+#include <utility>
 #include "internal.cuh"
 
 namespace zkq {
@@ -96,6 +99,25 @@ cudaError_t HostStage::flush(cudaStream_t st) {
   }
   pend_.clear();
   pieces_.clear();
+  return e;
+}
+
+cudaError_t raise_smem_limit(const void* kernel, int slot) {
+  static std::mutex mu;
+  static std::set<std::pair<int, int>> done;        // (slot, device)
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  std::lock_guard<std::mutex> g(mu);
+  if (done.count({slot, dev})) return cudaSuccess;
+  int optin = 0;
+  e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  if (e != cudaSuccess) return e;
+  cudaFuncAttributes a;
+  e = cudaFuncGetAttributes(&a, kernel);
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, optin - (int)a.sharedSizeBytes);
+  if (e == cudaSuccess) done.insert({slot, dev});
   return e;
 }
 

@@ -52,6 +52,12 @@ def test_invalid_arguments_are_rejected_without_gpu(zkq):
     assert L.zkq_eigh_batched(None, 1, None, None, None, 4, None, None, None, None) == zkq.ZKQ_EINVAL
     assert L.zkq_mw_op(9, 4, 1, None, None, None, 0, None) == zkq.ZKQ_EINVAL
     assert L.zkq_mw_op(0, 3, 1, None, None, None, 0, None) == zkq.ZKQ_EINVAL
+    h = ctypes.c_void_p()
+    assert L.zkq_plan_create(None, 1, None, None, 4, 4, ctypes.byref(h)) == zkq.ZKQ_EINVAL and not h.value
+    assert L.zkq_plan_execute(None, None, None, None, None, None, None, None, None, None) == zkq.ZKQ_EINVAL
+    assert L.zkq_plan_execute_graph(None, None, None, None, None, None, None, None, None, None) == zkq.ZKQ_EINVAL
+    assert L.zkq_plan_destroy(None) == zkq.ZKQ_OK
+    assert L.zkq_autotune_jacobi(None, 1, None, 4, 1, None) == zkq.ZKQ_EINVAL
 
 
 # published relative error bounds (unit roundoff u = 2^-53): double-double add 3u^2 (accurate sum),
