@@ -269,7 +269,7 @@ __global__ void __launch_bounds__(256) jacobi_smem_kernel(JacobiBatch jb, int fi
 
 // large problems: matrix and eigenvectors in global workspace, one cluster of CTAs per problem
 template <int WA>
-__global__ void __launch_bounds__(256) jacobi_global_kernel(JacobiBatch jb, int first) {
+__global__ void __launch_bounds__(256, 4) jacobi_global_kernel(JacobiBatch jb, int first) {
   extern __shared__ __align__(16) unsigned char smem[];
   cg::cluster_group cl = cg::this_cluster();
   const int part = (int)cl.block_rank(), nparts = (int)cl.num_blocks();
@@ -291,7 +291,7 @@ __global__ void __launch_bounds__(256) jacobi_global_kernel(JacobiBatch jb, int 
 // few large problems: a cooperative launch whose blocks form one group per problem, blocks
 // grp_start[q] .. grp_start[q+1]-1 for problem q, each group with its own barrier and reduction slots
 template <int WA>
-__global__ void __launch_bounds__(256) jacobi_grid_kernel(JacobiBatch jb, int first, int count, GridBar* gb,
+__global__ void __launch_bounds__(256, 4) jacobi_grid_kernel(JacobiBatch jb, int first, int count, GridBar* gb,
                                                           const int32_t* __restrict__ grp_start, int red_stride) {
   extern __shared__ __align__(16) unsigned char smem[];
   RotParams* rp = reinterpret_cast<RotParams*>(smem);
