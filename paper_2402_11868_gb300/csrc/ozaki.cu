@@ -753,7 +753,7 @@ __device__ __forceinline__ mw<WC> crt_value(const OzProd& p, const CrtConst* __r
 }
 
 template <int WC, int LW, int LT>
-__global__ void crt_combine_kernel(const OzProd* __restrict__ P, const CrtConst* __restrict__ cc) {
+__global__ void __launch_bounds__(128, (LW <= 9 ? 8 : 4)) crt_combine_kernel(const OzProd* __restrict__ P, const CrtConst* __restrict__ cc) {
   const OzProd p = P[blockIdx.y];
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= p.m * p.n) return;
