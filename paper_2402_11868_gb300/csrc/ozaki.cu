@@ -603,7 +603,7 @@ __global__ void crt_slice_A_kernel(const OzProd* __restrict__ P, const CrtConst*
 
 // B planes: column j' of [Re | Im] output, rows [Re; Im] of K' (real embedding of the complex product)
 template <int WB, int HD>
-__global__ void crt_slice_B_kernel(const OzProd* __restrict__ P, const CrtConst* __restrict__ cc) {
+__global__ void __launch_bounds__(256, 5) crt_slice_B_kernel(const OzProd* __restrict__ P, const CrtConst* __restrict__ cc) {
   __shared__ uint32_t sc[CRT_MAXR * (HD + 2)];
   const OzProd p = P[blockIdx.y];
   if (!p.sliceB) return;
