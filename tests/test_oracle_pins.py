@@ -325,3 +325,35 @@ def test_matmul_matches_exact_rationals():
             for l in range(m):
                 s = cadd(s, cmul(cconj((fr(A[l + i * m, 0]), fr(A[l + i * m, 1]))), (fr(A[l + j * m, 0]), fr(A[l + j * m, 1]))))
             assert abs(fr(Ch[i + j * k, 0]) - s[0]) <= Fraction(1, 2**300)
+            assert abs(fr(Ch[i + j * k, 1]) - s[1]) <= Fraction(1, 2**300)
+
+
+def test_residual_and_orthonormality_match_exact_values():
+    """The 320-bit residual ||A v_c - lambda_c v_c||_2 and the orthonormality defect max_d |v_d^H v_c -
+    delta_dc| against values known exactly.  The eigenvectors u_k of A = U diag(lam) U^H (U exactly
+    unitary) are perturbed in chosen ways:
+    * v_2 = u_2 + eps u_3 has residual eps |lam_3 - lam_2| and defect eps against column 3;
+    * lambda_0 shifted by delta gives residual delta in column 0;
+    * exact pairs give residual and defect 0."""
+    n = 5
+    U = dyadic_unitary(n, layers=12, seed=17)
+    lam = [Fraction(3), Fraction(1, 2), Fraction(-1, 4), Fraction(1, 2**20), Fraction(-5, 2**40)]
+    A = conj_herm_product(U, lam)
+    eps, delta = Fraction(1, 2**100), Fraction(3, 2**90)
+    cols = [[U[i][k] for i in range(n)] for k in range(n)]
+    cols[2] = [cadd(cols[2][i], (eps * U[i][3][0], eps * U[i][3][1])) for i in range(n)]
+    V = [[cols[k][i] for k in range(n)] for i in range(n)]            # V[i][k]
+    lam_given = list(lam)
+    lam_given[0] = lam[0] + delta
+    Aw, Vw = to_words_matrix(A, 8), to_words_matrix(V, 8)
+    assert exact_words_ok(A, Aw, 8) and exact_words_ok(V, Vw, 8)
+    lw = np.array([W.words_of(x, 8) for x in lam_given])
+    res, orth = oracle.residual(Aw, n, lw, Vw)
+    want_res = [float(delta), 0.0, float(eps * abs(lam[3] - lam[2])), 0.0, 0.0]
+    want_orth = [0.0, 0.0, float(eps), float(eps), 0.0]
+    for c in range(n):
+        assert abs(res[c] - want_res[c]) <= 2.0**-280 + 2.0**-60 * want_res[c], (c, res[c], want_res[c])
+        assert abs(orth[c] - want_orth[c]) <= 2.0**-280 + 2.0**-60 * want_orth[c], (c, orth[c], want_orth[c])
+    # a column subset returns the same values in the requested order
+    r2, o2 = oracle.residual(Aw, n, lw, Vw, cols=[3, 2])
+    assert r2[0] == res[3] and r2[1] == res[2] and o2[1] == orth[2]
