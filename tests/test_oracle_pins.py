@@ -174,20 +174,11 @@ def test_eigh_rejects_non_hermitian():
 
 
 # ------------------------------- footnote closed form ---------------------------------------------
-def _footnote_rho(p: Fraction, u0, u1):
-    """rho_target = (1-p)|-><-| + p |u><u| with |u> = U|-> (exact 2x2)."""
-    mm = [[Fraction(1, 2), Fraction(-1, 2)], [Fraction(-1, 2), Fraction(1, 2)]]
-    uu = [[cmul(a, cconj(b)) for b in (u0, u1)] for a in (u0, u1)]
-    return [[((1 - p) * mm[i][j] + p * uu[i][j][0], p * uu[i][j][1]) for j in range(2)] for i in range(2)]
-
-
 @pytest.mark.parametrize("n", [2, 10, 60, 120, 180])
 def test_eigh_footnote_reduced_matrix_u_is_z(n):
     """Footnote: C^{n-1}-Z on |+..+>|-> leaves the target with eigenvalues 1 - 2^-(n-1) and 2^-(n-1)."""
     p = Fraction(1, 2 ** (n - 1))
-    half = Fraction(1, 2)
-    rho = _footnote_rho(p, (half, Fraction(0)), (half, Fraction(0)))   # Z|-> = |+> = (1/2, 1/2) * sqrt2...
-    # |+> has components 1/sqrt2; |u><u| = 1/2 [[1,1],[1,1]] -> use exact form directly
+    # reduced state of the target: (1 - p)|-><-| + p|+><+| (Z|-> = |+>), with |+-><+-| = 1/2 [[1, +-1], [+-1, 1]]
     rho = [[((1 - p) * Fraction(1, 2) + p * Fraction(1, 2), Fraction(0)), ((1 - p) * Fraction(-1, 2) + p * Fraction(1, 2), Fraction(0))],
            [((1 - p) * Fraction(-1, 2) + p * Fraction(1, 2), Fraction(0)), ((1 - p) * Fraction(1, 2) + p * Fraction(1, 2), Fraction(0))]]
     # embed in a larger exactly-unitary conjugation so the solver does real work
@@ -357,3 +348,25 @@ def test_residual_and_orthonormality_match_exact_values():
     # a column subset returns the same values in the requested order
     r2, o2 = oracle.residual(Aw, n, lw, Vw, cols=[3, 2])
     assert r2[0] == res[3] and r2[1] == res[2] and o2[1] == orth[2]
+
+
+def test_footnote_golden_schmidt_values():
+    """tests/golden/footnote_schmidt.txt: the paper's footnote example (Section 1) with U = Z, for the
+    control sequences listed there; the state vector's squared Schmidt coefficients at the cut between
+    the controls and the target are exactly 1 - 2^e and 2^e."""
+    import os
+    path = os.path.join(os.path.dirname(__file__), "golden", "footnote_schmidt.txt")
+    rows = [l.split() for l in open(path) if l.strip() and not l.startswith("#")]
+    assert rows
+    Z = np.zeros((4, 2, 1)); Z[0, 0, 0] = 1.0; Z[3, 0, 0] = -1.0
+    for n_s, pattern, e_s in rows:
+        n, e = int(n_s), int(e_s)
+        assert len(pattern) == n - 1
+        sv = oracle.Statevector(n)
+        sv.set(_exact_pm_state(n))
+        ctrl = [int(c) for c in pattern] + [-1]     # qubit n-1 .. qubit 1 are sites 0 .. n-2; the target is last
+        sv.apply_mcu(n - 1, ctrl, Z)
+        lam2 = sv.schmidt2(n - 1)
+        eps = Fraction(2) ** e
+        assert abs(fr(lam2[0]) - (1 - eps)) <= Fraction(1, 2**300), (n, pattern)
+        assert abs(fr(lam2[1]) - eps) <= Fraction(1, 2**300), (n, pattern)
