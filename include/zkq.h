@@ -61,7 +61,8 @@ typedef struct {
   int max_sweeps;         /* Jacobi sweep limit (0: default 40) */
   int rqi_max_iter;       /* RQI steps per eigenpair (0: default 5) */
   int oa_max_iter;        /* Ogita-Aishima iterations (0: default 40) */
-  int jacobi_cluster;     /* CTAs per large Jacobi problem (0: default chosen by size) */
+  int jacobi_cluster;     /* CTAs per large Jacobi problem (0: the context's autotune table when
+                             zkq_autotune_jacobi has filled it, else 2 / 4 / 8 by the largest order) */
 } zkq_config;
 
 /* Human-readable name of a status code.  Never NULL. */
