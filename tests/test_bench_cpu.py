@@ -1,0 +1,43 @@
+"""The benchmark's reference arm runs the oracle on host cores and prints one JSON line with the
+contract's keys (no GPU needed); the roofline helper keeps the recorded traffic only for the kernel
+source it was measured on."""
+from __future__ import annotations
+
+import json
+import os
+import subprocess
+import sys
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def test_reference_arm_prints_one_contract_line():
+    out = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--steps", "1",
+                          "--warmup", "1"], capture_output=True, text=True, timeout=600, cwd=ROOT)
+    assert out.returncode == 0, out.stderr[-2000:]
+    lines = [l for l in out.stdout.splitlines() if l.startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    for k in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better", "scaling",
+              "vs_baseline", "dtype", "data", "config", "cpu_baseline", "e2e", "impl"):
+        assert k in d, k
+    assert d["impl"] == "reference" and d["value"] > 0 and d["higher_is_better"] is True
+    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] >= 1
+    assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["d2h_bytes_per_step"] == 0
+    assert d["config"]["workload"] == "batch256_qd"
+
+
+def test_recorded_traffic_needs_the_measured_source(tmp_path, monkeypatch):
+    sys.path.insert(0, ROOT)
+    import bench
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    (tmp_path / "profiles").mkdir()
+    src = tmp_path / "k.cu"
+    src.write_text("kernel v1")
+    import hashlib
+    h = hashlib.sha256(b"kernel v1").hexdigest()
+    (tmp_path / "profiles" / "jacobi_global_traffic.txt").write_text(
+        f"source_sha256: {h}\ndram_bytes_per_launch: 12345\n")
+    assert bench.recorded_traffic("k.cu") == 12345
+    src.write_text("kernel v2")                      # the kernel changed since the counters were taken
+    assert bench.recorded_traffic("k.cu") is None
