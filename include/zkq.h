@@ -133,6 +133,30 @@ zkq_status zkq_rqi_refine(zkq_ctx* ctx, int batch, const int32_t* n, const int64
                           int32_t* info, void* stream);
 
 /*
+ * zkq_workspace_size: device bytes that a context's workspace grows to when a batch is diagonalised
+ * (zkq_eigh_batched) and then, if target_words is not 0, refined (zkq_rqi_refine) -- the memory the batched
+ * diagonalisation of Section 2.1 holds beside the caller's arrays, for admission decisions before a call.
+ * Host-side: it launches nothing and allocates nothing (it makes the context's device current).
+ *   n (host)       n[b] >= 1, matrix orders (<= 4096; <= 2048 for the refinement methods)
+ *   a_words        1, 2 or 4: words per real of A
+ *   target_words   0 (eigensolve only), 2 or 4
+ *   method         ZKQ_PLAIN_RQI, ZKQ_OA_OZAKI or ZKQ_OA_FP64 (ignored when target_words is 0)
+ *   bytes (host)   out: the figure, for a context that held no workspace before.  The caller's arrays (A,
+ *                  W, V, the outputs) are not included.
+ * Exact for the eigensolve and plain RQI.  For the refinement methods the refinement state is exact and
+ * the split-product scratch is an upper bound over the products formed for every problem (A X, then
+ * X^H (A X) with I - X^H X, then X + X E).  Cluster separation steps, which run only when eigenvalues of a
+ * problem lie within its cluster threshold, form further products over the clustered columns and may grow
+ * the scratch beyond this figure; zkq_ctx_workspace_bytes reports what a context holds.
+ * Errors: ZKQ_EINVAL, ZKQ_ECUDA.
+ */
+zkq_status zkq_workspace_size(zkq_ctx* ctx, int batch, const int32_t* n, int a_words, int target_words, int method,
+                              size_t* bytes);
+/* Device bytes of workspace the context holds now (eigensolve, refinement, split-product and MPS gate-update
+ * buffers).  Errors: ZKQ_EINVAL. */
+zkq_status zkq_ctx_workspace_bytes(const zkq_ctx* ctx, size_t* bytes);
+
+/*
  * zkq_autotune_jacobi: measure the cluster width (CTAs per problem: 2, 4, 8 or 16) of the batched FP64
  * Jacobi for each order in sizes[0..nsizes) (81 .. 2048) and keep the fastest in the context's table; from
  * then on the context's eigensolves (zkq_eigh_batched, the refinement's cluster blocks, plans created

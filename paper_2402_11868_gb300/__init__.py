@@ -79,6 +79,10 @@ def lib():
                              ("zkq_mps_apply2q", [P, P, I, P, ctypes.c_double, I, P, P, P])):
                 getattr(L, nm).restype = I
                 getattr(L, nm).argtypes = args
+            L.zkq_workspace_size.restype = I
+            L.zkq_workspace_size.argtypes = [P, I, P, I, I, I, P]
+            L.zkq_ctx_workspace_bytes.restype = I
+            L.zkq_ctx_workspace_bytes.argtypes = [P, P]
             L.zkq_autotune_jacobi.restype = I
             L.zkq_autotune_jacobi.argtypes = [P, I, P, I, I, P]
             L.zkq_plan_create.restype = I
@@ -150,6 +154,12 @@ class Context:
                "zkq_autotune_jacobi")
         return [int(x) for x in best]
 
+    def workspace_bytes(self) -> int:
+        """Device bytes of workspace the context holds now (zkq_ctx_workspace_bytes)."""
+        b = ctypes.c_size_t()
+        _check(lib().zkq_ctx_workspace_bytes(self.handle, ctypes.byref(b)), "zkq_ctx_workspace_bytes")
+        return b.value
+
     def close(self):
         if getattr(self, "handle", None):
             lib().zkq_ctx_destroy(self.handle)
@@ -190,6 +200,15 @@ def zkq_rqi_refine(ctx: Context, n, a_off, A, a_words, W, V, target_words, metho
     _check(lib().zkq_rqi_refine(ctx.handle, len(n_arr), n_p, o_p, _ptr(A), a_words, _ptr(W), _ptr(V), target_words,
                                 method, _ptr(W_out), _ptr(V_out), _ptr(err_est), _ptr(info), _stream(stream)),
            "zkq_rqi_refine")
+
+
+def zkq_workspace_size(ctx: Context, n, a_words, target_words=0, method=ZKQ_OA_OZAKI) -> int:
+    """Device workspace bytes of an eigensolve (and refinement) of the batch on a fresh context."""
+    n_arr, n_p = _host_array(n, ctypes.c_int32)
+    b = ctypes.c_size_t()
+    _check(lib().zkq_workspace_size(ctx.handle, len(n_arr), n_p, a_words, target_words, method, ctypes.byref(b)),
+           "zkq_workspace_size")
+    return b.value
 
 
 def zkq_mw_gemm(ctx: Context, m, n, k, opA, A, a_off, wa, B, b_off, wb, C, c_off, wc, p_bits, method, stream=None):

@@ -181,6 +181,81 @@ zkq_status zkq_rqi_refine(zkq_ctx* ctx, int batch, const int32_t* n, const int64
   return rqi_refine_internal(ctx, batch, n, a_off, A, a_words, W, V, target_words, W_out, V_out, err_est, info, st);
 }
 
+zkq_status zkq_workspace_size(zkq_ctx* ctx, int batch, const int32_t* n, int a_words, int target_words,
+                              int method, size_t* bytes) {
+  if (!ctx || !bytes || batch < 0 || (batch > 0 && !n)) return ZKQ_EINVAL;
+  *bytes = 0;
+  if ((a_words != 1 && a_words != 2 && a_words != 4) || (target_words != 0 && target_words != 2 && target_words != 4))
+    return ZKQ_EINVAL;
+  if (method != ZKQ_PLAIN_RQI && method != ZKQ_OA_OZAKI && method != ZKQ_OA_FP64) return ZKQ_EINVAL;
+  if (batch == 0) return ZKQ_OK;
+  const bool oa = target_words != 0 && method != ZKQ_PLAIN_RQI;
+  int64_t xe = 0, le = 0;
+  for (int b = 0; b < batch; ++b) {
+    if (n[b] < 1 || n[b] > (oa ? 2048 : 4096)) return ZKQ_EINVAL;
+    xe += (int64_t)n[b] * n[b]; le += n[b];
+  }
+  ZKQ_CUDA_TRY(cudaSetDevice(ctx->device));          // the layout asks the device for grid occupancy
+  const std::vector<int64_t> zero(batch, 0);
+  const size_t floor_bytes = (size_t)1 << 20;        // smallest allocation of every workspace buffer
+  EighLayout L;
+  zkq_status s = eigh_layout(batch, n, zero.data(), a_words, ctx->cfg.jacobi_cluster, ctx->num_sms, &L,
+                             &ctx->jacobi_tune);
+  if (s != ZKQ_OK) return s;
+  size_t meta = std::max(L.meta_bytes(), floor_bytes), ws = std::max(L.ws_bytes(), floor_bytes);
+  if (target_words != 0 && method == ZKQ_PLAIN_RQI) {  // the RQI shares the eigensolve's buffers
+    RqiLayout R;
+    s = rqi_layout(batch, n, zero.data(), target_words, ctx->num_sms, &R);
+    if (s != ZKQ_OK) return s;
+    meta = std::max(meta, R.meta_bytes());
+    ws = std::max(ws, R.ws_bytes());
+  }
+  size_t total = meta + ws;
+  if (oa) {
+    total += oa_grow_bytes(oa_state_bytes(batch, xe, le, target_words));
+    // split products of one iteration over every problem: P = A X, then S = X^H P with R = I - X^H X, then
+    // X + X E.  Later iterations run subsets of these products.  When the batch mixes K' = 2n above and
+    // below 1024, its products take the digit form while any order above 512 is still refining, and the CRT
+    // form (with a modulus count set by the largest remaining K') once only orders up to 512 remain, so the
+    // bound takes both.  Distinct dummy addresses stand for the distinct matrices of each problem.
+    const int pm = method == ZKQ_OA_OZAKI ? 1 : 0, p_bits = 53 * target_words + 6, W = target_words;
+    std::vector<double> tag(4 * (size_t)batch);
+    auto ptr = [&](int t, int b) { return &tag[(size_t)t * batch + b]; };   // 0 A, 1 X, 2 P, 3 E
+    bool above = false, below = false;
+    for (int b = 0; b < batch; ++b) (n[b] > 512 ? above : below) = true;
+    size_t zw = 0, zm = 0;
+    for (int pass = 0; pass < (above && below ? 2 : 1); ++pass) {
+      std::vector<MwProd> p1, p2, p3;
+      for (int b = 0; b < batch; ++b) {
+        if (pass == 1 && n[b] > 512) continue;
+        const int k = n[b];
+        p1.push_back({k, k, k, 0, ptr(0, b), ptr(1, b), nullptr, nullptr, 1.0, 0});
+        p2.push_back({k, k, k, 1, ptr(1, b), ptr(2, b), nullptr, nullptr, 1.0, 0});
+        p2.push_back({k, k, k, 1, ptr(1, b), ptr(1, b), nullptr, nullptr, -1.0, 1});
+        p3.push_back({k, k, k, 0, ptr(1, b), ptr(3, b), nullptr, nullptr, 1.0, 0});
+      }
+      struct Call { const std::vector<MwProd>* p; int wa, wb; };
+      const Call calls[3] = {{&p1, a_words, W}, {&p2, W, W}, {&p3, W, 2}};   // E is double-double
+      for (const Call& c : calls) {
+        size_t w_need = 0, m_need = 0;
+        s = mw_gemm_workspace(c.p->data(), (int)c.p->size(), c.wa, c.wb, p_bits, pm, &w_need, &m_need);
+        if (s != ZKQ_OK) return s;
+        zw = std::max(zw, w_need); zm = std::max(zm, m_need);
+      }
+    }
+    if (zw) total += oz_grow_bytes(zw);                // the FP64-pipe products use no workspace
+    total += oz_grow_bytes(zm);
+  }
+  *bytes = total;
+  return ZKQ_OK;
+}
+
+zkq_status zkq_ctx_workspace_bytes(const zkq_ctx* ctx, size_t* bytes) {
+  if (!ctx || !bytes) return ZKQ_EINVAL;
+  *bytes = ctx->ws_bytes + ctx->meta_bytes + ctx->oa_bytes + ctx->oz_bytes + ctx->oz_meta_bytes + ctx->mps_bytes;
+  return ZKQ_OK;
+}
+
 zkq_status zkq_mw_gemm(zkq_ctx* ctx, int count, const int32_t* m, const int32_t* n, const int32_t* k,
                        const int32_t* opA, const double* A, const int64_t* a_off, int wa, const double* B,
                        const int64_t* b_off, int wb, double* C, const int64_t* c_off, int wc, int p_bits, int method,

@@ -81,6 +81,10 @@ struct OaBuffers {
 zkq_status oa_refine(void* ctx, const OaBuffers& buf, int batch, const int32_t* n, const int64_t* a_off,
                      const double* A, int wa, const double* V, int W, double* W_out, double* V_out, double* err,
                      int32_t* info, int max_iter, int prod_method, cudaStream_t st);
+// bytes of the refinement state oa_refine lays out (xe = sum n^2, le = sum n, W words per real), and the
+// device bytes its buffer holds once grown to `need` bytes from nothing
+size_t oa_state_bytes(int batch, int64_t xe, int64_t le, int W);
+size_t oa_grow_bytes(size_t need);
 
 // ---- batch layouts (layout.cu) -----------------------------------------------------------------------
 // FP64 eigensolve: device metadata [n | a_off | w_off | order | ws_off | block groups] (meta_bytes) and

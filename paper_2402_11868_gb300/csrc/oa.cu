@@ -386,6 +386,26 @@ static zkq_status grow_buf(void** p, size_t* have, size_t need) {
   return ZKQ_OK;
 }
 
+// Bytes of the refinement state that oa_refine_t lays out for a batch (the same regions in the same order,
+// each rounded to 256 bytes): xe = sum n^2 elements, le = sum n eigenpairs, W words per real.
+size_t oa_state_bytes(int batch, int64_t xe, int64_t le, int W) {
+  const size_t mat = (size_t)xe * 2 * W * sizeof(double);
+  const size_t dd = (size_t)xe * 2 * 2 * sizeof(double), fp = (size_t)xe * 2 * sizeof(double);
+  size_t off = 0;
+  for (size_t b : {mat, mat, mat, mat, mat, dd,                                    // X, X2, P, S, R, E
+                   (size_t)le * W * sizeof(double), (size_t)le * 4, (size_t)le * 4,   // lambda, cluster starts, lengths
+                   sizeof(OaStat) * batch, sizeof(OaProb) * batch, sizeof(int32_t) * batch,
+                   fp, (size_t)le * sizeof(double), fp, (size_t)le * sizeof(int32_t),   // T, its eigenpairs, info
+                   sizeof(OaCluster) * le, mat, mat, mat,                               // clusters, CT, CG, CW
+                   (size_t)le * sizeof(double), sizeof(int32_t) * batch,                 // coupling norms, flags
+                   (size_t)le * W * sizeof(double), dd})                                 // cluster means, couplings
+    off += alg(b);
+  return off;
+}
+
+// device bytes grow_buf holds after growing to `need` bytes from nothing
+size_t oa_grow_bytes(size_t need) { return std::max(need + need / 8, (size_t)1 << 20); }
+
 template <int W>
 zkq_status oa_refine_t(void* ctx, const OaBuffers& buf, int batch, const int32_t* n, const int64_t* a_off,
                        const double* A, int wa, const double* V, double* W_out, double* V_out, double* err,

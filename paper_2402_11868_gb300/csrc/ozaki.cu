@@ -1027,6 +1027,58 @@ zkq_status mw_gemm_batched(const MwProd* prods, int count, int wa, int wb, int w
   return ZKQ_OK;
 }
 
+// Bytes that mw_gemm_batched needs for a product batch: the workspace (residue or digit planes of every
+// operand it splits, GEMM outputs, exponents) exactly as it lays them out, and an upper bound of the
+// metadata (products, at most one tile per 128 x 128 output block, pair list, CRT constants).  Operands are
+// shared by the same pointer, role and shape test as in mw_gemm_batched; the pointers are only compared.
+zkq_status mw_gemm_workspace(const MwProd* prods, int count, int wa, int wb, int p_out_bits, int method,
+                             size_t* ws_need, size_t* meta_need) {
+  *ws_need = 0; *meta_need = 0;
+  if (count <= 0) return ZKQ_OK;
+  for (int w : {wa, wb}) if (w != 1 && w != 2 && w != 4) return ZKQ_EINVAL;
+  std::vector<int> mp(count), np2(count), kp(count);
+  int max_kp = 0;
+  for (int i = 0; i < count; ++i) {
+    const MwProd& q = prods[i];
+    if (q.m < 1 || q.n < 1 || q.k < 1 || 2 * q.k > 4096) return ZKQ_EINVAL;
+    mp[i] = (q.m + OZ_BM - 1) / OZ_BM * OZ_BM;
+    np2[i] = (2 * q.n + OZ_BN - 1) / OZ_BN * OZ_BN;
+    kp[i] = (2 * q.k + 63) / 64 * 64;
+    max_kp = std::max(max_kp, 2 * q.k);
+  }
+  if (method == 0) { *meta_need = al(sizeof(OzProd) * count); return ZKQ_OK; }
+  CrtConst cc;
+  size_t sA = 0, sB = 0, levels = 0, npairs = 0;
+  const bool crt = (method == 1) && crt_build(max_kp, p_out_bits, &cc);
+  if (crt) { sA = sB = 2 * cc.r; npairs = 3 * cc.r; }
+  else {
+    const OzPlan plan = ozaki_plan(max_kp, wa, wb, p_out_bits);
+    sA = plan.sA; sB = plan.sB; levels = plan.S + 1; npairs = make_pairs(plan).size();
+  }
+  size_t off = 0, tiles = 0;
+  for (int i = 0; i < count; ++i) {
+    const MwProd& a = prods[i];
+    bool ownA = true, ownB = true;
+    for (int j = 0; j < i; ++j) {              // the first product with the operand splits it
+      const MwProd& b = prods[j];
+      if (ownA && a.A == b.A && a.opA == b.opA && a.m == b.m && a.k == b.k) ownA = false;
+      if (ownB && a.B == b.B && a.n == b.n && a.k == b.k) ownB = false;
+    }
+    if (ownA) off += al(sA * mp[i] * kp[i] * sizeof(__half));
+    if (ownB) off += al(sB * np2[i] * kp[i] * sizeof(__half));
+    off += al(crt ? (size_t)3 * cc.r * mp[i] * np2[i] : levels * mp[i] * np2[i] * sizeof(int32_t));
+    off += al((size_t)(a.m + a.n) * sizeof(int32_t));
+    tiles += (size_t)(mp[i] / OZ_BM) * (np2[i] / OZ_BN);
+  }
+  *ws_need = off;
+  *meta_need = al(sizeof(OzProd) * count) + al(sizeof(OzTile) * std::max<size_t>(1, tiles)) +
+               al(sizeof(OzPair) * npairs) + (crt ? al(sizeof(CrtConst)) : 0);
+  return ZKQ_OK;
+}
+
+// device bytes grow() holds after growing to `need` bytes from nothing
+size_t oz_grow_bytes(size_t need) { return std::max(need + need / 4, (size_t)1 << 20); }
+
 int gemm_kernel_get() { return g_gemm_kernel; }
 void gemm_kernel_set(int k) { g_gemm_kernel = k; }
 // reads and clears the expired-wait flag of the tcgen05 kernel (synchronous)

@@ -55,5 +55,11 @@ class HostStage;
 zkq_status mw_gemm_batched(const MwProd* prods, int count, int wa, int wb, int wc, int p_out_bits, int method,
                            void** ws, size_t* ws_bytes, void** meta, size_t* meta_bytes, cudaStream_t st,
                            HostStage* stage);
+// Bytes mw_gemm_batched needs for the batch: its workspace exactly, its metadata as an upper bound
+// (host-side only; the operand pointers are compared, never read).
+zkq_status mw_gemm_workspace(const MwProd* prods, int count, int wa, int wb, int p_out_bits, int method,
+                             size_t* ws_need, size_t* meta_need);
+// device bytes held once the split-product workspace or metadata has grown to `need` bytes from nothing
+size_t oz_grow_bytes(size_t need);
 
 }  // namespace zkq

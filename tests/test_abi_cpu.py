@@ -58,6 +58,11 @@ def test_invalid_arguments_are_rejected_without_gpu(zkq):
     assert L.zkq_plan_execute_graph(None, None, None, None, None, None, None, None, None, None) == zkq.ZKQ_EINVAL
     assert L.zkq_plan_destroy(None) == zkq.ZKQ_OK
     assert L.zkq_autotune_jacobi(None, 1, None, 4, 1, None) == zkq.ZKQ_EINVAL
+    nb = ctypes.c_size_t(123)
+    n1 = (ctypes.c_int32 * 1)(64)
+    assert L.zkq_workspace_size(None, 1, n1, 4, 4, 1, ctypes.byref(nb)) == zkq.ZKQ_EINVAL and nb.value == 123
+    assert L.zkq_workspace_size(None, 1, n1, 4, 4, 1, None) == zkq.ZKQ_EINVAL
+    assert L.zkq_ctx_workspace_bytes(None, ctypes.byref(nb)) == zkq.ZKQ_EINVAL and nb.value == 123
 
 
 # published relative error bounds (unit roundoff u = 2^-53): double-double add 3u^2 (accurate sum),
