@@ -24,7 +24,8 @@
  *     library never frees them.  A context owns its workspace.
  *   Streams: `stream` is a cudaStream_t (NULL = legacy default stream).  Calls are asynchronous on that
  *     stream; argument and launch errors return synchronously; per-problem convergence is reported in
- *     device `info` arrays, readable after the stream synchronises.  No call aborts or traps.
+ *     device `info` arrays, readable after the stream synchronises.  No call aborts or traps, and no C++
+ *     exception leaves the library: a host allocation failure inside a call returns ZKQ_ENOMEM.
  */
 #ifndef ZKQ_H
 #define ZKQ_H
@@ -38,7 +39,7 @@ extern "C" {
 typedef enum {
   ZKQ_OK = 0,
   ZKQ_EINVAL = 1,    /* invalid argument (sizes, word counts, null pointers, method) */
-  ZKQ_ENOMEM = 2,    /* device workspace could not be allocated */
+  ZKQ_ENOMEM = 2,    /* device workspace or host memory could not be allocated */
   ZKQ_ENOCONV = 3,   /* reserved: a problem did not converge (per-problem detail is in info[]) */
   ZKQ_ETIMEOUT = 4,  /* a bounded device-side wait expired */
   ZKQ_ECUDA = 5,     /* a CUDA runtime call failed; see zkq_last_cuda_error() */
@@ -208,7 +209,8 @@ zkq_status zkq_plan_destroy(zkq_plan* plan);
  * (i j) x (k m), i the bit of `site`; a one-qubit gate is 2x2.  Gates are host arrays.
  */
 typedef struct zkq_mps zkq_mps;
-/* |0...0> on n_qubits sites (2 <= n <= 4096), bond dimensions capped at r_max (<= 2048), words 2 or 4.
+/* |0...0> on n_qubits sites (2 <= n <= 4096) on the context's device, bond dimensions capped at r_max
+ * (<= 2048), words 2 or 4.  Gate updates need a context on the same device (else ZKQ_EINVAL).
  * Allocates per-site capacity min(2^min(l+1, n-l-1), r_max).  Errors: ZKQ_EINVAL, ZKQ_ENOMEM. */
 zkq_status zkq_mps_create(zkq_ctx* ctx, int n_qubits, int r_max, int words, zkq_mps** out);
 zkq_status zkq_mps_destroy(zkq_mps* mps);

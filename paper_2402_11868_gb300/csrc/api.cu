@@ -56,6 +56,10 @@ const zkq_config& ctx_config(void* vctx) { return ((zkq_ctx*)vctx)->cfg; }
 zkq_config& ctx_config_mut(void* vctx) { return ((zkq_ctx*)vctx)->cfg; }
 int ctx_oa_max_iter(void* vctx) { return ((zkq_ctx*)vctx)->cfg.oa_max_iter; }
 void** ctx_mps_ws(void* vctx, size_t** bytes) { zkq_ctx* c = (zkq_ctx*)vctx; *bytes = &c->mps_bytes; return &c->mps_ws; }
+zkq_status api_exception(void* vctx) noexcept {
+  if (vctx) ((zkq_ctx*)vctx)->stage.discard();
+  return ZKQ_ENOMEM;
+}
 }  // namespace zkq
 
 static zkq_status ensure(void** p, size_t* have, size_t need) {
@@ -152,19 +156,21 @@ zkq_status rqi_refine_internal(void* vctx, int batch, const int32_t* n, const in
 extern "C" {
 
 zkq_status zkq_eigh_batched(zkq_ctx* ctx, int batch, const int32_t* n, const int64_t* a_off,
-                            const double* A, int a_words, double* W, double* V, int32_t* info, void* stream) {
+                            const double* A, int a_words, double* W, double* V, int32_t* info, void* stream) try {
   if (!ctx || batch < 0 || (batch > 0 && (!n || !a_off || !A || !W || !V || !info))) return ZKQ_EINVAL;
   if (a_words != 1 && a_words != 2 && a_words != 4) return ZKQ_EINVAL;
   if (batch == 0) return ZKQ_OK;
   for (int b = 0; b < batch; ++b) if (n[b] < 1 || n[b] > 4096 || a_off[b] < 0) return ZKQ_EINVAL;
   ZKQ_CUDA_TRY(cudaSetDevice(ctx->device));
   return eigh_internal(ctx, batch, n, a_off, A, a_words, W, V, info, (cudaStream_t)stream);
+} catch (...) {
+  return api_exception(ctx);
 }
 
 zkq_status zkq_rqi_refine(zkq_ctx* ctx, int batch, const int32_t* n, const int64_t* a_off,
                           const double* A, int a_words, const double* W, const double* V,
                           int target_words, int method, double* W_out, double* V_out, double* err_est,
-                          int32_t* info, void* stream) {
+                          int32_t* info, void* stream) try {
   if (!ctx || batch < 0 || (batch > 0 && (!n || !a_off || !A || !W || !V || !W_out || !V_out || !err_est || !info)))
     return ZKQ_EINVAL;
   if ((a_words != 1 && a_words != 2 && a_words != 4) || (target_words != 2 && target_words != 4)) return ZKQ_EINVAL;
@@ -179,10 +185,12 @@ zkq_status zkq_rqi_refine(zkq_ctx* ctx, int batch, const int32_t* n, const int64
                      ctx->cfg.oa_max_iter, method == ZKQ_OA_OZAKI ? 1 : 0, st);
   }
   return rqi_refine_internal(ctx, batch, n, a_off, A, a_words, W, V, target_words, W_out, V_out, err_est, info, st);
+} catch (...) {
+  return api_exception(ctx);
 }
 
 zkq_status zkq_workspace_size(zkq_ctx* ctx, int batch, const int32_t* n, int a_words, int target_words,
-                              int method, size_t* bytes) {
+                              int method, size_t* bytes) try {
   if (!ctx || !bytes || batch < 0 || (batch > 0 && !n)) return ZKQ_EINVAL;
   *bytes = 0;
   if ((a_words != 1 && a_words != 2 && a_words != 4) || (target_words != 0 && target_words != 2 && target_words != 4))
@@ -248,6 +256,8 @@ zkq_status zkq_workspace_size(zkq_ctx* ctx, int batch, const int32_t* n, int a_w
   }
   *bytes = total;
   return ZKQ_OK;
+} catch (...) {
+  return api_exception(nullptr);
 }
 
 zkq_status zkq_ctx_workspace_bytes(const zkq_ctx* ctx, size_t* bytes) {
@@ -259,7 +269,7 @@ zkq_status zkq_ctx_workspace_bytes(const zkq_ctx* ctx, size_t* bytes) {
 zkq_status zkq_mw_gemm(zkq_ctx* ctx, int count, const int32_t* m, const int32_t* n, const int32_t* k,
                        const int32_t* opA, const double* A, const int64_t* a_off, int wa, const double* B,
                        const int64_t* b_off, int wb, double* C, const int64_t* c_off, int wc, int p_bits, int method,
-                       void* stream) {
+                       void* stream) try {
   if (!ctx || count < 0 || (count > 0 && (!m || !n || !k || !opA || !A || !a_off || !B || !b_off || !C || !c_off)))
     return ZKQ_EINVAL;
   if (method != 0 && method != 1 && method != 2) return ZKQ_EINVAL;
@@ -275,6 +285,8 @@ zkq_status zkq_mw_gemm(zkq_ctx* ctx, int count, const int32_t* m, const int32_t*
   zkq_status s = mw_gemm_batched(pr.data(), count, wa, wb, wc, p_bits, method, &ctx->oz_ws, &ctx->oz_bytes,
                                  &ctx->oz_meta, &ctx->oz_meta_bytes, (cudaStream_t)stream, &ctx->stage);
   return s;
+} catch (...) {
+  return api_exception(ctx);
 }
 
 zkq_status zkq_set_gemm_kernel(int which) {
@@ -306,28 +318,36 @@ zkq_status zkq_profile_enable(int on) {
   return ZKQ_OK;
 }
 
-zkq_status zkq_profile_read(double* ms, int64_t* launches, double* work, int nclasses) {
+zkq_status zkq_profile_read(double* ms, int64_t* launches, double* work, int nclasses) try {
   if (!ms || !launches || !work || nclasses < 1) return ZKQ_EINVAL;
   Profiler& p = profiler();
   std::lock_guard<std::mutex> g(p.mu);
   for (int i = 0; i < nclasses; ++i) { ms[i] = 0.0; launches[i] = 0; work[i] = 0.0; }
-  for (auto& r : p.recs) {
-    cudaError_t e = cudaEventSynchronize(r.b);
-    if (e != cudaSuccess) { set_last_cuda_error(e); return ZKQ_ECUDA; }
+  p.pool.reserve(p.pool.size() + 2 * p.recs.size());   // the loop below cannot throw
+  // records read so far return their events to the pool and leave the list, also when a read fails
+  size_t done = 0;
+  cudaError_t e = cudaSuccess;
+  for (; done < p.recs.size(); ++done) {
+    const Profiler::Rec& r = p.recs[done];
+    e = cudaEventSynchronize(r.b);
+    if (e != cudaSuccess) break;
     float t = 0.f;
     cudaEventElapsedTime(&t, r.a, r.b);
     if (r.cls < nclasses) { ms[r.cls] += t; launches[r.cls] += 1; work[r.cls] += r.work; }
     p.pool.push_back(r.a); p.pool.push_back(r.b);
   }
-  p.recs.clear();
+  p.recs.erase(p.recs.begin(), p.recs.begin() + done);
+  if (e != cudaSuccess) { set_last_cuda_error(e); return ZKQ_ECUDA; }
   if (g_prof_ctr) {                              // device-counted work (all recorded launches are complete)
     unsigned long long h[PC_COUNT];
-    cudaError_t e = cudaMemcpy(h, g_prof_ctr, sizeof(h), cudaMemcpyDeviceToHost);
+    e = cudaMemcpy(h, g_prof_ctr, sizeof(h), cudaMemcpyDeviceToHost);
     if (e != cudaSuccess) { set_last_cuda_error(e); return ZKQ_ECUDA; }
     for (int i = 0; i < PC_COUNT && i < nclasses; ++i) work[i] += (double)h[i];
     cudaMemset(g_prof_ctr, 0, sizeof(h));
   }
   return ZKQ_OK;
+} catch (...) {
+  return api_exception(nullptr);
 }
 
 }  // extern "C"

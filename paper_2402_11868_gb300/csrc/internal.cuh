@@ -30,6 +30,8 @@ class HostStage {
   // several uploads through one pinned region and one event: add() the pieces (copied at once), then flush()
   void add(void* dst, const void* src, size_t bytes);
   cudaError_t flush(cudaStream_t st);
+  // drop the pieces add() collected since the last flush() (a call that failed before sending them)
+  void discard() noexcept { pend_.clear(); pieces_.clear(); }
  private:
   struct Span { size_t lo, hi; cudaEvent_t ev; };
   struct Piece { void* dst; size_t off, bytes; };
@@ -135,6 +137,17 @@ int ctx_oa_max_iter(void* ctx);
 void** ctx_mps_ws(void* ctx, size_t** bytes);
 HostStage* ctx_stage(void* ctx);
 JacobiTune* ctx_jacobi_tune(void* ctx);
+int ctx_num_sms(void* ctx);
+int ctx_device(void* ctx);
+const zkq_config& ctx_config(void* ctx);
+zkq_config& ctx_config_mut(void* ctx);
+
+// ---- exceptions at the C ABI ----------------------------------------------------------------------
+// No exception may cross the C ABI.  Host allocations (std::vector growth, new) can throw std::bad_alloc or
+// std::length_error; the entry points that allocate catch every exception and return api_exception(ctx):
+// ZKQ_ENOMEM, after dropping the uploads that the failed call collected in the context's staging ring, so
+// that no later call sends them (ctx may be null).
+zkq_status api_exception(void* ctx) noexcept;
 
 // ---- split-product GEMM kernel choice --------------------------------------------------------------
 int gemm_kernel_get();

@@ -14,6 +14,7 @@
 //       Gamma'[l]^i_{alpha beta} = (M V)[(i,alpha), beta] / (lambda_{l-1, alpha} sigma_beta)
 //   keep beta with sigma_beta^2 > tau sum sigma^2, at most r_max; lambda'_beta = sigma_beta / sqrt(sum kept).
 // The eigensolve of rho is the library's FP64 Jacobi + refinement to W words; products are split products.
+#include <new>
 #include <vector>
 #include <algorithm>
 #include <cstring>
@@ -164,15 +165,11 @@ static inline int right_cap(const zkq_mps* m, int l) { return l == m->n - 1 ? 1 
 
 template <int W> static unsigned blocks(size_t n) { return (unsigned)((n + 255) / 256); }
 
-extern "C" {
-
-zkq_status zkq_mps_create(zkq_ctx* ctx, int n_qubits, int r_max, int words, zkq_mps** out) {
-  if (!ctx || !out || n_qubits < 2 || n_qubits > 4096 || r_max < 1 || r_max > 2048 || (words != 2 && words != 4))
-    return ZKQ_EINVAL;
-  *out = nullptr;
-  zkq_mps* m = new zkq_mps();
+// |0...0> on the context's device; on failure the caller frees m (whatever it holds by then)
+static zkq_status mps_build(zkq_ctx* ctx, zkq_mps* m, int n_qubits, int r_max, int words) {
   m->n = n_qubits; m->r_max = r_max; m->W = words;
-  ZKQ_CUDA_TRY(cudaGetDevice(&m->device));
+  m->device = ctx_device(ctx);
+  ZKQ_CUDA_TRY(cudaSetDevice(m->device));
   m->chi.assign(n_qubits - 1, 1);
   m->cap.resize(n_qubits - 1);
   for (int l = 0; l < n_qubits - 1; ++l) {
@@ -182,12 +179,15 @@ zkq_status zkq_mps_create(zkq_ctx* ctx, int n_qubits, int r_max, int words, zkq_
     for (int k = 0; k < e && lim < r_max; ++k) lim *= 2;
     m->cap[l] = (int)std::min<long long>(lim, r_max);
   }
+  m->gamma.reserve(n_qubits);                  // the push_backs below cannot throw and lose a device buffer
+  m->lam.reserve(n_qubits - 1);
+  const std::vector<double> one = [&] { std::vector<double> v(words, 0.0); v[0] = 1.0; return v; }();
   size_t wb = (size_t)words * sizeof(double);
   for (int l = 0; l < n_qubits; ++l) {
     size_t elems = (size_t)2 * left_cap(m, l) * right_cap(m, l);
     double* g = nullptr;
     cudaError_t e = cudaMalloc(&g, elems * 2 * wb);
-    if (e != cudaSuccess) { set_last_cuda_error(e); zkq_mps_destroy(m); return ZKQ_ENOMEM; }
+    if (e != cudaSuccess) { set_last_cuda_error(e); return ZKQ_ENOMEM; }
     m->gamma.push_back(g);
     if (words == 2) mps_init_kernel<2><<<blocks<2>(elems), 256>>>(g, elems);
     else mps_init_kernel<4><<<blocks<4>(elems), 256>>>(g, elems);
@@ -195,20 +195,34 @@ zkq_status zkq_mps_create(zkq_ctx* ctx, int n_qubits, int r_max, int words, zkq_
   for (int l = 0; l < n_qubits - 1; ++l) {
     double* v = nullptr;
     cudaError_t e = cudaMalloc(&v, (size_t)m->cap[l] * wb);
-    if (e != cudaSuccess) { set_last_cuda_error(e); zkq_mps_destroy(m); return ZKQ_ENOMEM; }
-    std::vector<double> one(words, 0.0); one[0] = 1.0;
-    cudaMemcpy(v, one.data(), wb, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) { set_last_cuda_error(e); return ZKQ_ENOMEM; }
     m->lam.push_back(v);
+    ZKQ_CUDA_TRY(cudaMemcpy(v, one.data(), wb, cudaMemcpyHostToDevice));
   }
   cudaError_t e = cudaMalloc(&m->gate, 16 * 2 * wb);
-  if (e != cudaSuccess) { set_last_cuda_error(e); zkq_mps_destroy(m); return ZKQ_ENOMEM; }
+  if (e != cudaSuccess) { set_last_cuda_error(e); m->gate = nullptr; return ZKQ_ENOMEM; }
   ZKQ_CUDA_TRY(cudaDeviceSynchronize());
+  return ZKQ_OK;
+}
+
+extern "C" {
+
+zkq_status zkq_mps_create(zkq_ctx* ctx, int n_qubits, int r_max, int words, zkq_mps** out) {
+  if (!ctx || !out || n_qubits < 2 || n_qubits > 4096 || r_max < 1 || r_max > 2048 || (words != 2 && words != 4))
+    return ZKQ_EINVAL;
+  *out = nullptr;
+  zkq_mps* m = new (std::nothrow) zkq_mps();
+  if (!m) return ZKQ_ENOMEM;
+  zkq_status s;
+  try { s = mps_build(ctx, m, n_qubits, r_max, words); } catch (...) { s = api_exception(nullptr); }
+  if (s != ZKQ_OK) { zkq_mps_destroy(m); return s; }
   *out = m;
   return ZKQ_OK;
 }
 
 zkq_status zkq_mps_destroy(zkq_mps* m) {
   if (!m) return ZKQ_OK;
+  cudaSetDevice(m->device);
   cudaDeviceSynchronize();
   for (double* p : m->gamma) if (p) cudaFree(p);
   for (double* p : m->lam) if (p) cudaFree(p);
@@ -227,6 +241,7 @@ zkq_status zkq_mps_bond_dims(const zkq_mps* m, int32_t* chi) {
 // concatenated over l; W words per real.
 zkq_status zkq_mps_download(const zkq_mps* m, double* gammas, double* lambdas, void* stream) {
   if (!m || !gammas || !lambdas) return ZKQ_EINVAL;
+  ZKQ_CUDA_TRY(cudaSetDevice(m->device));
   cudaStream_t st = (cudaStream_t)stream;
   size_t go = 0, lo = 0, wb = (size_t)m->W * sizeof(double);
   for (int l = 0; l < m->n; ++l) {
@@ -245,6 +260,7 @@ zkq_status zkq_mps_download(const zkq_mps* m, double* gammas, double* lambdas, v
 zkq_status zkq_mps_upload(zkq_mps* m, const int32_t* chi, const double* gammas, const double* lambdas, void* stream) {
   if (!m || !chi || !gammas || !lambdas) return ZKQ_EINVAL;
   for (int l = 0; l < m->n - 1; ++l) if (chi[l] < 1 || chi[l] > m->cap[l]) return ZKQ_EINVAL;
+  ZKQ_CUDA_TRY(cudaSetDevice(m->device));
   cudaStream_t st = (cudaStream_t)stream;
   for (int l = 0; l < m->n - 1; ++l) m->chi[l] = chi[l];
   size_t go = 0, lo = 0, wb = (size_t)m->W * sizeof(double);
@@ -262,7 +278,8 @@ zkq_status zkq_mps_upload(zkq_mps* m, const int32_t* chi, const double* gammas, 
 }
 
 zkq_status zkq_mps_apply1q(zkq_ctx* ctx, zkq_mps* m, int site, const double* U, void* stream) {
-  if (!ctx || !m || !U || site < 0 || site >= m->n) return ZKQ_EINVAL;
+  if (!ctx || !m || !U || site < 0 || site >= m->n || ctx_device(ctx) != m->device) return ZKQ_EINVAL;
+  ZKQ_CUDA_TRY(cudaSetDevice(m->device));
   cudaStream_t st = (cudaStream_t)stream;
   const int W = m->W;
   ZKQ_CUDA_TRY(cudaMemcpyAsync(m->gate, U, 4 * 2 * W * sizeof(double), cudaMemcpyHostToDevice, st));
@@ -402,9 +419,14 @@ static zkq_status apply2q_t(zkq_ctx* ctx, zkq_mps* m, int l, const double* G, do
 }
 
 extern "C" zkq_status zkq_mps_apply2q(zkq_ctx* ctx, zkq_mps* m, int site, const double* G, double trunc_tau, int method,
-                                      int32_t* new_bond, double* discarded_weight, void* stream) {
-  if (!ctx || !m || !G || site < 0 || site + 1 >= m->n || !(trunc_tau >= 0.0) || method < 0 || method > 2) return ZKQ_EINVAL;
+                                      int32_t* new_bond, double* discarded_weight, void* stream) try {
+  if (!ctx || !m || !G || site < 0 || site + 1 >= m->n || !(trunc_tau >= 0.0) || method < 0 || method > 2 ||
+      ctx_device(ctx) != m->device)
+    return ZKQ_EINVAL;
+  ZKQ_CUDA_TRY(cudaSetDevice(m->device));
   cudaStream_t st = (cudaStream_t)stream;
   if (m->W == 2) return apply2q_t<2>(ctx, m, site, G, trunc_tau, method, new_bond, discarded_weight, st);
   return apply2q_t<4>(ctx, m, site, G, trunc_tau, method, new_bond, discarded_weight, st);
+} catch (...) {
+  return api_exception(ctx);
 }

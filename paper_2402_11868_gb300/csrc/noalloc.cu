@@ -37,7 +37,7 @@ static zkq_status noalloc_scratch(int dev, void** out) {
 static size_t al256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 extern "C" zkq_status zkq_eigh_batched_noalloc(int batch, const int32_t* n, const int64_t* a_off, const double* A,
-                                               int a_words, double* W, double* V, int32_t* info, void* stream) {
+                                               int a_words, double* W, double* V, int32_t* info, void* stream) try {
   if (batch < 0 || (batch > 0 && (!n || !a_off || !A || !W || !V || !info))) return ZKQ_EINVAL;
   if (a_words != 1 && a_words != 2 && a_words != 4) return ZKQ_EINVAL;
   if (batch == 0) return ZKQ_OK;
@@ -86,4 +86,6 @@ extern "C" zkq_status zkq_eigh_batched_noalloc(int batch, const int32_t* n, cons
                  (const int32_t*)(base + o_o), A, W, V, info, (double*)(base + o_ws), (const int64_t*)(base + o_s),
                  (double*)(base + o_red), 40, nullptr, 0};
   return launch_jacobi(jb, a_words, (int)small.size(), (int)large.size(), max_small, max_large, cluster, 0, nullptr, nullptr, 0, st);
+} catch (...) {
+  return api_exception(nullptr);
 }

@@ -390,15 +390,15 @@ static zkq_status grow_buf(void** p, size_t* have, size_t need) {
 // each rounded to 256 bytes): xe = sum n^2 elements, le = sum n eigenpairs, W words per real.
 size_t oa_state_bytes(int batch, int64_t xe, int64_t le, int W) {
   const size_t mat = (size_t)xe * 2 * W * sizeof(double);
-  const size_t dd = (size_t)xe * 2 * 2 * sizeof(double), fp = (size_t)xe * 2 * sizeof(double);
+  const size_t ddm = (size_t)xe * 2 * 2 * sizeof(double), fp = (size_t)xe * 2 * sizeof(double);
   size_t off = 0;
-  for (size_t b : {mat, mat, mat, mat, mat, dd,                                    // X, X2, P, S, R, E
+  for (size_t b : {mat, mat, mat, mat, mat, ddm,                                   // X, X2, P, S, R, E
                    (size_t)le * W * sizeof(double), (size_t)le * 4, (size_t)le * 4,   // lambda, cluster starts, lengths
                    sizeof(OaStat) * batch, sizeof(OaProb) * batch, sizeof(int32_t) * batch,
                    fp, (size_t)le * sizeof(double), fp, (size_t)le * sizeof(int32_t),   // T, its eigenpairs, info
                    sizeof(OaCluster) * le, mat, mat, mat,                               // clusters, CT, CG, CW
                    (size_t)le * sizeof(double), sizeof(int32_t) * batch,                 // coupling norms, flags
-                   (size_t)le * W * sizeof(double), dd})                                 // cluster means, couplings
+                   (size_t)le * W * sizeof(double), ddm})                                // cluster means, couplings
     off += alg(b);
   return off;
 }

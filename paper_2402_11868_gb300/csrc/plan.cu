@@ -8,12 +8,6 @@
 
 using namespace zkq;
 
-namespace zkq {
-int ctx_num_sms(void* ctx);
-int ctx_device(void* ctx);
-const zkq_config& ctx_config(void* ctx);
-}
-
 struct zkq_plan {
   void* ctx = nullptr;
   int device = 0, a_words = 1, target = 0, max_sweeps = 40, rqi_max_iter = 5;
@@ -40,6 +34,29 @@ bool args_ok(const zkq_plan* p, const double* A, double* W, double* V, int32_t* 
   if (!p || !A || !W || !V || !info) return false;
   return p->target == 0 || (W_out && V_out && err && rinfo);
 }
+// layout, device buffers and the one-time metadata upload of a plan; on failure the caller frees p
+zkq_status plan_build(zkq_plan* p, zkq_ctx* ctx, int batch, const int32_t* n, const int64_t* a_off) {
+  ZKQ_CUDA_TRY(cudaSetDevice(p->device));
+  zkq_status s = eigh_layout(batch, n, a_off, p->a_words, ctx_config(ctx).jacobi_cluster, ctx_num_sms(ctx), &p->el,
+                             ctx_jacobi_tune(ctx));
+  if (s != ZKQ_OK) return s;
+  if (p->target) {
+    s = rqi_layout(batch, n, a_off, p->target, ctx_num_sms(ctx), &p->rl);
+    if (s != ZKQ_OK) return s;
+  }
+  p->eigh_meta = p->el.meta_bytes();
+  const size_t meta = p->eigh_meta + (p->target ? p->rl.meta_bytes() : 0);
+  const size_t ws = std::max(p->el.ws_bytes(), p->target ? p->rl.ws_bytes() : (size_t)0);
+  cudaError_t e = cudaMalloc(&p->meta, meta);
+  if (e == cudaSuccess) e = cudaMalloc(&p->ws, std::max<size_t>(ws, 256));
+  if (e != cudaSuccess) { set_last_cuda_error(e); return ZKQ_ENOMEM; }
+  HostStage hs;                                 // one-time upload, then wait for it
+  s = eigh_upload(p->el, p->meta, hs, 0);
+  if (s == ZKQ_OK && p->target) s = rqi_upload(p->rl, (char*)p->meta + p->eigh_meta, hs, 0);
+  if (s != ZKQ_OK) return s;
+  ZKQ_CUDA_TRY(cudaDeviceSynchronize());
+  return ZKQ_OK;
+}
 }  // namespace
 
 extern "C" {
@@ -55,28 +72,9 @@ zkq_status zkq_plan_create(zkq_ctx* ctx, int batch, const int32_t* n, const int6
   if (!p) return ZKQ_ENOMEM;
   p->ctx = ctx; p->device = ctx_device(ctx); p->a_words = a_words; p->target = target_words;
   p->max_sweeps = ctx_config(ctx).max_sweeps; p->rqi_max_iter = ctx_config(ctx).rqi_max_iter;
-  auto fail = [&](zkq_status s) { zkq_plan_destroy(p); return s; };
-  cudaError_t e = cudaSetDevice(p->device);
-  if (e != cudaSuccess) { set_last_cuda_error(e); delete p; return ZKQ_ECUDA; }
-  zkq_status s = eigh_layout(batch, n, a_off, a_words, ctx_config(ctx).jacobi_cluster, ctx_num_sms(ctx), &p->el,
-                             ctx_jacobi_tune(ctx));
-  if (s != ZKQ_OK) return fail(s);
-  if (target_words) {
-    s = rqi_layout(batch, n, a_off, target_words, ctx_num_sms(ctx), &p->rl);
-    if (s != ZKQ_OK) return fail(s);
-  }
-  p->eigh_meta = p->el.meta_bytes();
-  const size_t meta = p->eigh_meta + (target_words ? p->rl.meta_bytes() : 0);
-  const size_t ws = std::max(p->el.ws_bytes(), target_words ? p->rl.ws_bytes() : (size_t)0);
-  e = cudaMalloc(&p->meta, meta);
-  if (e == cudaSuccess) e = cudaMalloc(&p->ws, std::max<size_t>(ws, 256));
-  if (e != cudaSuccess) { set_last_cuda_error(e); return fail(ZKQ_ENOMEM); }
-  HostStage hs;                                 // one-time upload, then wait for it
-  s = eigh_upload(p->el, p->meta, hs, 0);
-  if (s == ZKQ_OK && target_words) s = rqi_upload(p->rl, (char*)p->meta + p->eigh_meta, hs, 0);
-  if (s != ZKQ_OK) return fail(s);
-  e = cudaDeviceSynchronize();
-  if (e != cudaSuccess) { set_last_cuda_error(e); return fail(ZKQ_ECUDA); }
+  zkq_status s;
+  try { s = plan_build(p, ctx, batch, n, a_off); } catch (...) { s = api_exception(nullptr); }
+  if (s != ZKQ_OK) { zkq_plan_destroy(p); return s; }
   *out = p;
   return ZKQ_OK;
 }

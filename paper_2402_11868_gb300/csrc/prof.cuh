@@ -46,7 +46,12 @@ struct ProfScope {
     std::lock_guard<std::mutex> g(p.mu);
     cudaEvent_t b = p.get();
     cudaEventRecord(b, st);
-    p.recs.push_back({cls, a, b, work});
+    try {
+      p.recs.push_back({cls, a, b, work});
+    } catch (...) {                  // out of host memory: the launch goes unrecorded (a destructor may not throw)
+      cudaEventDestroy(a);
+      cudaEventDestroy(b);
+    }
   }
 };
 

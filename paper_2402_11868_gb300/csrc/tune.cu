@@ -7,12 +7,6 @@
 
 using namespace zkq;
 
-namespace zkq {
-int ctx_num_sms(void* ctx);
-int ctx_device(void* ctx);
-zkq_config& ctx_config_mut(void* ctx);
-}
-
 namespace {
 // a Hermitian test matrix per problem: entries from a counter hash in [-1, 1), real diagonal
 __device__ __forceinline__ double hash01(uint64_t x) {
@@ -39,7 +33,7 @@ __global__ void tune_fill_kernel(double* A, int n, int count, int words) {
 }  // namespace
 
 extern "C" zkq_status zkq_autotune_jacobi(zkq_ctx* ctx, int nsizes, const int32_t* sizes, int a_words, int reps,
-                                          int32_t* best) {
+                                          int32_t* best) try {
   if (!ctx || nsizes < 1 || !sizes || !best || reps < 1) return ZKQ_EINVAL;
   if (a_words != 1 && a_words != 2 && a_words != 4) return ZKQ_EINVAL;
   for (int i = 0; i < nsizes; ++i) if (sizes[i] <= 80 || sizes[i] > 2048) return ZKQ_EINVAL;   // cluster-path orders
@@ -47,7 +41,11 @@ extern "C" zkq_status zkq_autotune_jacobi(zkq_ctx* ctx, int nsizes, const int32_
   zkq_config& cfg = ctx_config_mut(ctx);
   const int saved = cfg.jacobi_cluster;
   const int count = ctx_num_sms(ctx);
+  // host memory first: once device buffers exist, only the eigensolve may throw, and it is caught in place
   JacobiTune table;
+  table.reserve(nsizes);
+  std::vector<int32_t> nv(count);
+  std::vector<int64_t> off(count);
   zkq_status s = ZKQ_OK;
   double *A = nullptr, *W = nullptr, *V = nullptr;
   int32_t* info = nullptr;
@@ -65,16 +63,15 @@ extern "C" zkq_status zkq_autotune_jacobi(zkq_ctx* ctx, int nsizes, const int32_
     }
     tune_fill_kernel<<<ctx_num_sms(ctx) * 4, 256, 0, st>>>(A, n, count, a_words);
     if (!cu(cudaGetLastError())) break;
-    std::vector<int32_t> nv(count, n);
-    std::vector<int64_t> off(count);
-    for (int b = 0; b < count; ++b) off[b] = (int64_t)b * n * n;
+    for (int b = 0; b < count; ++b) { nv[b] = n; off[b] = (int64_t)b * n * n; }
     float bestms = 1e30f; int bestc = 0;
     for (int c : {2, 4, 8, 16}) {
       cfg.jacobi_cluster = c;
       float tmin = 1e30f;
       for (int r = 0; r <= reps && s == ZKQ_OK; ++r) {      // the first run warms up
         if (!cu(cudaEventRecord(e0, st))) break;
-        s = eigh_internal(ctx, count, nv.data(), off.data(), A, a_words, W, V, info, st);
+        try { s = eigh_internal(ctx, count, nv.data(), off.data(), A, a_words, W, V, info, st); }
+        catch (...) { s = api_exception(ctx); }
         if (s != ZKQ_OK || !cu(cudaEventRecord(e1, st)) || !cu(cudaEventSynchronize(e1))) break;
         float ms = 0;
         if (!cu(cudaEventElapsedTime(&ms, e0, e1))) break;
@@ -100,7 +97,9 @@ done:
   if (st) cudaStreamDestroy(st);
   if (s == ZKQ_OK) {
     std::sort(table.begin(), table.end());
-    *ctx_jacobi_tune(ctx) = table;
+    ctx_jacobi_tune(ctx)->swap(table);
   }
   return s;
+} catch (...) {
+  return api_exception(ctx);
 }
