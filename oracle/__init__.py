@@ -7,7 +7,9 @@ Plain, slow, independent CPU implementation of what the accurate-eigensolve path
 * ``residual``: ||A v - lambda v|| and ||V^H V - I|| at 320 bits;
 * ``matmul``: plain 320-bit complex products (the refinement's dense products);
 * ``Statevector``: brute-force state vector at 320 bits, plus Schmidt values at a cut and the
-  amplitudes of a Vidal MPS (Section 1: MPS = nested Schmidt decomposition).
+  amplitudes of a Vidal MPS (Section 1: MPS = nested Schmidt decomposition);
+* ``mps_site_defect``: the Vidal canonical (weighted orthonormality) conditions of one MPS site, a
+  property of every exact gate update that holds at any qubit count.
 
 Only ``tests/``, ``__graft_entry__.smoke()`` and ``bench.py``'s CPU-baseline leg may import this
 package.  It shares no code with the CUDA path; both receive their inputs from ``workloads``.
@@ -74,6 +76,8 @@ def _load():
             L.oracle_sv_schmidt2.argtypes = [P, I, P, I]
             L.oracle_mps_amplitudes.restype = I
             L.oracle_mps_amplitudes.argtypes = [I, P, P, P, I, P, I]
+            L.oracle_mps_site_defect.restype = I
+            L.oracle_mps_site_defect.argtypes = [I, I, P, P, P, I, I, ctypes.POINTER(D)]
             _lib = L
     return _lib
 
@@ -196,6 +200,22 @@ def mps_amplitudes(n, chi, gammas, lambdas, w, w_out=WORDS):
     if rc:
         raise RuntimeError(f"oracle_mps_amplitudes failed ({rc})")
     return out
+
+
+def mps_site_defect(a, b, gamma, lam_left, lam_right, w, side):
+    """max |G - I| of the Vidal canonical Gram matrix of one site (Section 1: the MPS is a nested Schmidt
+    decomposition).  gamma: (2 a b, 2, w) words of Gamma (s, alpha, beta) row-major; lam_left (a, w) and
+    lam_right (b, w) words or None (all 1).  side 0: sum over s, alpha of lam_left^2 Gamma^H Gamma (b x b);
+    side 1: sum over s, beta of Gamma lam_right^2 Gamma^H (a x a)."""
+    g = _c(gamma)
+    assert g.size == 2 * a * b * 2 * w
+    lp = [None if x is None else _c(x) for x in (lam_left, lam_right)]
+    out = ctypes.c_double()
+    rc = _load().oracle_mps_site_defect(a, b, g.ctypes.data, None if lp[0] is None else lp[0].ctypes.data,
+                                        None if lp[1] is None else lp[1].ctypes.data, w, side, ctypes.byref(out))
+    if rc:
+        raise ValueError("bad arguments to oracle_mps_site_defect")
+    return out.value
 
 
 def to_fraction(words) -> Fraction:

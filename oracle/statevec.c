@@ -185,3 +185,53 @@ int oracle_mps_amplitudes(int n, const int* chi, const double* gam, const double
   free(T);
   return 0;
 }
+
+/* Canonical conditions of one site of a Vidal MPS (Section 1: the MPS is a nested Schmidt decomposition,
+ * so at every bond the tensors on each side are orthonormal once weighted by the squared Schmidt
+ * coefficients).  Gamma is (s, alpha, beta) row-major with alpha < a, beta < b, complex, w words per real;
+ * lamL holds a weights and lamR b weights (NULL: all 1).
+ *   side 0: G[beta][beta'] = sum over s, alpha of lamL_alpha^2 conj(Gamma^s[alpha][beta]) Gamma^s[alpha][beta']
+ *   side 1: G[alpha][alpha'] = sum over s, beta of lamR_beta^2 Gamma^s[alpha][beta] conj(Gamma^s[alpha'][beta])
+ * *defect receives max |G - I| over all entries (320 bits, rounded to double).  Returns 0, or 1 on bad
+ * arguments. */
+int oracle_mps_site_defect(int a, int b, const double* gam, const double* lamL, const double* lamR, int w, int side,
+                           double* defect) {
+  if (a < 1 || b < 1 || w < 1 || (side != 0 && side != 1) || !gam || !defect) return 1;
+  const size_t ne = (size_t)2 * a * b;
+  cmp_t* g = (cmp_t*)malloc(sizeof(cmp_t) * ne);
+  mp* wt = (mp*)malloc(sizeof(mp) * (side == 0 ? a : b));
+  for (size_t e = 0; e < ne; ++e) {
+    mp_from_words(&g[e].re, gam + (e * 2 + 0) * w, w);
+    mp_from_words(&g[e].im, gam + (e * 2 + 1) * w, w);
+  }
+  const double* lw = side == 0 ? lamL : lamR;
+  const int nw = side == 0 ? a : b;
+  for (int k = 0; k < nw; ++k) {
+    if (lw) { mp t; mp_from_words(&t, lw + (size_t)k * w, w); mp_mul(&wt[k], &t, &t); }
+    else mp_from_double(&wt[k], 1.0);
+  }
+  const int d = side == 0 ? b : a;                     /* the Gram matrix is d x d */
+  mp worst; mp_zero(&worst);
+  mp one; mp_from_double(&one, 1.0);
+  for (int p = 0; p < d; ++p)
+    for (int q = 0; q < d; ++q) {
+      cmp_t acc; cmp_zero(&acc);
+      for (int s = 0; s < 2; ++s)
+        for (int k = 0; k < nw; ++k) {
+          /* side 0: k = alpha, entries (alpha, p) and (alpha, q); side 1: k = beta, entries (q, beta), (p, beta) */
+          const cmp_t* x = side == 0 ? &g[((size_t)s * a + k) * b + p] : &g[((size_t)s * a + q) * b + k];
+          const cmp_t* y = side == 0 ? &g[((size_t)s * a + k) * b + q] : &g[((size_t)s * a + p) * b + k];
+          cmp_t t;
+          cmp_mul_conj(&t, x, y);                        /* conj(x) y */
+          cmp_scale(&t, &t, &wt[k]);
+          cmp_add(&acc, &acc, &t);
+        }
+      if (p == q) mp_sub(&acc.re, &acc.re, &one);
+      mp m2; cmp_abs2(&m2, &acc);
+      if (mp_cmp(&m2, &worst) > 0) worst = m2;
+    }
+  mp r; mp_sqrt(&r, &worst);
+  *defect = mp_to_double(&r);
+  free(g); free(wt);
+  return 0;
+}

@@ -370,3 +370,64 @@ def test_footnote_golden_schmidt_values():
         eps = Fraction(2) ** e
         assert abs(fr(lam2[0]) - (1 - eps)) <= Fraction(1, 2**300), (n, pattern)
         assert abs(fr(lam2[1]) - eps) <= Fraction(1, 2**300), (n, pattern)
+
+
+def _site_words(a, b, entry, w=8):
+    """(2 a b, 2, w) words of Gamma (s, alpha, beta) row-major from entry(s, alpha, beta) -> (re, im)."""
+    out = np.zeros((2 * a * b, 2, w))
+    for s in range(2):
+        for al in range(a):
+            for be in range(b):
+                re, im = entry(s, al, be)
+                e = (s * a + al) * b + be
+                out[e, 0, :] = words(re, w)
+                out[e, 1, :] = words(im, w)
+                assert fr(out[e, 0]) == re and fr(out[e, 1]) == im
+    return out
+
+
+@pytest.mark.parametrize("a,b,seed", [(3, 5, 2), (4, 4, 5), (2, 3, 8)])
+def test_mps_site_defect_exact_isometries(a, b, seed):
+    """Weighted isometries built from an exactly unitary complex U (Section 1: the tensors beside a bond are
+    orthonormal in the weight of its Schmidt coefficients) have canonical defect exactly 0:
+    * left: Gamma^s[alpha][beta] = U[s a + alpha][beta] / lam_alpha, so that the lam^2-weighted Gram of the
+      columns is (U^H U) restricted to the first b columns;
+    * right: Gamma^s[alpha][beta] = conj(U[s b + beta][alpha]) / lam_beta.
+    Dyadic weights other than 1 make a weight taken once instead of squared fail, complex U makes a missing
+    conjugate fail, and non-square shapes make swapped indices fail."""
+    lamL = [Fraction(1, 2 ** k) for k in range(a)]
+    lamR = [Fraction(1, 2 ** (2 * k)) for k in range(b)]
+    lw = lambda v: np.array([words(x, 8) for x in v])
+    if b <= 2 * a:
+        U = dyadic_unitary(2 * a, layers=4 * a, seed=seed)
+        g = _site_words(a, b, lambda s, al, be: (U[s * a + al][be][0] / lamL[al], U[s * a + al][be][1] / lamL[al]))
+        assert oracle.mps_site_defect(a, b, g, lw(lamL), None, 8, 0) == 0.0
+        assert oracle.mps_site_defect(a, b, g, None, None, 8, 0) > 0.1          # weights ignored: not orthonormal
+    if a <= 2 * b:
+        U = dyadic_unitary(2 * b, layers=4 * b, seed=seed + 1)
+        g = _site_words(a, b, lambda s, al, be: (U[s * b + be][al][0] / lamR[be], -U[s * b + be][al][1] / lamR[be]))
+        assert oracle.mps_site_defect(a, b, g, None, lw(lamR), 8, 1) == 0.0
+        assert oracle.mps_site_defect(a, b, g, None, lw(lamR), 8, 0) > 0.1      # the other side's contraction
+
+
+def test_mps_site_defect_closed_forms_and_sensitivity():
+    """Sites of the GHZ state's Vidal form, Gamma^s[alpha][beta] = c delta_{alpha s} delta_{beta s} (2 x 2),
+    whose left Gram is diag(c^2 lam_0^2, c^2 lam_1^2):
+    * c = 1 with weights (1, 1/2): defect exactly 3/4;
+    * the GHZ state itself, c = sqrt(2) and weights 1/sqrt(2), each rounded to 4 words: the Gram misses I
+      only by that rounding (nonzero, below 2^-200).
+    A 2^-90 change of one entry of an exact isometry shows up at that size."""
+    ghz = lambda c: (lambda s, al, be: (c if (al == s and be == s) else Fraction(0), Fraction(0)))
+    lam = np.array([words(Fraction(1), 8), words(Fraction(1, 2), 8)])
+    assert oracle.mps_site_defect(2, 2, _site_words(2, 2, ghz(Fraction(1))), lam, None, 8, 0) == 0.75
+    r = W.words_of(Fraction(math.isqrt(2 ** 501), 2 ** 250), 4)                # sqrt(2) in 4 words
+    inv = np.concatenate([oracle.scalar("div", [1.0], r, 4), np.zeros(4)])        # 1 / sqrt(2) in 4 words
+    d = oracle.mps_site_defect(2, 2, _site_words(2, 2, ghz(fr(r))), np.array([inv, inv]), None, 8, 0)
+    assert 0.0 < d < 2.0 ** -200
+    U = dyadic_unitary(6, layers=12, seed=21)
+    base = lambda s, al, be: U[s * 3 + al][be]
+    bump = Fraction(1, 2 ** 90)
+    g2 = _site_words(3, 4, lambda s, al, be: (base(s, al, be)[0] + (bump if (s, al, be) == (1, 2, 0) else 0),
+                                              base(s, al, be)[1]))
+    d2 = oracle.mps_site_defect(3, 4, g2, None, None, 8, 0)
+    assert 2.0 ** -96 < d2 < 2.0 ** -88
