@@ -38,9 +38,14 @@ sys.path.insert(0, ROOT)
 import numpy as np
 
 METRIC = "quad-double refined eigenpairs/sec (err <=2^-200||A||), p50/p99 latency vs plain RQI path"
-# FP64 pipe instruction rate of one GB300 measured by a DFMA-throughput microbenchmark on this machine
-# (1.006 TFLOP/s counting an FMA as two flops, i.e. 0.503 T FP64 instructions/s)
-FP64_INSTR_PEAK = 0.503e12
+# FP64 peak of one GB300 from its unit counts and clock: 152 SMs x 2 FP64 operations (FMA, add or multiply)
+# per clock per SM x 2.07 GHz = 0.629 T FP64 instructions/s, 1.259 TFLOP/s with an FMA as two flops (the
+# nominal 1.25 TFLOP/s).  The roofline fractions use this figure.
+FP64_INSTR_PEAK = 152 * 2 * 2.07e9
+FP64_TFLOPS_PEAK = 2 * FP64_INSTR_PEAK / 1e12
+# a DFMA-throughput microbenchmark on this machine reached 1.006 TFLOP/s (1.6 FMA per clock per SM); reported
+# beside the derived peak
+FP64_TFLOPS_MEASURED = 1.006
 # FP64 instructions of one complex quad-double multiply-add (QD mul 142, QD add 109; 4 mul + 4 add)
 QD_CMAC_INSTR = 4 * 142 + 4 * 109
 
@@ -329,7 +334,7 @@ def roofline(Z, prof, ns, steps):
                     frac=achieved / peak, peak_source=f"{peak_kind} bf16_tflops_sustained (fp16 dense has the bf16 rate)",
                     work="2 m (2n) (2k) flops per kept slice pair, unpadded sizes")
     if dom_name in ("jacobi", "jacobi_cluster"):
-        peak = 1.006   # measured DFMA throughput of this GB300 pool, TFLOP/s (FMA = 2 flops)
+        peak = FP64_TFLOPS_PEAK
         achieved = dom_work / (dom_ms / 1e3) / 1e12
         what = "FP64 eigensolve of the inputs" if dom_name == "jacobi" else "FP64 eigensolves of the refinement's cluster blocks"
         if dom_name == "jacobi":   # the batch's large problems: one jacobi_global_kernel launch per step
@@ -337,7 +342,9 @@ def roofline(Z, prof, ns, steps):
             base["traffic_kernel"] = "jacobi_global_kernel<4> (DRAM read + write per launch, ncu)"
         return dict(base, bound="alu", kernel=f"jacobi_smem/global/grid_kernel ({what})",
                     achieved=achieved, peak=peak, unit="TFLOP/s", frac=achieved / peak,
-                    peak_source="measured FP64 DFMA microbenchmark (MEASURED_PEAKS.json has no FP64 entry)",
+                    peak_source="derived: 152 SMs x 2 FP64 FMA per clock per SM x 2.07 GHz x 2 flops "
+                                "(MEASURED_PEAKS.json has no FP64 entry)",
+                    peak_measured_dfma=FP64_TFLOPS_MEASURED, frac_of_measured_dfma=achieved / FP64_TFLOPS_MEASURED,
                     work="48 n flops per applied rotation (24 n FMA: Hermitian 2x2-block update of A 12 n + V 12 n)")
     if dom_name == "rqi":
         it = 2.0
@@ -345,8 +352,9 @@ def roofline(Z, prof, ns, steps):
         achieved = cmacs * QD_CMAC_INSTR / (dom_ms / 1e3) / 1e12
         return dict(base, bound="alu", kernel="rqi_kernel<4,4>", achieved=achieved, peak=FP64_INSTR_PEAK / 1e12,
                     unit="TFLOP/s", frac=achieved / (FP64_INSTR_PEAK / 1e12),
-                    peak_source="measured DFMA issue rate (FP64 instructions/s, one op per DADD/DMUL/DFMA)")
-    return dict(base, bound="alu", kernel=dom_name, achieved=None, peak=FP64_INSTR_PEAK / 1e12, unit="TFLOP/s",
+                    peak_source="derived: 152 SMs x 2 FP64 instructions per clock per SM x 2.07 GHz",
+                    work="FP64 operations, one per DADD, DMUL or DFMA (1004 per complex quad-double multiply-add)")
+    return dict(base, bound="alu", kernel=dom_name, achieved=None, peak=FP64_TFLOPS_PEAK, unit="TFLOP/s",
                 frac=None)
 
 

@@ -41,3 +41,32 @@ def test_recorded_traffic_needs_the_measured_source(tmp_path, monkeypatch):
     assert bench.recorded_traffic("k.cu") == 12345
     src.write_text("kernel v2")                      # the kernel changed since the counters were taken
     assert bench.recorded_traffic("k.cu") is None
+
+
+class _FakeLib:
+    @staticmethod
+    def zkq_get_gemm_kernel():
+        return 1
+
+
+def test_roofline_objects_of_each_dominant_class():
+    """The roofline object has the contract's keys for whichever kernel class dominates; FP64-pipe classes
+    use the FP64 peak derived from 152 SMs x 2 operations per clock x 2.07 GHz."""
+    sys.path.insert(0, ROOT)
+    import bench
+    ns = [128]
+    for dom, work in (("jacobi", 6.0e11), ("jacobi_cluster", 5.0e11), ("ozaki_gemm", 4.0e14), ("rqi", 0.0),
+                      ("oa_elementwise", 0.0)):
+        prof = {"jacobi": (100.0, 3, 1.0e10), "ozaki_gemm": (50.0, 7, 1.0e12), dom: (1000.0, 4, work)}
+        r = bench.roofline(_FakeLib, prof, ns, 2)
+        for k in ("bound", "peak", "unit", "frac", "traffic", "launches", "avg_launch_ms"):
+            assert k in r, (dom, k)
+        assert r["launches"] == 4 and r["avg_launch_ms"] == 250.0
+        assert r["unit"] in ("GB/s", "TFLOP/s")
+        if dom == "ozaki_gemm":
+            assert r["bound"] == "tensor" and abs(r["achieved"] - 400.0) < 1e-9
+        else:
+            assert r["bound"] == "alu"
+        if dom.startswith("jacobi"):
+            assert abs(r["peak"] - 1.25856) < 1e-4 and abs(r["frac"] - r["achieved"] / r["peak"]) < 1e-12
+            assert r["peak_measured_dfma"] == 1.006
