@@ -33,13 +33,19 @@ _lock = threading.Lock()
 WORDS = 6  # 6 doubles cover the 320-bit results
 
 
+def compile_library(src_dir: str, out: str) -> str:
+    """Compile the oracle's C sources found in src_dir into the shared library `out`."""
+    subprocess.check_call(["gcc", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared", "-o", out]
+                          + [os.path.join(src_dir, s) for s in _SRC] + ["-lm"])
+    return out
+
+
 def build(force: bool = False) -> str:
     srcs = [os.path.join(_HERE, s) for s in _SRC] + [os.path.join(_HERE, "mp.h")]
     newest = max(os.path.getmtime(s) for s in srcs)
     if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < newest:
         tmp = _SO + f".{os.getpid()}.tmp"
-        subprocess.check_call(["gcc", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared", "-o", tmp]
-                              + [os.path.join(_HERE, s) for s in _SRC] + ["-lm"])
+        compile_library(_HERE, tmp)
         os.replace(tmp, _SO)
     return _SO
 
@@ -49,37 +55,43 @@ def _load():
     with _lock:
         if _lib is None:
             build()
-            L = ctypes.CDLL(_SO)
-            P, I, D = ctypes.c_void_p, ctypes.c_int, ctypes.c_double
-            L.oracle_eigh.restype = I
-            L.oracle_eigh.argtypes = [I, P, I, I, P, P, P]
-            L.oracle_residual.restype = I
-            L.oracle_residual.argtypes = [I, P, I, P, P, I, I, P, P, P]
-            L.oracle_matmul.restype = I
-            L.oracle_matmul.argtypes = [I, I, I, I, P, I, P, I, P, I]
-            L.oracle_rewords.restype = None
-            L.oracle_rewords.argtypes = [ctypes.c_long, P, I, P, I]
-            L.oracle_scalar.restype = None
-            L.oracle_scalar.argtypes = [I, P, P, I, P, I]
-            L.oracle_sv_new.restype = P
-            L.oracle_sv_new.argtypes = [I]
-            L.oracle_sv_free.argtypes = [P]
-            for nm in ("oracle_sv_apply1", "oracle_sv_apply2"):
-                getattr(L, nm).restype = I
-                getattr(L, nm).argtypes = [P, I, P, I]
-            L.oracle_sv_apply_mcu.restype = I
-            L.oracle_sv_apply_mcu.argtypes = [P, I, P, P, I]
-            L.oracle_sv_set.argtypes = [P, P, I]
-            L.oracle_sv_get.argtypes = [P, P, I]
-            L.oracle_sv_norm2.argtypes = [P, P, I]
-            L.oracle_sv_schmidt2.restype = I
-            L.oracle_sv_schmidt2.argtypes = [P, I, P, I]
-            L.oracle_mps_amplitudes.restype = I
-            L.oracle_mps_amplitudes.argtypes = [I, P, P, P, I, P, I]
-            L.oracle_mps_site_defect.restype = I
-            L.oracle_mps_site_defect.argtypes = [I, I, P, P, P, I, I, ctypes.POINTER(D)]
-            _lib = L
+            _lib = load_library(_SO)
     return _lib
+
+
+def load_library(path: str):
+    """ctypes handle of an oracle library with every entry point's signature set (the tests that plant
+    mistakes in copies of the oracle load their builds through this, then swap `_lib`)."""
+    L = ctypes.CDLL(path)
+    P, I, D = ctypes.c_void_p, ctypes.c_int, ctypes.c_double
+    L.oracle_eigh.restype = I
+    L.oracle_eigh.argtypes = [I, P, I, I, P, P, P]
+    L.oracle_residual.restype = I
+    L.oracle_residual.argtypes = [I, P, I, P, P, I, I, P, P, P]
+    L.oracle_matmul.restype = I
+    L.oracle_matmul.argtypes = [I, I, I, I, P, I, P, I, P, I]
+    L.oracle_rewords.restype = None
+    L.oracle_rewords.argtypes = [ctypes.c_long, P, I, P, I]
+    L.oracle_scalar.restype = None
+    L.oracle_scalar.argtypes = [I, P, P, I, P, I]
+    L.oracle_sv_new.restype = P
+    L.oracle_sv_new.argtypes = [I]
+    L.oracle_sv_free.argtypes = [P]
+    for nm in ("oracle_sv_apply1", "oracle_sv_apply2"):
+        getattr(L, nm).restype = I
+        getattr(L, nm).argtypes = [P, I, P, I]
+    L.oracle_sv_apply_mcu.restype = I
+    L.oracle_sv_apply_mcu.argtypes = [P, I, P, P, I]
+    L.oracle_sv_set.argtypes = [P, P, I]
+    L.oracle_sv_get.argtypes = [P, P, I]
+    L.oracle_sv_norm2.argtypes = [P, P, I]
+    L.oracle_sv_schmidt2.restype = I
+    L.oracle_sv_schmidt2.argtypes = [P, I, P, I]
+    L.oracle_mps_amplitudes.restype = I
+    L.oracle_mps_amplitudes.argtypes = [I, P, P, P, I, P, I]
+    L.oracle_mps_site_defect.restype = I
+    L.oracle_mps_site_defect.argtypes = [I, I, P, P, P, I, I, ctypes.POINTER(D)]
+    return L
 
 
 def _c(a):

@@ -431,3 +431,55 @@ def test_mps_site_defect_closed_forms_and_sensitivity():
                                               base(s, al, be)[1]))
     d2 = oracle.mps_site_defect(3, 4, g2, None, None, 8, 0)
     assert 2.0 ** -96 < d2 < 2.0 ** -88
+
+
+def test_statevector_gates_on_basis_states():
+    """Gates applied to basis states give the gate's columns (the definition of a matrix acting on a basis
+    vector), with the conventions of the oracle: site 0 is the most significant bit, a two-qubit gate on
+    (site, site+1) has row index 2 i + j with i the bit of `site`, a controlled gate acts only where every
+    control bit matches.  Complex dyadic gates keep everything exact."""
+    n = 4
+    U4 = dyadic_unitary(4, layers=6, seed=33)
+    U2 = dyadic_unitary(2, layers=3, seed=34)
+    # to_words_matrix stores M[i][j] at i + j dim: M[c][r] = U[r][c] puts U row-major at r dim + c
+    G = to_words_matrix([[U4[r][c] for r in range(4)] for c in range(4)], 4)
+    U = to_words_matrix([[U2[r][c] for r in range(2)] for c in range(2)], 4)
+    bit = lambda site: 1 << (n - 1 - site)
+
+    def run(x, op):
+        sv = oracle.Statevector(n)
+        amps = np.zeros((1 << n, 2, 1)); amps[x, 0, 0] = 1.0
+        sv.set(amps)
+        op(sv)
+        out = sv.amplitudes()
+        return {y: (fr(out[y, 0]), fr(out[y, 1])) for y in range(1 << n) if fr(out[y, 0]) or fr(out[y, 1])}
+
+    rest = bit(0) | bit(3)                                   # spectator bits set, to catch stray indices
+    for site in range(n - 1):
+        for col in range(4):
+            k, m = col >> 1, col & 1
+            x = (rest & ~(bit(site) | bit(site + 1))) | (bit(site) if k else 0) | (bit(site + 1) if m else 0)
+            got = run(x, lambda sv: sv.apply2(site, G))
+            base = x & ~(bit(site) | bit(site + 1))
+            want = {}
+            for r in range(4):
+                y = base | (bit(site) if r >> 1 else 0) | (bit(site + 1) if r & 1 else 0)
+                if U4[r][col] != (0, 0):
+                    want[y] = U4[r][col]
+            assert got == want, (site, col)
+    for site in range(n):
+        for c in range(2):
+            x = (rest & ~bit(site)) | (bit(site) if c else 0)
+            got = run(x, lambda sv: sv.apply1(site, U))
+            want = {((x & ~bit(site)) | (bit(site) if r else 0)): U2[r][c] for r in range(2) if U2[r][c] != (0, 0)}
+            assert got == want, (site, c)
+    # controlled U on target 2, controls: site 0 must be 1, site 3 must be 0, site 1 free
+    ctrl = [1, -1, -1, 0]
+    for x in range(1 << n):
+        got = run(x, lambda sv: sv.apply_mcu(2, ctrl, U))
+        if (x & bit(0)) and not (x & bit(3)):
+            c = 1 if x & bit(2) else 0
+            want = {((x & ~bit(2)) | (bit(2) if r else 0)): U2[r][c] for r in range(2) if U2[r][c] != (0, 0)}
+        else:
+            want = {x: (Fraction(1), Fraction(0))}
+        assert got == want, x
