@@ -38,6 +38,9 @@ def test_mp_scalar_ops_match_exact_rationals(op):
             eb = int(rng.integers(-60, 60))
             b = [math.ldexp(float(rng.standard_normal()), eb)]
             b += [b[-1] * 2**-55 * float(rng.standard_normal()) for _ in range(3)]
+        if trial % 5 == 4:   # full-width operands: 6 words span ~318 of the 320 mantissa bits
+            a = a[:1] + [a[0] * 2.0**(-53 * k) * (1 + float(rng.uniform(0, 0.5))) for k in range(1, 6)]
+            b = b[:1] + [b[0] * 2.0**(-53 * k) * (1 + float(rng.uniform(0, 0.5))) for k in range(1, 6)]
         A, B = fr(a), fr(b)
         got = fr(oracle.scalar(op, a, b))
         exact = {"add": A + B, "sub": A - B, "mul": A * B, "div": A / B if B else None}[op]
