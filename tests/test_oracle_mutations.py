@@ -2,7 +2,8 @@
 a slip in writing it out would make: a wrong sign, a dropped term, a missing conjugate, a transposed
 operand or index, too few iterations.  The copy is built into a library of its own, and the pins run
 against it.  At least one pin must fail for every mistake.  CPU only; the mistakes live in the copies,
-never in the oracle."""
+never in the oracle.  Every planted mistake keeps all memory accesses in bounds (the copies run in this
+process)."""
 from __future__ import annotations
 
 import os
@@ -79,6 +80,15 @@ MUTATIONS = [
     ("canonical defect weights not squared", "statevec.c",
      "mp_mul(&wt[k], &t, &t);", "wt[k] = t;",
      [lambda: P.test_mps_site_defect_exact_isometries(3, 5, 2)]),
+    ("Schmidt values: right Gram matrix summed over the wrong index", "statevec.c",
+     "cmp_mul_conj(&t, &h->psi[l * R + b], &h->psi[l * R + a])", "cmp_mul_conj(&t, &h->psi[b * R + l], &h->psi[a * R + l])",
+     [lambda: P.test_statevector_footnote_schmidt_values_u_is_z(8), P.test_footnote_golden_schmidt_values]),
+    ("jacobi stops at 2^-100 of the norm", "eigh.c",
+     "mp_ldexp(&tol, &fro, -300);", "mp_ldexp(&tol, &fro, -100);",
+     [lambda: P.test_eigh_exact_known_spectrum(6, 2), P.test_eigh_2x2_closed_form]),
+    ("non-Hermitian input accepted", "eigh.c",
+     "free(a); free(v); free(vs); free(lam); free(order); return 1;", "(void)0;",
+     [P.test_eigh_rejects_non_hermitian]),
     ("conjugate-transpose product without the conjugate", "products.c",
      "if (opA) cmp_mul_conj(&t,", "if (opA) cmp_mul(&t,",
      [P.test_matmul_matches_exact_rationals]),
@@ -102,7 +112,7 @@ def test_planted_mistake_fails_a_pin(tmp_path, monkeypatch, name, fname, old, ne
     for pin in pins:
         try:
             pin()
-        except (AssertionError, RuntimeError, ValueError, ZeroDivisionError):
+        except (AssertionError, RuntimeError, ValueError, ZeroDivisionError, pytest.fail.Exception):
             failed.append(pin)
     assert failed, f"no pin noticed the planted mistake: {name}"
 
