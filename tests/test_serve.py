@@ -1,4 +1,4 @@
-"""Serving loop: footprint estimates, admission, continuous batching (CPU checks of the scheduler), and
+"""Serving loop: footprint estimates and the scheduler with recorded device work (CPU), and
 on the GPU: every result is the same alone and in a mix, gates keep their per-simulation order."""
 from __future__ import annotations
 
@@ -86,3 +86,100 @@ def test_gate_requests_keep_order_per_simulation():
             assert worst <= Fraction(1, 2**185)
     finally:
         eng.close()
+
+
+def test_scheduler_admission_order_and_batching_on_cpu():
+    """The engine's host-side scheduling with the device work replaced by recorders (no GPU): admitted
+    eigensolves never exceed the HBM budget, a batch holds one target precision and at most max_batch
+    requests, gates of one simulation run one at a time in submission order, no more batches run at once
+    than there are slots, and a request larger than the whole budget is refused."""
+    import contextlib
+    import itertools
+    import threading
+    import time
+    from paper_2402_11868_gb300.serve import Engine, Request
+
+    class FakeCtx:
+        def close(self):
+            pass
+
+    class FakeTorch:
+        class cuda:
+            @staticmethod
+            def stream(s):
+                return contextlib.nullcontext()
+
+    eng = Engine.__new__(Engine)
+    eng.Z, eng.torch, eng.dev = None, FakeTorch, None
+    eng.budget, eng.max_batch, eng.method = 1000, 3, 1
+    eng.slots = [(FakeCtx(), None) for _ in range(2)]
+    eng.free_slots = [0, 1]
+    eng.lock = threading.Condition()
+    eng.pending, eng.in_use, eng.sims, eng.sim_busy = [], 0, {}, set()
+    eng.ids, eng.completed, eng.stop = itertools.count(), [], False
+    log = {"batches": [], "running": 0, "max_running": 0, "over_budget": 0, "gates": {0: [], 1: []},
+           "gate_overlap": 0}
+    mu = threading.Lock()
+
+    def run_eig(ctx, stream, batch):
+        with mu:
+            log["running"] += 1
+            log["max_running"] = max(log["max_running"], log["running"])
+            log["batches"].append([(r.payload["target"], r.footprint) for r in batch])
+            if eng.in_use > eng.budget:
+                log["over_budget"] += 1
+        time.sleep(0.01)
+        for r in batch:
+            r.result = {"ok": True}
+        with mu:
+            log["running"] -= 1
+
+    class FakeMPS:
+        def __init__(self, sid):
+            self.sid, self.active = sid, False
+
+        def apply2q(self, site, G, tau, method, stream=None, ctx=None):
+            with mu:
+                if self.active:
+                    log["gate_overlap"] += 1
+                self.active = True
+                log["gates"][self.sid].append(site)
+            time.sleep(0.002)
+            with mu:
+                self.active = False
+            return (1, 0.0)
+
+        def close(self):
+            pass
+
+    eng._run_eig = run_eig
+    eng.sims = {0: (FakeMPS(0), 0), 1: (FakeMPS(1), 0)}
+    eng.thread = threading.Thread(target=eng._loop, daemon=True)
+    eng.thread.start()
+    reqs, gate_order = [], {0: [], 1: []}
+    try:
+        rng = np.random.default_rng(7)
+        for k in range(40):
+            if k % 3 == 2:
+                sid = k % 2
+                site = int(rng.integers(0, 20))
+                gate_order[sid].append(site)
+                reqs.append(eng.submit_gate(sid, site, None, 0.0))
+            else:
+                fp = int(rng.integers(50, 600))
+                r = Request("eig", -1, {"target": 2 if k % 2 else 4}, fp)
+                reqs.append(eng._enqueue(r))
+        big = eng._enqueue(Request("eig", -1, {"target": 4}, 2000))
+        assert big.error and "EADMIT" in big.error
+        for r in reqs:
+            assert r.done.wait(30) and r.error is None, r.error
+    finally:
+        eng.close()
+    assert log["over_budget"] == 0 and eng.in_use == 0
+    assert log["max_running"] <= 2
+    for b in log["batches"]:
+        assert 1 <= len(b) <= 3 and len({t for t, _ in b}) == 1
+        assert sum(fp for _, fp in b) <= 1000
+    assert sum(len(b) for b in log["batches"]) == sum(1 for r in reqs if r.kind == "eig")
+    assert log["gate_overlap"] == 0
+    assert log["gates"] == gate_order
