@@ -70,3 +70,19 @@ def test_roofline_objects_of_each_dominant_class():
         if dom.startswith("jacobi"):
             assert abs(r["peak"] - 1.25856) < 1e-4 and abs(r["frac"] - r["achieved"] / r["peak"]) < 1e-12
             assert r["peak_measured_dfma"] == 1.006
+
+
+def test_clock_sampler_summary_from_nvidia_smi_rows():
+    """The clocks object of the bench line: median SM clock under load, the maximum, and every throttle
+    reason seen Active (rows as nvidia-smi prints them with the bench's query fields)."""
+    sys.path.insert(0, ROOT)
+    import bench
+    cs = bench.ClockSampler(0)
+    cs.rows = [["2070", "2070", "900.5", "0x0000000000000000", "Not Active", "Not Active", "Not Active", "Not Active"],
+               ["1980", "2070", "1390.2", "0x0000000000000004", "Not Active", "Not Active", "Not Active", "Active"],
+               ["2010", "2070", "1200.0", "0x0000000000000000", "Not Active", "Not Active", "Not Active", "Not Active"],
+               ["[N/A]", "[N/A]", "[N/A]", "[N/A]", "[N/A]", "[N/A]", "[N/A]", "[N/A]"]]
+    r = cs.stop()
+    assert r == {"sm_mhz": 2010.0, "sm_max_mhz": 2070.0, "reasons": ["sw_power_cap"], "samples": 4}
+    cs.rows = [["1500", "2070", "700", "0x8", "Active", "Not Active", "Not Active", "Not Active"]]
+    assert cs.stop()["reasons"] == ["hw_slowdown"]
