@@ -11,6 +11,7 @@ if ROOT not in sys.path:
 def pytest_configure(config):
     # temporary directories stay inside the repository (in the git-ignored build folder)
     if not config.option.basetemp:
+        os.makedirs(os.path.join(ROOT, "_build"), exist_ok=True)
         config.option.basetemp = os.path.join(ROOT, "_build", "pytest_tmp")
     config.addinivalue_line("markers", "gpu: needs a GB300 (sm_103a) GPU and the CUDA library")
     config.addinivalue_line("markers", "slow: long-running CPU test")
