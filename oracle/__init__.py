@@ -9,7 +9,8 @@ Plain, slow, independent CPU implementation of what the accurate-eigensolve path
 * ``Statevector``: brute-force state vector at 320 bits, plus Schmidt values at a cut and the
   amplitudes of a Vidal MPS (Section 1: MPS = nested Schmidt decomposition);
 * ``mps_site_defect``: the Vidal canonical (weighted orthonormality) conditions of one MPS site, a
-  property of every exact gate update that holds at any qubit count.
+  property of every exact gate update that holds at any qubit count;
+* ``Statevector.vidal``: the Vidal MPS of a state from its Schmidt decompositions at every cut.
 
 Only ``tests/``, ``__graft_entry__.smoke()`` and ``bench.py``'s CPU-baseline leg may import this
 package.  It shares no code with the CUDA path; both receive their inputs from ``workloads``.
@@ -89,6 +90,8 @@ def load_library(path: str):
     L.oracle_sv_schmidt2.argtypes = [P, I, P, I]
     L.oracle_mps_amplitudes.restype = I
     L.oracle_mps_amplitudes.argtypes = [I, P, P, P, I, P, I]
+    L.oracle_sv_vidal.restype = I
+    L.oracle_sv_vidal.argtypes = [P, I, P, P, P, I]
     L.oracle_mps_site_defect.restype = I
     L.oracle_mps_site_defect.argtypes = [I, I, P, P, P, I, I, ctypes.POINTER(D)]
     return L
@@ -192,6 +195,22 @@ class Statevector:
         out = np.zeros(w)
         _load().oracle_sv_norm2(self._h, out.ctypes.data, w)
         return out
+
+    def vidal(self, tol_log2=200, w=WORDS):
+        """Vidal MPS of the state (chi, gammas (elements, 2, w), lambdas (values, w)) in the layout of
+        mps_amplitudes, from the Schmidt decomposition at every cut; Schmidt values with lambda^2 at or below
+        2^-tol_log2 lambda_0^2 are dropped."""
+        n = self.n
+        cmax = [1 << min(c, n - c) for c in range(n + 1)]
+        ge = sum(2 * cmax[l] * cmax[l + 1] for l in range(n))
+        chi = np.zeros(n - 1, dtype=np.int32)
+        gam = np.zeros((ge, 2, w)); lam = np.zeros((sum(cmax[1:n]), w))
+        rc = _load().oracle_sv_vidal(self._h, tol_log2, chi.ctypes.data, gam.ctypes.data, lam.ctypes.data, w)
+        if rc:
+            raise RuntimeError(f"oracle_sv_vidal failed ({rc})")
+        dims = [1] + [int(c) for c in chi] + [1]
+        used = sum(2 * dims[l] * dims[l + 1] for l in range(n))
+        return chi, gam[:used], lam[:int(chi.sum())]
 
     def schmidt2(self, cut, w=WORDS):
         m = 1 << min(cut, self.n - cut)

@@ -235,3 +235,113 @@ int oracle_mps_site_defect(int a, int b, const double* gam, const double* lamL, 
   free(g); free(wt);
   return 0;
 }
+
+/* Vidal form of the state (Section 1: the MPS is a nested Schmidt decomposition).  At every cut c = 1..n-1
+ * the state is Psi[a][r] = psi[a * 2^(n-c) + r] = sum_k lambda_k u_k[a] v_k[r] with orthonormal u_k, v_k;
+ * the Schmidt pairs come from the Jacobi eigensolve of the smaller Gram matrix (Psi Psi^H, eigenvectors
+ * u_k; or Psi^H Psi, eigenvectors conj(v_k)), the other vector of each pair from Psi, and only values with
+ * lambda_k^2 > 2^-tol_log2 lambda_0^2 are kept.  Then
+ *   Gamma[l]^s[alpha][beta] = <u^(l)_alpha (x) s (x) v^(l+1)_beta | psi> / (lambda^(l)_alpha lambda^(l+1)_beta)
+ * with u^(0) = v^(n) = (1) and lambda^(0) = lambda^(n) = 1, and lambda[l] = lambda^(l+1).
+ * chi[l] (l = 0..n-2) receives the bond dimensions; gam and lam receive the tensors in the layout of
+ * oracle_mps_amplitudes (w words), packed.  The caller sizes gam for sum over l of 2 cmax(l) cmax(l+1)
+ * complex elements and lam for sum of cmax, cmax(c) = 2^min(c, n-c).  Returns 0, or 1 / 2 on bad
+ * arguments / an eigensolve that did not converge. */
+int oracle_sv_vidal(void* hv, int tol_log2, int* chi, double* gam, double* lam, int w) {
+  sv_t* h = (sv_t*)hv;
+  const int n = h->n;
+  if (n < 2 || n > 14 || w < 1) return 1;
+  cmp_t** U = (cmp_t**)calloc(n + 1, sizeof(cmp_t*));   /* U[c]: 2^c x chi_c, column k = u_k */
+  cmp_t** V = (cmp_t**)calloc(n + 1, sizeof(cmp_t*));   /* V[c]: 2^(n-c) x chi_c, column k = v_k */
+  mp** L = (mp**)calloc(n + 1, sizeof(mp*));
+  int* ch = (int*)calloc(n + 1, sizeof(int));
+  int rc = 0;
+  ch[0] = ch[n] = 1;
+  for (int c = 0; c <= n; c += n) {                     /* the trivial cuts */
+    U[c] = (cmp_t*)malloc(sizeof(cmp_t) * (c == 0 ? 1 : h->dim));
+    V[c] = (cmp_t*)malloc(sizeof(cmp_t) * (c == 0 ? h->dim : 1));
+    L[c] = (mp*)malloc(sizeof(mp));
+    mp_from_double(&L[c][0], 1.0);
+  }
+  cmp_zero(&U[0][0]); mp_from_double(&U[0][0].re, 1.0);
+  cmp_zero(&V[n][0]); mp_from_double(&V[n][0].re, 1.0);
+  for (int c = 1; c < n && !rc; ++c) {
+    const size_t Ld = (size_t)1 << c, Rd = (size_t)1 << (n - c);
+    const int left = Ld <= Rd;
+    const size_t m = left ? Ld : Rd;
+    cmp_t* g = (cmp_t*)malloc(sizeof(cmp_t) * m * m);
+    cmp_t* ev = (cmp_t*)malloc(sizeof(cmp_t) * m * m);
+    mp* mu = (mp*)malloc(sizeof(mp) * m);
+    int* order = (int*)malloc(sizeof(int) * m);
+    for (size_t a = 0; a < m; ++a) for (size_t b = 0; b < m; ++b) {
+      cmp_t s, t; cmp_zero(&s);
+      if (left) for (size_t r = 0; r < Rd; ++r) { cmp_mul_conj(&t, &h->psi[b * Rd + r], &h->psi[a * Rd + r]); cmp_add(&s, &s, &t); }
+      else for (size_t l = 0; l < Ld; ++l) { cmp_mul_conj(&t, &h->psi[l * Rd + a], &h->psi[l * Rd + b]); cmp_add(&s, &s, &t); }
+      g[a + b * m] = s;                                 /* left: (Psi Psi^H)_ab; right: (Psi^H Psi)_ab */
+    }
+    if (oracle_jacobi_mp((int)m, g, ev, 80) < 0) rc = 2;
+    else {
+      oracle_finish_mp((int)m, g, ev, mu, order);
+      mp cut; mp_ldexp(&cut, &mu[0], -tol_log2);
+      int k = 0;
+      while (k < (int)m && mp_cmp(&mu[k], &cut) > 0) ++k;
+      if (k == 0) k = 1;
+      ch[c] = k;
+      U[c] = (cmp_t*)malloc(sizeof(cmp_t) * Ld * k);
+      V[c] = (cmp_t*)malloc(sizeof(cmp_t) * Rd * k);
+      L[c] = (mp*)malloc(sizeof(mp) * k);
+      for (int q = 0; q < k; ++q) {
+        mp_sqrt(&L[c][q], &mu[q]);
+        const cmp_t* e = ev + (size_t)order[q] * m;     /* eigenvector of mu[q] */
+        if (left) {                                       /* u = e; v[r] = sum_a conj(u[a]) Psi[a][r] / lambda */
+          for (size_t a = 0; a < Ld; ++a) U[c][a + Ld * q] = e[a];
+          for (size_t r = 0; r < Rd; ++r) {
+            cmp_t s, t; cmp_zero(&s);
+            for (size_t a = 0; a < Ld; ++a) { cmp_mul_conj(&t, &e[a], &h->psi[a * Rd + r]); cmp_add(&s, &s, &t); }
+            mp_div(&s.re, &s.re, &L[c][q]); mp_div(&s.im, &s.im, &L[c][q]);
+            V[c][r + Rd * q] = s;
+          }
+        } else {                                          /* v = conj(e); u[a] = sum_r Psi[a][r] e[r] / lambda */
+          for (size_t r = 0; r < Rd; ++r) cmp_conj(&V[c][r + Rd * q], &e[r]);
+          for (size_t a = 0; a < Ld; ++a) {
+            cmp_t s, t; cmp_zero(&s);
+            for (size_t r = 0; r < Rd; ++r) { cmp_mul(&t, &h->psi[a * Rd + r], &e[r]); cmp_add(&s, &s, &t); }
+            mp_div(&s.re, &s.re, &L[c][q]); mp_div(&s.im, &s.im, &L[c][q]);
+            U[c][a + Ld * q] = s;
+          }
+        }
+      }
+    }
+    free(g); free(ev); free(mu); free(order);
+  }
+  if (!rc) {
+    size_t go = 0, lo = 0;
+    for (int l = 0; l < n; ++l) {
+      const int ca = ch[l], cb = ch[l + 1];
+      const size_t La = (size_t)1 << l, Rb = (size_t)1 << (n - l - 1);
+      for (int s = 0; s < 2; ++s) for (int al = 0; al < ca; ++al) for (int be = 0; be < cb; ++be) {
+        cmp_t acc, t, u; cmp_zero(&acc);
+        for (size_t a = 0; a < La; ++a) for (size_t r = 0; r < Rb; ++r) {
+          /* conj(u_alpha[a]) conj(v_beta[r]) psi[(a, s, r)] */
+          cmp_mul(&u, &U[l][a + La * al], &V[l + 1][r + Rb * be]);
+          cmp_mul_conj(&t, &u, &h->psi[(a * 2 + s) * Rb + r]);
+          cmp_add(&acc, &acc, &t);
+        }
+        mp den; mp_mul(&den, &L[l][al], &L[l + 1][be]);
+        mp_div(&acc.re, &acc.re, &den); mp_div(&acc.im, &acc.im, &den);
+        const size_t e = go + ((size_t)s * ca + al) * cb + be;
+        mp_to_words(&acc.re, gam + (e * 2 + 0) * w, w);
+        mp_to_words(&acc.im, gam + (e * 2 + 1) * w, w);
+      }
+      go += (size_t)2 * ca * cb;
+      if (l < n - 1) {
+        chi[l] = cb;
+        for (int be = 0; be < cb; ++be) mp_to_words(&L[l + 1][be], lam + (lo + be) * w, w);
+        lo += cb;
+      }
+    }
+  }
+  for (int c = 0; c <= n; ++c) { free(U[c]); free(V[c]); free(L[c]); }
+  free(U); free(V); free(L); free(ch);
+  return rc;
+}

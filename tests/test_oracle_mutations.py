@@ -89,6 +89,13 @@ MUTATIONS = [
     ("non-Hermitian input accepted", "eigh.c",
      "free(a); free(v); free(vs); free(lam); free(order); return 1;", "(void)0;",
      [P.test_eigh_rejects_non_hermitian]),
+    ("Vidal tensors divided by the right weight only", "statevec.c",
+     "mp den; mp_mul(&den, &L[l][al], &L[l + 1][be]);", "mp den = L[l + 1][be];",
+     [P.test_statevector_vidal_form_reproduces_the_state]),
+    ("Vidal right Schmidt vectors without the conjugate", "statevec.c",
+     "for (size_t r = 0; r < Rd; ++r) cmp_conj(&V[c][r + Rd * q], &e[r]);",
+     "for (size_t r = 0; r < Rd; ++r) V[c][r + Rd * q] = e[r];",
+     [P.test_statevector_vidal_form_reproduces_the_state]),
     ("conjugate-transpose product without the conjugate", "products.c",
      "if (opA) cmp_mul_conj(&t,", "if (opA) cmp_mul(&t,",
      [P.test_matmul_matches_exact_rationals]),

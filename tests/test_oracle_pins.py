@@ -486,3 +486,68 @@ def test_statevector_gates_on_basis_states():
         else:
             want = {x: (Fraction(1), Fraction(0))}
         assert got == want, x
+
+
+def _site_views(n, chi, g, lam):
+    """(a, b, Gamma words, left weights, right weights) of every site of a packed Vidal MPS."""
+    dims = [1] + [int(c) for c in chi] + [1]
+    out, go, lo = [], 0, 0
+    for l in range(n):
+        a, b = dims[l], dims[l + 1]
+        left = lam[lo - a:lo] if l > 0 else None
+        right = lam[lo:lo + b] if l < n - 1 else None
+        out.append((a, b, g[go:go + 2 * a * b], left, right))
+        go += 2 * a * b
+        if l < n - 1:
+            lo += b
+    return out
+
+
+def test_statevector_vidal_form_reproduces_the_state():
+    """The oracle's Vidal MPS of an entangled 6-qubit state (exactly unitary dyadic gates on a brickwork of
+    bonds): its amplitudes equal the state vector's to 2^-300, every site meets both canonical conditions
+    to 2^-290, the squared weights at each bond are the Schmidt values of the state at that cut, and they
+    sum to 1.  Three routes (state vector, MPS contraction, Schmidt values) must agree."""
+    n = 6
+    sv = oracle.Statevector(n)
+    U4 = dyadic_unitary(4, layers=7, seed=5)
+    G = to_words_matrix([[U4[r][c] for r in range(4)] for c in range(4)], 4)
+    for s in (0, 2, 4, 1, 3, 0, 2):
+        sv.apply2(s, G)
+    chi, g, lam = sv.vidal()
+    assert list(chi) == [2, 4, 8, 4, 2]
+    amps = oracle.mps_amplitudes(n, chi, g, lam, oracle.WORDS)
+    ref = sv.amplitudes()
+    for x in range(1 << n):
+        for p in range(2):
+            assert abs(fr(amps[x, p]) - fr(ref[x, p])) <= Fraction(1, 2**300)
+    for a, b, gl, left, right in _site_views(n, chi, g, lam):
+        assert oracle.mps_site_defect(a, b, gl, left, None, oracle.WORDS, 0) <= 2.0**-290
+        assert oracle.mps_site_defect(a, b, gl, None, right, oracle.WORDS, 1) <= 2.0**-290
+    lo = 0
+    for l, c in enumerate(chi):
+        s2 = sv.schmidt2(l + 1)
+        tot = Fraction(0)
+        for k in range(c):
+            lk2 = fr(lam[lo + k]) ** 2
+            tot += lk2
+            assert abs(lk2 - fr(s2[k])) <= Fraction(1, 2**290)
+        assert abs(tot - 1) <= Fraction(1, 2**290)
+        lo += c
+
+
+def test_statevector_vidal_form_of_ghz_and_product_states():
+    """(|0000> + |1111>) / 2, a GHZ state scaled by 1/sqrt(2), has bond dimension 2 and Schmidt weights
+    (1/2, 1/2) at every bond; |0000> has bond dimension 1 and weight 1."""
+    n = 4
+    sv = oracle.Statevector(n)
+    amps = np.zeros((1 << n, 2, 1)); amps[0, 0, 0] = 0.5; amps[(1 << n) - 1, 0, 0] = 0.5
+    sv.set(amps)
+    chi, g, lam = sv.vidal()
+    assert list(chi) == [2, 2, 2]
+    for k in range(6):
+        assert abs(fr(lam[k]) - Fraction(1, 2)) <= Fraction(1, 2**300)
+    sv0 = oracle.Statevector(n)
+    chi0, g0, lam0 = sv0.vidal()
+    assert list(chi0) == [1, 1, 1]
+    assert all(fr(lam0[k]) == 1 for k in range(3))
