@@ -240,19 +240,21 @@ zkq_status zkq_mps_apply2q(zkq_ctx* ctx, zkq_mps* mps, int site, const double* G
  * zkq_mw_gemm: batched multi-word complex products C_i = op(A_i) B_i, the dense products of the refinement
  * step (A X, X^H X, X^H (A X), X E) that recover the precision of the FP64 eigenpairs (Section 2, ZKCM_CUS
  * paragraph).  Rows of op(A) and columns of B are scaled by powers of two and truncated to integers.
- * Method 1 (Chinese-remainder form, Ozaki-Uchino-Imamura): residues modulo ~60 pairwise coprime moduli
- * <= 256, one exact fp16 tensor-core product per modulus (fp32 accumulation exact below 2^24), exact
- * reconstruction by the CRT.  Method 2 (digit form, Ozaki-Ogita-Oishi-Rump 2012): 8-bit (7-bit when
- * k > 512) balanced digits, one exact product per kept digit pair, exact recombination.  Method 0 computes
- * the same products directly in multi-word arithmetic on the FP64 pipe.
+ * Method 1 (Chinese-remainder form, Ozaki-Uchino-Imamura): each scaled integer is split in two halves,
+ * the halves are reduced modulo r pairwise coprime moduli <= 256 (r is 17-18 for double-double and 32-33
+ * for quad-double accuracy), three exact fp16 tensor-core products are formed per modulus (high x high,
+ * high x low, low x high; fp32 accumulation is exact below 2^24), and the CRT reconstructs the exact
+ * integer results; k > 512 takes the digit form instead.  Method 2 (digit form, Ozaki-Ogita-Oishi-Rump
+ * 2012): 8-bit (7-bit when k > 512) balanced digits, one exact product per kept digit pair, exact
+ * recombination.  Method 0 computes the same products directly in multi-word arithmetic on the FP64 pipe.
  *   count (>= 0)   number of products; m, n, k, opA (host, int32[count])
  *   opA[i]         0: A_i is m x k (column-major, ld m);  1: A_i is stored k x m (ld k), op(A) = A^H
  *   A, B, C        device arrays; product i uses element offsets a_off[i], b_off[i], c_off[i] (host int64)
  *   wa, wb, wc     words per real of A, B, C (1, 2 or 4); B_i is k x n (ld k), C_i is m x n (ld m)
- *   p_bits         requested accuracy: |C - op(A) B| <= k 2^-p_bits 2^(e_row + f_col) per element, where
- *                  2^e_row <= 8 max|row of op(A)| and 2^f_col <= 8 max|column of B| are the power-of-two
- *                  scales of the split (methods 1 and 2)
- *                  (method 1; method 0 rounds in wc-word arithmetic); 1 <= p_bits <= 252
+ *   p_bits         requested accuracy of methods 1 and 2: |C - op(A) B| <= k 2^-p_bits 2^(e_row + f_col) per
+ *                  element, where 2^e_row <= 8 max|row of op(A)| and 2^f_col <= 8 max|column of B| are the
+ *                  power-of-two scales of the split; method 0 rounds in wc-word arithmetic instead.
+ *                  1 <= p_bits <= 252
  * Constraints: k <= 2048.  C must not overlap A or B.
  * Errors: ZKQ_EINVAL, ZKQ_ENOMEM, ZKQ_ECUDA.
  */
@@ -290,7 +292,8 @@ zkq_status zkq_mw_op(int op, int words, int64_t count, const double* a, const do
 /*
  * Launch profiler (tracing): when enabled, every kernel launch of the library is bracketed by CUDA events
  * on its launching stream and device time is accumulated per kernel class (jacobi, rqi, ozaki_scale,
- * ozaki_slice, ozaki_gemm, ozaki_combine, oa_elementwise, mps, other).  The paper reports only wall
+ * ozaki_slice, ozaki_gemm, ozaki_combine, oa_elementwise, mps, other, jacobi_cluster: the refinement's
+ * cluster eigensolves).  The paper reports only wall
  * times; this breaks them down for the roofline of each kernel.  Process-wide.
  *   zkq_profile_classes()        number of classes
  *   zkq_profile_class_name(c)    name of class c (never NULL)
@@ -298,8 +301,8 @@ zkq_status zkq_mw_op(int op, int words, int64_t count, const double* a, const do
  *   zkq_profile_read(ms, n, w, k) waits for the recorded launches, writes per-class milliseconds, launch
  *                                counts and algorithmic work for the first k classes, then clears the
  *                                record.  Work: ozaki_gemm counts 2 m (2n) (2k) flops per exact slice
- *                                product (at launch); jacobi counts 48 n flops per applied rotation
- *                                (on the device); 0 where not counted
+ *                                product (at launch); jacobi and jacobi_cluster count 48 n flops per
+ *                                applied rotation (on the device); 0 where not counted
  * Errors: ZKQ_EINVAL (null arrays, k < 1), ZKQ_ECUDA.
  */
 int zkq_profile_classes(void);
