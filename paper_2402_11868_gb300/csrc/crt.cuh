@@ -6,8 +6,8 @@
 // Pairwise coprime moduli <= 256 multiply to at most lcm(1..256) ~ 2^369, less than a quad-double product
 // needs, so each scaled integer is split in halves, A' = A_h 2^s + A_l, and the three products
 // A_h B_h, A_h B_l, A_l B_h (each below K 2^(q-2)) are reconstructed by the CRT; A_l B_l is below the
-// requested accuracy and dropped.  3 r ~ 93 exact products per quad-double product instead of ~500 digit
-// pairs.
+// requested accuracy and dropped.  3 r = 96-99 exact products (r = 32-33) per quad-double product instead
+// of ~500 digit pairs.
 #pragma once
 #include <cstdint>
 
