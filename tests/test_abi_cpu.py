@@ -104,3 +104,25 @@ def test_host_multiword_ops_within_published_bounds(zkq, words, op):
         else:
             scale = abs(ref)
         assert abs(got - ref) <= BOUND[words][op] * scale, (op, i)
+
+
+def test_empty_batches_return_ok_before_any_device_work(zkq):
+    """Empty batches are valid and return ZKQ_OK at once: no CUDA call, no use of the context beyond the
+    null check (a zeroed stand-in handle is passed; the machine has no GPU, so any CUDA call would fail)."""
+    L = zkq.lib()
+    buf = ctypes.create_string_buffer(1 << 16)
+    ctx = ctypes.addressof(buf)
+    one = (ctypes.c_int32 * 1)(8)
+    off = (ctypes.c_int64 * 1)(0)
+    assert L.zkq_eigh_batched(ctx, 0, None, None, None, 4, None, None, None, None) == zkq.ZKQ_OK
+    assert L.zkq_rqi_refine(ctx, 0, None, None, None, 4, None, None, 4, 1, None, None, None, None, None) == zkq.ZKQ_OK
+    assert L.zkq_mw_gemm(ctx, 0, None, None, None, None, None, None, 4, None, None, 4, None, None, 4, 200, 1,
+                         None) == zkq.ZKQ_OK
+    nb = ctypes.c_size_t(7)
+    assert L.zkq_workspace_size(ctx, 0, None, 4, 4, 1, ctypes.byref(nb)) == zkq.ZKQ_OK and nb.value == 0
+    assert L.zkq_eigh_batched_noalloc(0, None, None, None, 4, None, None, None, None) == zkq.ZKQ_OK
+    assert L.zkq_mw_op(0, 4, 0, None, None, None, 1, None) == zkq.ZKQ_OK
+    # argument errors still come first
+    assert L.zkq_eigh_batched(ctx, 0, None, None, None, 3, None, None, None, None) == zkq.ZKQ_EINVAL
+    assert L.zkq_rqi_refine(ctx, 0, None, None, None, 4, None, None, 3, 1, None, None, None, None, None) == zkq.ZKQ_EINVAL
+    assert L.zkq_eigh_batched(ctx, -1, one, off, None, 4, None, None, None, None) == zkq.ZKQ_EINVAL
