@@ -37,7 +37,7 @@ sys.path.insert(0, ROOT)
 
 import numpy as np
 
-METRIC = "quad-double refined eigenpairs/sec (err <=2^-200||A||), p50/p99 latency vs plain RQI path"
+METRIC = "quad-double refined eigenpairs/sec (err ≤2^-200‖A‖), p50/p99 latency vs plain RQI path"
 # FP64 peak of one GB300 from its unit counts and clock: 152 SMs x 2 FP64 operations (FMA, add or multiply)
 # per clock per SM x 2.07 GHz = 0.629 T FP64 instructions/s, 1.259 TFLOP/s with an FMA as two flops (the
 # nominal 1.25 TFLOP/s).  The roofline fractions use this figure.
