@@ -13,6 +13,10 @@ def pytest_configure(config):
     if not config.option.basetemp:
         os.makedirs(os.path.join(ROOT, "_build"), exist_ok=True)
         config.option.basetemp = os.path.join(ROOT, "_build", "pytest_tmp")
+    # and so do the compilers' scratch files of the builds the tests run
+    tmp = os.path.join(ROOT, "_build", "tmp")
+    os.makedirs(tmp, exist_ok=True)
+    os.environ["TMPDIR"] = tmp
     config.addinivalue_line("markers", "gpu: needs a GB300 (sm_103a) GPU and the CUDA library")
     config.addinivalue_line("markers", "slow: long-running CPU test")
 

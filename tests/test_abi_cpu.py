@@ -8,6 +8,8 @@ import os
 import re
 import subprocess
 
+from fractions import Fraction
+
 import numpy as np
 import pytest
 
@@ -80,11 +82,32 @@ def random_mw(rng, count, words, spread=30):
     return x
 
 
-@pytest.mark.parametrize("words", [2, 4])
-@pytest.mark.parametrize("op", [0, 1, 2, 3, 4])
-def test_host_multiword_ops_within_published_bounds(zkq, words, op):
+def check_host_op(mw_op, words, op):
+    """Raise AssertionError unless the multi-word op (run through mw_op(op, words, count, a, b, out) on host
+    arrays) meets its error bound on 400 random operands.  Real ops are compared with the oracle against
+    the published bounds; complex multiply and divide (ops 5 and 6) with exact rationals, in norm, against
+    bounds that follow from the real ones: |error| <= bound |a| |b| for the product and bound |a| / |b| for
+    the quotient."""
     rng = np.random.default_rng(100 * words + op)
     count = 400
+    if op >= 5:
+        a = random_mw(rng, 2 * count, words).reshape(count, 2, words)
+        b = random_mw(rng, 2 * count, words).reshape(count, 2, words)
+        out = np.zeros_like(a)
+        mw_op(op, words, count, a, b, out)
+        for i in range(count):
+            ar, ai, br, bi = fr(a[i, 0]), fr(a[i, 1]), fr(b[i, 0]), fr(b[i, 1])
+            if op == 5:
+                want = (ar * br - ai * bi, ar * bi + ai * br)
+                scale2 = (ar * ar + ai * ai) * (br * br + bi * bi)
+            else:
+                d = br * br + bi * bi
+                want = ((ar * br + ai * bi) / d, (ai * br - ar * bi) / d)
+                scale2 = (ar * ar + ai * ai) / d
+            err2 = (fr(out[i, 0]) - want[0]) ** 2 + (fr(out[i, 1]) - want[1]) ** 2
+            bound = {2: 2.0**-100, 4: 2.0**-203}[words]
+            assert err2 <= Fraction(bound) ** 2 * scale2, (op, i)
+        return
     a = random_mw(rng, count, words)
     b = random_mw(rng, count, words)
     if op == 4:
@@ -93,7 +116,7 @@ def test_host_multiword_ops_within_published_bounds(zkq, words, op):
         k = count // 3
         b[:k, 0] = -a[:k, 0] if op == 0 else a[:k, 0]
     out = np.zeros_like(a)
-    zkq.zkq_mw_op(op, words, count, a, b, out, on_device=False)
+    mw_op(op, words, count, a, b, out)
     name = {0: "add", 1: "sub", 2: "mul", 3: "div", 4: "sqrt"}[op]
     for i in range(count):
         ref = fr(oracle.scalar(name, a[i], b[i]))
@@ -104,6 +127,12 @@ def test_host_multiword_ops_within_published_bounds(zkq, words, op):
         else:
             scale = abs(ref)
         assert abs(got - ref) <= BOUND[words][op] * scale, (op, i)
+
+
+@pytest.mark.parametrize("words", [2, 4])
+@pytest.mark.parametrize("op", [0, 1, 2, 3, 4, 5, 6])
+def test_host_multiword_ops_within_published_bounds(zkq, words, op):
+    check_host_op(lambda *args: zkq.zkq_mw_op(*args, on_device=False), words, op)
 
 
 def test_empty_batches_return_ok_before_any_device_work(zkq):
