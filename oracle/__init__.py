@@ -10,7 +10,9 @@ Plain, slow, independent CPU implementation of what the accurate-eigensolve path
   amplitudes of a Vidal MPS (Section 1: MPS = nested Schmidt decomposition);
 * ``mps_site_defect``: the Vidal canonical (weighted orthonormality) conditions of one MPS site, a
   property of every exact gate update that holds at any qubit count;
-* ``Statevector.vidal``: the Vidal MPS of a state from its Schmidt decompositions at every cut.
+* ``Statevector.vidal``: the Vidal MPS of a state from its Schmidt decompositions at every cut;
+* ``Statevector.expect1`` and ``mps_expect1``: one-qubit expectation values, from the state vector by
+  definition and from a canonical MPS through its local tensor and Schmidt weights.
 
 Only ``tests/``, ``__graft_entry__.smoke()`` and ``bench.py``'s CPU-baseline leg may import this
 package.  It shares no code with the CUDA path; both receive their inputs from ``workloads``.
@@ -90,6 +92,10 @@ def load_library(path: str):
     L.oracle_sv_schmidt2.argtypes = [P, I, P, I]
     L.oracle_mps_amplitudes.restype = I
     L.oracle_mps_amplitudes.argtypes = [I, P, P, P, I, P, I]
+    L.oracle_sv_expect1.restype = I
+    L.oracle_sv_expect1.argtypes = [P, I, P, I, P, I]
+    L.oracle_mps_expect1.restype = I
+    L.oracle_mps_expect1.argtypes = [I, P, P, P, I, I, P, I, P, I]
     L.oracle_sv_vidal.restype = I
     L.oracle_sv_vidal.argtypes = [P, I, P, P, P, I]
     L.oracle_mps_site_defect.restype = I
@@ -196,6 +202,14 @@ class Statevector:
         _load().oracle_sv_norm2(self._h, out.ctypes.data, w)
         return out
 
+    def expect1(self, site, O, w=WORDS):
+        """<psi| O_site |psi> for a 2x2 operator O given as words (4, 2, wo), row-major: (re words, im words)."""
+        O = _c(O)
+        out = np.zeros((2, w))
+        if _load().oracle_sv_expect1(self._h, site, O.ctypes.data, O.shape[-1], out.ctypes.data, w):
+            raise ValueError("bad site")
+        return out
+
     def vidal(self, tol_log2=200, w=WORDS):
         """Vidal MPS of the state (chi, gammas (elements, 2, w), lambdas (values, w)) in the layout of
         mps_amplitudes, from the Schmidt decomposition at every cut; Schmidt values with lambda^2 at or below
@@ -247,6 +261,17 @@ def mps_site_defect(a, b, gamma, lam_left, lam_right, w, side):
     if rc:
         raise ValueError("bad arguments to oracle_mps_site_defect")
     return out.value
+
+
+def mps_expect1(n, chi, gammas, lambdas, w, site, O, w_out=WORDS):
+    """<O_site> of a Vidal MPS in canonical form from site's tensor and its two weight vectors."""
+    chi = np.ascontiguousarray(chi, dtype=np.int32)
+    g = _c(gammas); l = _c(lambdas) if len(lambdas) else np.zeros(1); O = _c(O)
+    out = np.zeros((2, w_out))
+    if _load().oracle_mps_expect1(n, chi.ctypes.data, g.ctypes.data, l.ctypes.data, w, site, O.ctypes.data,
+                                  O.shape[-1], out.ctypes.data, w_out):
+        raise ValueError("bad arguments to oracle_mps_expect1")
+    return out
 
 
 def to_fraction(words) -> Fraction:

@@ -345,3 +345,74 @@ int oracle_sv_vidal(void* hv, int tol_log2, int* chi, double* gam, double* lam, 
   free(U); free(V); free(L); free(ch);
   return rc;
 }
+
+/* Expectation value of a one-qubit operator O (2x2 row-major complex, w words) on `site`:
+ * <psi| O_site |psi> = sum over x of conj(psi_x) (O_site psi)_x, the plain definition.  out: re, im words. */
+int oracle_sv_expect1(void* hv, int site, const double* O, int w, double* out, int w_out) {
+  sv_t* h = (sv_t*)hv;
+  if (site < 0 || site >= h->n) return 1;
+  cmp_t g[4]; load_mat(g, O, 2, w);
+  size_t bit = (size_t)1 << (h->n - 1 - site);
+  cmp_t acc; cmp_zero(&acc);
+  for (size_t x = 0; x < h->dim; ++x) {
+    if (x & bit) continue;
+    cmp_t a0 = h->psi[x], a1 = h->psi[x | bit], t, r0, r1;
+    cmp_mul(&r0, &g[0], &a0); cmp_mul(&t, &g[1], &a1); cmp_add(&r0, &r0, &t);
+    cmp_mul(&r1, &g[2], &a0); cmp_mul(&t, &g[3], &a1); cmp_add(&r1, &r1, &t);
+    cmp_mul_conj(&t, &a0, &r0); cmp_add(&acc, &acc, &t);
+    cmp_mul_conj(&t, &a1, &r1); cmp_add(&acc, &acc, &t);
+  }
+  mp_to_words(&acc.re, out, w_out);
+  mp_to_words(&acc.im, out + w_out, w_out);
+  return 0;
+}
+
+/* The same expectation value from a Vidal MPS in canonical form (the layout of oracle_mps_amplitudes):
+ * the environments left of bond l-1 and right of bond l reduce to the squared Schmidt weights, so
+ *   <O_l> = sum over alpha, beta, s, s' of lam[l-1]_alpha^2 lam[l]_beta^2 conj(Gamma[l]^s_{alpha beta})
+ *           O_{s s'} Gamma[l]^{s'}_{alpha beta}.
+ * Only site l's tensor and its two weight vectors are read.  out: re, im words. */
+int oracle_mps_expect1(int n, const int* chi, const double* gam, const double* lam, int w, int site,
+                       const double* O, int wo, double* out, int w_out) {
+  if (n < 2 || site < 0 || site >= n) return 1;
+  size_t goff = 0, loff = 0;
+  for (int l = 0; l < site; ++l) {
+    const int cl = l == 0 ? 1 : chi[l - 1], cr = chi[l];
+    goff += (size_t)2 * cl * cr;
+    if (l < site - 1) loff += cr;                     /* lam[site-1] starts after lam[0..site-2] */
+  }
+  const int a = site == 0 ? 1 : chi[site - 1], b = site == n - 1 ? 1 : chi[site];
+  cmp_t o[4]; load_mat(o, O, 2, wo);
+  mp* wl = (mp*)malloc(sizeof(mp) * a);
+  mp* wr = (mp*)malloc(sizeof(mp) * b);
+  for (int k = 0; k < a; ++k) {
+    if (site == 0) mp_from_double(&wl[k], 1.0);
+    else { mp t; mp_from_words(&t, lam + (loff + k) * w, w); mp_mul(&wl[k], &t, &t); }
+  }
+  const size_t roff = site == 0 ? 0 : loff + a;       /* lam[site] follows lam[site-1] */
+  for (int k = 0; k < b; ++k) {
+    if (site == n - 1) mp_from_double(&wr[k], 1.0);
+    else { mp t; mp_from_words(&t, lam + (roff + k) * w, w); mp_mul(&wr[k], &t, &t); }
+  }
+  cmp_t acc; cmp_zero(&acc);
+  for (int al = 0; al < a; ++al) for (int be = 0; be < b; ++be) {
+    cmp_t gs[2];
+    for (int s = 0; s < 2; ++s) {
+      const size_t e = goff + ((size_t)s * a + al) * b + be;
+      mp_from_words(&gs[s].re, gam + (e * 2 + 0) * w, w);
+      mp_from_words(&gs[s].im, gam + (e * 2 + 1) * w, w);
+    }
+    mp wt; mp_mul(&wt, &wl[al], &wr[be]);
+    for (int s = 0; s < 2; ++s) {
+      cmp_t og, t, u; cmp_zero(&og);                   /* (O Gamma)^s = sum over s' of O_{s s'} Gamma^{s'} */
+      for (int s2 = 0; s2 < 2; ++s2) { cmp_mul(&t, &o[s * 2 + s2], &gs[s2]); cmp_add(&og, &og, &t); }
+      cmp_mul_conj(&u, &gs[s], &og);
+      cmp_scale(&u, &u, &wt);
+      cmp_add(&acc, &acc, &u);
+    }
+  }
+  mp_to_words(&acc.re, out, w_out);
+  mp_to_words(&acc.im, out + w_out, w_out);
+  free(wl); free(wr);
+  return 0;
+}

@@ -96,6 +96,13 @@ MUTATIONS = [
      "for (size_t r = 0; r < Rd; ++r) cmp_conj(&V[c][r + Rd * q], &e[r]);",
      "for (size_t r = 0; r < Rd; ++r) V[c][r + Rd * q] = e[r];",
      [P.test_statevector_vidal_form_reproduces_the_state]),
+    ("MPS expectation with the left weights not squared", "statevec.c",
+     "else { mp t; mp_from_words(&t, lam + (loff + k) * w, w); mp_mul(&wl[k], &t, &t); }",
+     "else { mp_from_words(&wl[k], lam + (loff + k) * w, w); }",
+     [P.test_one_qubit_expectation_values_two_ways]),
+    ("state-vector expectation without the conjugate", "statevec.c",
+     "cmp_mul_conj(&t, &a0, &r0); cmp_add(&acc, &acc, &t);", "cmp_mul(&t, &a0, &r0); cmp_add(&acc, &acc, &t);",
+     [P.test_one_qubit_expectation_values_two_ways]),
     ("conjugate-transpose product without the conjugate", "products.c",
      "if (opA) cmp_mul_conj(&t,", "if (opA) cmp_mul(&t,",
      [P.test_matmul_matches_exact_rationals]),

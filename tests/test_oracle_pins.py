@@ -551,3 +551,45 @@ def test_statevector_vidal_form_of_ghz_and_product_states():
     chi0, g0, lam0 = sv0.vidal()
     assert list(chi0) == [1, 1, 1]
     assert all(fr(lam0[k]) == 1 for k in range(3))
+
+
+def test_one_qubit_expectation_values_two_ways():
+    """One-qubit expectation values: by definition from the state vector, and from the canonical Vidal MPS
+    through one tensor and its Schmidt weights (Section 1: the MPS is a nested Schmidt decomposition, so the
+    environments of a site reduce to its weights).  They agree to 2^-290 on an entangled complex state for
+    Pauli X, Y, Z and a general complex 2x2 operator, Hermitian operators give real values, the identity
+    gives the norm 1, and |0..0> and a GHZ state give their closed forms."""
+    n = 6
+    sv = oracle.Statevector(n)
+    U4 = dyadic_unitary(4, layers=7, seed=5)
+    G = to_words_matrix([[U4[r][c] for r in range(4)] for c in range(4)], 4)
+    for s in (0, 2, 4, 1, 3, 0, 2):
+        sv.apply2(s, G)
+    chi, g, lam = sv.vidal()
+    one, zero, half = Fraction(1), Fraction(0), Fraction(1, 2)
+    ops = {"I": [[(one, zero), (zero, zero)], [(zero, zero), (one, zero)]],
+           "X": [[(zero, zero), (one, zero)], [(one, zero), (zero, zero)]],
+           "Y": [[(zero, zero), (zero, -one)], [(zero, one), (zero, zero)]],
+           "Z": [[(one, zero), (zero, zero)], [(zero, zero), (-one, zero)]],
+           "M": [[(half, Fraction(3, 4)), (Fraction(-1, 8), zero)], [(zero, Fraction(5, 16)), (Fraction(7, 2), -half)]]}
+    words_of = {k: to_words_matrix([[v[r][c] for r in range(2)] for c in range(2)], 2) for k, v in ops.items()}
+    for site in range(n):
+        for name, O in words_of.items():
+            a = sv.expect1(site, O)
+            b = oracle.mps_expect1(n, chi, g, lam, oracle.WORDS, site, O)
+            for part in range(2):
+                assert abs(fr(a[part]) - fr(b[part])) <= Fraction(1, 2**290), (site, name, part)
+            if name != "M":
+                assert abs(fr(a[1])) <= Fraction(1, 2**300), (site, name)
+            if name == "I":
+                assert abs(fr(a[0]) - 1) <= Fraction(1, 2**300)
+    z = words_of["Z"]
+    sv0 = oracle.Statevector(n)
+    for site in range(n):
+        assert fr(sv0.expect1(site, z)[0]) == 1
+    ghz = oracle.Statevector(4)
+    amps = np.zeros((16, 2, 1)); amps[0, 0, 0] = 0.5; amps[15, 0, 0] = 0.5
+    ghz.set(amps)
+    for site in range(4):
+        assert fr(ghz.expect1(site, z)[0]) == 0 and fr(ghz.expect1(site, words_of["X"])[0]) == 0
+        assert fr(ghz.expect1(site, words_of["I"])[0]) == Fraction(1, 2)
