@@ -62,7 +62,8 @@ MUTATIONS = [
      "cmp_mul(&t, &g[r * 4 + c], &in[c]);", "cmp_mul(&t, &g[c * 4 + r], &in[c]);",
      [P.test_statevector_gates_on_basis_states]),
     ("one-qubit gate on the mirrored site", "statevec.c",
-     "size_t bit = (size_t)1 << (h->n - 1 - site);", "size_t bit = (size_t)1 << site;",
+     "cmp_t g[4]; load_mat(g, U, 2, w);\n  size_t bit = (size_t)1 << (h->n - 1 - site);",
+     "cmp_t g[4]; load_mat(g, U, 2, w);\n  size_t bit = (size_t)1 << site;",
      [P.test_statevector_gates_on_basis_states]),
     ("controlled gate ignores the control value", "statevec.c",
      "ok = bit == ctrl[l];", "ok = 1;",
