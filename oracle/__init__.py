@@ -11,6 +11,7 @@ Plain, slow, independent CPU implementation of what the accurate-eigensolve path
 * ``mps_site_defect``: the Vidal canonical (weighted orthonormality) conditions of one MPS site, a
   property of every exact gate update that holds at any qubit count;
 * ``Statevector.vidal``: the Vidal MPS of a state from its Schmidt decompositions at every cut;
+* ``svd``: one-sided Jacobi singular value decomposition at 320 bits (the SVD variant of the gate update);
 * ``Statevector.expect1`` and ``mps_expect1``: one-qubit expectation values, from the state vector by
   definition and from a canonical MPS through its local tensor and Schmidt weights.
 
@@ -29,7 +30,7 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SO = os.path.join(_HERE, "_oracle.so")
-_SRC = ["mp.c", "eigh.c", "statevec.c", "products.c"]
+_SRC = ["mp.c", "eigh.c", "statevec.c", "products.c", "svd.c"]
 _lib = None
 _lock = threading.Lock()
 
@@ -92,6 +93,8 @@ def load_library(path: str):
     L.oracle_sv_schmidt2.argtypes = [P, I, P, I]
     L.oracle_mps_amplitudes.restype = I
     L.oracle_mps_amplitudes.argtypes = [I, P, P, P, I, P, I]
+    L.oracle_svd.restype = I
+    L.oracle_svd.argtypes = [I, I, P, I, I, P, P, P]
     L.oracle_sv_expect1.restype = I
     L.oracle_sv_expect1.argtypes = [P, I, P, I, P, I]
     L.oracle_mps_expect1.restype = I
@@ -261,6 +264,18 @@ def mps_site_defect(a, b, gamma, lam_left, lam_right, w, side):
     if rc:
         raise ValueError("bad arguments to oracle_mps_site_defect")
     return out.value
+
+
+def svd(M, m, n, w_out=WORDS):
+    """Singular value decomposition of the complex m x n matrix given as words (m*n, 2, w), column-major,
+    by one-sided Jacobi at 320 bits.  Returns (sigma (n, w_out) descending, U (m*n, 2, w_out),
+    V (n*n, 2, w_out)) with M = U diag(sigma) V^H."""
+    M = _c(M)
+    sig = np.zeros((n, w_out)); U = np.zeros((m * n, 2, w_out)); V = np.zeros((n * n, 2, w_out))
+    rc = _load().oracle_svd(m, n, M.ctypes.data, M.shape[-1], w_out, sig.ctypes.data, U.ctypes.data, V.ctypes.data)
+    if rc:
+        raise RuntimeError(f"oracle_svd failed ({rc})")
+    return sig, U, V
 
 
 def mps_expect1(n, chi, gammas, lambdas, w, site, O, w_out=WORDS):

@@ -104,6 +104,13 @@ MUTATIONS = [
     ("state-vector expectation without the conjugate", "statevec.c",
      "cmp_mul_conj(&t, &a0, &r0); cmp_add(&acc, &acc, &t);", "cmp_mul(&t, &a0, &r0); cmp_add(&acc, &acc, &t);",
      [P.test_one_qubit_expectation_values_two_ways]),
+    ("one-sided Jacobi inner product without the conjugate", "svd.c",
+     "cmp_mul_conj(&t, &a[IX(i, p, m)], &a[IX(i, q, m)]); cmp_add(&g, &g, &t);",
+     "cmp_mul(&t, &a[IX(i, p, m)], &a[IX(i, q, m)]); cmp_add(&g, &g, &t);",
+     [lambda: P.test_svd_of_exact_construction(5, 3, 3)]),
+    ("one-sided Jacobi rotations not accumulated in V", "svd.c",
+     "for (int pass = 0; pass < 2; ++pass) {", "for (int pass = 0; pass < 1; ++pass) {",
+     [lambda: P.test_svd_of_exact_construction(5, 3, 3)]),
     ("conjugate-transpose product without the conjugate", "products.c",
      "if (opA) cmp_mul_conj(&t,", "if (opA) cmp_mul(&t,",
      [P.test_matmul_matches_exact_rationals]),

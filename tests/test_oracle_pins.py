@@ -593,3 +593,66 @@ def test_one_qubit_expectation_values_two_ways():
     for site in range(4):
         assert fr(ghz.expect1(site, z)[0]) == 0 and fr(ghz.expect1(site, words_of["X"])[0]) == 0
         assert fr(ghz.expect1(site, words_of["I"])[0]) == Fraction(1, 2)
+
+
+def _cmat(words, rows, cols):
+    """Fractions (re, im) M[i][j] of column-major complex words (rows*cols, 2, w)."""
+    return [[(fr(words[i + j * rows, 0]), fr(words[i + j * rows, 1])) for j in range(cols)] for i in range(rows)]
+
+
+@pytest.mark.parametrize("m,n,seed", [(5, 3, 3), (4, 4, 4), (2, 4, 6)])
+def test_svd_of_exact_construction(m, n, seed):
+    """M = U0 diag(sigma) V0^H with exactly unitary dyadic U0 (m x m), V0 (n x n) and dyadic singular values
+    spanning 2^0..2^-120 (zeros beyond rank min(m, n)): the oracle's one-sided Jacobi returns the singular
+    values to 2^-300, orthonormal U (on the nonzero values) and V to 2^-300, and M = U diag(sigma) V^H to
+    2^-295; sigma^2 equal the eigenvalues of M^H M from the oracle's Hermitian eigensolver."""
+    U0 = dyadic_unitary(m, layers=3 * m, seed=seed)
+    V0 = dyadic_unitary(n, layers=3 * n, seed=seed + 50)
+    r = min(m, n)
+    sig = [Fraction(3, 2 ** (40 * k)) * (1 + Fraction(k, 4)) for k in range(r)]
+    M = [[(Fraction(0), Fraction(0)) for _ in range(n)] for _ in range(m)]
+    for i in range(m):
+        for j in range(n):
+            acc = (Fraction(0), Fraction(0))
+            for k in range(r):
+                acc = cadd(acc, cmul(U0[i][k], cmul((sig[k], Fraction(0)), cconj(V0[j][k]))))
+            M[i][j] = acc
+    Mw = to_words_matrix(M, 8)
+    assert exact_words_ok(M, Mw, 8)
+    s, U, V = oracle.svd(Mw, m, n)
+    want = sorted(sig, reverse=True) + [Fraction(0)] * (n - r)
+    for k in range(n):
+        assert abs(fr(s[k]) - want[k]) <= Fraction(1, 2**300), k
+    Uf, Vf = _cmat(U, m, n), _cmat(V, n, n)
+    for c in range(n):
+        for d in range(n):
+            vv = (Fraction(0), Fraction(0))
+            for i in range(n):
+                vv = cadd(vv, cmul(cconj(Vf[i][c]), Vf[i][d]))
+            assert abs(vv[0] - (1 if c == d else 0)) <= Fraction(1, 2**300) and abs(vv[1]) <= Fraction(1, 2**300)
+            if c < r and d < r:
+                uu = (Fraction(0), Fraction(0))
+                for i in range(m):
+                    uu = cadd(uu, cmul(cconj(Uf[i][c]), Uf[i][d]))
+                assert abs(uu[0] - (1 if c == d else 0)) <= Fraction(1, 2**300) and abs(uu[1]) <= Fraction(1, 2**300)
+    for i in range(m):
+        for j in range(n):
+            rec = (Fraction(0), Fraction(0))
+            for k in range(r):
+                rec = cadd(rec, cmul(Uf[i][k], cmul((fr(s[k]), Fraction(0)), cconj(Vf[j][k]))))
+            assert abs(rec[0] - M[i][j][0]) <= Fraction(1, 2**295) and abs(rec[1] - M[i][j][1]) <= Fraction(1, 2**295)
+    G = oracle.matmul(Mw, Mw, n, n, m, opA=1)          # M^H M
+    lam, _, _ = oracle.eigh(G, n)
+    for k in range(n):
+        assert abs(fr(lam[k]) - fr(s[k]) ** 2) <= Fraction(1, 2**295)
+
+
+def test_svd_of_rank_one_and_zero_matrices():
+    """u v^H has the single singular value |u| |v| (here 3 * 5 / 4 exactly); the zero matrix has none."""
+    u = [(Fraction(2), Fraction(1)), (Fraction(0), Fraction(-2)), (Fraction(0), Fraction(0))]      # |u| = 3
+    v = [(Fraction(3, 4), Fraction(0)), (Fraction(0), Fraction(1))]                                 # |v| = 5/4
+    M = [[cmul(u[i], cconj(v[j])) for j in range(2)] for i in range(3)]
+    s, _, _ = oracle.svd(to_words_matrix(M, 4), 3, 2)
+    assert abs(fr(s[0]) - Fraction(15, 4)) <= Fraction(1, 2**300) and abs(fr(s[1])) <= Fraction(1, 2**300)
+    s0, U0, _ = oracle.svd(np.zeros((6, 2, 1)), 3, 2)
+    assert fr(s0[0]) == 0 and fr(s0[1]) == 0 and not U0.any()
