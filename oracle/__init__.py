@@ -11,6 +11,8 @@ Plain, slow, independent CPU implementation of what the accurate-eigensolve path
 * ``mps_site_defect``: the Vidal canonical (weighted orthonormality) conditions of one MPS site, a
   property of every exact gate update that holds at any qubit count;
 * ``Statevector.vidal``: the Vidal MPS of a state from its Schmidt decompositions at every cut;
+* ``mps_two_products``: the Vidal MPS of a sum of two product states at any qubit count, such as the
+  state of the paper's footnote example;
 * ``svd``: one-sided Jacobi singular value decomposition at 320 bits (the SVD variant of the gate update);
 * ``Statevector.expect1`` and ``mps_expect1``: one-qubit expectation values, from the state vector by
   definition and from a canonical MPS through its local tensor and Schmidt weights.
@@ -93,6 +95,8 @@ def load_library(path: str):
     L.oracle_sv_schmidt2.argtypes = [P, I, P, I]
     L.oracle_mps_amplitudes.restype = I
     L.oracle_mps_amplitudes.argtypes = [I, P, P, P, I, P, I]
+    L.oracle_mps_two_products.restype = I
+    L.oracle_mps_two_products.argtypes = [I, P, P, I, I, P, P, P, I]
     L.oracle_svd.restype = I
     L.oracle_svd.argtypes = [I, I, P, I, I, P, P, P]
     L.oracle_sv_expect1.restype = I
@@ -264,6 +268,24 @@ def mps_site_defect(a, b, gamma, lam_left, lam_right, w, side):
     if rc:
         raise ValueError("bad arguments to oracle_mps_site_defect")
     return out.value
+
+
+def mps_two_products(vecs, coef, tol_log2=200, w_out=WORDS):
+    """Vidal MPS (chi, gammas, lambdas; the layout of mps_amplitudes) of psi = coef[0] (x)_l vecs[0][l] +
+    coef[1] (x)_l vecs[1][l], at any number of sites: vecs (2, n, 2, 2, w) words of the local 2-vectors
+    (amplitude, re/im), coef (2, 2, w).  Schmidt rank is at most 2 at every cut."""
+    vecs = _c(vecs); coef = _c(coef)
+    n, w = vecs.shape[1], vecs.shape[-1]
+    assert vecs.shape == (2, n, 2, 2, w) and coef.shape == (2, 2, w)
+    chi = np.zeros(n - 1, dtype=np.int32)
+    gam = np.zeros((8 * n, 2, w_out)); lam = np.zeros((2 * (n - 1), w_out))
+    rc = _load().oracle_mps_two_products(n, vecs.ctypes.data, coef.ctypes.data, w, tol_log2, chi.ctypes.data,
+                                         gam.ctypes.data, lam.ctypes.data, w_out)
+    if rc:
+        raise RuntimeError(f"oracle_mps_two_products failed ({rc})")
+    dims = [1] + [int(c) for c in chi] + [1]
+    used = sum(2 * dims[l] * dims[l + 1] for l in range(n))
+    return chi, gam[:used], lam[:int(chi.sum())]
 
 
 def svd(M, m, n, w_out=WORDS):

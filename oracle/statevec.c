@@ -416,3 +416,165 @@ int oracle_mps_expect1(int n, const int* chi, const double* gam, const double* l
   free(wl); free(wr);
   return 0;
 }
+
+/* Vidal MPS of a sum of two product states, psi = sum over t of c_t (x)_l v^t_l (t = 0, 1), at any n: the
+ * footnote's state C^{n-1}-U |+...+>|-> is |+...+>|-> + 2^{-(n-1)/2} |c> (U - 1)|->, such a sum, with Schmidt
+ * rank 2 at every cut.  At the cut before site l, with L^t = (x)_{k<l} v^t_k and R^t = (x)_{k>=l} v^t_k,
+ * psi = sum_t c_t L^t R^t.  The Grams GL_st = <L^s|L^t> and GR_st = <R^s|R^t> are products of local inner
+ * products.  In the orthonormal bases e = L Q^{-1}, f = R P^{-1} from the Cholesky factors
+ * GL = Q^H Q, GR = P^H P, the coefficients are Psi = Q diag(c) P^T; its Schmidt pairs come from the
+ * Jacobi eigensolve of Psi Psi^H (u_k: eigenvectors, lambda_k^2: eigenvalues, v_k = Psi^T conj(u_k) /
+ * lambda_k).  Each Schmidt vector is then a combination of L^0, L^1 (or R^0, R^1), and
+ *   Gamma[l]^s_{alpha beta} = sum_t c_t <u^(l)_alpha|L^t> <s|v^t_l> <v^(l+1)_beta|R^t_{l+1}> / (lambda^(l)_alpha lambda^(l+1)_beta).
+ * When the two terms are parallel on one side of a cut (GL or GR singular below 2^-tol_log2 of its
+ * trace) that cut has rank 1.  vecs: [t][l][amplitude 0, 1] complex, w words; coef: 2 complex, w words.
+ * Output as for oracle_sv_vidal.  Returns 0, or 1 on bad arguments. */
+typedef struct { cmp_t x[2][2]; } c22;
+
+static void c22_zero(c22* m) { for (int i = 0; i < 2; ++i) for (int j = 0; j < 2; ++j) cmp_zero(&m->x[i][j]); }
+
+/* Cholesky-type factor of a Hermitian positive semi-definite 2x2 G = Q^H Q with Q upper triangular;
+ * returns the rank (1 if the trailing pivot is below 2^-tol of the trace) */
+static int chol22(const c22* G, int tol_log2, c22* Q) {
+  c22_zero(Q);
+  mp q00; mp_sqrt(&q00, &G->x[0][0].re);
+  Q->x[0][0].re = q00;
+  cmp_t q01; mp_div(&q01.re, &G->x[0][1].re, &q00); mp_div(&q01.im, &G->x[0][1].im, &q00);   /* conj(Q00) Q01 = G01 */
+  Q->x[0][1] = q01;
+  mp d, t, tr; cmp_abs2(&t, &q01); mp_sub(&d, &G->x[1][1].re, &t);
+  mp_add(&tr, &G->x[0][0].re, &G->x[1][1].re); mp_ldexp(&tr, &tr, -tol_log2);
+  if (mp_cmp(&d, &tr) <= 0) return 1;
+  mp_sqrt(&Q->x[1][1].re, &d);
+  return 2;
+}
+
+int oracle_mps_two_products(int n, const double* vecs, const double* coef, int w, int tol_log2, int* chi,
+                            double* gam, double* lam, int w_out) {
+  if (n < 2 || n > 100000 || w < 1) return 1;
+  cmp_t* v = (cmp_t*)malloc(sizeof(cmp_t) * 2 * (size_t)n * 2);     /* v[(t n + l) 2 + s] */
+  for (size_t e = 0; e < (size_t)4 * n; ++e) {
+    mp_from_words(&v[e].re, vecs + (e * 2 + 0) * w, w);
+    mp_from_words(&v[e].im, vecs + (e * 2 + 1) * w, w);
+  }
+  cmp_t c[2];
+  for (int t = 0; t < 2; ++t) { mp_from_words(&c[t].re, coef + (t * 2 + 0) * w, w); mp_from_words(&c[t].im, coef + (t * 2 + 1) * w, w); }
+  /* local inner products g_l[s][t] = <v^s_l|v^t_l>, prefix (left) and suffix (right) Gram products */
+  c22* GLp = (c22*)malloc(sizeof(c22) * (n + 1));                   /* GLp[l]: sites < l */
+  c22* GRs = (c22*)malloc(sizeof(c22) * (n + 1));                   /* GRs[l]: sites >= l */
+  for (int i = 0; i < 2; ++i) for (int j = 0; j < 2; ++j) {
+    cmp_zero(&GLp[0].x[i][j]); mp_from_double(&GLp[0].x[i][j].re, 1.0);
+    cmp_zero(&GRs[n].x[i][j]); mp_from_double(&GRs[n].x[i][j].re, 1.0);
+  }
+  cmp_t* gl = (cmp_t*)malloc(sizeof(cmp_t) * 4 * (size_t)n);
+  for (int l = 0; l < n; ++l) for (int s = 0; s < 2; ++s) for (int t = 0; t < 2; ++t) {
+    cmp_t acc, u; cmp_zero(&acc);
+    for (int a = 0; a < 2; ++a) { cmp_mul_conj(&u, &v[((size_t)s * n + l) * 2 + a], &v[((size_t)t * n + l) * 2 + a]); cmp_add(&acc, &acc, &u); }
+    gl[(size_t)l * 4 + s * 2 + t] = acc;
+  }
+  for (int l = 0; l < n; ++l) for (int s = 0; s < 2; ++s) for (int t = 0; t < 2; ++t)
+    cmp_mul(&GLp[l + 1].x[s][t], &GLp[l].x[s][t], &gl[(size_t)l * 4 + s * 2 + t]);
+  for (int l = n - 1; l >= 0; --l) for (int s = 0; s < 2; ++s) for (int t = 0; t < 2; ++t)
+    cmp_mul(&GRs[l].x[s][t], &GRs[l + 1].x[s][t], &gl[(size_t)l * 4 + s * 2 + t]);
+  /* per cut l (between sites l-1 and l, l = 1..n-1): rank k, weights, and coefficient matrices A (u_alpha =
+   * sum_s A[alpha][s] L^s) and B (v_beta = sum_t B[beta][t] R^t); cuts 0 and n are the trivial ones */
+  int* rk = (int*)calloc(n + 1, sizeof(int));
+  c22* A = (c22*)calloc(n + 1, sizeof(c22));
+  c22* B = (c22*)calloc(n + 1, sizeof(c22));
+  mp* lw = (mp*)calloc((size_t)2 * (n + 1), sizeof(mp));
+  rk[0] = rk[n] = 1;
+  mp_from_double(&lw[0], 1.0); mp_from_double(&lw[2 * n], 1.0);
+  /* trivial cuts: the "left vector" of the empty prefix is 1 = L^0 = L^1 (A = (1, 0)); the right vector of
+   * the empty suffix likewise (B = (1, 0)) */
+  c22_zero(&A[0]); mp_from_double(&A[0].x[0][0].re, 1.0);
+  c22_zero(&B[n]); mp_from_double(&B[n].x[0][0].re, 1.0);
+  for (int l = 1; l < n; ++l) {
+    c22 Q, P;
+    const int rl = chol22(&GLp[l], tol_log2, &Q), rr = chol22(&GRs[l], tol_log2, &P);
+    /* Psi = Q diag(c) P^T restricted to the ranks (a rank-1 side keeps only row/column 0) */
+    c22 Psi; c22_zero(&Psi);
+    for (int a = 0; a < rl; ++a) for (int b = 0; b < rr; ++b)
+      for (int t = 0; t < 2; ++t) {
+        cmp_t u, z; cmp_mul(&u, &Q.x[a][t], &c[t]); cmp_mul(&z, &u, &P.x[b][t]); cmp_add(&Psi.x[a][b], &Psi.x[a][b], &z);
+      }
+    /* rho = Psi Psi^H (rl x rl), eigen-decomposition */
+    cmp_t g[4], ev[4]; mp mu[2]; int order[2];
+    for (int a = 0; a < rl; ++a) for (int b = 0; b < rl; ++b) {
+      cmp_t acc, u; cmp_zero(&acc);
+      for (int k = 0; k < rr; ++k) { cmp_mul_conj(&u, &Psi.x[b][k], &Psi.x[a][k]); cmp_add(&acc, &acc, &u); }
+      g[a + b * rl] = acc;
+    }
+    oracle_jacobi_mp(rl, g, ev, 80);
+    oracle_finish_mp(rl, g, ev, mu, order);
+    mp cut; mp_ldexp(&cut, &mu[0], -tol_log2);
+    int k = 0; while (k < rl && mp_cmp(&mu[k], &cut) > 0) ++k;
+    if (k == 0) k = 1;
+    rk[l] = k;
+    /* Q^{-1} (upper triangular, rank rl): e_a = sum_s L^s Qinv[s][a] */
+    c22 Qi, Pi; c22_zero(&Qi); c22_zero(&Pi);
+    for (int side = 0; side < 2; ++side) {
+      const c22* F = side == 0 ? &Q : &P; c22* Fi = side == 0 ? &Qi : &Pi; const int r = side == 0 ? rl : rr;
+      mp one; mp_from_double(&one, 1.0);
+      mp_div(&Fi->x[0][0].re, &one, &F->x[0][0].re);
+      if (r == 2) {
+        mp_div(&Fi->x[1][1].re, &one, &F->x[1][1].re);
+        cmp_t t1; cmp_scale(&t1, &F->x[0][1], &Fi->x[1][1].re); cmp_scale(&t1, &t1, &Fi->x[0][0].re);
+        mp_neg(&Fi->x[0][1].re, &t1.re); mp_neg(&Fi->x[0][1].im, &t1.im);                    /* -q01 / (q00 q11) */
+      }
+    }
+    for (int q = 0; q < k; ++q) {
+      mp_sqrt(&lw[2 * l + q], &mu[q]);
+      const cmp_t* e = ev + (size_t)order[q] * rl;      /* u_q in the basis e_a */
+      /* A[q][s] = sum_a Qinv[s][a] e[a] (coefficients on L^s) */
+      for (int s = 0; s < 2; ++s) {
+        cmp_t acc, u; cmp_zero(&acc);
+        for (int a = 0; a < rl; ++a) { cmp_mul(&u, &Qi.x[s][a], &e[a]); cmp_add(&acc, &acc, &u); }
+        A[l].x[q][s] = acc;
+      }
+      /* v_q = Psi^T conj(u_q) / lambda_q in the basis f_b, then B[q][t] = sum_b Pinv[t][b] v[b] */
+      cmp_t vb[2];
+      for (int b = 0; b < 2; ++b) {
+        cmp_t acc, u; cmp_zero(&acc);
+        if (b < rr) for (int a = 0; a < rl; ++a) { cmp_mul_conj(&u, &e[a], &Psi.x[a][b]); cmp_add(&acc, &acc, &u); }
+        mp_div(&acc.re, &acc.re, &lw[2 * l + q]); mp_div(&acc.im, &acc.im, &lw[2 * l + q]);
+        vb[b] = acc;
+      }
+      for (int t = 0; t < 2; ++t) {
+        cmp_t acc, u; cmp_zero(&acc);
+        for (int b = 0; b < rr; ++b) { cmp_mul(&u, &Pi.x[t][b], &vb[b]); cmp_add(&acc, &acc, &u); }
+        B[l].x[q][t] = acc;
+      }
+    }
+  }
+  /* Gamma[l]^s_{alpha beta} = sum_t c_t <u^(l)_alpha|L^t_l> v^t_l[s] <v^(l+1)_beta|R^t_{l+1}> / (lam lam) */
+  size_t go = 0, lo = 0;
+  for (int l = 0; l < n; ++l) {
+    const int ca = rk[l], cb = rk[l + 1];
+    for (int s = 0; s < 2; ++s) for (int al = 0; al < ca; ++al) for (int be = 0; be < cb; ++be) {
+      cmp_t acc; cmp_zero(&acc);
+      for (int t = 0; t < 2; ++t) {
+        cmp_t ul, vr, u, z;
+        cmp_zero(&ul);                                 /* <u_alpha|L^t> = sum_s' conj(A[alpha][s']) GL[s'][t] */
+        for (int s2 = 0; s2 < 2; ++s2) { cmp_mul_conj(&u, &A[l].x[al][s2], &GLp[l].x[s2][t]); cmp_add(&ul, &ul, &u); }
+        cmp_zero(&vr);                                 /* <v_beta|R^t_{l+1}> = sum_t' conj(B[beta][t']) GR[t'][t] */
+        for (int t2 = 0; t2 < 2; ++t2) { cmp_mul_conj(&u, &B[l + 1].x[be][t2], &GRs[l + 1].x[t2][t]); cmp_add(&vr, &vr, &u); }
+        cmp_mul(&u, &c[t], &ul);
+        cmp_mul(&z, &u, &v[((size_t)t * n + l) * 2 + s]);
+        cmp_mul(&u, &z, &vr);
+        cmp_add(&acc, &acc, &u);
+      }
+      mp den; mp_mul(&den, &lw[2 * l + al], &lw[2 * (l + 1) + be]);
+      mp_div(&acc.re, &acc.re, &den); mp_div(&acc.im, &acc.im, &den);
+      const size_t e = go + ((size_t)s * ca + al) * cb + be;
+      mp_to_words(&acc.re, gam + (e * 2 + 0) * w_out, w_out);
+      mp_to_words(&acc.im, gam + (e * 2 + 1) * w_out, w_out);
+    }
+    go += (size_t)2 * ca * cb;
+    if (l < n - 1) {
+      chi[l] = cb;
+      for (int be = 0; be < cb; ++be) mp_to_words(&lw[2 * (l + 1) + be], lam + (lo + be) * w_out, w_out);
+      lo += cb;
+    }
+  }
+  free(v); free(GLp); free(GRs); free(gl); free(rk); free(A); free(B); free(lw);
+  return 0;
+}

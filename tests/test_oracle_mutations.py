@@ -111,6 +111,13 @@ MUTATIONS = [
     ("one-sided Jacobi rotations not accumulated in V", "svd.c",
      "for (int pass = 0; pass < 2; ++pass) {", "for (int pass = 0; pass < 1; ++pass) {",
      [lambda: P.test_svd_of_exact_construction(5, 3, 3)]),
+    ("two-product Vidal form: Cholesky off-diagonal not divided by the pivot", "statevec.c",
+     "cmp_t q01; mp_div(&q01.re, &G->x[0][1].re, &q00); mp_div(&q01.im, &G->x[0][1].im, &q00);",
+     "cmp_t q01 = G->x[0][1];",
+     [P.test_two_product_vidal_form_matches_the_state_vector]),
+    ("two-product Vidal tensors without the term coefficients", "statevec.c",
+     "cmp_mul(&u, &c[t], &ul);", "u = ul;",
+     [P.test_two_product_vidal_form_matches_the_state_vector]),
     ("conjugate-transpose product without the conjugate", "products.c",
      "if (opA) cmp_mul_conj(&t,", "if (opA) cmp_mul(&t,",
      [P.test_matmul_matches_exact_rationals]),

@@ -656,3 +656,89 @@ def test_svd_of_rank_one_and_zero_matrices():
     assert abs(fr(s[0]) - Fraction(15, 4)) <= Fraction(1, 2**300) and abs(fr(s[1])) <= Fraction(1, 2**300)
     s0, U0, _ = oracle.svd(np.zeros((6, 2, 1)), 3, 2)
     assert fr(s0[0]) == 0 and fr(s0[1]) == 0 and not U0.any()
+
+
+def _two_product_words(vecs, coef, w=8):
+    """words arrays for oracle.mps_two_products from Fractions: vecs[t][l] = ((re0, im0), (re1, im1))."""
+    n = len(vecs[0])
+    V = np.zeros((2, n, 2, 2, w)); C = np.zeros((2, 2, w))
+    for t in range(2):
+        for l in range(n):
+            for s in range(2):
+                for p in range(2):
+                    V[t, l, s, p] = words(vecs[t][l][s][p], w)
+        for p in range(2):
+            C[t, p] = words(coef[t][p], w)
+    return V, C
+
+
+def test_two_product_vidal_form_matches_the_state_vector():
+    """The Vidal MPS of c_0 (x) v^0_l + c_1 (x) v^1_l built from Gram products (no state vector) equals, on
+    8 qubits with Gaussian-dyadic local vectors, the oracle's state-vector route: the same Schmidt weights
+    to 2^-290 and amplitudes to 2^-290 relative, and every site canonical."""
+    rng = np.random.default_rng(8)
+    n = 8
+    q = lambda: Fraction(int(rng.integers(-64, 65)), 32)
+    vecs = [[((q(), q()), (q(), q())) for _ in range(n)] for _ in range(2)]
+    coef = [(Fraction(3, 4), Fraction(-1, 8)), (Fraction(5, 16), Fraction(1, 2))]
+    V, C = _two_product_words(vecs, coef)
+    chi, g, lam = oracle.mps_two_products(V, C)
+    assert list(chi) == [2] * (n - 1)
+    amps = []
+    for x in range(1 << n):
+        acc = (Fraction(0), Fraction(0))
+        for t in range(2):
+            term = coef[t]
+            for l in range(n):
+                term = cmul(term, vecs[t][l][(x >> (n - 1 - l)) & 1])
+            acc = cadd(acc, term)
+        amps.append(acc)
+    sv = oracle.Statevector(n)
+    sv.set(np.array([[words(a[0], 8), words(a[1], 8)] for a in amps]))
+    _, _, lam_sv = sv.vidal()
+    norm = sum(a * a + b * b for a, b in amps)
+    for k in range(len(lam)):
+        assert abs(fr(lam[k]) - fr(lam_sv[k])) <= Fraction(1, 2**290) * norm
+    got = oracle.mps_amplitudes(n, chi, g, lam, oracle.WORDS)
+    for x in range(1 << n):
+        for p in range(2):
+            assert abs(fr(got[x, p]) - amps[x][p]) <= Fraction(1, 2**290) * norm
+    _check_canonical(n, chi, g, lam, norm, range(n))
+
+
+def _check_canonical(n, chi, g, lam, norm2, sites):
+    """Canonical conditions of an MPS of a state with squared norm norm2: both sides orthonormal, except
+    that the outer weights are 1, so the right Gram of site 0 and the left Gram of site n-1 are norm2 I."""
+    views = _site_views(n, chi, g, lam)
+    for l in sites:
+        a, b, gl, left, right = views[l]
+        d0 = oracle.mps_site_defect(a, b, gl, left, None, oracle.WORDS, 0)
+        d1 = oracle.mps_site_defect(a, b, gl, None, right, oracle.WORDS, 1)
+        for d, edge in ((d0, l == n - 1), (d1, l == 0)):
+            want = abs(float(norm2) - 1) if edge else 0.0
+            assert abs(d - want) <= 2.0**-280 * float(norm2), (l, d, want)
+
+
+@pytest.mark.parametrize("n", [6, 40, 180])
+def test_footnote_state_vidal_form_at_large_n(n):
+    """The paper's footnote example (Section 1) at qubit counts no state vector reaches: C^{n-1}-Z on
+    |+>^{n-1}|-> (unnormalised, |+> = (1, 1), |-> = (1, -1), norm^2 2^n) is
+    |+...+>|-> + |c> (Z - 1)|-> = |+...+>|-> + |c>(0, 2), a sum of two product states.  At the cut between the
+    controls and the target its squared Schmidt coefficients are 2^n (1 - 2^-(n-1)) and 2^n 2^-(n-1), so the
+    normalised ones are 1 - eps and eps with eps = 2^-(n-1), as the footnote states.  Sampled sites are
+    canonical, and every bond has rank 2."""
+    rng = np.random.default_rng(n)
+    ctrl = [int(b) for b in rng.integers(0, 2, n - 1)]
+    one, zero = Fraction(1), Fraction(0)
+    plus, minus = ((one, zero), (one, zero)), ((one, zero), (-one, zero))
+    e = lambda b: (((one, zero), (zero, zero)) if b == 0 else ((zero, zero), (one, zero)))
+    vecs = [[plus] * (n - 1) + [minus], [e(b) for b in ctrl] + [((zero, zero), (Fraction(2), zero))]]
+    V, C = _two_product_words(vecs, [(one, zero), (one, zero)])
+    chi, g, lam = oracle.mps_two_products(V, C)
+    assert list(chi) == [2] * (n - 1)
+    last = lam[-2:]
+    total = Fraction(2) ** n
+    eps = Fraction(1, 2 ** (n - 1))
+    assert abs(fr(last[0]) ** 2 / total - (1 - eps)) <= Fraction(1, 2**290)
+    assert abs(fr(last[1]) ** 2 / total - eps) <= Fraction(1, 2**290)
+    _check_canonical(n, chi, g, lam, total, sorted({0, 1, n // 2, n - 2, n - 1}))
