@@ -49,7 +49,7 @@ def test_arithmetic_matches_exact_rationals(a, b, op):
         assert abs(got - exact) <= abs(exact) / 2**312
 
 
-@SETTINGS
+@hyp.settings(max_examples=400, deadline=None, derandomize=True, suppress_health_check=list(hyp.HealthCheck))
 @hyp.given(a=WORDS)
 def test_square_root_squares_back(a):
     hyp.assume(_span_ok(a))
