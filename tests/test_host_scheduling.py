@@ -6,7 +6,9 @@ sources with g++ against the CUDA headers (no GPU, no kernel):
 * the batch layout of the FP64 eigensolve, `eigh_layout` in layout.cu: the problem order (orders <= 80
   in input order, then the larger ones by decreasing order), the eigenvalue and workspace offsets, the
   cluster width (configured, from the tuning table, or by the largest order), and the block groups of the
-  cooperative grid for a few large problems."""
+  cooperative grid for a few large problems;
+* the plain RQI layout, `rqi_layout` in layout.cu: the eigenpair-to-problem map, the grid and the
+  workspace slots."""
 from __future__ import annotations
 
 import ctypes
@@ -63,6 +65,18 @@ extern "C" int layout_probe(int batch, const int* n, int cfg_cluster, int num_sm
   bytes[3] = (long long)L.meta_bytes(); bytes[4] = (long long)L.ws_bytes();
   return 0;
 }
+extern "C" int rqi_probe(int batch, const int* n, int target_words, int num_sms, long long* scalars, int* pair_prob,
+                         long long* w_off) {
+  std::vector<int64_t> a_off(batch, 0);
+  zkq::RqiLayout L;
+  zkq_status s = zkq::rqi_layout(batch, n, a_off.data(), target_words, num_sms, &L);
+  if (s != ZKQ_OK) return (int)s;
+  scalars[0] = L.total; scalars[1] = L.grid; scalars[2] = (long long)L.slot;
+  scalars[3] = (long long)L.meta_bytes(); scalars[4] = (long long)L.ws_bytes();
+  for (int64_t i = 0; i < L.total; ++i) pair_prob[i] = L.pair_prob[i];
+  for (int b = 0; b < batch; ++b) w_off[b] = L.w_off[b];
+  return 0;
+}
 """
 
 
@@ -88,6 +102,8 @@ def libs(tmp_path_factory):
     rr.rr_fill.argtypes = [I, P, P]
     lay.layout_probe.restype = I
     lay.layout_probe.argtypes = [I, P, I, I, I, I, P, P, P, P, P, P, P]
+    lay.rqi_probe.restype = I
+    lay.rqi_probe.argtypes = [I, P, I, I, P, P, P]
     return rr, lay
 
 
@@ -165,3 +181,23 @@ def test_eigh_layout_block_groups_for_few_large_problems(libs):
     assert L["grp"] == [each * k for k in range(10)] and L["grid_blocks"] <= 608
     assert _probe(lay, [512] * 10, per_sm=4)["grid_blocks"] == 0   # 10 x 8 x 2 > 152: a cluster each
     assert _probe(lay, [512, 300], per_sm=0)["grid_blocks"] == 0   # no co-residency information: clusters
+
+
+def test_rqi_layout_maps_every_eigenpair_to_its_problem(libs):
+    """The plain RQI layout: one work item per eigenpair, mapped to its problem in batch order, a grid of
+    min(eigenpairs, SMs) persistent blocks, each with a workspace slot sized for the largest order (the
+    LU of A - mu I plus two vectors, complex, W words)."""
+    _, lay = libs
+    n = [3, 5, 2, 1, 4]
+    na = np.array(n, dtype=np.int32)
+    sc = np.zeros(5, dtype=np.int64); pp = np.zeros(sum(n), dtype=np.int32); wo = np.zeros(len(n), dtype=np.int64)
+    assert lay.rqi_probe(len(n), na.ctypes.data, 4, 152, sc.ctypes.data, pp.ctypes.data, wo.ctypes.data) == 0
+    assert sc[0] == sum(n) and sc[1] == min(sum(n), 152)
+    assert list(pp) == [b for b, x in enumerate(n) for _ in range(x)]
+    assert list(wo) == list(np.cumsum([0] + n[:-1]))
+    nmax = max(n)
+    assert sc[2] == (nmax * (nmax + 1) + 2 * nmax) * 2 * 4 and sc[4] == sc[2] * 8 * sc[1]
+    big = np.array([300] * 2, dtype=np.int32)
+    pp2 = np.zeros(600, dtype=np.int32)
+    assert lay.rqi_probe(2, big.ctypes.data, 2, 152, sc.ctypes.data, pp2.ctypes.data, wo.ctypes.data) == 0
+    assert sc[1] == 152
