@@ -47,6 +47,8 @@ zkq_status launch_jacobi(const JacobiBatch&, int, int, int, int, int, int, int, 
 zkq_status launch_rqi(const RqiBatch&, int, int, int, cudaStream_t) { return ZKQ_OK; }
 size_t rqi_slot_doubles(int nmax, int W) { return ((size_t)nmax * (nmax + 1) + 2 * (size_t)nmax) * 2 * W; }
 }
+// the one runtime call layout.cu makes (in the RQI launch, which the test never reaches)
+extern "C" cudaError_t cudaMemsetAsync(void*, int, size_t, cudaStream_t) { return cudaErrorNotSupported; }
 extern "C" int layout_probe(int batch, const int* n, int cfg_cluster, int num_sms, int per_sm, int ntune,
                             const int* tune, int* scalars, int* order, long long* w_off, long long* ws_off,
                             int* grp, long long* bytes) {
@@ -84,9 +86,10 @@ def _build(tmp, name, src, extra=()):
     (tmp / f"{name}.cpp").write_text(src)
     out = tmp / f"{name}.so"
     # the device helpers of common.cuh call fma unqualified, as nvcc allows: give the host compile ::fma
-    subprocess.run(["g++", "-std=c++17", "-O1", "-fPIC", "-shared", "-include", "math.h", f"-I{CSRC}", f"-I{CUDA_INC}",
-                    "-x", "c++", str(tmp / f"{name}.cpp"), *extra, "-o", str(out)], check=True, capture_output=True,
-                   text=True)
+    # -Bsymbolic: the stubs bind inside this library even when a CUDA runtime is loaded with global symbols
+    subprocess.run(["g++", "-std=c++17", "-O1", "-fPIC", "-shared", "-Wl,-Bsymbolic", "-include", "math.h",
+                    f"-I{CSRC}", f"-I{CUDA_INC}", "-x", "c++", str(tmp / f"{name}.cpp"), *extra, "-o", str(out)],
+                   check=True, capture_output=True, text=True)
     return ctypes.CDLL(str(out))
 
 
