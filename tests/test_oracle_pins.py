@@ -742,3 +742,46 @@ def test_footnote_state_vidal_form_at_large_n(n):
     assert abs(fr(last[0]) ** 2 / total - (1 - eps)) <= Fraction(1, 2**290)
     assert abs(fr(last[1]) ** 2 / total - eps) <= Fraction(1, 2**290)
     _check_canonical(n, chi, g, lam, total, sorted({0, 1, n // 2, n - 2, n - 1}))
+
+
+@pytest.mark.parametrize("k,seed,general", [(1, 1, False), (2, 2, False), (4, 3, False), (5, 4, True), (6, 5, False)])
+def test_footnote_circuit_equals_the_multi_controlled_gate(k, seed, general):
+    """The nearest-neighbour circuit of the footnote's C^k-U (workloads.footnote_circuit, for an MPS
+    simulation) acts on |+>^k |-> with its ancillas in |0> exactly as the multi-controlled gate itself
+    (oracle state vector, apply_mcu): same amplitudes to 2^-300, ancillas back in |0>.  For U = Z the
+    Schmidt coefficients at the cut before the target are then the footnote's 1 - 2^-k and 2^-k."""
+    rng = np.random.default_rng(seed)
+    ctrl = [int(b) for b in rng.integers(0, 2, k)]
+    U = None
+    if general:
+        D = dyadic_unitary(2, layers=3, seed=seed)
+        U = [[D[r][c] for c in range(2)] for r in range(2)]
+    sites, gates = W.footnote_circuit(ctrl, U)
+    assert sites == 2 * k and all(s + (2 if kind == "2q" else 1) <= sites for kind, s, _ in gates)
+    pos = [0] + [2 * l - 1 for l in range(1, k)]
+    target = 2 * k - 1
+    amps = np.zeros((1 << sites, 2, 1))
+    for x in range(1 << sites):
+        bits = [(x >> (sites - 1 - q)) & 1 for q in range(sites)]
+        if any(bits[q] for q in range(sites) if q not in pos and q != target):
+            continue                                              # ancillas in |0>
+        amps[x, 0, 0] = -1.0 if bits[target] else 1.0             # |+> = (1, 1) on controls, |-> = (1, -1)
+    a = oracle.Statevector(sites); a.set(amps)
+    for kind, s, G in gates:
+        (a.apply2 if kind == "2q" else a.apply1)(s, G)
+    b = oracle.Statevector(sites); b.set(amps)
+    cl = [-1] * sites
+    for l in range(k):
+        cl[pos[l]] = ctrl[l]
+    Uw = W._mat_words(U if U is not None else [[(1, 0), (0, 0)], [(0, 0), (-1, 0)]], 4)
+    b.apply_mcu(target, cl, Uw)
+    A, B = a.amplitudes(), b.amplitudes()
+    for x in range(1 << sites):
+        for p in range(2):
+            assert abs(fr(A[x, p]) - fr(B[x, p])) <= Fraction(1, 2**300), (x, p)
+    if not general:
+        lam2 = a.schmidt2(sites - 1)                              # cut before the target: 2 values
+        tot = fr(lam2[0]) + fr(lam2[1])
+        eps = Fraction(1, 2 ** k)
+        assert abs(fr(lam2[0]) / tot - (1 - eps)) <= Fraction(1, 2**290)
+        assert abs(fr(lam2[1]) / tot - eps) <= Fraction(1, 2**290)

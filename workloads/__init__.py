@@ -250,3 +250,61 @@ def brickwork(n_qubits: int, depth: int):
 def brickwork_circuit(seed: int, n_qubits: int, depth: int, w: int = 4):
     """[(site, G)] with a fresh Haar gate per position, in seed order."""
     return [(s, haar_gate(seed, i, w)) for i, s in enumerate(brickwork(n_qubits, depth))]
+
+
+# ----------------------------------------------------------------------------------------------------
+# the footnote circuit: C^k-U on nearest-neighbour qubits with a ladder of ancillas
+def _mat_words(M, w):
+    """Row-major (dim*dim, 2, w) words of a square matrix of (re, im) Fractions."""
+    dim = len(M)
+    out = np.zeros((dim * dim, 2, w))
+    for r in range(dim):
+        for c in range(dim):
+            out[r * dim + c, 0, :] = words_of(Fraction(M[r][c][0]), w)
+            out[r * dim + c, 1, :] = words_of(Fraction(M[r][c][1]), w)
+    return out
+
+
+def _controlled(V):
+    """4x4 controlled-V with the control on the first qubit of the pair (row index 2 i + j)."""
+    z, o = (Fraction(0), Fraction(0)), (Fraction(1), Fraction(0))
+    return [[o, z, z, z], [z, o, z, z], [z, z, V[0][0], V[0][1]], [z, z, V[1][0], V[1][1]]]
+
+
+def footnote_circuit(ctrl, U=None, w: int = 4):
+    """The multi-controlled gate of the paper's footnote example (Section 1), C^k-U with control pattern
+    ctrl (k = len(ctrl) bits) and a target, as one- and two-qubit gates on neighbouring qubits only, for an
+    MPS simulation.  Layout: control 0 at site 0, control l at site 2l - 1, ancilla l (starting in |0>)
+    at site 2l, the target at site 2k - 1; 2k sites in all.  The ancillas hold the running AND of the
+    controls through a ladder of Toffoli gates (Barenco et al. 1995: controlled-sqrt(X), CNOT, controlled-
+    sqrt(X)^H, CNOT, controlled-sqrt(X), the last one between non-neighbours carried by two SWAPs), the last
+    ancilla controls U on the target, and the ladder is undone.  Controls whose pattern bit is 0 are
+    conjugated by X.  U: 2x2 of (re, im) Fractions, default Z.  All entries are dyadic, so the circuit is
+    exact in binary.  Returns (sites, gates) with gates a list of ("1q" | "2q", site, words)."""
+    k = len(ctrl)
+    assert k >= 1
+    z, o, h = Fraction(0), Fraction(1), Fraction(1, 2)
+    if U is None:
+        U = [[(o, z), (z, z)], [(z, z), (-o, z)]]
+    X = [[(z, z), (o, z)], [(o, z), (z, z)]]
+    SX = [[(h, h), (h, -h)], [(h, -h), (h, h)]]                      # sqrt(X)
+    SXH = [[(h, -h), (h, h)], [(h, h), (h, -h)]]                     # its conjugate transpose
+    Z0, O1 = (z, z), (o, z)
+    CNOT = [[O1, Z0, Z0, Z0], [Z0, O1, Z0, Z0], [Z0, Z0, Z0, O1], [Z0, Z0, O1, Z0]]
+    SWAP = [[O1, Z0, Z0, Z0], [Z0, Z0, O1, Z0], [Z0, O1, Z0, Z0], [Z0, Z0, Z0, O1]]
+    g = lambda M: _mat_words(M, w)
+    cv, cvh, cx, sw = g(_controlled(SX)), g(_controlled(SXH)), g(CNOT), g(SWAP)
+    pos = [0] + [2 * l - 1 for l in range(1, k)]
+    target = 2 * k - 1
+
+    def toffoli(q):                                   # controls at q, q + 1; target q + 2
+        return [("2q", q + 1, cv), ("2q", q, cx), ("2q", q + 1, cvh), ("2q", q, cx),
+                ("2q", q, sw), ("2q", q + 1, cv), ("2q", q, sw)]
+
+    flips = [("1q", pos[l], g(X)) for l in range(k) if ctrl[l] == 0]
+    ladder = []
+    for l in range(1, k):                             # ancilla l = (control 0 and ... and control l)
+        ladder += toffoli(0 if l == 1 else 2 * l - 2)
+    last = 0 if k == 1 else 2 * k - 2                 # the qubit that controls U, next to the target
+    gates = flips + ladder + [("2q", last, g(_controlled(U)))] + ladder[::-1] + flips
+    return 2 * k, gates
