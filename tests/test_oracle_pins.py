@@ -785,3 +785,37 @@ def test_footnote_circuit_equals_the_multi_controlled_gate(k, seed, general):
         eps = Fraction(1, 2 ** k)
         assert abs(fr(lam2[0]) / tot - (1 - eps)) <= Fraction(1, 2**290)
         assert abs(fr(lam2[1]) / tot - eps) <= Fraction(1, 2**290)
+
+
+def test_footnote_circuit_state_is_the_two_product_vidal_state():
+    """After the footnote circuit (k = 5 controls, ancillas back in |0>), the state is
+    |+..+>|0..0>|-> + |c>|0..0> (Z - 1)|->, a sum of two product states: the oracle's two-product Vidal MPS of
+    it reproduces the state vector's amplitudes to 2^-290, so it can stand in for the state vector at
+    the qubit counts the device runs the circuit at."""
+    k = 5
+    ctrl = [1, 0, 1, 1, 0]
+    sites, gates = W.footnote_circuit(ctrl)
+    pos = [0] + [2 * l - 1 for l in range(1, k)]
+    target = 2 * k - 1
+    amps = np.zeros((1 << sites, 2, 1))
+    for x in range(1 << sites):
+        bits = [(x >> (sites - 1 - q)) & 1 for q in range(sites)]
+        if any(bits[q] for q in range(sites) if q not in pos and q != target):
+            continue
+        amps[x, 0, 0] = -1.0 if bits[target] else 1.0
+    sv = oracle.Statevector(sites); sv.set(amps)
+    for kind, s, G in gates:
+        (sv.apply2 if kind == "2q" else sv.apply1)(s, G)
+    one, zero = Fraction(1), Fraction(0)
+    e0, e1 = ((one, zero), (zero, zero)), ((zero, zero), (one, zero))
+    plus, minus = ((one, zero), (one, zero)), ((one, zero), (-one, zero))
+    t0 = [plus if q in pos else (minus if q == target else e0) for q in range(sites)]
+    t1 = [(e1 if ctrl[pos.index(q)] else e0) if q in pos else
+          (((zero, zero), (Fraction(2), zero)) if q == target else e0) for q in range(sites)]
+    V, C = _two_product_words([t0, t1], [(one, zero), (one, zero)])
+    chi, g, lam = oracle.mps_two_products(V, C)
+    got = oracle.mps_amplitudes(sites, chi, g, lam, oracle.WORDS)
+    ref = sv.amplitudes()
+    for x in range(1 << sites):
+        for p in range(2):
+            assert abs(fr(got[x, p]) - fr(ref[x, p])) <= Fraction(1, 2**290) * 2 ** sites
