@@ -13,6 +13,7 @@ Plain, slow, independent CPU implementation of what the accurate-eigensolve path
 * ``Statevector.vidal``: the Vidal MPS of a state from its Schmidt decompositions at every cut;
 * ``mps_two_products``: the Vidal MPS of a sum of two product states at any qubit count, such as the
   state of the paper's footnote example;
+* ``mps_apply2``: one two-site gate update of a Vidal MPS (theta, SVD, truncation, split back);
 * ``svd``: one-sided Jacobi singular value decomposition at 320 bits (the SVD variant of the gate update);
 * ``Statevector.expect1`` and ``mps_expect1``: one-qubit expectation values, from the state vector by
   definition and from a canonical MPS through its local tensor and Schmidt weights.
@@ -32,7 +33,7 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SO = os.path.join(_HERE, "_oracle.so")
-_SRC = ["mp.c", "eigh.c", "statevec.c", "products.c", "svd.c"]
+_SRC = ["mp.c", "eigh.c", "statevec.c", "products.c", "svd.c", "mpsgate.c"]
 _lib = None
 _lock = threading.Lock()
 
@@ -97,6 +98,8 @@ def load_library(path: str):
     L.oracle_mps_amplitudes.argtypes = [I, P, P, P, I, P, I]
     L.oracle_mps_two_products.restype = I
     L.oracle_mps_two_products.argtypes = [I, P, P, I, I, P, P, P, I]
+    L.oracle_mps_apply2.restype = I
+    L.oracle_mps_apply2.argtypes = [I, P, P, P, I, I, P, I, I, I, P, P, P, I, ctypes.POINTER(D)]
     L.oracle_svd.restype = I
     L.oracle_svd.argtypes = [I, I, P, I, I, P, P, P]
     L.oracle_sv_expect1.restype = I
@@ -286,6 +289,31 @@ def mps_two_products(vecs, coef, tol_log2=200, w_out=WORDS):
     dims = [1] + [int(c) for c in chi] + [1]
     used = sum(2 * dims[l] * dims[l + 1] for l in range(n))
     return chi, gam[:used], lam[:int(chi.sum())]
+
+
+def mps_apply2(n, chi, gammas, lambdas, w, site, G, tol_log2=300, r_max=1 << 20, w_out=WORDS):
+    """One two-site gate update of a Vidal MPS at 320 bits (theta contraction, one-sided Jacobi SVD of the
+    reshaped tensor, truncation to sigma^2 > 2^-tol_log2 sum sigma^2 and at most r_max values,
+    renormalisation, split back).  G: (16, 2, wg) words, row-major in (i j) x (k m) with i the bit of
+    `site`.  Returns (chi, gammas, lambdas, discarded weight)."""
+    chi = np.ascontiguousarray(chi, dtype=np.int32)
+    g = _c(gammas); l = _c(lambdas); G = _c(G)
+    dims = [1] + [int(c) for c in chi] + [1]
+    a, d = dims[site], dims[site + 2]
+    new = min(2 * a, 2 * d, r_max)
+    dims2 = list(dims); dims2[site + 1] = new
+    ge = sum(2 * dims2[k] * dims2[k + 1] for k in range(n))
+    chi_o = np.zeros(n - 1, dtype=np.int32)
+    gam_o = np.zeros((ge, 2, w_out)); lam_o = np.zeros((sum(dims2[1:n]), w_out))
+    disc = ctypes.c_double()
+    rc = _load().oracle_mps_apply2(n, chi.ctypes.data, g.ctypes.data, l.ctypes.data if l.size else None, w, site,
+                                   G.ctypes.data, G.shape[-1], tol_log2, r_max, chi_o.ctypes.data, gam_o.ctypes.data,
+                                   lam_o.ctypes.data, w_out, ctypes.byref(disc))
+    if rc:
+        raise RuntimeError(f"oracle_mps_apply2 failed ({rc})")
+    dims3 = [1] + [int(c) for c in chi_o] + [1]
+    used = sum(2 * dims3[k] * dims3[k + 1] for k in range(n))
+    return chi_o, gam_o[:used], lam_o[:int(chi_o.sum())], disc.value
 
 
 def svd(M, m, n, w_out=WORDS):

@@ -17,19 +17,10 @@
 
 #define IX(i, j, ld) ((size_t)(i) + (size_t)(j) * (size_t)(ld))
 
-/* M: m x n column-major complex, w words per real.  sigma_out: n values (w_out words, descending);
- * U_out (m x n) and V_out (n x n), column-major complex, w_out words.  Returns 0, 1 on bad arguments,
- * 2 if 80 sweeps did not converge. */
-int oracle_svd(int m, int n, const double* M, int w, int w_out, double* sigma_out, double* U_out, double* V_out) {
-  if (m < 1 || n < 1 || w < 1) return 1;
-  cmp_t* a = (cmp_t*)malloc(sizeof(cmp_t) * (size_t)m * n);
-  cmp_t* v = (cmp_t*)malloc(sizeof(cmp_t) * (size_t)n * n);
-  mp* sg = (mp*)malloc(sizeof(mp) * n);
-  int* order = (int*)malloc(sizeof(int) * n);
-  for (size_t e = 0; e < (size_t)m * n; ++e) {
-    mp_from_words(&a[e].re, M + (e * 2 + 0) * w, w);
-    mp_from_words(&a[e].im, M + (e * 2 + 1) * w, w);
-  }
+/* The one-sided Jacobi on an mp matrix: a (m x n, overwritten by A V), v (n x n, out: V), sg (n, out:
+ * column norms sigma_j), order (n, out: column indices by descending sigma, ties in column order).
+ * Returns 0, or 2 if 80 sweeps did not converge. */
+int oracle_svd_mp(int m, int n, cmp_t* a, cmp_t* v, mp* sg, int* order) {
   for (int i = 0; i < n; ++i) for (int j = 0; j < n; ++j) {
     cmp_zero(&v[IX(i, j, n)]);
     if (i == j) mp_from_double(&v[IX(i, j, n)].re, 1.0);
@@ -82,12 +73,10 @@ int oracle_svd(int m, int n, const double* M, int w, int w_out, double* sigma_ou
     if (rotations == 0) { rc = 0; break; }
   }
   if (rc == 0) {
-    mp smax; mp_zero(&smax);
     for (int j = 0; j < n; ++j) {
       mp acc, t1; mp_zero(&acc);
       for (int i = 0; i < m; ++i) { cmp_abs2(&t1, &a[IX(i, j, m)]); mp_add(&acc, &acc, &t1); }
       mp_sqrt(&sg[j], &acc);
-      if (mp_cmp(&sg[j], &smax) > 0) smax = sg[j];
     }
     for (int i = 0; i < n; ++i) order[i] = i;
     for (int i = 1; i < n; ++i) {                     /* stable insertion sort, descending */
@@ -95,6 +84,26 @@ int oracle_svd(int m, int n, const double* M, int w, int w_out, double* sigma_ou
       while (j >= 0 && mp_cmp(&sg[order[j]], &sg[k]) < 0) { order[j + 1] = order[j]; --j; }
       order[j + 1] = k;
     }
+  }
+  return rc;
+}
+
+/* M: m x n column-major complex, w words per real.  sigma_out: n values (w_out words, descending);
+ * U_out (m x n) and V_out (n x n), column-major complex, w_out words.  Returns 0, 1 on bad arguments,
+ * 2 if 80 sweeps did not converge. */
+int oracle_svd(int m, int n, const double* M, int w, int w_out, double* sigma_out, double* U_out, double* V_out) {
+  if (m < 1 || n < 1 || w < 1) return 1;
+  cmp_t* a = (cmp_t*)malloc(sizeof(cmp_t) * (size_t)m * n);
+  cmp_t* v = (cmp_t*)malloc(sizeof(cmp_t) * (size_t)n * n);
+  mp* sg = (mp*)malloc(sizeof(mp) * n);
+  int* order = (int*)malloc(sizeof(int) * n);
+  for (size_t e = 0; e < (size_t)m * n; ++e) {
+    mp_from_words(&a[e].re, M + (e * 2 + 0) * w, w);
+    mp_from_words(&a[e].im, M + (e * 2 + 1) * w, w);
+  }
+  int rc = oracle_svd_mp(m, n, a, v, sg, order);
+  if (rc == 0) {
+    mp smax = sg[order[0]];
     mp floor_; mp_ldexp(&floor_, &smax, -300);
     for (int c = 0; c < n; ++c) {
       const int j = order[c];

@@ -118,6 +118,16 @@ MUTATIONS = [
     ("two-product Vidal tensors without the term coefficients", "statevec.c",
      "cmp_mul(&u, &c[t], &ul);", "u = ul;",
      [P.test_two_product_vidal_form_matches_the_state_vector]),
+    ("gate update: theta without the middle weights", "mpsgate.c",
+     "      cmp_scale(&x, &x, &wc[be]);\n", "",
+     [P.test_mps_gate_update_matches_the_state_vector]),
+    ("gate update: right tensor without the conjugate", "mpsgate.c",
+     "cmp_t u; cmp_conj(&u, &Vm[(size_t)(s * d + ga) + (size_t)j * C]);",
+     "cmp_t u = Vm[(size_t)(s * d + ga) + (size_t)j * C];",
+     [P.test_mps_gate_update_matches_the_state_vector]),
+    ("gate update: kept weights not renormalised", "mpsgate.c",
+     "mp t; mp_div(&t, &sg[order[be]], &nrm);", "mp t = sg[order[be]];",
+     [P.test_mps_gate_update_matches_the_state_vector, P.test_mps_gate_update_truncation_keeps_the_schmidt_fidelity]),
     ("conjugate-transpose product without the conjugate", "products.c",
      "if (opA) cmp_mul_conj(&t,", "if (opA) cmp_mul(&t,",
      [P.test_matmul_matches_exact_rationals]),

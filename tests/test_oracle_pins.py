@@ -819,3 +819,71 @@ def test_footnote_circuit_state_is_the_two_product_vidal_state():
     for x in range(1 << sites):
         for p in range(2):
             assert abs(fr(got[x, p]) - fr(ref[x, p])) <= Fraction(1, 2**290) * 2 ** sites
+
+
+def _entangled_state(n=6):
+    sv = oracle.Statevector(n)
+    U4 = dyadic_unitary(4, layers=7, seed=5)
+    G = to_words_matrix([[U4[r][c] for r in range(4)] for c in range(4)], 4)
+    for s in (0, 2, 4, 1, 3):
+        sv.apply2(s, G)
+    return sv
+
+
+def test_mps_gate_update_matches_the_state_vector():
+    """The oracle's two-site update of a Vidal MPS (theta contraction, one-sided Jacobi SVD of the reshaped
+    tensor, split back; Section 2) applied to the Vidal form of an entangled 6-qubit state gives, at every
+    bond, the state vector's amplitudes after the same gate to 2^-300, the Schmidt values of the new state
+    at that cut, and canonical updated sites; the identity gate leaves the weights as they were."""
+    n = 6
+    sv = _entangled_state(n)
+    chi, g, lam = sv.vidal()
+    U4 = dyadic_unitary(4, layers=9, seed=11)
+    G = to_words_matrix([[U4[r][c] for r in range(4)] for c in range(4)], 4)
+    one, zero = Fraction(1), Fraction(0)
+    I4 = to_words_matrix([[(one if r == c else zero, zero) for r in range(4)] for c in range(4)], 4)
+    for site in range(n - 1):
+        chi2, g2, lam2, disc = oracle.mps_apply2(n, chi, g, lam, oracle.WORDS, site, G)
+        assert disc == 0.0
+        ref = oracle.Statevector(n); ref.set(sv.amplitudes()); ref.apply2(site, G)
+        got = oracle.mps_amplitudes(n, chi2, g2, lam2, oracle.WORDS)
+        want = ref.amplitudes()
+        for x in range(1 << n):
+            for p in range(2):
+                assert abs(fr(got[x, p]) - fr(want[x, p])) <= Fraction(1, 2**300), (site, x)
+        s2 = ref.schmidt2(site + 1)
+        lo = int(sum(chi2[:site]))
+        for k in range(int(chi2[site])):
+            assert abs(fr(lam2[lo + k]) ** 2 - fr(s2[k])) <= Fraction(1, 2**290)
+        _check_canonical(n, chi2, g2, lam2, 1, [site, site + 1])
+        chi3, _, lam3, _ = oracle.mps_apply2(n, chi, g, lam, oracle.WORDS, site, I4)
+        assert list(chi3) == list(chi)
+        for k in range(len(lam)):
+            assert abs(fr(lam3[k]) - fr(lam[k])) <= Fraction(1, 2**300)
+
+
+def test_mps_gate_update_truncation_keeps_the_schmidt_fidelity():
+    """Truncating the updated bond to its leading Schmidt value (r_max = 1) reports the discarded weight
+    1 - sigma_0^2 / sum sigma^2, renormalises (weight 1, norm 1), and leaves a state whose overlap with the
+    exact one is |<psi|psi_1>|^2 = sigma_0^2 / sum sigma^2, the fidelity of a Schmidt truncation."""
+    n = 6
+    sv = _entangled_state(n)
+    chi, g, lam = sv.vidal()
+    U4 = dyadic_unitary(4, layers=9, seed=11)
+    G = to_words_matrix([[U4[r][c] for r in range(4)] for c in range(4)], 4)
+    site = 2
+    chi1, g1, lam1, disc = oracle.mps_apply2(n, chi, g, lam, oracle.WORDS, site, G, r_max=1)
+    assert chi1[site] == 1 and abs(fr(lam1[int(sum(chi1[:site]))]) - 1) <= Fraction(1, 2**300)
+    ref = oracle.Statevector(n); ref.set(sv.amplitudes()); ref.apply2(site, G)
+    s2 = ref.schmidt2(site + 1)
+    tot = sum(fr(x) for x in s2)
+    keep = fr(s2[0]) / tot
+    assert abs(Fraction(disc) - (1 - keep)) <= Fraction(1, 2**50)
+    got = oracle.mps_amplitudes(n, chi1, g1, lam1, oracle.WORDS)
+    want = ref.amplitudes()
+    norm = sum(fr(got[x, 0]) ** 2 + fr(got[x, 1]) ** 2 for x in range(1 << n))
+    assert abs(norm - 1) <= Fraction(1, 2**290)
+    ov = (Fraction(0), Fraction(0))
+    for x in range(1 << n):
+        ov = cadd(ov, cmul(cconj((fr(want[x, 0]), fr(want[x, 1]))), (fr(got[x, 0]), fr(got[x, 1]))))
+    assert abs(ov[0] ** 2 + ov[1] ** 2 - keep) <= Fraction(1, 2**280)
