@@ -13,6 +13,7 @@ Plain, slow, independent CPU implementation of what the accurate-eigensolve path
 * ``Statevector.vidal``: the Vidal MPS of a state from its Schmidt decompositions at every cut;
 * ``mps_two_products``: the Vidal MPS of a sum of two product states at any qubit count, such as the
   state of the paper's footnote example;
+* ``mps_sample``: a bit string from the Born distribution of a canonical MPS by the chain rule;
 * ``mps_apply2``: one two-site gate update of a Vidal MPS (theta, SVD, truncation, split back);
 * ``svd``: one-sided Jacobi singular value decomposition at 320 bits (the SVD variant of the gate update);
 * ``Statevector.expect1`` and ``mps_expect1``: one-qubit expectation values, from the state vector by
@@ -98,6 +99,8 @@ def load_library(path: str):
     L.oracle_mps_amplitudes.argtypes = [I, P, P, P, I, P, I]
     L.oracle_mps_two_products.restype = I
     L.oracle_mps_two_products.argtypes = [I, P, P, I, I, P, P, P, I]
+    L.oracle_mps_sample.restype = I
+    L.oracle_mps_sample.argtypes = [I, P, P, P, I, P, P, P, I]
     L.oracle_mps_apply2.restype = I
     L.oracle_mps_apply2.argtypes = [I, P, P, P, I, I, P, I, I, I, P, P, P, I, ctypes.POINTER(D)]
     L.oracle_svd.restype = I
@@ -314,6 +317,18 @@ def mps_apply2(n, chi, gammas, lambdas, w, site, G, tol_log2=300, r_max=1 << 20,
     dims3 = [1] + [int(c) for c in chi_o] + [1]
     used = sum(2 * dims3[k] * dims3[k + 1] for k in range(n))
     return chi_o, gam_o[:used], lam_o[:int(chi_o.sum())], disc.value
+
+
+def mps_sample(n, chi, gammas, lambdas, w, u, w_out=WORDS):
+    """A bit string drawn from the Born distribution of a canonical Vidal MPS by the chain rule, with the
+    uniform numbers u (n of them, in [0, 1)) passed in: returns (bits, probability words)."""
+    chi = np.ascontiguousarray(chi, dtype=np.int32)
+    g = _c(gammas); l = _c(lambdas) if len(lambdas) else np.zeros(1); u = _c(u)
+    bits = np.zeros(n, dtype=np.int32); prob = np.zeros(w_out)
+    if _load().oracle_mps_sample(n, chi.ctypes.data, g.ctypes.data, l.ctypes.data, w, u.ctypes.data,
+                                 bits.ctypes.data, prob.ctypes.data, w_out):
+        raise ValueError("bad arguments to oracle_mps_sample")
+    return bits, prob
 
 
 def svd(M, m, n, w_out=WORDS):

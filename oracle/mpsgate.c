@@ -158,3 +158,55 @@ int oracle_mps_apply2(int n, const int* chi, const double* gam, const double* la
   free(wl); free(wc); free(wr); free(T); free(M); free(Vm); free(sg); free(order);
   return rc;
 }
+
+/* Sampling a bit string from a Vidal MPS in canonical form, by the chain rule of its Born probabilities:
+ * with the left vector l^(k)_beta = (Gamma[0]^{s_0} lam[0] Gamma[1]^{s_1} ... lam[k-1] Gamma[k]^{s_k})_beta, the
+ * marginal of the prefix s_0..s_k is p = sum over beta of |l^(k)_beta|^2 lam[k]_beta^2 (lam[n-1] = 1), because the
+ * sites to the right are orthonormal in the weights.  Site k takes s_k = 1 when u[k] >= p(prefix, 0) /
+ * p(prefix) (inverse CDF with the uniform numbers u passed in), else 0.  bits receives the string, prob the
+ * probability of the whole string (w_out words).  Returns 0, or 1 on bad arguments. */
+int oracle_mps_sample(int n, const int* chi, const double* gam, const double* lam, int w, const double* u,
+                      int* bits, double* prob, int w_out) {
+  if (n < 1 || w < 1) return 1;
+  int maxc = 1;
+  for (int k = 0; k < n - 1; ++k) if (chi[k] > maxc) maxc = chi[k];
+  cmp_t* lv = (cmp_t*)malloc(sizeof(cmp_t) * maxc);
+  cmp_t* nv[2];
+  nv[0] = (cmp_t*)malloc(sizeof(cmp_t) * maxc);
+  nv[1] = (cmp_t*)malloc(sizeof(cmp_t) * maxc);
+  cmp_zero(&lv[0]); mp_from_double(&lv[0].re, 1.0);      /* the empty prefix */
+  mp pprev; mp_from_double(&pprev, 1.0);
+  size_t go = 0, lo = 0;
+  for (int k = 0; k < n; ++k) {
+    const int a = k == 0 ? 1 : chi[k - 1], b = k == n - 1 ? 1 : chi[k];
+    mp pk[2];
+    for (int s = 0; s < 2; ++s) {
+      mp_zero(&pk[s]);
+      for (int be = 0; be < b; ++be) {
+        cmp_t acc, x, t; cmp_zero(&acc);
+        for (int al = 0; al < a; ++al) {
+          ld(&x, gam, go + ((size_t)s * a + al) * b + be, w);
+          cmp_mul(&t, &lv[al], &x); cmp_add(&acc, &acc, &t);
+        }
+        nv[s][be] = acc;
+        mp m2, wt; cmp_abs2(&m2, &acc);
+        if (k < n - 1) { mp_from_words(&wt, lam + (lo + be) * w, w); mp_mul(&wt, &wt, &wt); mp_mul(&m2, &m2, &wt); }
+        mp_add(&pk[s], &pk[s], &m2);
+      }
+    }
+    mp thr, uu; mp_div(&thr, &pk[0], &pprev); mp_from_double(&uu, u[k]);
+    const int s = mp_cmp(&uu, &thr) >= 0 ? 1 : 0;
+    bits[k] = s;
+    pprev = pk[s];
+    /* carry the chosen branch, weighted by lam[k] for the next site */
+    for (int be = 0; be < b; ++be) {
+      lv[be] = nv[s][be];
+      if (k < n - 1) { mp wt; mp_from_words(&wt, lam + (lo + be) * w, w); cmp_scale(&lv[be], &lv[be], &wt); }
+    }
+    go += (size_t)2 * a * b;
+    if (k < n - 1) lo += chi[k];
+  }
+  mp_to_words(&pprev, prob, w_out);
+  free(lv); free(nv[0]); free(nv[1]);
+  return 0;
+}

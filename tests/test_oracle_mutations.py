@@ -128,6 +128,9 @@ MUTATIONS = [
     ("gate update: kept weights not renormalised", "mpsgate.c",
      "mp t; mp_div(&t, &sg[order[be]], &nrm);", "mp t = sg[order[be]];",
      [P.test_mps_gate_update_matches_the_state_vector, P.test_mps_gate_update_truncation_keeps_the_schmidt_fidelity]),
+    ("sampling marginals without the Schmidt weights", "mpsgate.c",
+     "if (k < n - 1) { mp_from_words(&wt, lam + (lo + be) * w, w); mp_mul(&wt, &wt, &wt); mp_mul(&m2, &m2, &wt); }",
+     "(void)wt;", [P.test_mps_sampling_follows_the_born_rule]),
     ("conjugate-transpose product without the conjugate", "products.c",
      "if (opA) cmp_mul_conj(&t,", "if (opA) cmp_mul(&t,",
      [P.test_matmul_matches_exact_rationals]),

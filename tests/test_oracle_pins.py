@@ -887,3 +887,33 @@ def test_mps_gate_update_truncation_keeps_the_schmidt_fidelity():
     for x in range(1 << n):
         ov = cadd(ov, cmul(cconj((fr(want[x, 0]), fr(want[x, 1]))), (fr(got[x, 0]), fr(got[x, 1]))))
     assert abs(ov[0] ** 2 + ov[1] ** 2 - keep) <= Fraction(1, 2**280)
+
+
+def test_mps_sampling_follows_the_born_rule():
+    """Chain-rule sampling from the canonical Vidal MPS of an entangled 6-qubit state: every bit string x is
+    returned for uniform numbers inside its inverse-CDF cell (built here from the state vector's |psi_x|^2
+    in the same site order), with the probability |psi_x|^2 to 2^-290; and the cells' lengths sum to 1."""
+    n = 6
+    sv = _entangled_state(n)
+    chi, g, lam = sv.vidal()
+    amp = sv.amplitudes()
+    p = [fr(amp[x, 0]) ** 2 + fr(amp[x, 1]) ** 2 for x in range(1 << n)]
+    assert abs(sum(p) - 1) <= Fraction(1, 2**290)
+
+    def marginal(prefix):                                   # sum of p over strings starting with prefix
+        k = len(prefix)
+        base = sum(b << (n - 1 - i) for i, b in enumerate(prefix))
+        return sum(p[base + r] for r in range(1 << (n - k)))
+
+    for x in range(1 << n):
+        if p[x] < Fraction(1, 2**200):
+            continue
+        bits = [(x >> (n - 1 - i)) & 1 for i in range(n)]
+        u = []
+        for k in range(n):                                  # midpoint of the cell of bit k given the prefix
+            m_all, m0 = marginal(bits[:k]), marginal(bits[:k] + [0])
+            lo, hi = (Fraction(0), m0 / m_all) if bits[k] == 0 else (m0 / m_all, Fraction(1))
+            u.append(float((lo + hi) / 2))
+        got, prob = oracle.mps_sample(n, chi, g, lam, oracle.WORDS, u)
+        assert list(got) == bits, x
+        assert abs(fr(prob) - p[x]) <= Fraction(1, 2**290), x
