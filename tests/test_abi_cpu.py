@@ -155,3 +155,35 @@ def test_empty_batches_return_ok_before_any_device_work(zkq):
     assert L.zkq_eigh_batched(ctx, 0, None, None, None, 3, None, None, None, None) == zkq.ZKQ_EINVAL
     assert L.zkq_rqi_refine(ctx, 0, None, None, None, 4, None, None, 3, 1, None, None, None, None, None) == zkq.ZKQ_EINVAL
     assert L.zkq_eigh_batched(ctx, -1, one, off, None, 4, None, None, None, None) == zkq.ZKQ_EINVAL
+
+
+def test_header_is_plain_c_and_links(zkq, tmp_path):
+    """include/zkq.h is a C header (C99, no C++ constructs, every declaration a plain function of
+    pointers and sizes): a C program that includes it and takes the address of every declared entry
+    point compiles with -Wall -Werror, links against libzkq.so, and calls the entry points that need no
+    GPU."""
+    syms = declared_symbols()
+    body = "\n".join(f"  table[{i}] = (void (*)(void)){s};" for i, s in enumerate(syms))
+    src = tmp_path / "c_abi.c"
+    src.write_text(f"""#include <stdio.h>
+#include <string.h>
+#include "zkq.h"
+int main(void) {{
+  void (*table[{len(syms)}])(void);
+{body}
+  size_t b = 0;
+  if (zkq_workspace_size(NULL, 1, NULL, 4, 4, ZKQ_OA_OZAKI, &b) != ZKQ_EINVAL) return 1;
+  if (strncmp(zkq_status_string(ZKQ_OK), "ZKQ_OK", 6) != 0) return 2;
+  if (zkq_profile_classes() < 1) return 3;
+  printf("%d\\n", (int)(sizeof(table) / sizeof(table[0])));
+  return 0;
+}}
+""")
+    exe = tmp_path / "c_abi"
+    libdir = os.path.dirname(zkq.LIB_PATH)
+    subprocess.run(["gcc", "-std=c99", "-Wall", "-Wextra", "-Werror", "-pedantic",
+                    f"-I{os.path.join(ROOT, 'include')}", str(src), f"-L{libdir}", "-lzkq", f"-Wl,-rpath,{libdir}",
+                    "-o", str(exe)], check=True, capture_output=True, text=True)
+    out = subprocess.run([str(exe)], capture_output=True, text=True, timeout=60)
+    assert out.returncode == 0, (out.returncode, out.stderr)
+    assert int(out.stdout.strip()) == len(syms)
