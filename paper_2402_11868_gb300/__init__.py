@@ -342,6 +342,87 @@ class MPS:
 
 
 # --------------------------------------------------------------------------------------------------
+# the remaining entry points under their C names (thin forms of the classes above)
+def zkq_status_string(status: int) -> str:
+    return lib().zkq_status_string(status).decode()
+
+
+def zkq_last_cuda_error() -> int:
+    return lib().zkq_last_cuda_error()
+
+
+def zkq_profile_classes() -> int:
+    return lib().zkq_profile_classes()
+
+
+def zkq_profile_class_name(cls: int) -> str:
+    return lib().zkq_profile_class_name(cls).decode()
+
+
+def zkq_ctx_create(device: int = 0, **config) -> Context:
+    return Context(device, **config)
+
+
+def zkq_ctx_destroy(ctx: Context):
+    ctx.close()
+
+
+def zkq_ctx_workspace_bytes(ctx: Context) -> int:
+    return ctx.workspace_bytes()
+
+
+def zkq_autotune_jacobi(ctx: Context, sizes, a_words: int = 4, reps: int = 2):
+    return ctx.autotune_jacobi(sizes, a_words, reps)
+
+
+def zkq_plan_create(ctx: Context, n, a_off, a_words: int, target_words: int = 0) -> Plan:
+    return Plan(ctx, n, a_off, a_words, target_words)
+
+
+def zkq_plan_execute(plan: Plan, A, W, V, info, W_out=None, V_out=None, err_est=None, rinfo=None, stream=None):
+    plan.execute(A, W, V, info, W_out, V_out, err_est, rinfo, stream)
+
+
+def zkq_plan_execute_graph(plan: Plan, A, W, V, info, W_out=None, V_out=None, err_est=None, rinfo=None,
+                           stream=None):
+    plan.execute_graph(A, W, V, info, W_out, V_out, err_est, rinfo, stream)
+
+
+def zkq_plan_destroy(plan: Plan):
+    plan.close()
+
+
+def zkq_mps_create(ctx: Context, n_qubits: int, r_max: int, words: int = 4) -> MPS:
+    return MPS(ctx, n_qubits, r_max, words)
+
+
+def zkq_mps_destroy(mps: MPS):
+    mps.close()
+
+
+def zkq_mps_bond_dims(mps: MPS):
+    return mps.bond_dims()
+
+
+def zkq_mps_download(mps: MPS, stream=None):
+    return mps.download(stream)
+
+
+def zkq_mps_upload(mps: MPS, chi, gammas, lambdas, stream=None):
+    mps.upload(chi, gammas, lambdas, stream)
+
+
+def zkq_mps_apply1q(ctx: Context, mps: MPS, site: int, U, stream=None):
+    if ctx is not mps.ctx:
+        raise ValueError("zkq_mps_apply1q: the MPS uses the context it was created with")
+    mps.apply1q(site, U, stream)
+
+
+def zkq_mps_apply2q(ctx: Context, mps: MPS, site: int, G, trunc_tau=0.0, method=ZKQ_OA_OZAKI, stream=None):
+    return mps.apply2q(site, G, trunc_tau, method, stream, ctx=ctx)
+
+
+# --------------------------------------------------------------------------------------------------
 # batch helpers (host-side packing; no arithmetic of the method)
 def batch_offsets(ns):
     """Element offsets a_off and eigenvalue offsets w_off for a list of matrix orders."""

@@ -187,3 +187,13 @@ int main(void) {{
     out = subprocess.run([str(exe)], capture_output=True, text=True, timeout=60)
     assert out.returncode == 0, (out.returncode, out.stderr)
     assert int(out.stdout.strip()) == len(syms)
+
+
+def test_binding_has_every_entry_point_under_its_c_name(zkq):
+    """The Python binding offers each declared entry point under the same name (argument marshalling
+    only); the GPU-free ones return what the library returns."""
+    missing = [s for s in declared_symbols() if not callable(getattr(zkq, s, None))]
+    assert not missing, missing
+    assert zkq.zkq_status_string(zkq.ZKQ_EINVAL).startswith("ZKQ_EINVAL")
+    assert zkq.zkq_profile_classes() >= 1 and zkq.zkq_profile_class_name(0) == "jacobi"
+    assert isinstance(zkq.zkq_last_cuda_error(), int)
