@@ -355,24 +355,36 @@ def test_residual_and_orthonormality_match_exact_values():
 
 def test_footnote_golden_schmidt_values():
     """tests/golden/footnote_schmidt.txt: the paper's footnote example (Section 1) with U = Z, for the
-    control sequences listed there; the state vector's squared Schmidt coefficients at the cut between
-    the controls and the target are exactly 1 - 2^e and 2^e."""
+    control sequences listed there; the squared Schmidt coefficients at the cut between the controls and
+    the target are 1 - 2^e and 2^e (the state vector up to n = 12, the two-product Vidal form beyond)."""
     import os
     path = os.path.join(os.path.dirname(__file__), "golden", "footnote_schmidt.txt")
     rows = [l.split() for l in open(path) if l.strip() and not l.startswith("#")]
     assert rows
     Z = np.zeros((4, 2, 1)); Z[0, 0, 0] = 1.0; Z[3, 0, 0] = -1.0
+    one, zero = Fraction(1), Fraction(0)
     for n_s, pattern, e_s in rows:
         n, e = int(n_s), int(e_s)
         assert len(pattern) == n - 1
-        sv = oracle.Statevector(n)
-        sv.set(_exact_pm_state(n))
-        ctrl = [int(c) for c in pattern] + [-1]     # qubit n-1 .. qubit 1 are sites 0 .. n-2; the target is last
-        sv.apply_mcu(n - 1, ctrl, Z)
-        lam2 = sv.schmidt2(n - 1)
         eps = Fraction(2) ** e
-        assert abs(fr(lam2[0]) - (1 - eps)) <= Fraction(1, 2**300), (n, pattern)
-        assert abs(fr(lam2[1]) - eps) <= Fraction(1, 2**300), (n, pattern)
+        ctrl = [int(c) for c in pattern]             # qubit n-1 .. qubit 1 are sites 0 .. n-2; the target is last
+        if n <= 12:
+            sv = oracle.Statevector(n)
+            sv.set(_exact_pm_state(n))
+            sv.apply_mcu(n - 1, ctrl + [-1], Z)
+            l0, l1 = (fr(x) for x in sv.schmidt2(n - 1))
+            tol = Fraction(1, 2**300)
+        else:                                        # |+..+>|-> + |c> (Z - 1)|->, unnormalised, norm^2 2^n
+            plus, minus = ((one, zero), (one, zero)), ((one, zero), (-one, zero))
+            e_ = lambda b: (((one, zero), (zero, zero)) if b == 0 else ((zero, zero), (one, zero)))
+            vecs = [[plus] * (n - 1) + [minus], [e_(b) for b in ctrl] + [((zero, zero), (Fraction(2), zero))]]
+            V, C = _two_product_words(vecs, [(one, zero), (one, zero)])
+            chi, _, lam = oracle.mps_two_products(V, C)
+            tot = Fraction(2) ** n
+            l0, l1 = fr(lam[-2]) ** 2 / tot, fr(lam[-1]) ** 2 / tot
+            tol = Fraction(1, 2**290)                # Gram products and a 2 x 2 eigensolve per cut
+        assert abs(l0 - (1 - eps)) <= tol, (n, pattern)
+        assert abs(l1 - eps) <= tol, (n, pattern)
 
 
 def _site_words(a, b, entry, w=8):
