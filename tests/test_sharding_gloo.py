@@ -56,7 +56,10 @@ def test_two_gloo_ranks_cover_every_problem_once():
     ns = W.batch_sizes(1, count=64)
     ctx = mp.get_context("spawn")
     q = ctx.Queue()
-    port = 29500 + (os.getpid() % 1000)
+    import socket
+    with socket.socket() as sk:                 # a port that is free now (the ranks bind it right after)
+        sk.bind(("127.0.0.1", 0))
+        port = sk.getsockname()[1]
     procs = [ctx.Process(target=_worker, args=(r, 2, port, ns, q)) for r in range(2)]
     for p in procs:
         p.start()
