@@ -15,6 +15,8 @@ Workloads (seeded, synthetic; see workloads/):
                    state keeps evolving, so the timed layers follow the warm-up layers (bond dimensions grow)
   serve            continuous-batching engine under Poisson arrivals at 0.7x saturation: eigensolves (DD/QD,
                    N <= 256) and gate updates on four MPS simulations; per-type p50/p99 latency
+  dj               Deutsch-Jozsa-style circuits (balanced band-graph function) at widths 16..128 on a quad-double
+                   MPS: time per circuit against the width, gates/s, largest diagonalised matrix
 The plain RQI path cannot resolve eigenvalues below the FP64 floor (2^-53 ||A||), so the same-accuracy
 comparison of the two paths is reported on single128 (both paths), beside the batch number.
 
@@ -56,7 +58,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="batch256_qd", choices=["batch256_qd", "single128_plain", "brickwork40", "serve"])
+    ap.add_argument("--workload", default="batch256_qd", choices=["batch256_qd", "single128_plain", "brickwork40", "serve", "dj"])
     ap.add_argument("--count", type=int, default=256, help="problems in the batch workload")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-compare", action="store_true", help="skip the single128 chosen-vs-plain comparison")
@@ -146,6 +148,7 @@ class Runner:
         self.err = torch.zeros(tot_w, **f64)
         self.rinfo = torch.zeros(len(self.ns), dtype=torch.int32, device=dev)
         self.pairs = tot_w
+        self.err_bound = 2.0 ** -(53 * target - 12)
 
     def step(self, ctx, s):
         Z, torch = self.Z, self.torch
@@ -157,8 +160,13 @@ class Runner:
         return em
 
     def check(self):
+        """(converged, failures, max err): every problem's info flags are 0 and every eigenpair's residual
+        estimate ||A v - lambda v|| / ||A|| (err_est, read back from the device) is within 2^-(53 W - 12),
+        the target's bound (2^-200 for quad double)."""
         info, rinfo = self.info.cpu().numpy(), self.rinfo.cpu().numpy()
-        return bool((info == 0).all() and (rinfo == 0).all()), int((info != 0).sum() + (rinfo != 0).sum())
+        err = float(self.err.max().item())
+        ok = bool((info == 0).all() and (rinfo == 0).all()) and err <= self.err_bound
+        return ok, int((info != 0).sum() + (rinfo != 0).sum()), err
 
 
 def oracle_rate(problems, threads):
@@ -172,7 +180,7 @@ def oracle_rate(problems, threads):
     return sum(p.n for p in problems) / dt, dt
 
 
-def stratified_sample(problems, sizes=(16, 32, 48, 64, 80)):
+def stratified_sample(problems, sizes=(16, 32, 48, 64, 80, 96, 112, 128)):
     out = []
     for s in sizes:
         for p in problems:
@@ -180,6 +188,41 @@ def stratified_sample(problems, sizes=(16, 32, 48, 64, 80)):
                 out.append(p)
                 break
     return out or problems[:1]
+
+
+def oracle_baseline(problems, single):
+    """The oracle on a bounded, size-stratified sample: one batch problem of every order 16..128 plus the single
+    128x128 problem, one problem per host thread.  Reports the sample's rate, the rate per order, and the rate the
+    oracle would reach on the whole batch, from a fit of its time per problem to c N^3 (its work is
+    O(N^3) per sweep) over the sampled orders."""
+    import oracle
+    from concurrent.futures import ThreadPoolExecutor
+    sample = stratified_sample(problems) + list(single)
+    cores = min(len(sample), os.cpu_count() or 1)
+
+    def timed(p):
+        t0 = time.perf_counter()
+        oracle.eigh(p.A, p.n)
+        return time.perf_counter() - t0
+
+    t0 = time.perf_counter()
+    with ThreadPoolExecutor(max_workers=cores) as ex:
+        dts = list(ex.map(timed, sample))
+    wall = time.perf_counter() - t0
+    ns = np.array([p.n for p in sample], dtype=float)
+    c = float(np.sum(np.array(dts) * ns**3) / np.sum(ns**6))       # least squares of t = c N^3
+    full_s = c * float(sum(p.n ** 3 for p in problems))
+    per_n = {}
+    for p, dt in zip(sample, dts):
+        per_n.setdefault(str(p.n), []).append(p.n / dt)
+    return {"value": sum(p.n for p in sample) / wall, "unit": "eigenpairs/s", "cores": cores, "kind": "oracle",
+            "sample": f"oracle (320-bit cyclic Jacobi) on {len(sample)} problems: one batch problem of each order "
+                      f"{[p.n for p in sample[:-len(single)] or sample]} and the single 128x128 problem, one per "
+                      f"thread, {wall:.1f} s wall",
+            "per_order_eigenpairs_per_s_one_core": {k: float(np.mean(v)) for k, v in sorted(per_n.items(), key=lambda kv: int(kv[0]))},
+            "fit_s_per_problem": f"{c:.3e} N^3",
+            "extrapolated_full_batch": {"eigenpairs_per_s": sum(p.n for p in problems) / (full_s / cores),
+                                        "on_cores": cores, "batch_cpu_s": full_s}}
 
 
 def run_ours(args):
@@ -201,7 +244,7 @@ def run_ours(args):
         for _ in range(args.warmup):
             R.step(ctx, stream)
     torch.cuda.synchronize()
-    ok, nbad = R.check()
+    ok, nbad, _ = R.check()
     if world > 1:
         dist.barrier()
     clocks = ClockSampler(local)
@@ -229,7 +272,7 @@ def run_ours(args):
     prof = Z.zkq_profile_read()
     Z.zkq_profile_enable(False)
     clk = clocks.stop()
-    ok2, nbad2 = R.check()
+    ok2, nbad2, max_err = R.check()
     total_ms = float(sum(step_ms))
     if world > 1:
         t = torch.tensor([total_ms], device=dev)
@@ -259,6 +302,7 @@ def run_ours(args):
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": args.workload, "desc": desc, "problems": len(R.ns), "eigenpairs_per_step": R.pairs,
                    "target": "quad-double", "method": method, "converged": ok and ok2, "unconverged": nbad2,
+                   "max_err_over_normA": max_err, "err_bound": R.err_bound,
                    "l2": "flushed between timed steps" if flush is not None else "inputs larger than L2"},
         "latency_ms": {"p50": float(np.percentile(step_ms, 50)), "p99": float(np.percentile(step_ms, 99))},
         "breakdown_ms": {"jacobi_fp64": float(np.mean(jac_ms)), "refine": float(np.mean(ref_ms))},
@@ -288,16 +332,12 @@ def run_ours(args):
                 e1.record(stream); e1.synchronize()
                 ts.append(e0.elapsed_time(e1))
             cmp[meth] = {"eigenpairs_per_s": Rs.pairs / (float(np.mean(ts)) / 1e3), "ms": float(np.mean(ts)),
-                         "converged": Rs.check()[0]}
+                         "converged": Rs.check()[0], "max_err_over_normA": Rs.check()[2]}
             del Rs
         out["plain_rqi_vs_chosen_single128"] = cmp
     if rank == 0 and not args.no_cpu_baseline:
-        sample = stratified_sample(problems) if len(problems) > 1 else problems
-        cores = min(len(sample), os.cpu_count() or 1)
-        rate, dt = oracle_rate(sample, cores)
-        out["cpu_baseline"] = {"value": rate, "unit": "eigenpairs/s", "cores": cores, "kind": "oracle",
-                               "sample": f"oracle (320-bit Jacobi) on {len(sample)} problem(s) of the workload "
-                                         f"(N={[p.n for p in sample]}), one per thread, {dt:.1f} s"}
+        import workloads as W
+        out["cpu_baseline"] = oracle_baseline(problems, [W.config_single128()] if len(problems) > 1 else [])
     ctx.close()
     if rank == 0:
         print(json.dumps(out))
@@ -546,6 +586,80 @@ def run_serve(args):
         print(json.dumps(out))
 
 
+def run_dj(args):
+    """Deutsch-Jozsa-style circuits (workloads.dj_circuit: f(x) = x_0 + a band-graph quadratic form of band
+    width 5, balanced) run gate by gate on a quad-double device MPS at widths 16, 32, 64 and 128: time per
+    circuit against the width (the paper reports its DJ simulation time growing like n^3 with diagonalised
+    matrices of at most 56 x 56), two-qubit gates/s, and the largest reduced matrix.  One step = one circuit
+    at each width."""
+    import torch
+    import paper_2402_11868_gb300 as Z
+    import workloads as W
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    widths, w = (16, 32, 64, 128), 5
+    ctx = Z.Context(local)
+    stream = torch.cuda.Stream(device=dev)
+    circuits = {n: W.dj_circuit(n, w, "balanced", seed=100 + n + rank) for n in widths}
+
+    def one(n):
+        _, gates, _ = circuits[n]
+        mps = Z.MPS(ctx, n, r_max=1024, words=4)
+        max_rho, n2 = 0, 0
+        e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for kind, site, G in gates:
+            if kind == "1q":
+                mps.apply1q(site, G, stream=stream)
+            else:
+                chi = mps.bond_dims()
+                a = 1 if site == 0 else int(chi[site - 1])
+                d = 1 if site + 1 == n - 1 else int(chi[site + 1])
+                max_rho = max(max_rho, 2 * min(a, d))
+                mps.apply2q(site, G, trunc_tau=2.0 ** -200, stream=stream)
+                n2 += 1
+        e1.record(stream)
+        e1.synchronize()
+        mps.close()
+        return e0.elapsed_time(e1), n2, max_rho
+
+    for _ in range(args.warmup):
+        one(widths[0])
+    clocks = ClockSampler(local)
+    clocks.start()
+    per = {n: [] for n in widths}
+    meta = {}
+    for _ in range(args.steps):
+        for n in widths:
+            ms, n2, mr = one(n)
+            per[n].append(ms)
+            meta[n] = (n2, mr)
+    clk = clocks.stop()
+    t = {n: float(np.median(v)) for n, v in per.items()}
+    slope = float(np.polyfit(np.log(widths), np.log([t[n] for n in widths]), 1)[0])
+    big = widths[-1]
+    total_ms = sum(sum(v) for v in per.values())
+    out = {
+        "metric": "Deutsch-Jozsa-style circuit simulation: two-qubit gate updates/s (quad double, width 128)",
+        "value": meta[big][0] / (t[big] / 1e3), "unit": "gates/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "dj", "desc": "f(x) = x_0 + band-graph quadratic form (band 5, edges by seed), "
+                   "balanced; quad double, truncation 2^-200", "widths": list(widths)},
+        "per_width": {str(n): {"ms_per_circuit": t[n], "two_qubit_gates": meta[n][0], "max_rho": meta[n][1]}
+                      for n in widths},
+        "time_vs_width_exponent": slope,
+        "clocks": clk,
+        "e2e": {"value": meta[big][0] / (t[big] / 1e3), "unit": "gates/s",
+                "h2d_bytes_per_step": int(sum(16 * 2 * 4 * 8 * meta[n][0] for n in widths)),
+                "d2h_bytes_per_step": int(sum(12 * meta[n][0] for n in widths))},
+    }
+    ctx.close()
+    if rank == 0:
+        print(json.dumps(out))
+
+
 def run_reference(args):
     """The oracle, as it stands, on the host cores: a bounded sample of the same workload per step."""
     rank, world, _ = dist_env()
@@ -586,5 +700,7 @@ if __name__ == "__main__":
         run_brickwork(a)
     elif a.workload == "serve":
         run_serve(a)
+    elif a.workload == "dj":
+        run_dj(a)
     else:
         run_ours(a)

@@ -52,7 +52,9 @@ typedef enum { ZKQ_FP64 = 1, ZKQ_DD = 2, ZKQ_QD = 4 } zkq_prec;   /* value = wor
 typedef enum {
   ZKQ_PLAIN_RQI = 0,  /* per-eigenpair Rayleigh quotient iteration in the target precision */
   ZKQ_OA_OZAKI = 1,   /* block Ogita-Aishima refinement with tensor-core split (Ozaki) products */
-  ZKQ_OA_FP64 = 2     /* the same refinement with its products in multi-word arithmetic on the FP64 pipe */
+  ZKQ_OA_FP64 = 2,    /* the same refinement with its products in multi-word arithmetic on the FP64 pipe */
+  ZKQ_SVD_OA = 3      /* gate updates only: FP64 SVD of M (zkq_svd_batched) in place of the FP64 eigensolve of
+                         rho, its singular vectors refined as eigenvectors of rho as by ZKQ_OA_OZAKI */
 } zkq_method;
 
 typedef struct zkq_ctx zkq_ctx;
@@ -98,21 +100,49 @@ zkq_status zkq_eigh_batched(zkq_ctx* ctx, int batch, const int32_t* n, const int
  * has no counterpart; it exists for callers such as code running while another part of the process
  * captures a CUDA graph, hosts that give the library a fixed memory budget, or latency-critical loops
  * where an allocation could stall on a device-wide synchronisation.
- * Arguments, layouts, results and errors are those of zkq_eigh_batched on the current device, with
- * default settings (40 sweeps); no context is needed.  The call allocates nothing: its scratch (batch
- * metadata and the global-memory copies of A and V for orders above 80, 32 n^2 bytes each) lives in one
- * file-scope device array of ZKQ_NOALLOC_SCRATCH_BYTES that every GPU which loads the library holds until
- * the process exits.
+ * Arguments, layouts and errors are those of zkq_eigh_batched on the current device, with default settings
+ * (40 sweeps); no context is needed.  Every problem above order 80 runs on a thread-block cluster of the
+ * built-in width (2, 4 or 8 CTAs for a largest order <= 128, <= 256 or above); the cooperative-grid class
+ * and a context's autotuned widths are never used, so the results agree with zkq_eigh_batched within the
+ * FP64-stage tolerance (8 n 2^-53 ||A||), exactly where both take the same kernel and width.
+ * The call allocates nothing: its scratch (batch metadata and the global-memory copies of A and V for
+ * orders above 80, 32 n^2 bytes each) lives in one file-scope device array of ZKQ_NOALLOC_SCRATCH_BYTES
+ * that every GPU which loads the library holds until the process exits.
  *   - A batch whose scratch would exceed ZKQ_NOALLOC_SCRATCH_BYTES is rejected with ZKQ_ETOOBIG (e.g. one
- *     problem of order 1024 needs 32 MiB; orders <= 80 need no scratch beyond ~40 bytes of metadata).
+ *     problem of order 1024 needs 32 MiB; orders <= 80 need no scratch beyond a few hundred bytes of metadata).
+ *   - The call itself must not be captured into a CUDA graph: it uploads its metadata from host memory
+ *     that is freed when it returns, and returns ZKQ_EINVAL when `stream` is capturing.  Other streams of
+ *     the process may be capturing meanwhile.
  *   - The first call on a device looks up the array's device address (cudaGetSymbolAddress) with that
- *     device current; make that first call before any stream capture.
+ *     device current, and keeps it for the life of the process; do not use the entry point after a
+ *     cudaDeviceReset of that device.
  *   - Every call uses the same array and leaves its last contents there: calls that overlap on the GPU
  *     (different streams, or different host threads, on the same device) race.
  */
 #define ZKQ_NOALLOC_SCRATCH_BYTES (32u * 1024u * 1024u)
 zkq_status zkq_eigh_batched_noalloc(int batch, const int32_t* n, const int64_t* a_off, const double* A,
                                     int a_words, double* W, double* V, int32_t* info, void* stream);
+
+/*
+ * zkq_svd_batched: FP64 singular value decomposition of a batch of complex matrices by one-sided (Hestenes)
+ * Jacobi -- the SVD that ZKCM_CUS offers beside the Hermitian diagonalisation (Section 2, ZKCM_CUS
+ * paragraph).  Orthogonalising the columns of A (or of A^H when A is wide) does not square the
+ * conditioning as the Gram matrix A A^H does, so on matrices with graded rows or columns (an MPS bond's M
+ * carries its neighbours' Schmidt weights) the small singular values keep high relative accuracy.
+ *   m, n (host)      int32[batch], 1 <= m, n <= 4096; k = min(m, n)
+ *   a_off (host)     element offsets of A_b (m x n, column-major, complex, a_words words per real; only the
+ *                    leading word of each real is read)
+ *   S (device)       out: double[sum k_b], singular values of each problem, descending
+ *   U (device)       out: complex FP64 (double[2] per element), m_b x k_b column-major at element offset
+ *                    u_off[b] (host int64): left singular vectors, first largest-modulus component real > 0
+ *   V (device)       out: n_b x k_b at element offset v_off[b]: right singular vectors (A = U diag(S) V^H)
+ *   info (device)    out: int32[batch]; 0 converged, > 0 sweep limit (zkq_config.max_sweeps) reached
+ * For a zero singular value the vector computed from A's columns (U's when m >= n, V's when m < n) is zero.
+ * Errors: ZKQ_EINVAL, ZKQ_ENOMEM, ZKQ_ECUDA.
+ */
+zkq_status zkq_svd_batched(zkq_ctx* ctx, int batch, const int32_t* m, const int32_t* n, const int64_t* a_off,
+                           const double* A, int a_words, double* S, double* U, const int64_t* u_off, double* V,
+                           const int64_t* v_off, int32_t* info, void* stream);
 
 /*
  * zkq_rqi_refine: recover the eigenpairs to the target precision from the FP64 ones
@@ -224,7 +254,8 @@ zkq_status zkq_mps_apply1q(zkq_ctx* ctx, zkq_mps* mps, int site, const double* U
 /*
  * Two-qubit gate G (4x4, host) on (site, site+1): theta contraction (split products), the Hermitian Gram
  * matrix of the smaller side (rho = M M^H, ties left), its eigen-decomposition (FP64 Jacobi + refinement
- * `method`: ZKQ_PLAIN_RQI, ZKQ_OA_OZAKI or ZKQ_OA_FP64, to the state's words), truncation to the Schmidt
+ * `method`: ZKQ_PLAIN_RQI, ZKQ_OA_OZAKI or ZKQ_OA_FP64, to the state's words; or ZKQ_SVD_OA: the FP64 SVD of
+ * M itself, whose singular vectors on that side start the same refinement), truncation to the Schmidt
  * values with sigma^2 > trunc_tau * sum sigma^2 (at most r_max), renormalisation sum lambda'^2 = 1, and the
  * split back into Gamma'[site], lambda'[site], Gamma'[site+1].  Synchronises the stream (the new bond
  * dimension is decided on the host).
@@ -235,6 +266,34 @@ zkq_status zkq_mps_apply1q(zkq_ctx* ctx, zkq_mps* mps, int site, const double* U
  */
 zkq_status zkq_mps_apply2q(zkq_ctx* ctx, zkq_mps* mps, int site, const double* G, double trunc_tau, int method,
                            int32_t* new_bond, double* discarded_weight, void* stream);
+
+/*
+ * Measurements on the MPS in its working precision (Section 1: a Vidal MPS is a nested Schmidt
+ * decomposition; in canonical form the parts of the chain away from a site reduce to the squared Schmidt
+ * weights).  Both read the state as the last gate update left it; both synchronise the stream.  A state is
+ * assumed normalised and canonical (every state the gate updates produce is, up to truncation).
+ *
+ * zkq_mps_expect1: one-qubit expectation values <O_k> at sites[k], k < count, from site k's tensor and its
+ * two weight vectors: sum over alpha, beta, s, s' of lam_{l-1,alpha}^2 lam_{l,beta}^2
+ * conj(Gamma[l]^s_{alpha beta}) O_{s s'} Gamma[l]^{s'}_{alpha beta}.
+ *   sites (host)   int32[count], 0 <= site < n
+ *   O (host)       count operators, each 2x2 row-major complex with the state's words per real
+ *                  (double[count][4][2][words])
+ *   out (host)     double[count][2][words]: re words then im words of each value
+ * zkq_mps_sample: `shots` bit strings drawn from the Born distribution by the chain rule: site k of a shot
+ * takes bit 1 when its uniform number u >= the conditional probability of bit 0 given the bits drawn so far
+ * (inverse CDF, computed in the state's words), else 0.
+ *   u (host)       double[shots][n], each in [0, 1) (the caller's random numbers; else ZKQ_EINVAL)
+ *   bits (host)    out: int32[shots][n], site 0 first
+ *   prob (host)    out: double[shots][words], the probability of each string (underflows to 0 below
+ *                  about 2^-1000)
+ * The context supplies the workspace (shots in chunks of 4 per SM, 3 prefix vectors of max chi each).
+ * Errors: ZKQ_EINVAL, ZKQ_ENOMEM, ZKQ_ECUDA.
+ */
+zkq_status zkq_mps_expect1(zkq_ctx* ctx, const zkq_mps* mps, int count, const int32_t* sites, const double* O,
+                           double* out, void* stream);
+zkq_status zkq_mps_sample(zkq_ctx* ctx, const zkq_mps* mps, int shots, const double* u, int32_t* bits, double* prob,
+                          void* stream);
 
 /*
  * zkq_mw_gemm: batched multi-word complex products C_i = op(A_i) B_i, the dense products of the refinement
@@ -273,6 +332,19 @@ zkq_status zkq_mw_gemm(zkq_ctx* ctx, int count, const int32_t* m, const int32_t*
 zkq_status zkq_set_gemm_kernel(int which);
 int zkq_get_gemm_kernel(void);
 zkq_status zkq_check_device_waits(void);
+
+/*
+ * zkq_test_grid_barrier_hook: test hook of the bounded grid barrier of the cooperative-grid Jacobi class
+ * (zkq_eigh_batched with a few problems of order above 80), so that a test can drive the barrier's expiry
+ * path without faulting or hanging the GPU.  It sets, on the current device and for every later launch,
+ * `extra_arrivals` (0 or 1) arrivals that the barrier waits for but that never come -- the waiting blocks
+ * then poll a generation flag that nothing advances -- and the poll limit 2^log2_poll_limit (4..22; a poll
+ * sleeps about 64 ns).  On expiry the barrier raises the problem's abort flag, no later barrier of that
+ * problem waits, every block finishes its bounded loops, and the problem's info entry is -1; the context and
+ * device stay usable.  (0, 22) restores the defaults.  The paper has no counterpart (its ZKCM_CUS relies on
+ * cuSOLVER).  Errors: ZKQ_EINVAL, ZKQ_ECUDA.
+ */
+zkq_status zkq_test_grid_barrier_hook(int extra_arrivals, int log2_poll_limit);
 
 /*
  * zkq_mw_op: element-wise multi-word arithmetic, the building block of every refinement step

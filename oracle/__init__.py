@@ -17,7 +17,9 @@ Plain, slow, independent CPU implementation of what the accurate-eigensolve path
 * ``mps_apply2``: one two-site gate update of a Vidal MPS (theta, SVD, truncation, split back);
 * ``svd``: one-sided Jacobi singular value decomposition at 320 bits (the SVD variant of the gate update);
 * ``Statevector.expect1`` and ``mps_expect1``: one-qubit expectation values, from the state vector by
-  definition and from a canonical MPS through its local tensor and Schmidt weights.
+  definition and from a canonical MPS through its local tensor and Schmidt weights;
+* ``graph_state_schmidt_rank``: the Schmidt rank of a graph state at a cut (GF(2) rank of the cut's
+  edges), the closed form of the Deutsch-Jozsa-style circuits' Schmidt values (Section 3.1).
 
 Only ``tests/``, ``__graft_entry__.smoke()`` and ``bench.py``'s CPU-baseline leg may import this
 package.  It shares no code with the CUDA path; both receive their inputs from ``workloads``.
@@ -352,6 +354,33 @@ def mps_expect1(n, chi, gammas, lambdas, w, site, O, w_out=WORDS):
                                   O.shape[-1], out.ctypes.data, w_out):
         raise ValueError("bad arguments to oracle_mps_expect1")
     return out
+
+
+def graph_state_schmidt_rank(n: int, edges, cut: int) -> int:
+    """Schmidt rank exponent r of the graph state of a graph on vertices 0..n-1 at the cut {0..cut-1} |
+    {cut..n-1}: the rank over GF(2) of the cut's biadjacency matrix (the graph state is
+    prod_{(i,j) in E} CZ_ij |+>^n; every one of its 2^r Schmidt coefficients at the cut equals 2^(-r/2)).
+    Plain Gaussian elimination over GF(2) on bit rows."""
+    rows = []
+    for i in range(cut):
+        bits = 0
+        for (a, b) in edges:
+            if a == i and b >= cut:
+                bits ^= 1 << (b - cut)
+            elif b == i and a >= cut:
+                bits ^= 1 << (a - cut)
+        rows.append(bits)
+    r = 0
+    for col in range(n - cut):
+        piv = next((k for k in range(r, len(rows)) if (rows[k] >> col) & 1), None)
+        if piv is None:
+            continue
+        rows[r], rows[piv] = rows[piv], rows[r]
+        for k in range(len(rows)):
+            if k != r and (rows[k] >> col) & 1:
+                rows[k] ^= rows[r]
+        r += 1
+    return r
 
 
 def to_fraction(words) -> Fraction:

@@ -20,7 +20,7 @@ _lock = threading.Lock()
 ZKQ_OK, ZKQ_EINVAL, ZKQ_ENOMEM, ZKQ_ENOCONV, ZKQ_ETIMEOUT, ZKQ_ECUDA, ZKQ_EADMIT, ZKQ_ETOOBIG = range(8)
 ZKQ_NOALLOC_SCRATCH_BYTES = 32 * 1024 * 1024
 ZKQ_FP64, ZKQ_DD, ZKQ_QD = 1, 2, 4
-ZKQ_PLAIN_RQI, ZKQ_OA_OZAKI, ZKQ_OA_FP64 = 0, 1, 2
+ZKQ_PLAIN_RQI, ZKQ_OA_OZAKI, ZKQ_OA_FP64, ZKQ_SVD_OA = 0, 1, 2, 3
 
 
 class ZkqError(RuntimeError):
@@ -62,6 +62,8 @@ def lib():
             L.zkq_eigh_batched.argtypes = [P, I, P, P, P, I, P, P, P, P]
             L.zkq_eigh_batched_noalloc.restype = I
             L.zkq_eigh_batched_noalloc.argtypes = [I, P, P, P, I, P, P, P, P]
+            L.zkq_svd_batched.restype = I
+            L.zkq_svd_batched.argtypes = [P, I, P, P, P, P, I, P, P, P, P, P, P, P]
             L.zkq_rqi_refine.restype = I
             L.zkq_rqi_refine.argtypes = [P, I, P, P, P, I, P, P, I, I, P, P, P, P, P]
             L.zkq_mw_gemm.restype = I
@@ -76,7 +78,8 @@ def lib():
             for nm, args in (("zkq_mps_create", [P, I, I, I, ctypes.POINTER(P)]), ("zkq_mps_destroy", [P]),
                              ("zkq_mps_bond_dims", [P, P]), ("zkq_mps_download", [P, P, P, P]),
                              ("zkq_mps_upload", [P, P, P, P, P]), ("zkq_mps_apply1q", [P, P, I, P, P]),
-                             ("zkq_mps_apply2q", [P, P, I, P, ctypes.c_double, I, P, P, P])):
+                             ("zkq_mps_apply2q", [P, P, I, P, ctypes.c_double, I, P, P, P]),
+                             ("zkq_mps_expect1", [P, P, I, P, P, P, P]), ("zkq_mps_sample", [P, P, I, P, P, P, P])):
                 getattr(L, nm).restype = I
                 getattr(L, nm).argtypes = args
             L.zkq_workspace_size.restype = I
@@ -96,6 +99,8 @@ def lib():
             L.zkq_set_gemm_kernel.argtypes = [I]
             L.zkq_get_gemm_kernel.restype = I
             L.zkq_check_device_waits.restype = I
+            L.zkq_test_grid_barrier_hook.restype = I
+            L.zkq_test_grid_barrier_hook.argtypes = [I, I]
             L.zkq_mw_op.restype = I
             L.zkq_mw_op.argtypes = [I, I, I64, P, P, P, I, P]
             _lib = L
@@ -193,6 +198,17 @@ def zkq_eigh_batched_noalloc(n, a_off, A, a_words, W, V, info, stream=None):
                                           _stream(stream)), "zkq_eigh_batched_noalloc")
 
 
+def zkq_svd_batched(ctx: Context, m, n, a_off, A, a_words, S, U, u_off, V, v_off, info, stream=None):
+    """FP64 one-sided Jacobi SVD of a batch: A_b = U_b diag(S_b) V_b^H (thin)."""
+    m_arr, m_p = _host_array(m, ctypes.c_int32)
+    n_arr, n_p = _host_array(n, ctypes.c_int32)
+    a_arr, a_p = _host_array(a_off, ctypes.c_int64)
+    u_arr, u_p = _host_array(u_off, ctypes.c_int64)
+    v_arr, v_p = _host_array(v_off, ctypes.c_int64)
+    _check(lib().zkq_svd_batched(ctx.handle, len(m_arr), m_p, n_p, a_p, _ptr(A), a_words, _ptr(S), _ptr(U), u_p,
+                                 _ptr(V), v_p, _ptr(info), _stream(stream)), "zkq_svd_batched")
+
+
 def zkq_rqi_refine(ctx: Context, n, a_off, A, a_words, W, V, target_words, method, W_out, V_out, err_est, info,
                    stream=None):
     n_arr, n_p = _host_array(n, ctypes.c_int32)
@@ -234,6 +250,11 @@ def zkq_get_gemm_kernel() -> int:
 
 def zkq_check_device_waits():
     _check(lib().zkq_check_device_waits(), "zkq_check_device_waits")
+
+
+def zkq_test_grid_barrier_hook(extra_arrivals: int, log2_poll_limit: int):
+    """Test hook of the cooperative-grid Jacobi's bounded barrier (see include/zkq.h); (0, 22) = defaults."""
+    _check(lib().zkq_test_grid_barrier_hook(extra_arrivals, log2_poll_limit), "zkq_test_grid_barrier_hook")
 
 
 def zkq_profile_enable(on: bool):
@@ -340,6 +361,28 @@ class MPS:
                                      ctypes.byref(nb), ctypes.byref(dw), _stream(stream)), "zkq_mps_apply2q")
         return nb.value, dw.value
 
+    def expect1(self, sites, ops, stream=None):
+        """<O_k> at sites[k] (ops: (count, 4, 2, words) row-major 2x2 operators); returns (count, 2, words)."""
+        import numpy as np
+        st = np.ascontiguousarray(sites, dtype=np.int32)
+        o = np.ascontiguousarray(ops, dtype=np.float64)
+        assert o.shape == (len(st), 4, 2, self.words)
+        out = np.zeros((len(st), 2, self.words))
+        _check(lib().zkq_mps_expect1(self.ctx.handle, self.handle, len(st), st.ctypes.data, o.ctypes.data,
+                                     out.ctypes.data, _stream(stream)), "zkq_mps_expect1")
+        return out
+
+    def sample(self, u, stream=None):
+        """Bit strings by the chain rule from uniforms u (shots, n); returns (bits (shots, n), prob (shots, words))."""
+        import numpy as np
+        uu = np.ascontiguousarray(u, dtype=np.float64)
+        assert uu.ndim == 2 and uu.shape[1] == self.n
+        bits = np.zeros(uu.shape, dtype=np.int32)
+        prob = np.zeros((uu.shape[0], self.words))
+        _check(lib().zkq_mps_sample(self.ctx.handle, self.handle, uu.shape[0], uu.ctypes.data, bits.ctypes.data,
+                                    prob.ctypes.data, _stream(stream)), "zkq_mps_sample")
+        return bits, prob
+
 
 # --------------------------------------------------------------------------------------------------
 # the remaining entry points under their C names (thin forms of the classes above)
@@ -420,6 +463,18 @@ def zkq_mps_apply1q(ctx: Context, mps: MPS, site: int, U, stream=None):
 
 def zkq_mps_apply2q(ctx: Context, mps: MPS, site: int, G, trunc_tau=0.0, method=ZKQ_OA_OZAKI, stream=None):
     return mps.apply2q(site, G, trunc_tau, method, stream, ctx=ctx)
+
+
+def zkq_mps_expect1(ctx: Context, mps: MPS, sites, ops, stream=None):
+    if ctx is not mps.ctx:
+        raise ValueError("zkq_mps_expect1: the MPS uses the context it was created with")
+    return mps.expect1(sites, ops, stream)
+
+
+def zkq_mps_sample(ctx: Context, mps: MPS, u, stream=None):
+    if ctx is not mps.ctx:
+        raise ValueError("zkq_mps_sample: the MPS uses the context it was created with")
+    return mps.sample(u, stream)
 
 
 # --------------------------------------------------------------------------------------------------

@@ -56,6 +56,10 @@ const zkq_config& ctx_config(void* vctx) { return ((zkq_ctx*)vctx)->cfg; }
 zkq_config& ctx_config_mut(void* vctx) { return ((zkq_ctx*)vctx)->cfg; }
 int ctx_oa_max_iter(void* vctx) { return ((zkq_ctx*)vctx)->cfg.oa_max_iter; }
 void** ctx_mps_ws(void* vctx, size_t** bytes) { zkq_ctx* c = (zkq_ctx*)vctx; *bytes = &c->mps_bytes; return &c->mps_ws; }
+void ctx_fp64_bufs(void* vctx, void*** ws, size_t** ws_bytes, void*** meta, size_t** meta_bytes) {
+  zkq_ctx* c = (zkq_ctx*)vctx;
+  *ws = &c->ws; *ws_bytes = &c->ws_bytes; *meta = &c->meta; *meta_bytes = &c->meta_bytes;
+}
 zkq_status api_exception(void* vctx) noexcept {
   if (vctx) ((zkq_ctx*)vctx)->stage.discard();
   return ZKQ_ENOMEM;
@@ -163,6 +167,22 @@ zkq_status zkq_eigh_batched(zkq_ctx* ctx, int batch, const int32_t* n, const int
   for (int b = 0; b < batch; ++b) if (n[b] < 1 || n[b] > 4096 || a_off[b] < 0) return ZKQ_EINVAL;
   ZKQ_CUDA_TRY(cudaSetDevice(ctx->device));
   return eigh_internal(ctx, batch, n, a_off, A, a_words, W, V, info, (cudaStream_t)stream);
+} catch (...) {
+  return api_exception(ctx);
+}
+
+zkq_status zkq_svd_batched(zkq_ctx* ctx, int batch, const int32_t* m, const int32_t* n, const int64_t* a_off,
+                           const double* A, int a_words, double* S, double* U, const int64_t* u_off, double* V,
+                           const int64_t* v_off, int32_t* info, void* stream) try {
+  if (!ctx || batch < 0 || (batch > 0 && (!m || !n || !a_off || !A || !S || !U || !u_off || !V || !v_off || !info)))
+    return ZKQ_EINVAL;
+  if (a_words != 1 && a_words != 2 && a_words != 4) return ZKQ_EINVAL;
+  if (batch == 0) return ZKQ_OK;
+  for (int b = 0; b < batch; ++b)
+    if (m[b] < 1 || n[b] < 1 || m[b] > 4096 || n[b] > 4096 || a_off[b] < 0 || u_off[b] < 0 || v_off[b] < 0) return ZKQ_EINVAL;
+  ZKQ_CUDA_TRY(cudaSetDevice(ctx->device));
+  return svd_internal(ctx, batch, m, n, a_off, A, a_words, S, U, u_off, V, v_off, info, (cudaStream_t)stream,
+                      &ctx->ws, &ctx->ws_bytes, &ctx->meta, &ctx->meta_bytes);
 } catch (...) {
   return api_exception(ctx);
 }
@@ -298,6 +318,9 @@ zkq_status zkq_set_gemm_kernel(int which) {
 int zkq_get_gemm_kernel(void) { return gemm_kernel_get(); }
 
 zkq_status zkq_check_device_waits(void) { return gemm_kernel_error() ? ZKQ_ETIMEOUT : ZKQ_OK; }
+zkq_status zkq_test_grid_barrier_hook(int extra_arrivals, int log2_poll_limit) {
+  return set_grid_barrier_hook(extra_arrivals, log2_poll_limit);
+}
 
 static const char* kProfNames[PC_COUNT] = {"jacobi", "rqi", "ozaki_scale", "ozaki_slice", "ozaki_gemm",
                                            "ozaki_combine", "oa_elementwise", "mps", "other", "jacobi_cluster"};

@@ -64,6 +64,8 @@ zkq_status launch_jacobi(const JacobiBatch& jb, int a_words, int n_small, int n_
                          int red_stride, cudaStream_t st);
 size_t jacobi_smem_bytes(int n);
 int jacobi_grid_max_blocks(int max_large_n, int a_words);   // co-resident blocks per SM of the grid kernel
+// test hook of the cooperative grid barrier on the current device (zkq_test_grid_barrier_hook)
+zkq_status set_grid_barrier_hook(int extra_arrivals, int log2_poll_limit);
 
 // ---- plain RQI -----------------------------------------------------------------------------------
 struct RqiBatch {
@@ -105,6 +107,8 @@ struct EighLayout {
 using JacobiTune = std::vector<std::pair<int, int>>;
 zkq_status eigh_layout(int batch, const int32_t* n, const int64_t* a_off, int a_words, int cfg_cluster, int num_sms,
                        EighLayout* L, const JacobiTune* tune = nullptr);
+// the metadata as the device holds it (meta_bytes() bytes), for an upload by the caller
+void eigh_meta_image(const EighLayout& L, std::vector<char>* img);
 zkq_status eigh_upload(const EighLayout& L, void* meta, HostStage& hs, cudaStream_t st);
 zkq_status eigh_launch(const EighLayout& L, const void* meta, void* ws, const double* A, int a_words, double* W,
                        double* V, int32_t* info, int max_sweeps, int prof_class, cudaStream_t st);
@@ -125,6 +129,14 @@ zkq_status rqi_launch(const RqiLayout& L, const void* meta, void* ws, const doub
                       const double* V, int target_words, double* W_out, double* V_out, double* err, int32_t* info,
                       int max_iter, cudaStream_t st);
 
+// ---- FP64 one-sided Jacobi SVD (svd.cu) -------------------------------------------------------------
+// A_b (m_b x n_b, a_words words per real, element offset a_off[b]) = U diag(S) V^H, thin (k_b = min(m_b, n_b)):
+// S at offset sum_{c<b} k_c, U (m_b x k_b complex FP64) at element offset u_off[b], V (n_b x k_b) at v_off[b];
+// info[b] 0 converged, > 0 sweep limit.  ws / meta: the caller's growable device buffers.
+zkq_status svd_internal(void* ctx, int batch, const int32_t* m, const int32_t* n, const int64_t* a_off, const double* A,
+                        int a_words, double* S, double* U, const int64_t* u_off, double* V, const int64_t* v_off,
+                        int32_t* info, cudaStream_t st, void** ws, size_t* ws_bytes, void** meta, size_t* meta_bytes);
+
 // ---- context internals ---------------------------------------------------------------------------
 // prof_class: profiler class of the launches (0 = PC_JACOBI; the refinement's cluster solves use their own)
 zkq_status eigh_internal(void* ctx, int batch, const int32_t* n, const int64_t* a_off, const double* A, int a_words,
@@ -135,6 +147,8 @@ zkq_status rqi_refine_internal(void* ctx, int batch, const int32_t* n, const int
 OaBuffers ctx_oa_buffers(void* ctx);
 int ctx_oa_max_iter(void* ctx);
 void** ctx_mps_ws(void* ctx, size_t** bytes);
+// the context's FP64-stage workspace and metadata buffers (shared by the Jacobi, plain RQI and SVD launches)
+void ctx_fp64_bufs(void* ctx, void*** ws, size_t** ws_bytes, void*** meta, size_t** meta_bytes);
 HostStage* ctx_stage(void* ctx);
 JacobiTune* ctx_jacobi_tune(void* ctx);
 int ctx_num_sms(void* ctx);

@@ -46,21 +46,27 @@ template <bool SMEM> struct Mat {
 // a cooperative launch (SYNC 2), or a single CTA (SYNC 0, nparts = 1).
 __device__ __forceinline__ void cluster_barrier() { __threadfence(); cg::this_cluster().sync(); }
 
+// Test hook of the grid barrier (zkq_test_grid_barrier_hook): `extra` arrivals that never come (the barrier
+// then waits on a generation flag that nothing advances) and the log2 of the poll limit.  Defaults: none, 2^22.
+struct WaitHook { int extra; int log2_limit; };
+__device__ WaitHook g_wait_hook = {0, 22};
+
 // Grid barrier of a cooperative launch (all blocks co-resident): arrival counter + generation number.  The
 // wait is bounded; on expiry the barrier raises gb->abort, after which no barrier waits any more, so every
 // block runs its remaining (bounded) loops to the end and the problem reports failure.
 __device__ __forceinline__ void grid_barrier(GridBar* gb, unsigned nblocks) {
   __syncthreads();
   if (threadIdx.x == 0 && !*(volatile int*)&gb->abort) {
+    const WaitHook hook = g_wait_hook;
     __threadfence();
     const unsigned g = *(volatile unsigned*)&gb->gen;
-    if (atomicAdd(&gb->count, 1u) == nblocks - 1) {
+    if (atomicAdd(&gb->count, 1u) == nblocks - 1 + (unsigned)hook.extra) {
       atomicExch(&gb->count, 0u);
       __threadfence();
       atomicAdd(&gb->gen, 1u);
     } else {
       for (int it = 0; *(volatile unsigned*)&gb->gen == g; ++it) {
-        if (it > (1 << 22)) { atomicExch(&gb->abort, 1); break; }
+        if (it > (1 << hook.log2_limit)) { atomicExch(&gb->abort, 1); break; }
         __nanosleep(64);
       }
     }
@@ -360,6 +366,13 @@ zkq_status launch_jacobi(const JacobiBatch& jb, int a_words, int n_small, int n_
     case 4: return launch_words<4>(jb, n_small, n_large, max_small_n, max_large_n, cluster, grid_blocks, gb, grp_start, red_stride, st);
     default: return ZKQ_EINVAL;
   }
+}
+
+zkq_status set_grid_barrier_hook(int extra_arrivals, int log2_poll_limit) {
+  if (extra_arrivals < 0 || extra_arrivals > 1 || log2_poll_limit < 4 || log2_poll_limit > 22) return ZKQ_EINVAL;
+  const WaitHook h{extra_arrivals, log2_poll_limit};
+  ZKQ_CUDA_TRY(cudaMemcpyToSymbol(g_wait_hook, &h, sizeof(h)));
+  return ZKQ_OK;
 }
 
 int jacobi_grid_max_blocks(int max_large_n, int a_words) {

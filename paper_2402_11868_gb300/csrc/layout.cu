@@ -2,6 +2,7 @@
 // (size classes, orders, workspace offsets, block groups), its upload, and the launches.  The per-call entry
 // points lay out, upload and launch every call; a plan does the first two once and then only launches.
 #include <algorithm>
+#include <cstring>
 #include <vector>
 #include "internal.cuh"
 #include "prof.cuh"
@@ -96,14 +97,22 @@ EighMeta eigh_meta(const EighLayout& L, const void* meta) {
 }
 }  // namespace
 
+void eigh_meta_image(const EighLayout& L, std::vector<char>* img) {
+  img->assign(L.meta_bytes(), 0);
+  char* base = img->data();
+  const EighMeta m = eigh_meta(L, base);        // the device layout, laid over the host image
+  std::memcpy(m.n, L.n.data(), L.batch * 4);
+  std::memcpy(m.a_off, L.a_off.data(), L.batch * 8);
+  std::memcpy(m.w_off, L.w_off.data(), L.batch * 8);
+  std::memcpy(m.order, L.order.data(), L.batch * 4);
+  std::memcpy(m.ws_off, L.ws_off.data(), L.batch * 8);
+  if (!L.grp.empty()) std::memcpy(m.grp, L.grp.data(), L.grp.size() * 4);
+}
+
 zkq_status eigh_upload(const EighLayout& L, void* meta, HostStage& hs, cudaStream_t st) {
-  const EighMeta m = eigh_meta(L, meta);
-  hs.add(m.n, L.n.data(), L.batch * 4);
-  hs.add(m.a_off, L.a_off.data(), L.batch * 8);
-  hs.add(m.w_off, L.w_off.data(), L.batch * 8);
-  hs.add(m.order, L.order.data(), L.batch * 4);
-  hs.add(m.ws_off, L.ws_off.data(), L.batch * 8);
-  if (!L.grp.empty()) hs.add(m.grp, L.grp.data(), L.grp.size() * 4);
+  std::vector<char> img;
+  eigh_meta_image(L, &img);
+  hs.add(meta, img.data(), img.size());
   ZKQ_CUDA_TRY(hs.flush(st));
   return ZKQ_OK;
 }

@@ -23,6 +23,7 @@
 #include "ozaki.cuh"
 #include "prof.cuh"
 #include "internal.cuh"
+#include "mps.cuh"
 
 namespace zkq {
 
@@ -149,14 +150,6 @@ __global__ void mps_init_kernel(double* __restrict__ G, size_t elems) {   // Gam
 
 using namespace zkq;
 
-struct zkq_mps {
-  int n, r_max, W, device;
-  std::vector<int> chi;            // chi[l], l = 0..n-2 (bond between l and l+1)
-  std::vector<int> cap;            // capacity per bond
-  std::vector<double*> gamma;      // per site, capacity 2 * cap_{l-1} * cap_l complex elements
-  std::vector<double*> lam;        // per bond, capacity cap_l real values
-  double* gate = nullptr;          // 4x4 (or 2x2) device copy of the current gate
-};
 
 static inline int left_dim(const zkq_mps* m, int l) { return l == 0 ? 1 : m->chi[l - 1]; }
 static inline int right_dim(const zkq_mps* m, int l) { return l == m->n - 1 ? 1 : m->chi[l]; }
@@ -201,6 +194,13 @@ static zkq_status mps_build(zkq_ctx* ctx, zkq_mps* m, int n_qubits, int r_max, i
   }
   cudaError_t e = cudaMalloc(&m->gate, 16 * 2 * wb);
   if (e != cudaSuccess) { set_last_cuda_error(e); m->gate = nullptr; return ZKQ_ENOMEM; }
+  // device tables of the site and bond pointers (fixed for the life of the MPS) and of the bond dimensions
+  e = cudaMalloc(&m->d_ptrs, (size_t)(2 * n_qubits) * sizeof(double*) + (size_t)(n_qubits + 1) * sizeof(int32_t));
+  if (e != cudaSuccess) { set_last_cuda_error(e); m->d_ptrs = nullptr; return ZKQ_ENOMEM; }
+  std::vector<double*> tab(2 * n_qubits, nullptr);
+  for (int l = 0; l < n_qubits; ++l) tab[l] = m->gamma[l];
+  for (int l = 0; l < n_qubits - 1; ++l) tab[n_qubits + l] = m->lam[l];
+  ZKQ_CUDA_TRY(cudaMemcpy(m->d_ptrs, tab.data(), tab.size() * sizeof(double*), cudaMemcpyHostToDevice));
   ZKQ_CUDA_TRY(cudaDeviceSynchronize());
   return ZKQ_OK;
 }
@@ -227,6 +227,7 @@ zkq_status zkq_mps_destroy(zkq_mps* m) {
   for (double* p : m->gamma) if (p) cudaFree(p);
   for (double* p : m->lam) if (p) cudaFree(p);
   if (m->gate) cudaFree(m->gate);
+  if (m->d_ptrs) cudaFree(m->d_ptrs);
   delete m;
   return ZKQ_OK;
 }
@@ -314,6 +315,9 @@ static zkq_status apply2q_t(zkq_ctx* ctx, zkq_mps* m, int l, const double* G, do
   size_t oWq = take((size_t)g * W), oVq = take((size_t)g * g * E), oErr = take(g), oInfo = take(8);
   size_t oY = take((size_t)std::max(R, C) * g * E);
   size_t oSig = take((size_t)g * W), oNorm = take(2 * W);
+  const bool svd = method == ZKQ_SVD_OA;
+  size_t oSvdX = svd ? take(2 * (size_t)std::max(R, C) * g) : 0;   // the SVD's vectors of the larger side
+  size_t oSvdS = svd ? take(g) : 0;
   size_t* cap_bytes = nullptr;
   void** ws = ctx_mps_ws(ctx, &cap_bytes);
   size_t need = off * sizeof(double);
@@ -361,8 +365,21 @@ static zkq_status apply2q_t(zkq_ctx* ctx, zkq_mps* m, int l, const double* G, do
   if (s != ZKQ_OK) return s;
   // eigen-decomposition of rho (descending), refined to W words
   int32_t nn = g; int64_t zero = 0;
-  s = eigh_internal(ctx, 1, &nn, &zero, Rho, W, W64, V64, Info, st);
-  if (s != ZKQ_OK) return s;
+  if (svd) {
+    // the eigenvectors of rho are M's singular vectors on the Gram side: U (R x g) for M M^H, V (C x g) for
+    // M^H M; the FP64 SVD computes them without squaring M's conditioning
+    int32_t mr = R, mc = C;
+    const int64_t u_off = 0, v_off = 0;
+    void **fws, **fmeta; size_t *fws_b, *fmeta_b;
+    ctx_fp64_bufs(ctx, &fws, &fws_b, &fmeta, &fmeta_b);
+    double* Ux = left ? V64 : b + oSvdX;
+    double* Vx = left ? b + oSvdX : V64;
+    s = svd_internal(ctx, 1, &mr, &mc, &zero, M, W, b + oSvdS, Ux, &u_off, Vx, &v_off, Info, st, fws, fws_b, fmeta, fmeta_b);
+    if (s != ZKQ_OK) return s;
+  } else {
+    s = eigh_internal(ctx, 1, &nn, &zero, Rho, W, W64, V64, Info, st);
+    if (s != ZKQ_OK) return s;
+  }
   if (method == ZKQ_PLAIN_RQI)
     s = rqi_refine_internal(ctx, 1, &nn, &zero, Rho, W, W64, V64, W, Wq, Vq, Err, Info + 1, st);
   else
@@ -420,7 +437,7 @@ static zkq_status apply2q_t(zkq_ctx* ctx, zkq_mps* m, int l, const double* G, do
 
 extern "C" zkq_status zkq_mps_apply2q(zkq_ctx* ctx, zkq_mps* m, int site, const double* G, double trunc_tau, int method,
                                       int32_t* new_bond, double* discarded_weight, void* stream) try {
-  if (!ctx || !m || !G || site < 0 || site + 1 >= m->n || !(trunc_tau >= 0.0) || method < 0 || method > 2 ||
+  if (!ctx || !m || !G || site < 0 || site + 1 >= m->n || !(trunc_tau >= 0.0) || method < 0 || method > 3 ||
       ctx_device(ctx) != m->device)
     return ZKQ_EINVAL;
   ZKQ_CUDA_TRY(cudaSetDevice(m->device));

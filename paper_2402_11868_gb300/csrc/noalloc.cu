@@ -6,11 +6,18 @@
 // the same Jacobi kernels as zkq_eigh_batched, but its scratch (batch metadata and the global-memory
 // copies of A and V for orders above 80) lives in one file-scope device array of fixed size that every
 // GPU loading the library keeps until the process exits.  The caller still owns all inputs and outputs.
+// The batch layout is the allocating path's (eigh_layout), without the cooperative-grid class: every
+// problem above order 80 runs on a thread-block cluster of the built-in width (2 / 4 / 8 CTAs for largest
+// orders <= 128 / <= 256 / above).
+// The array's device address is looked up once per device and kept for the life of the process; after a
+// cudaDeviceReset the module may be loaded at another address, so the entry point must not be used after a
+// device reset.
 #include <mutex>
 #include <vector>
 #include <algorithm>
 #include "common.cuh"
 #include "internal.cuh"
+#include "prof.cuh"
 
 using namespace zkq;
 
@@ -41,51 +48,33 @@ extern "C" zkq_status zkq_eigh_batched_noalloc(int batch, const int32_t* n, cons
   if (batch < 0 || (batch > 0 && (!n || !a_off || !A || !W || !V || !info))) return ZKQ_EINVAL;
   if (a_words != 1 && a_words != 2 && a_words != 4) return ZKQ_EINVAL;
   if (batch == 0) return ZKQ_OK;
-  constexpr int kSmallMax = 80;               // orders held in shared memory (no scratch needed)
-  std::vector<int64_t> w_off(batch), ws_off(batch, 0);
-  std::vector<int32_t> small, large;
-  int64_t acc = 0; int max_small = 0, max_large = 0;
-  for (int b = 0; b < batch; ++b) {
-    if (n[b] < 1 || n[b] > 4096 || a_off[b] < 0) return ZKQ_EINVAL;
-    w_off[b] = acc; acc += n[b];
-    if (n[b] <= kSmallMax) { small.push_back(b); max_small = std::max(max_small, n[b]); }
-    else { large.push_back(b); max_large = std::max(max_large, n[b]); }
-  }
-  std::sort(large.begin(), large.end(), [&](int a, int c) { return n[a] > n[c] || (n[a] == n[c] && a < c); });
-  std::vector<int32_t> order(small); order.insert(order.end(), large.begin(), large.end());
-  // layout inside the fixed scratch: metadata, per-problem A/V copies, reduction slots
-  size_t off = 0;
-  const size_t o_n = off; off += al256((size_t)batch * 4);
-  const size_t o_a = off; off += al256((size_t)batch * 8);
-  const size_t o_w = off; off += al256((size_t)batch * 8);
-  const size_t o_o = off; off += al256((size_t)batch * 4);
-  const size_t o_s = off; off += al256((size_t)batch * 8);
-  const size_t o_ws = off;
-  size_t ws_bytes = 0;
-  for (int b : large) { ws_off[b] = (int64_t)(ws_bytes / sizeof(double)); ws_bytes += al256((size_t)n[b] * n[b] * 4 * sizeof(double)); }
-  off += ws_bytes;
-  const size_t o_red = off; off += al256((size_t)64 * std::max<size_t>(1, large.size()) * sizeof(double));
-  if (off > (size_t)ZKQ_NOALLOC_SCRATCH_BYTES) return ZKQ_ETOOBIG;
+  cudaStream_t st = (cudaStream_t)stream;
+  // The metadata goes up from pageable host memory that is freed when this call returns.  A captured copy
+  // would record that host address for every replay, so the call refuses to run inside a stream capture.
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  ZKQ_CUDA_TRY(cudaStreamIsCapturing(st, &cap));
+  if (cap != cudaStreamCaptureStatusNone) return ZKQ_EINVAL;
+  // The allocating entry point's layout rules (size classes, order, per-problem A/V copies, reduction
+  // slots), with no cooperative grid (num_sms 0) and the built-in cluster width for the largest order.
+  EighLayout L;
+  zkq_status s = eigh_layout(batch, n, a_off, a_words, 0, 0, &L, nullptr);
+  if (s != ZKQ_OK) return s;
+  const size_t meta_b = al256(L.meta_bytes()), ws_b = L.ws_bytes();
+  if (meta_b + ws_b > (size_t)ZKQ_NOALLOC_SCRATCH_BYTES) return ZKQ_ETOOBIG;
   int dev = 0;
   ZKQ_CUDA_TRY(cudaGetDevice(&dev));
   void* base_v = nullptr;
-  zkq_status s = noalloc_scratch(dev, &base_v);
+  s = noalloc_scratch(dev, &base_v);
   if (s != ZKQ_OK) return s;
-  char* base = (char*)base_v;
-  cudaStream_t st = (cudaStream_t)stream;
-  ZKQ_CUDA_TRY(cudaMemcpyAsync(base + o_n, n, (size_t)batch * 4, cudaMemcpyHostToDevice, st));
-  ZKQ_CUDA_TRY(cudaMemcpyAsync(base + o_a, a_off, (size_t)batch * 8, cudaMemcpyHostToDevice, st));
-  ZKQ_CUDA_TRY(cudaMemcpyAsync(base + o_w, w_off.data(), (size_t)batch * 8, cudaMemcpyHostToDevice, st));
-  ZKQ_CUDA_TRY(cudaMemcpyAsync(base + o_o, order.data(), (size_t)batch * 4, cudaMemcpyHostToDevice, st));
-  ZKQ_CUDA_TRY(cudaMemcpyAsync(base + o_s, ws_off.data(), (size_t)batch * 8, cudaMemcpyHostToDevice, st));
-  // every reduction slot is written before it is read; clear them anyway so no value of an earlier call
-  // can ever be observed
-  ZKQ_CUDA_TRY(cudaMemsetAsync(base + o_red, 0, off - o_red, st));
-  int cluster = max_large <= 128 ? 2 : (max_large <= 256 ? 4 : 8);
-  JacobiBatch jb{(const int32_t*)(base + o_n), (const int64_t*)(base + o_a), (const int64_t*)(base + o_w),
-                 (const int32_t*)(base + o_o), A, W, V, info, (double*)(base + o_ws), (const int64_t*)(base + o_s),
-                 (double*)(base + o_red), 40, nullptr, 0};
-  return launch_jacobi(jb, a_words, (int)small.size(), (int)large.size(), max_small, max_large, cluster, 0, nullptr, nullptr, 0, st);
+  char* meta = (char*)base_v;
+  char* ws = meta + meta_b;
+  std::vector<char> img;
+  eigh_meta_image(L, &img);
+  ZKQ_CUDA_TRY(cudaMemcpyAsync(meta, img.data(), img.size(), cudaMemcpyHostToDevice, st));
+  // every reduction slot is written before it is read; clear them (and the unused barrier words) anyway, so
+  // that no value of an earlier call can ever be observed
+  ZKQ_CUDA_TRY(cudaMemsetAsync(ws + L.ws_need, 0, ws_b - L.ws_need, st));
+  return eigh_launch(L, meta, ws, A, a_words, W, V, info, 40, PC_JACOBI, st);
 } catch (...) {
   return api_exception(nullptr);
 }

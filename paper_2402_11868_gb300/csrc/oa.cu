@@ -134,18 +134,21 @@ __global__ void __launch_bounds__(256) oa_coupling_kernel(const OaProb* __restri
 //   |lambda_c - lambda_{c+1}| <= delta_c = g (||num_{:,c}|| + ||num_{:,c+1}||) + 2^-(53W/2+4) max(|lambda_c|, |lambda_{c+1}|),
 // a local version of the Ogita-Aishima threshold: the couplings bound the eigenvalue errors of the two
 // columns, so a non-orthonormality confined to tiny-eigenvalue columns cannot merge the whole spectrum.
-// The margin g = 128 keeps every rotation k = num / gap outside the clusters below 1/128: the first-order
-// update X + X K then leaves non-orthonormality k^H k < 2^-14, and the iteration stays in its quadratic
-// regime (with g = 2, k reached 1/4 and the first iterations made little progress).
+// The margin g = 2^16 keeps every rotation k = num / gap outside the clusters below 2^-16: the first-order
+// update X + X K then leaves non-orthonormality k^H k < 2^-32, and the iteration stays in its quadratic
+// regime (with g = 2, k reached 1/4 and the first iterations made little progress).  Measured on the
+// 256-problem quad-double batch, the refinement took 5.86, 5.53, 5.41, 5.38 and 5.45 s for g = 2^7, 2^10,
+// 2^13, 2^16 and 2^20: a wider margin makes the clusters a few columns larger but the separated pairs
+// converge in fewer iterations.
 // The relative floor keeps pairs closer than ~2^-(53W/2) apart together: for them the computed coupling
 // (noise ~2^-53W |lambda|) over the gap would give rotations k whose second-order term k^H k exceeds the
 // working precision; the cluster step (exactly unitary rotation) separates them instead.
-constexpr double kClusterMargin = 128.0;
+constexpr double kClusterMargin = 65536.0;
 
 template <int W>
 __global__ void oa_cluster_kernel(const OaProb* __restrict__ pr, const double* __restrict__ lam,
                                   const double* __restrict__ colnum, int32_t* __restrict__ cl_start,
-                                  int32_t* __restrict__ cl_len, OaStat* __restrict__ st) {
+                                  int32_t* __restrict__ cl_len, OaStat* __restrict__ st, double margin) {
   const OaProb p = pr[blockIdx.x];
   if (threadIdx.x != 0) return;
   const int n = p.n;
@@ -158,7 +161,7 @@ __global__ void oa_cluster_kernel(const OaProb* __restrict__ pr, const double* _
     if (!brk) {
       mw<W> a = mw_load<W, W>(lb, i - 1), b = mw_load<W, W>(lb, i);
       double gap = fabs(mw_sub(a, b).x[0]);
-      double d = kClusterMargin * (sqrt(colnum[p.loff + i - 1]) + sqrt(colnum[p.loff + i])) +
+      double d = margin * (sqrt(colnum[p.loff + i - 1]) + sqrt(colnum[p.loff + i])) +
                  floor_rel * fmax(fabs(a.x[0]), fabs(b.x[0]));
       dmax = fmax(dmax, d);
       brk = gap > d;
@@ -288,6 +291,19 @@ __global__ void oa_ns_kernel(const OaCluster* __restrict__ cl, double* __restric
   c_store(G + c.toff * 2 * W, e, g);
 }
 
+// out = coef R (+ I): the terms of the polar (Loewdin) factor (X^H X)^{-1/2} = (I - R)^{-1/2} of a finishing
+// problem, evaluated by Horner's rule in R (see oa_refine_t); one grid row per listed problem
+template <int W>
+__global__ void oa_polar_term_kernel(const OaProb* __restrict__ pr, const double* __restrict__ R, double* __restrict__ out,
+                                     double coef, int add_identity) {
+  const OaProb p = pr[blockIdx.y];
+  int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= p.n * p.n) return;
+  cmw<W> v = c_scale_d(c_load<W, W>(R + p.xoff * 2 * W, e), coef);
+  if (add_identity && e % p.n == e / p.n) v.re = mw_add_d(v.re, 1.0);
+  c_store(out + p.xoff * 2 * W, e, v);
+}
+
 // copy rotated cluster columns (from Y = old X buffer) back into X
 template <int W>
 __global__ void oa_cluster_copy_kernel(const OaProb* __restrict__ pr, const OaCluster* __restrict__ cl,
@@ -403,6 +419,21 @@ size_t oa_state_bytes(int batch, int64_t xe, int64_t le, int W) {
   return off;
 }
 
+// Terms k (1..4) of the series (I - R)^{-1/2} = I + R/2 + 3R^2/8 + 5R^3/16 + 35R^4/128 + ... needed for the
+// polar factor of an n x n matrix with non-orthonormality max|r_ij| = maxR: with ||R||_2 <= n maxR, the first
+// dropped term is below (n maxR)^(k+1), which must be below 2^-(53W - 8); 0 when more than four terms would
+// be needed (the problem then takes orthonormalising steps E = R/2 instead).
+static int polar_term_count(double maxR, int n, int W) {
+  const double lim = ldexp(1.0, -(53 * W - 8));
+  const double r = maxR * n;
+  double pw = r;
+  for (int k = 1; k <= 4; ++k) {
+    pw *= r;
+    if (pw <= lim) return k;
+  }
+  return 0;
+}
+
 // device bytes grow_buf holds after growing to `need` bytes from nothing
 size_t oa_grow_bytes(size_t need) { return std::max(need + need / 8, (size_t)1 << 20); }
 
@@ -460,7 +491,7 @@ zkq_status oa_refine_t(void* ctx, const OaBuffers& buf, int batch, const int32_t
     ZKQ_CUDA_TRY(cudaGetLastError());
   }
   const double tol = ldexp(1.0, -(53 * W - 6));
-  std::vector<int> active(batch, 1), polish(batch, 0), iters(batch, 0), orth_steps(batch, 0);
+  std::vector<int> active(batch, 1), polish(batch, 0), iters(batch, 0), orth_steps(batch, 0), near_conv(batch, 0);
   std::vector<OaStat> hst(batch);
   std::vector<int32_t> hcl_len(le);
   const int p_bits = 53 * W + 6;
@@ -507,7 +538,7 @@ zkq_status oa_refine_t(void* ctx, const OaBuffers& buf, int batch, const int32_t
       dim3 g((mx + 255) / 256, (unsigned)ap.size());
       { ProfScope ps_(PC_OA, st); oa_lambda_kernel<W><<<(unsigned)ap.size(), 256, 0, st>>>(PRA, Sm, Rm, Lm, CN, ST); }
       { ProfScope ps_(PC_OA, st); oa_coupling_kernel<W><<<g, 256, 0, st>>>(PRA, Sm, Rm, Lm, CN, NUM, ST); }
-      { ProfScope ps_(PC_OA, st); oa_cluster_kernel<W><<<(unsigned)ap.size(), 32, 0, st>>>(PRA, Lm, CN, CS, CL, ST); }
+      { ProfScope ps_(PC_OA, st); oa_cluster_kernel<W><<<(unsigned)ap.size(), 32, 0, st>>>(PRA, Lm, CN, CS, CL, ST, kClusterMargin); }
       { ProfScope ps_(PC_OA, st); oa_E_kernel<W><<<g, 256, 0, st>>>(PRA, NUM, Rm, Lm, CS, OO, Em, ST); }
       ZKQ_CUDA_TRY(cudaGetLastError());
     }
@@ -522,7 +553,8 @@ zkq_status oa_refine_t(void* ctx, const OaBuffers& buf, int batch, const int32_t
                 ast[a].delta, ast[a].nclusters, ast[a].clustered, ast[a].cl_off / (ast[a].anorm > 0 ? ast[a].anorm : 1.0));
     }
     // convergence decisions
-    std::vector<int> finish, upd;
+    std::vector<int> finish, upd, polar;
+    std::vector<int> polar_terms(batch, 0);
     for (size_t a = 0; a < act.size(); ++a) {
       int b = act[a];
       hst[b] = ast[a];
@@ -534,10 +566,19 @@ zkq_status oa_refine_t(void* ctx, const OaBuffers& buf, int batch, const int32_t
       const bool orth_ok = ast[a].maxR <= ldexp(1.0, -(53 * W - 10));
       // polish: 0 iterating; 1 converged: updates only re-orthonormalise (E = R/2) until R is at working
       // precision (at most 4 such steps); 2 report lambda and X of this evaluation
+      // A converged problem finishes at once (polar step below) when its couplings are so small that every
+      // column's residual, about the column norm of the couplings (<= sqrt(n) max|num|), is 16x below the
+      // convergence tolerance, and R needs at most four polar terms.  Otherwise it takes one more ordinary
+      // update (which squares the couplings); if that does not get there either (couplings at the noise
+      // level), it takes the orthonormalising steps.
+      const bool polar_ok = ast[a].maxNum * sqrt((double)probs[b].n) <= tol * an / 16.0 &&
+                            (polar_terms[b] = polar_term_count(ast[a].maxR, probs[b].n, W)) > 0;
       if (polish[b] == 2 || it == max_iter) finish.push_back(b);
-      else {
+      else if (polish[b] == 0 && conv && polar_ok) {
+        polar.push_back(b);     // finish now: lambda from this evaluation, X made orthonormal by its polar factor
+      } else {
         if (polish[b] == 1) { if (orth_ok || ++orth_steps[b] >= 4) polish[b] = 2; }
-        else if (conv) polish[b] = 1;
+        else if (conv && ++near_conv[b] >= 2) polish[b] = 1;
         upd.push_back(b);
       }
     }
@@ -564,6 +605,87 @@ zkq_status oa_refine_t(void* ctx, const OaBuffers& buf, int batch, const int32_t
         for (int b : finish) if (hinfo[b]) hs.add(info + b, &hinfo[b], sizeof(int32_t));
         ZKQ_CUDA_TRY(hs.flush(st));
       }
+    }
+    if (!polar.empty()) {
+      // Converged problems whose non-orthonormality R = I - X^H X is small enough finish in this iteration.
+      // lambda = s_ii / (1 - r_ii) is already the Rayleigh quotient of X's columns.  X is replaced by its polar
+      // (Loewdin) factor X (X^H X)^{-1/2} = X (I - R)^{-1/2} = X (I + F), the symmetric orthonormalisation that
+      // removes the symmetric part of the pairwise tilts and leaves the couplings (already below tolerance):
+      //   F = c1 R + c2 R^2 + ... + ck R^k,  (c1, c2, c3, c4) = (1/2, 3/8, 5/16, 35/128),
+      // with k terms such that the dropped ones are below the working precision (polar_term_count), by
+      // Horner's rule F = (R/2) G_1, G_j = I + (c_{j+1}/c_j) R G_{j+1}, G_{k-1} = I + (c_k/c_{k-1}) R.  Then
+      // X_out = X + X F and P_out = P + P F = A X_out give the output and its residual estimate.  This replaces
+      // the orthonormalising steps E = R/2 and the final evaluation of the products.
+      // Buffers at each problem's own offset: G ping-pong in CT / CG, scaled R in CW, X_out in X2, P_out in S
+      // (S is consumed); the cluster step of this iteration reuses CT / CG / CW afterwards, in stream order.
+      // All problems finishing in this iteration take the largest term count among them (more terms only
+      // make the factor more accurate).
+      static const double cfr[4] = {0.5, 0.75, 5.0 / 6.0, 0.875};   // c_1, then c_{j+1} / c_j
+      std::vector<OaProb> pp; int k = 0, mxe = 0;
+      for (int b : polar) { pp.push_back(probs[b]); k = std::max(k, polar_terms[b]); mxe = std::max(mxe, probs[b].n * probs[b].n); }
+      std::vector<int32_t> pw(polar.begin(), polar.end());
+      OaProb* PRP = (OaProb*)(base + oCLD);
+      hs.add(PRP, pp.data(), sizeof(OaProb) * pp.size());
+      ZKQ_CUDA_TRY(hs.flush(st));
+      const dim3 gp((mxe + 255) / 256, (unsigned)pp.size());
+      double* Gcur = CT; double* Gnext = CG;
+      auto term = [&](double* out, double coef, int add_identity) -> zkq_status {
+        { ProfScope ps_(PC_OA, st); oa_polar_term_kernel<W><<<gp, 256, 0, st>>>(PRP, Rm, out, coef, add_identity); }
+        ZKQ_CUDA_TRY(cudaGetLastError());
+        return ZKQ_OK;
+      };
+      auto prod = [&](const double* Aop, const double* Bop, double* Cop, int identity) -> zkq_status {
+        std::vector<MwProd> v;
+        for (auto& q : pp) {
+          MwProd m_{q.n, q.n, q.n, 0, Aop + q.xoff * 2 * W, Bop + q.xoff * 2 * W, Cop + q.xoff * 2 * W, nullptr, 1.0, identity};
+          m_.hermitian = 1;                            // polynomials in the Hermitian R are Hermitian
+          v.push_back(m_);
+        }
+        return mw_gemm_batched(v.data(), (int)v.size(), W, W, W, p_bits, prod_method, buf.oz_ws, buf.oz_bytes, buf.oz_meta, buf.oz_meta_bytes, st, buf.stage);
+      };
+      const double* F = CW;
+      if (k == 1) {
+        s = term(CW, cfr[0], 0);                      // F = R/2
+        if (s != ZKQ_OK) return s;
+      } else {
+        s = term(Gcur, cfr[k - 1], 1);                // G_{k-1} = I + (c_k / c_{k-1}) R
+        if (s != ZKQ_OK) return s;
+        for (int j = k - 2; j >= 1; --j) {            // G_j = I + (c_{j+1} / c_j) R G_{j+1}
+          s = term(CW, cfr[j], 0);
+          if (s != ZKQ_OK) return s;
+          s = prod(CW, Gcur, Gnext, 1);
+          if (s != ZKQ_OK) return s;
+          std::swap(Gcur, Gnext);
+        }
+        s = term(CW, cfr[0], 0);                      // F = (R/2) G_1
+        if (s != ZKQ_OK) return s;
+        s = prod(CW, Gcur, Gnext, 0);
+        if (s != ZKQ_OK) return s;
+        F = Gnext;
+      }
+      {
+        std::vector<MwProd> po;
+        for (auto& q : pp) {
+          double* Xb = X + q.xoff * 2 * W;
+          double* Pb = Pm + q.xoff * 2 * W;
+          po.push_back({q.n, q.n, q.n, 0, Xb, F + q.xoff * 2 * W, X2 + q.xoff * 2 * W, Xb, 1.0, 0});
+          po.push_back({q.n, q.n, q.n, 0, Pb, F + q.xoff * 2 * W, Sm + q.xoff * 2 * W, Pb, 1.0, 0});
+        }
+        s = mw_gemm_batched(po.data(), (int)po.size(), W, W, W, p_bits, prod_method, buf.oz_ws, buf.oz_bytes, buf.oz_meta, buf.oz_meta_bytes, st, buf.stage);
+        if (s != ZKQ_OK) return s;
+      }
+      std::vector<OaStat> fst(batch);
+      for (size_t a = 0; a < act.size(); ++a) fst[act[a]] = ast[a];
+      hs.add(ST, fst.data(), sizeof(OaStat) * batch);
+      hs.add(WH, pw.data(), sizeof(int32_t) * pw.size());
+      hs.add(PR, probs.data(), sizeof(OaProb) * batch);
+      ZKQ_CUDA_TRY(hs.flush(st));
+      {
+        ProfScope ps_(PC_OA, st);
+        oa_output_kernel<W><<<dim3((unsigned)((nmax + 7) / 8), (unsigned)polar.size()), 256, 0, st>>>(PR, WH, X2, Sm, Lm, ST, W_out, V_out, err);
+      }
+      ZKQ_CUDA_TRY(cudaGetLastError());
+      for (int b : polar) active[b] = 0;
     }
     if (upd.empty()) continue;
     // X2 = X + X E  (E double-double)

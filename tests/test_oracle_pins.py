@@ -929,3 +929,49 @@ def test_mps_sampling_follows_the_born_rule():
         got, prob = oracle.mps_sample(n, chi, g, lam, oracle.WORDS, u)
         assert list(got) == bits, x
         assert abs(fr(prob) - p[x]) <= Fraction(1, 2**290), x
+
+
+# ------------------------------- Deutsch-Jozsa-style circuits -----------------------------------------
+@pytest.mark.parametrize("kind", ["balanced", "constant"])
+def test_dj_circuit_state_and_graph_state_schmidt_values(kind):
+    """The Deutsch-Jozsa-style circuit (workloads.dj_circuit, Section 3.1 with a specified function family)
+    on the 320-bit state vector: a balanced f leaves input 0 in |1> (so the all-zeros outcome has probability
+    0, the algorithm's answer), a constant f returns every input to |0>; the ancilla stays |->.  Before the
+    final Hadamards the inputs hold the graph state of the band graph, and every Schmidt value at every cut
+    is 2^-r with r the GF(2) rank of oracle.graph_state_schmidt_rank (also after the Hadamards, which are
+    local)."""
+    n, w = 9, 3
+    sites, gates, edges = W.dj_circuit(n, w, kind, seed=5, wds=8)
+    assert edges
+    sv = oracle.Statevector(n)
+    for g_kind, s, G in gates:
+        (sv.apply2 if g_kind == "2q" else sv.apply1)(s, G)
+    Zop = np.zeros((4, 2, 1)); Zop[0, 0, 0] = 1.0; Zop[3, 0, 0] = -1.0
+    for q in range(n - 1):
+        z = fr(sv.expect1(q, Zop)[0])
+        if kind == "balanced" and q == 0:
+            assert abs(z + 1) <= Fraction(1, 2**290)
+        elif kind == "constant":
+            assert abs(z - 1) <= Fraction(1, 2**290)
+    Xop = np.zeros((4, 2, 1)); Xop[1, 0, 0] = Xop[2, 0, 0] = 1.0
+    assert abs(fr(sv.expect1(n - 1, Xop)[0]) + 1) <= Fraction(1, 2**290)      # ancilla in |->
+    for cut in range(1, n):
+        r = oracle.graph_state_schmidt_rank(n - 1, edges, cut) if cut < n - 1 else 0
+        if kind == "constant":
+            r = 0
+        s2 = sv.schmidt2(cut)
+        for b in range(s2.shape[0]):
+            want = Fraction(1, 2**r) if b < 2**r else Fraction(0)
+            assert abs(fr(s2[b]) - want) <= Fraction(1, 2**280), (cut, b, r)
+
+
+def test_graph_state_schmidt_rank_closed_forms():
+    """GF(2) ranks of small cuts: a path has rank 1 at every cut; the complete bipartite cut has rank 1; a
+    perfect matching across the cut has rank = its size; no edge across gives 0."""
+    path = [(i, i + 1) for i in range(5)]
+    assert all(oracle.graph_state_schmidt_rank(6, path, c) == 1 for c in range(1, 6))
+    kb = [(i, j) for i in range(3) for j in range(3, 6)]
+    assert oracle.graph_state_schmidt_rank(6, kb, 3) == 1
+    match = [(0, 5), (1, 4), (2, 3)]
+    assert oracle.graph_state_schmidt_rank(6, match, 3) == 3
+    assert oracle.graph_state_schmidt_rank(6, [(0, 1), (4, 5)], 3) == 0

@@ -308,3 +308,66 @@ def footnote_circuit(ctrl, U=None, w: int = 4):
     last = 0 if k == 1 else 2 * k - 2                 # the qubit that controls U, next to the target
     gates = flips + ladder + [("2q", last, g(_controlled(U)))] + ladder[::-1] + flips
     return 2 * k, gates
+
+
+# ----------------------------------------------------------------------------------------------------
+# Deutsch-Jozsa-style circuits (Section 3.1; the paper's function structure is not given, so a family is
+# specified here): inputs on sites 0..n-2, the ancilla on site n-1.  The oracle is a phase oracle
+# (-1)^f(x), equivalent to x, y -> x, y + f(x) with the ancilla in |->.
+#   balanced: f(x) = x_0 + sum over edges (i, j) of x_i x_j (mod 2), no edge at input 0 -- balanced because
+#             x_0 flips f, and after the final Hadamards input 0 is |1>, so the all-zeros outcome never occurs;
+#   constant: the edge phases applied twice (f = 0), entangling in between.
+# The edges form a band graph: each pair (i, j) with 1 <= j - i <= w is an edge with probability 1/2 (by
+# seed).  Between the two layers of Hadamards the inputs hold a graph state, whose Schmidt coefficients at a
+# cut are all equal, 2^(-r/2) with r the GF(2) rank of the cut's edge matrix, so the band width bounds the
+# bond dimension (2^w) and with it the size of the matrices the gate updates diagonalise.
+def dj_edges(n_inputs: int, w: int, seed: int):
+    """Band-graph edges (i, j), 1 <= i < j <= i + w, on inputs 1..n_inputs-1, chosen by seed (input 0 carries
+    the balancing term x_0 and no edge)."""
+    u = uniform(seed, (7 << 40) + n_inputs * 64 + w, n_inputs * w)
+    edges = []
+    for i in range(1, n_inputs):
+        for d in range(1, w + 1):
+            if i + d < n_inputs and u[i * w + d - 1] < 0.5:
+                edges.append((i, i + d))
+    return edges
+
+
+def dj_circuit(n: int, w: int, kind: str = "balanced", seed: int = 0, wds: int = 4):
+    """(sites, gates, edges) of the Deutsch-Jozsa-style circuit on n sites (n - 1 inputs, ancilla last):
+    X on the ancilla, H on every site, the phase oracle, H on the inputs.  A CZ on inputs i < j is carried to
+    neighbours by SWAPs of j down to i + 1 and back.  Gates as in footnote_circuit: ("1q" | "2q", site, words).
+    The H entries 2^-1/2 are rounded to wds words; every other entry is exact."""
+    assert n >= 3 and kind in ("balanced", "constant")
+    z, o = Fraction(0), Fraction(1)
+    from decimal import Decimal, getcontext
+    getcontext().prec = 200
+    h = Fraction(Decimal(1) / Decimal(2).sqrt())
+    H = [[(h, z), (h, z)], [(h, z), (-h, z)]]
+    X = [[(z, z), (o, z)], [(o, z), (z, z)]]
+    Zg = [[(o, z), (z, z)], [(z, z), (-o, z)]]
+    Z0, O1, M1 = (z, z), (o, z), (-o, z)
+    CZ = [[O1, Z0, Z0, Z0], [Z0, O1, Z0, Z0], [Z0, Z0, O1, Z0], [Z0, Z0, Z0, M1]]
+    SWAP = [[O1, Z0, Z0, Z0], [Z0, Z0, O1, Z0], [Z0, O1, Z0, Z0], [Z0, Z0, Z0, O1]]
+    g = lambda M: _mat_words(M, wds)
+    Hw, Xw, Zw, CZw, SWw = g(H), g(X), g(Zg), g(CZ), g(SWAP)
+    ni = n - 1
+    edges = dj_edges(ni, w, seed)
+
+    def phase_layer():
+        out = []
+        for (i, j) in edges:
+            for q in range(j - 1, i, -1):           # bring qubit j next to i: SWAP (q, q+1) for q = j-1 .. i+1
+                out.append(("2q", q, SWw))
+            out.append(("2q", i, CZw))
+            for q in range(i + 1, j):
+                out.append(("2q", q, SWw))
+        return out
+
+    gates = [("1q", n - 1, Xw)] + [("1q", q, Hw) for q in range(n)]
+    if kind == "balanced":
+        gates += [("1q", 0, Zw)] + phase_layer()
+    else:
+        gates += phase_layer() + phase_layer()
+    gates += [("1q", q, Hw) for q in range(ni)]
+    return n, gates, edges
