@@ -13,8 +13,9 @@ Workloads (seeded, synthetic; see workloads/):
   brickwork40      MPS simulation of a 40-qubit brickwork circuit of Haar two-qubit gates (r_max = 256,
                    quad-double, truncation 2^-200): one step = one layer of gates on disjoint bonds; the
                    state keeps evolving, so the timed layers follow the warm-up layers (bond dimensions grow)
-  serve            continuous-batching engine under Poisson arrivals at 0.7x saturation: eigensolves (DD/QD,
-                   N <= 256) and gate updates on four MPS simulations; per-type p50/p99 latency
+  serve            continuous-batching engine under Poisson arrivals at 0.7x saturation: 64 MPS simulations
+                   (n 24..64, r_max 32..1024, DD/QD) admitted by HBM footprint, gate updates and eigensolves
+                   (DD/QD, N <= 512); per-type p50/p99 latency
   dj               Deutsch-Jozsa-style circuits (balanced band-graph function) at widths 16..128 on a quad-double
                    MPS: time per circuit against the width, gates/s, largest diagonalised matrix
 The plain RQI path cannot resolve eigenvalues below the FP64 floor (2^-53 ||A||), so the same-accuracy
@@ -487,99 +488,148 @@ def run_brickwork(args):
 
 
 def run_serve(args):
-    """Continuous-batching request loop (paper_2402_11868_gb300.serve.Engine) under an open Poisson load:
-    eigensolve requests (double-double and quad-double, N <= 256 from the batch distribution) and two-qubit
-    gate requests on device-resident MPS simulations.  The arrival rate is 0.7x the throughput measured
-    with all warm-up requests submitted at once."""
+    """Continuous-batching request loop (paper_2402_11868_gb300.serve.Engine) on the serving configuration:
+    64 MPS simulations with n ~ U{24..64} qubits and r_max ~ 2^U{5..10} (32..1024), half of them double-double
+    and half quad-double, admitted by their HBM footprint (zkq_mps_footprint: the MPS at capacity and its
+    widest gate update) into a 160 GB budget -- those that do not fit wait until admitted ones finish their
+    gate quota and free their memory.  Requests arrive as an open Poisson stream at 0.7x the throughput
+    measured with the warm-up requests submitted at once: half are gate updates (the next brickwork gate of
+    a random admitted simulation, in its precision), half eigensolves (an order from the 256-problem batch's
+    distribution, N <= 512, double-double or quad-double at random).  Per-type p50/p99 latency from arrival to
+    completion."""
+    import collections
     import torch
     import paper_2402_11868_gb300 as Z
     import workloads as W
     from paper_2402_11868_gb300.serve import Engine
     rank, world, local = dist_env()
     torch.cuda.set_device(local)
-    per_step = 16
+    per_step, quota, budget = 32, 12, 160 << 30
     rng = np.random.default_rng(4 + rank)
-    eng = Engine(device=local, hbm_budget=96 << 30, slots=2, max_batch=32)
-    sims = []                                     # (sid, n, words, next gate index)
-    for n_q, r_max, words in ((24, 32, 4), (32, 64, 2), (40, 32, 4), (48, 64, 2)):
-        sims.append([eng.create_simulation(n_q, r_max, words), n_q, words, 0])
+    eng = Engine(device=local, hbm_budget=budget, slots=4, max_batch=32)
+    specs = [(int(rng.integers(24, 65)), int(2 ** rng.integers(5, 11)), 4 if k % 2 else 2) for k in range(64)]
+    waiting = collections.deque(range(64))
+    state = {}                                   # spec index -> [sid, gates issued, gates completed]
+    refused = [k for k in range(64) if eng.mps_footprint(*specs[k]) > budget]
+    for k in refused:
+        waiting.remove(k)
+    admitted_total, max_live = 0, 0
+    lock = threading.Lock()
+
+    def admit():
+        nonlocal admitted_total, max_live
+        with lock:
+            while waiting:
+                k = waiting[0]
+                sid = eng.try_create_simulation(*specs[k])
+                if sid is None:
+                    break
+                waiting.popleft()
+                state[k] = [sid, 0, 0]
+                admitted_total += 1
+            max_live = max(max_live, len(state))
+
+    def finished_gate(k):
+        with lock:
+            st_ = state[k]
+            st_[2] += 1
+            done = st_[2] >= quota
+            if done:
+                eng.destroy_simulation(st_[0])
+                del state[k]
+        if done:
+            admit()
+
+    admit()
     total_req = (args.warmup + args.steps) * per_step
-    sizes = [min(s, 256) for s in W.batch_sizes(4 + rank, total_req)]
+    sizes = W.batch_sizes(4 + rank, total_req)
     kinds = rng.random(total_req) < 0.5            # True: eigensolve, False: gate
     precs = rng.random(total_req) < 0.5            # True: quad-double eigensolve
-    which_sim = rng.integers(0, len(sims), total_req)
-    reqs = []
-    for i in range(total_req):
+
+    def make(i):
         if kinds[i]:
             cfg = 2 if precs[i] else 1
             p = W.config_batch(cfg, seed=4 + rank, count=1, sizes=[sizes[i]])[0]
-            reqs.append(("eig", p, 4 if cfg == 2 else 2))
-        else:
-            sm = sims[int(which_sim[i])]
-            sid, n_q, words, g = sm
-            layer, k = divmod(g, (n_q - 1 + 1) // 2)
-            sites = list(range(layer % 2, n_q - 1, 2))
-            site = sites[k % len(sites)]
-            sm[3] += 1
-            reqs.append(("gate", (sid, site, W.haar_gate(5 + rank, g + 1000 * sid, words)), words))
+            return ("eig", p, 4 if cfg == 2 else 2)
+        with lock:
+            live = [k for k, v in state.items() if v[1] < quota]
+            if not live:
+                return None
+            k = live[int(rng.integers(0, len(live)))]
+            sid, g = state[k][0], state[k][1]
+            state[k][1] += 1
+        n_q, _, words = specs[k]
+        layer, j = divmod(g, max(1, (n_q - 1) // 2))
+        sites = list(range(layer % 2, n_q - 1, 2))
+        site = sites[j % len(sites)]
+        return ("gate", (k, sid, site, W.haar_gate(5 + rank, g + 1000 * k, words)), words)
 
     def submit(r):
         if r[0] == "eig":
             return eng.submit_eig(r[1].A, r[1].n, r[2])
-        sid, site, G = r[1]
-        return eng.submit_gate(sid, site, G, 2.0 ** -(53 * r[2] - 12))
+        k, sid, site, G = r[1]
+        h = eng.submit_gate(sid, site, G, 2.0 ** -(53 * r[2] - 12))
+        threading.Thread(target=lambda: (h.done.wait(600), finished_gate(k)), daemon=True).start()
+        return h
+
+    def issue(i):
+        r = make(i)
+        while r is None:                          # every admitted simulation has all its gates issued
+            time.sleep(0.01)
+            r = make(i)
+        return r, submit(r)
 
     # saturation: the warm-up requests all at once
-    warm = reqs[:args.warmup * per_step]
     t0 = time.perf_counter()
-    hs = [submit(r) for r in warm]
+    hs = [issue(i)[1] for i in range(args.warmup * per_step)]
     for h in hs:
-        h.done.wait(600)
-    cap = len(warm) / (time.perf_counter() - t0)
+        h.done.wait(900)
+    cap = len(hs) / (time.perf_counter() - t0)
     eng.completed.clear()
-    # open loop at 0.7x saturation
     rate = 0.7 * cap
     clocks = ClockSampler(local)
     clocks.start()
-    timed = reqs[args.warmup * per_step:]
-    gaps = rng.exponential(1.0 / rate, len(timed))
+    gaps = rng.exponential(1.0 / rate, args.steps * per_step)
     t0 = time.perf_counter()
-    hs, t_next = [], t0
-    for r, gp in zip(timed, gaps):
+    out_reqs, t_next = [], t0
+    for i, gp in zip(range(args.warmup * per_step, total_req), gaps):
         t_next += gp
         dt = t_next - time.perf_counter()
         if dt > 0:
             time.sleep(dt)
-        hs.append((r, submit(r)))
-    for _, h in hs:
-        h.done.wait(600)
+        out_reqs.append(issue(i))
+    for _, h in out_reqs:
+        h.done.wait(900)
     wall = time.perf_counter() - t0
     clk = clocks.stop()
-    errors = [h.error for _, h in hs if h.error]
+    errors = [h.error for _, h in out_reqs if h.error]
     lat = {}
-    for (r, h) in hs:
+    for (r, h) in out_reqs:
         key = f"{r[0]}_{'qd' if r[2] == 4 else 'dd'}"
         lat.setdefault(key, []).append(1e3 * (h.t_done - h.t_arrive))
     stats = {k: {"count": len(v), "p50_ms": float(np.percentile(v, 50)), "p99_ms": float(np.percentile(v, 99))}
              for k, v in sorted(lat.items())}
-    eig_pairs = sum(r[1].n for r, h in hs if r[0] == "eig" and not h.error)
-    ngates = sum(1 for r, h in hs if r[0] == "gate" and not h.error)
+    eig_pairs = sum(r[1].n for r, h in out_reqs if r[0] == "eig" and not h.error)
+    ngates = sum(1 for r, h in out_reqs if r[0] == "gate" and not h.error)
     all_lat = [x for v in lat.values() for x in v]
     out = {
         "metric": "serving: eigenpairs/s and p50/p99 request latency at 0.7x saturation (Poisson arrivals)",
         "value": eig_pairs / wall, "unit": "eigenpairs/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * wall / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": "serve", "requests_timed": len(timed), "arrival_rate_per_s": rate,
-                   "saturated_requests_per_s": cap, "simulations": [(s[1], s[2]) for s in sims],
-                   "eig_sizes": "N from the batch distribution, capped at 256", "errors": len(errors)},
+        "config": {"workload": "serve", "simulations": 64, "n_qubits": "U{24..64}", "r_max": "2^U{5..10}",
+                   "sim_precision": "half double-double, half quad-double", "hbm_budget_gb": budget >> 30,
+                   "gate_quota_per_simulation": quota, "admitted": admitted_total, "max_resident": max_live,
+                   "refused_larger_than_budget": len(refused), "requests_timed": len(out_reqs),
+                   "arrival_rate_per_s": rate, "saturated_requests_per_s": cap,
+                   "eig_sizes": "N from the 256-problem batch distribution (16..512)", "errors": len(errors)},
         "latency_ms": {"p50": float(np.percentile(all_lat, 50)), "p99": float(np.percentile(all_lat, 99)),
                        "by_type": stats},
         "gates_per_s": ngates / wall,
         "clocks": clk,
         "e2e": {"value": eig_pairs / wall, "unit": "eigenpairs/s",
-                "h2d_bytes_per_step": int(sum(r[1].A.nbytes for r, _ in hs if r[0] == "eig") / args.steps),
-                "d2h_bytes_per_step": int(sum(r[1].n * r[2] * 8 * (1 + 2 * r[1].n) for r, _ in hs if r[0] == "eig") / args.steps)},
+                "h2d_bytes_per_step": int(sum(r[1].A.nbytes for r, _ in out_reqs if r[0] == "eig") / args.steps),
+                "d2h_bytes_per_step": int(sum(r[1].n * r[2] * 8 * (1 + 2 * r[1].n) for r, _ in out_reqs if r[0] == "eig") / args.steps)},
     }
     eng.close()
     if rank == 0:

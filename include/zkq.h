@@ -243,6 +243,13 @@ typedef struct zkq_mps zkq_mps;
  * (<= 2048), words 2 or 4.  Gate updates need a context on the same device (else ZKQ_EINVAL).
  * Allocates per-site capacity min(2^min(l+1, n-l-1), r_max).  Errors: ZKQ_EINVAL, ZKQ_ENOMEM. */
 zkq_status zkq_mps_create(zkq_ctx* ctx, int n_qubits, int r_max, int words, zkq_mps** out);
+/* zkq_mps_footprint: device bytes for admitting a simulation before it exists (the many concurrent gate
+ * updates of Section 2.1 held resident): *state_bytes, what zkq_mps_create(n_qubits, r_max, words) allocates;
+ * *gate_bytes, what a context's workspace grows to for the widest gate update of that MPS with `method`
+ * (gate scratch plus the eigensolve and refinement of zkq_workspace_size at the largest reduced matrix).
+ * Host-side; allocates nothing.  Errors: ZKQ_EINVAL, ZKQ_ECUDA. */
+zkq_status zkq_mps_footprint(zkq_ctx* ctx, int n_qubits, int r_max, int words, int method, size_t* state_bytes,
+                             size_t* gate_bytes);
 zkq_status zkq_mps_destroy(zkq_mps* mps);
 /* current bond dimensions chi[0..n-2] (host) */
 zkq_status zkq_mps_bond_dims(const zkq_mps* mps, int32_t* chi);

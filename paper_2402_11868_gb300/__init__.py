@@ -79,7 +79,8 @@ def lib():
                              ("zkq_mps_bond_dims", [P, P]), ("zkq_mps_download", [P, P, P, P]),
                              ("zkq_mps_upload", [P, P, P, P, P]), ("zkq_mps_apply1q", [P, P, I, P, P]),
                              ("zkq_mps_apply2q", [P, P, I, P, ctypes.c_double, I, P, P, P]),
-                             ("zkq_mps_expect1", [P, P, I, P, P, P, P]), ("zkq_mps_sample", [P, P, I, P, P, P, P])):
+                             ("zkq_mps_expect1", [P, P, I, P, P, P, P]), ("zkq_mps_sample", [P, P, I, P, P, P, P]),
+                             ("zkq_mps_footprint", [P, I, I, I, I, P, P])):
                 getattr(L, nm).restype = I
                 getattr(L, nm).argtypes = args
             L.zkq_workspace_size.restype = I
@@ -437,6 +438,14 @@ def zkq_plan_destroy(plan: Plan):
 
 def zkq_mps_create(ctx: Context, n_qubits: int, r_max: int, words: int = 4) -> MPS:
     return MPS(ctx, n_qubits, r_max, words)
+
+
+def zkq_mps_footprint(ctx: Context, n_qubits: int, r_max: int, words: int = 4, method=ZKQ_OA_OZAKI):
+    """(state bytes, gate-update workspace bytes) of an MPS before it is created."""
+    a = ctypes.c_size_t(0); b = ctypes.c_size_t(0)
+    _check(lib().zkq_mps_footprint(ctx.handle, n_qubits, r_max, words, method, ctypes.byref(a), ctypes.byref(b)),
+           "zkq_mps_footprint")
+    return a.value, b.value
 
 
 def zkq_mps_destroy(mps: MPS):

@@ -158,20 +158,65 @@ static inline int right_cap(const zkq_mps* m, int l) { return l == m->n - 1 ? 1 
 
 template <int W> static unsigned blocks(size_t n) { return (unsigned)((n + 255) / 256); }
 
+// Bond capacities: the Schmidt rank across bond l is at most 2^min(l+1, n-l-1), and at most r_max.
+static std::vector<int> mps_caps(int n_qubits, int r_max) {
+  std::vector<int> cap(n_qubits - 1);
+  for (int l = 0; l < n_qubits - 1; ++l) {
+    long long lim = 1;
+    int e = std::min(l + 1, n_qubits - l - 1);
+    for (int k = 0; k < e && lim < r_max; ++k) lim *= 2;
+    cap[l] = (int)std::min<long long>(lim, r_max);
+  }
+  return cap;
+}
+
+// Device bytes an MPS handle allocates: Gamma per site at capacity, lambda per bond, the gate buffer and the
+// pointer table (the allocations of mps_build).
+static size_t mps_state_bytes(int n_qubits, int words, const std::vector<int>& cap) {
+  const size_t wb = (size_t)words * sizeof(double);
+  size_t tot = 0;
+  for (int l = 0; l < n_qubits; ++l) {
+    const size_t a = l == 0 ? 1 : cap[l - 1], b = l == n_qubits - 1 ? 1 : cap[l];
+    tot += 2 * a * b * 2 * wb;
+  }
+  for (int l = 0; l < n_qubits - 1; ++l) tot += (size_t)cap[l] * wb;
+  tot += 16 * 2 * wb;
+  tot += (size_t)(2 * n_qubits) * sizeof(double*) + (size_t)(n_qubits + 1) * sizeof(int32_t);
+  return tot;
+}
+
+// Scratch layout of one two-site gate update (offsets in doubles) for bond dimensions a (left), c (middle),
+// d (right): theta operands, M and M^H, rho, the FP64 and refined eigenpairs, the split-back product, and
+// the SVD variant's buffers.
+struct GateScratch {
+  size_t Mk, Nm, Mc, Nc, T, M, MH, Rho, W64, V64, Wq, Vq, Err, Info, Y, Sig, Norm, SvdX, SvdS, total;
+};
+static GateScratch gate_scratch(int a, int c, int d, int W, bool svd) {
+  const size_t E = 2 * W;
+  const int R = 2 * a, C = 2 * d, g = std::min(R, C);
+  GateScratch L{};
+  size_t off = 0;
+  auto take = [&](size_t doubles) { size_t o = off; off += (doubles + 31) & ~(size_t)31; return o; };
+  L.Mk = take(2 * (size_t)a * c * E); L.Nm = take(2 * (size_t)c * d * E);
+  L.Mc = take(2 * (size_t)a * c * E); L.Nc = take(2 * (size_t)c * d * E);
+  L.T = take(4 * (size_t)a * d * E); L.M = take((size_t)R * C * E); L.MH = take((size_t)R * C * E);
+  L.Rho = take((size_t)g * g * E); L.W64 = take(g); L.V64 = take(2 * (size_t)g * g);
+  L.Wq = take((size_t)g * W); L.Vq = take((size_t)g * g * E); L.Err = take(g); L.Info = take(8);
+  L.Y = take((size_t)std::max(R, C) * g * E);
+  L.Sig = take((size_t)g * W); L.Norm = take(2 * W);
+  L.SvdX = svd ? take(2 * (size_t)std::max(R, C) * g) : 0;   // the SVD's vectors of the larger side
+  L.SvdS = svd ? take(g) : 0;
+  L.total = off;
+  return L;
+}
+
 // |0...0> on the context's device; on failure the caller frees m (whatever it holds by then)
 static zkq_status mps_build(zkq_ctx* ctx, zkq_mps* m, int n_qubits, int r_max, int words) {
   m->n = n_qubits; m->r_max = r_max; m->W = words;
   m->device = ctx_device(ctx);
   ZKQ_CUDA_TRY(cudaSetDevice(m->device));
   m->chi.assign(n_qubits - 1, 1);
-  m->cap.resize(n_qubits - 1);
-  for (int l = 0; l < n_qubits - 1; ++l) {
-    // Schmidt rank across bond l is at most 2^min(l+1, n-l-1)
-    long long lim = 1;
-    int e = std::min(l + 1, n_qubits - l - 1);
-    for (int k = 0; k < e && lim < r_max; ++k) lim *= 2;
-    m->cap[l] = (int)std::min<long long>(lim, r_max);
-  }
+  m->cap = mps_caps(n_qubits, r_max);
   m->gamma.reserve(n_qubits);                  // the push_backs below cannot throw and lose a device buffer
   m->lam.reserve(n_qubits - 1);
   const std::vector<double> one = [&] { std::vector<double> v(words, 0.0); v[0] = 1.0; return v; }();
@@ -305,19 +350,12 @@ static zkq_status apply2q_t(zkq_ctx* ctx, zkq_mps* m, int l, const double* G, do
   const int R = 2 * a, C = 2 * d;
   const bool left = R <= C;                                 // Gram matrix of the smaller side (ties: left)
   const int g = left ? R : C;
-  // scratch layout (doubles)
-  size_t off = 0;
-  auto take = [&](size_t doubles) { size_t o = off; off += (doubles + 31) & ~(size_t)31; return o; };
-  size_t oMk = take(2 * (size_t)a * c * E), oNm = take(2 * (size_t)c * d * E);
-  size_t oMc = take(2 * (size_t)a * c * E), oNc = take(2 * (size_t)c * d * E);
-  size_t oT = take(4 * (size_t)a * d * E), oM = take((size_t)R * C * E), oMH = take((size_t)R * C * E);
-  size_t oRho = take((size_t)g * g * E), oW64 = take(g), oV64 = take(2 * (size_t)g * g);
-  size_t oWq = take((size_t)g * W), oVq = take((size_t)g * g * E), oErr = take(g), oInfo = take(8);
-  size_t oY = take((size_t)std::max(R, C) * g * E);
-  size_t oSig = take((size_t)g * W), oNorm = take(2 * W);
   const bool svd = method == ZKQ_SVD_OA;
-  size_t oSvdX = svd ? take(2 * (size_t)std::max(R, C) * g) : 0;   // the SVD's vectors of the larger side
-  size_t oSvdS = svd ? take(g) : 0;
+  const GateScratch gs = gate_scratch(a, c, d, W, svd);
+  const size_t oMk = gs.Mk, oNm = gs.Nm, oMc = gs.Mc, oNc = gs.Nc, oT = gs.T, oM = gs.M, oMH = gs.MH, oRho = gs.Rho;
+  const size_t oW64 = gs.W64, oV64 = gs.V64, oWq = gs.Wq, oVq = gs.Vq, oErr = gs.Err, oInfo = gs.Info, oY = gs.Y;
+  const size_t oSig = gs.Sig, oNorm = gs.Norm, oSvdX = gs.SvdX, oSvdS = gs.SvdS;
+  const size_t off = gs.total;
   size_t* cap_bytes = nullptr;
   void** ws = ctx_mps_ws(ctx, &cap_bytes);
   size_t need = off * sizeof(double);
@@ -433,6 +471,32 @@ static zkq_status apply2q_t(zkq_ctx* ctx, zkq_mps* m, int l, const double* G, do
     *discarded = all > 0 ? (all - kept) / all : 0.0;
   }
   return (hinfo[0] == 0 && hinfo[1] == 0) ? ZKQ_OK : ZKQ_ENOCONV;
+}
+
+extern "C" zkq_status zkq_mps_footprint(zkq_ctx* ctx, int n_qubits, int r_max, int words, int method,
+                                        size_t* state_bytes, size_t* gate_bytes) try {
+  if (!ctx || !state_bytes || !gate_bytes || n_qubits < 2 || n_qubits > 4096 || r_max < 1 || r_max > 2048 ||
+      (words != 2 && words != 4) || method < 0 || method > 3)
+    return ZKQ_EINVAL;
+  const std::vector<int> cap = mps_caps(n_qubits, r_max);
+  *state_bytes = mps_state_bytes(n_qubits, words, cap);
+  // the widest gate update: bond dimensions at capacity on both sides of a middle bond
+  size_t worst = 0; int gmax = 1;
+  for (int l = 0; l + 1 < n_qubits; ++l) {
+    const int a = l == 0 ? 1 : cap[l - 1], c = cap[l], d = l + 1 == n_qubits - 1 ? 1 : cap[l + 1];
+    const GateScratch gs = gate_scratch(a, c, d, words, method == ZKQ_SVD_OA);
+    worst = std::max(worst, gs.total * sizeof(double));
+    gmax = std::max(gmax, std::min(2 * a, 2 * d));
+  }
+  worst += worst / 4;                                   // the growth slack of the gate buffer
+  size_t eig = 0;
+  const int rm = method == ZKQ_SVD_OA ? ZKQ_OA_OZAKI : method;
+  zkq_status s = zkq_workspace_size(ctx, 1, &gmax, words, words, rm, &eig);
+  if (s != ZKQ_OK) return s;
+  *gate_bytes = worst + eig;
+  return ZKQ_OK;
+} catch (...) {
+  return api_exception(ctx);
 }
 
 extern "C" zkq_status zkq_mps_apply2q(zkq_ctx* ctx, zkq_mps* m, int site, const double* G, double trunc_tau, int method,

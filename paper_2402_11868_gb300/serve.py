@@ -3,7 +3,8 @@
 Requests (from many simulations) are eigensolves of Hermitian reduced matrices and two-qubit gate
 applications on device-resident MPS states.  The engine
   * admits a request when its HBM footprint fits the budget (else it waits; a request larger than the
-    whole budget is refused at submission with ZKQ_EADMIT semantics);
+    whole budget is refused at submission with ZKQ_EADMIT semantics); footprints come from the library
+    (zkq_workspace_size, zkq_mps_footprint), so they follow its layouts;
   * packs every admitted eigensolve of the same target precision into one uneven batch (one FP64 Jacobi
     launch + one refinement call) on a free execution slot — each slot owns a library context and a CUDA
     stream, so batches on different slots overlap on the device; requests arriving while batches run join
@@ -26,31 +27,11 @@ from dataclasses import dataclass, field
 import numpy as np
 
 
-def eig_footprint(n: int, a_words: int, target: int) -> int:
-    """Device bytes an eigensolve of order n holds while in flight (inputs, outputs, refinement state and
-    split-product scratch, per the library's workspace layout)."""
+def caller_bytes(n: int, a_words: int, target: int) -> int:
+    """Device bytes of the arrays the engine allocates for one eigensolve request: the input (n^2 complex,
+    a_words words), FP64 eigenpairs and info, refined eigenpairs, residual estimates and info."""
     el = n * n
-    inputs = el * 2 * a_words * 8
-    outputs = n * target * 8 + el * 2 * target * 8 + n * 8 + el * 16 + n * 8
-    refine = el * 2 * target * 8 * 8 + el * 2 * 2 * 8          # X, X2, P, S, R, CT, CG, CW + E
-    kp = -(-2 * n // 64) * 64
-    mp = -(-n // 128) * 128
-    np2 = -(-2 * n // 128) * 128
-    scratch = 4 * (2 * 34 * (mp + np2) * kp * 2 + 3 * 34 * mp * np2)  # fp16 residue planes + uint8 GEMM residues
-    return int(inputs + outputs + refine + scratch)
-
-
-def mps_footprint(n_qubits: int, r_max: int, words: int) -> int:
-    tot = 0
-    caps = [min(2 ** min(l + 1, n_qubits - l - 1), r_max) for l in range(n_qubits - 1)]
-    for l in range(n_qubits):
-        a = 1 if l == 0 else caps[l - 1]
-        b = 1 if l == n_qubits - 1 else caps[l]
-        tot += 2 * a * b * 2 * words * 8
-    tot += sum(caps) * words * 8
-    # gate-update scratch for the widest bond
-    g = 2 * max(caps + [1])
-    return int(tot + eig_footprint(g, words, words) + 16 * g * g * 2 * words * 8)
+    return int(el * 2 * a_words * 8 + (n * 8 + el * 16 + 4) + (n * target * 8 + el * 2 * target * 8 + n * 8 + 4))
 
 
 @dataclass(eq=False)
@@ -91,16 +72,44 @@ class Engine:
         self.thread = threading.Thread(target=self._loop, daemon=True)
         self.thread.start()
 
+    # ---------------------------------------------------------------- footprints (from the library)
+    def eig_footprint(self, n: int, a_words: int, target: int) -> int:
+        """Device bytes an eigensolve request holds in flight: its arrays plus the workspace the library
+        reports for it (zkq_workspace_size: eigensolve, refinement state and split-product scratch)."""
+        ws = self.Z.zkq_workspace_size(self.slots[0][0], [n], a_words, target, self.method)
+        return caller_bytes(n, a_words, target) + int(ws)
+
+    def mps_footprint(self, n_qubits: int, r_max: int, words: int) -> int:
+        """Device bytes a simulation holds while it exists: its MPS at capacity and the workspace of its
+        widest gate update (zkq_mps_footprint)."""
+        state, gate = self.Z.zkq_mps_footprint(self.slots[0][0], n_qubits, r_max, words, self.method)
+        return int(state + gate)
+
     # ---------------------------------------------------------------- submission
     def create_simulation(self, n_qubits: int, r_max: int, words: int = 4) -> int:
-        fp = mps_footprint(n_qubits, r_max, words)
+        sid = self.try_create_simulation(n_qubits, r_max, words)
+        if sid is None:
+            raise MemoryError("simulation does not fit the HBM budget")
+        return sid
+
+    def try_create_simulation(self, n_qubits: int, r_max: int, words: int = 4):
+        """Admit a simulation if its footprint fits the budget now (else None: the caller retries once memory
+        frees up)."""
+        fp = self.mps_footprint(n_qubits, r_max, words)
         with self.lock:
             if fp > self.budget - self.in_use:
-                raise MemoryError("simulation does not fit the HBM budget")
+                return None
             self.in_use += fp
             sid = next(self.ids)
             ctx = self.slots[0][0]
-            self.sims[sid] = (self.Z.MPS(ctx, n_qubits, r_max, words), fp)
+        try:
+            mps = self.Z.MPS(ctx, n_qubits, r_max, words)
+        except Exception:
+            with self.lock:
+                self.in_use -= fp
+            raise
+        with self.lock:
+            self.sims[sid] = (mps, fp)
         return sid
 
     def destroy_simulation(self, sid: int):
@@ -112,7 +121,7 @@ class Engine:
 
     def submit_eig(self, A_words: np.ndarray, n: int, target: int, sim: int = -1) -> Request:
         a_words = A_words.shape[-1]
-        fp = eig_footprint(n, a_words, target)
+        fp = self.eig_footprint(n, a_words, target)
         r = Request("eig", sim, {"A": A_words, "n": n, "target": target, "a_words": a_words}, fp)
         return self._enqueue(r)
 

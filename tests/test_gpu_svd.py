@@ -101,12 +101,13 @@ def _conj_t(A, m, n):
     return out
 
 
-@pytest.mark.parametrize("shape", [(24, 24), (16, 40), (40, 16)])
-def test_svd_keeps_relative_accuracy_on_graded_rows(ctx, shape):
-    """Rows scaled from 1 down to 2^-80: every singular value (down to about 2^-80 of the largest) within 2^-40
-    of its own size, where the Gram matrix would have lost everything below 2^-26.5 of the largest."""
+@pytest.mark.parametrize("shape,grade", [((24, 24), 80.0), ((16, 40), 80.0), ((40, 16), 200.0)])
+def test_svd_keeps_relative_accuracy_on_graded_rows(ctx, shape, grade):
+    """Rows scaled from 1 down to 2^-grade: every singular value (the smallest below 2^-50 of the largest)
+    within 2^-40 of its own size, where the Gram matrix would have lost everything below 2^-26.5 of the
+    largest."""
     m, n = shape
-    A = _matrix(m, n, 300 + m, grade=80.0)
+    A = _matrix(m, n, 300 + m, grade=grade)
     S, _, _, info, _, _ = _svd(ctx, [A], [shape])
     assert info[0] == 0
     sig_ref, _, _ = oracle.svd(A, m, n) if m >= n else oracle.svd(_conj_t(A, m, n), n, m)

@@ -10,17 +10,34 @@ import pytest
 import workloads as W
 
 
-def test_footprints_grow_with_size_and_precision():
-    from paper_2402_11868_gb300.serve import eig_footprint, mps_footprint
-    assert eig_footprint(512, 4, 4) > eig_footprint(256, 4, 4) > eig_footprint(16, 4, 4) > 0
-    assert eig_footprint(128, 4, 4) > eig_footprint(128, 2, 2)
-    assert mps_footprint(40, 256, 4) > mps_footprint(40, 32, 4) > mps_footprint(10, 32, 4)
+@pytest.mark.gpu
+def test_footprints_come_from_the_library_and_grow_with_size_and_precision():
+    import paper_2402_11868_gb300 as Z
+    from paper_2402_11868_gb300.serve import Engine, caller_bytes
+    Z.build()
+    eng = Engine(hbm_budget=8 << 30, slots=1)
+    try:
+        ef, mf = eng.eig_footprint, eng.mps_footprint
+        assert ef(512, 4, 4) > ef(256, 4, 4) > ef(16, 4, 4) > 0
+        assert ef(128, 4, 4) > ef(128, 2, 2)
+        assert mf(40, 256, 4) > mf(40, 32, 4) > mf(10, 32, 4)
+        ctx = eng.slots[0][0]
+        assert ef(96, 4, 4) == caller_bytes(96, 4, 4) + Z.zkq_workspace_size(ctx, [96], 4, 4, Z.ZKQ_OA_OZAKI)
+        state, gate = Z.zkq_mps_footprint(ctx, 12, 16, 4)
+        assert mf(12, 16, 4) == state + gate
+        # the state figure is what an MPS of that shape holds: Gamma and lambda at capacity
+        caps = [min(2 ** min(l + 1, 11 - l), 16) for l in range(11)]
+        dims = [1] + caps + [1]
+        tensors = sum(2 * dims[l] * dims[l + 1] * 2 * 4 * 8 for l in range(12)) + sum(caps) * 4 * 8
+        assert tensors < state < tensors + 4096
+    finally:
+        eng.close()
 
 
 @pytest.mark.gpu
 def test_results_same_alone_and_in_mix_and_admission():
     import paper_2402_11868_gb300 as Z
-    from paper_2402_11868_gb300.serve import Engine, eig_footprint
+    from paper_2402_11868_gb300.serve import Engine
     from tests._util import fr
     Z.build()
     probe = W.herm_spectrum(91, 0, W.spectrum_graded(48, 150), 4)
@@ -43,11 +60,24 @@ def test_results_same_alone_and_in_mix_and_admission():
         anorm = abs(fr(la[0]))
         for i in range(probe.n):
             assert abs(fr(la[i]) - fr(lm[i])) <= anorm / 2**200
+        # and against the oracle: every eigenvalue of the probe, 320-bit residuals of every mixed request
+        import oracle
+        L, _, _ = oracle.eigh(probe.A, probe.n)
+        for i in range(probe.n):
+            assert abs(fr(lm[i]) - fr(L[i])) <= anorm / 2**200
+        for i, (r, n) in enumerate(zip(others, [16, 96, 33, 130, 64, 20])):
+            p = W.herm_spectrum(92, i, W.spectrum_graded(n, 100 if i % 2 else 40), 4)
+            t = 4 if i % 2 else 2
+            lam, V = r.result["lam"], r.result["V"]
+            an = max(abs(float(fr(lam[0]))), abs(float(fr(lam[-1]))))
+            res, orth = oracle.residual(p.A, n, lam, V, cols=[0, n // 2, n - 1])
+            bits = 200 if t == 4 else 100
+            assert res.max() <= an * 2.0**-bits and orth.max() <= 2.0**-(bits - 8), (n, t)
         # a request larger than the whole budget is refused at submission
         small = Engine.__new__(Engine)
-        small.budget = eig_footprint(64, 4, 4) // 2
+        small.budget = eng.eig_footprint(64, 4, 4) // 2
         big = Engine._enqueue(small, __import__("paper_2402_11868_gb300.serve", fromlist=["Request"]).Request(
-            "eig", -1, {}, eig_footprint(64, 4, 4)))
+            "eig", -1, {}, eng.eig_footprint(64, 4, 4)))
         assert big.error and "EADMIT" in big.error
         st = eng.latency_stats()
         assert st["count"] >= 8 and st["p99_ms"] >= st["p50_ms"] > 0
