@@ -579,9 +579,13 @@ def run_serve(args):
             r = make(i)
         return r, submit(r)
 
-    # saturation: the warm-up requests all at once
+    # warm-up: the first half of the warm-up requests (first calls grow the contexts' workspaces and admit the
+    # simulations); saturation: the second half submitted at once
+    nw = args.warmup * per_step
+    for h in [issue(i)[1] for i in range(nw // 2)]:
+        h.done.wait(900)
     t0 = time.perf_counter()
-    hs = [issue(i)[1] for i in range(args.warmup * per_step)]
+    hs = [issue(i)[1] for i in range(nw // 2, nw)]
     for h in hs:
         h.done.wait(900)
     cap = len(hs) / (time.perf_counter() - t0)
