@@ -123,12 +123,22 @@ class ClockSampler:
 
 
 # ---------------------------------------------------------------------------------------------------
-def load_workload(name, seed, count):
+def load_workload(name, rank, count, world=1):
+    """The rank's problems.  The batch workload is one job of count x world problems (seed 1) sharded across
+    the ranks by the package's N^3-balanced partition (paper_2402_11868_gb300.shard): weak scaling, about
+    count problems' work per GPU, no data-path collective."""
     import workloads as W
     if name == "single128_plain":
-        return [W.config_single128(seed=seed)], 4, "plain", "single 128x128 Hermitian, lambda_k=2^-0.3(k-1), QD input"
-    return (W.config_batch(2, seed=1 + seed, count=count), 4, "chosen",
-            f"{count} Hermitian problems, N~U{{16..512}}, lambda graded to 2^-180, 8 pairs split 2^-60 (rel), QD input")
+        return [W.config_single128(seed=rank)], 4, "plain", "single 128x128 Hermitian, lambda_k=2^-0.3(k-1), QD input"
+    total = count * world
+    if world == 1:
+        mine = None
+    else:
+        from paper_2402_11868_gb300.shard import my_share
+        mine = my_share(W.batch_sizes(1, total), world, rank)
+    return (W.config_batch(2, seed=1, count=total, indices=mine), 4, "chosen",
+            f"{total} Hermitian problems, N~U{{16..512}}, lambda graded to 2^-180, 8 pairs split 2^-60 (rel), QD "
+            f"input" + (f"; sharded by N^3 over {world} ranks" if world > 1 else ""))
 
 
 class Runner:
@@ -235,7 +245,7 @@ def run_ours(args):
         dist.init_process_group("nccl")
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    problems, words, method, desc = load_workload(args.workload, rank, args.count)
+    problems, words, method, desc = load_workload(args.workload, rank, args.count, world)
     R = Runner(Z, torch, dev, problems, words, method)
     ctx = Z.Context(local)
     stream = torch.cuda.Stream(device=dev)
@@ -275,11 +285,15 @@ def run_ours(args):
     clk = clocks.stop()
     ok2, nbad2, max_err = R.check()
     total_ms = float(sum(step_ms))
+    job_pairs = R.pairs
     if world > 1:
         t = torch.tensor([total_ms], device=dev)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         total_ms = float(t.item())
-    value = R.pairs * world * args.steps / (total_ms / 1e3)
+        pc = torch.tensor([float(R.pairs)], device=dev)
+        dist.all_reduce(pc, op=dist.ReduceOp.SUM)    # the ranks' shares differ: count them all
+        job_pairs = int(pc.item())
+    value = job_pairs * args.steps / (total_ms / 1e3)
     # end to end through the C ABI: pinned host input -> device, hot path, results back to pinned host
     Wo_h = torch.empty(R.Wo.numel(), dtype=torch.float64).pin_memory()
     Vo_h = torch.empty(R.Vo.numel(), dtype=torch.float64).pin_memory()
@@ -295,13 +309,18 @@ def run_ours(args):
         e1.record(stream)
         e1.synchronize()
         e2e_ms.append(e0.elapsed_time(e1))
-    e2e_value = R.pairs / (float(np.mean(e2e_ms)) / 1e3)
+    e2e_t = float(np.mean(e2e_ms))
+    if world > 1:
+        t = torch.tensor([e2e_t], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_t = float(t.item())
+    e2e_value = job_pairs / (e2e_t / 1e3)
     roof = roofline(Z, prof, R.ns, args.steps)
     out = {
         "metric": METRIC, "value": value, "unit": "eigenpairs/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": args.workload, "desc": desc, "problems": len(R.ns), "eigenpairs_per_step": R.pairs,
+        "config": {"workload": args.workload, "desc": desc, "problems": len(R.ns), "eigenpairs_per_step": job_pairs,
                    "target": "quad-double", "method": method, "converged": ok and ok2, "unconverged": nbad2,
                    "max_err_over_normA": max_err, "err_bound": R.err_bound,
                    "l2": "flushed between timed steps" if flush is not None else "inputs larger than L2"},

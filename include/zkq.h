@@ -201,6 +201,21 @@ zkq_status zkq_ctx_workspace_bytes(const zkq_ctx* ctx, size_t* bytes);
 zkq_status zkq_autotune_jacobi(zkq_ctx* ctx, int nsizes, const int32_t* sizes, int a_words, int reps, int32_t* best);
 
 /*
+ * zkq_autotune_gemm: measure the tile width of the tcgen05 split-product GEMM (256 or 128 output columns per
+ * CTA tile) for each order in sizes[0..nsizes) (16..512: the Chinese-remainder form, K' = 2n <= 1024) and keep
+ * the faster in a process-wide table (by K') that every later split product consults -- the batched products
+ * of the refinement (Section 2, ZKCM_CUS paragraph: recovering the precision), tuned like the Jacobi width.
+ * Each order is timed on a synthetic batch of n x n x n complex products in `words` words per real (enough
+ * 128-column tiles to fill the GPU about four times), reps timed runs after one warm-up per width; the call
+ * allocates that batch, uses the context's split-product workspace and synchronises its stream.  Both widths
+ * form the same exact integer slice products: results do not change.  Needs the tcgen05 kernel selected
+ * (zkq_set_gemm_kernel(1), the default).
+ *   best (host)   out: int32[nsizes], 256 or 128
+ * Errors: ZKQ_EINVAL, ZKQ_ENOMEM, ZKQ_ECUDA (the table is unchanged then).
+ */
+zkq_status zkq_autotune_gemm(zkq_ctx* ctx, int nsizes, const int32_t* sizes, int words, int reps, int32_t* best);
+
+/*
  * Plans: a fixed-shape batch of the FP64 eigensolve (zkq_eigh_batched) followed, optionally, by plain RQI
  * refinement (zkq_rqi_refine with ZKQ_PLAIN_RQI) -- the batched diagonalisation of Section 2.1 repeated on
  * batches of one shape.  zkq_plan_create lays the batch out, allocates the plan's own device metadata and
@@ -241,7 +256,9 @@ zkq_status zkq_plan_destroy(zkq_plan* plan);
 typedef struct zkq_mps zkq_mps;
 /* |0...0> on n_qubits sites (2 <= n <= 4096) on the context's device, bond dimensions capped at r_max
  * (<= 2048), words 2 or 4.  Gate updates need a context on the same device (else ZKQ_EINVAL).
- * Allocates per-site capacity min(2^min(l+1, n-l-1), r_max).  Errors: ZKQ_EINVAL, ZKQ_ENOMEM. */
+ * Allocates per-site capacity min(2^min(l+1, n-l-1), r_max) from the device's stream-ordered memory pool
+ * (cudaMallocAsync on a private stream; the pool keeps freed memory cached for later simulations), so
+ * neither create nor destroy synchronises the whole device.  Errors: ZKQ_EINVAL, ZKQ_ENOMEM. */
 zkq_status zkq_mps_create(zkq_ctx* ctx, int n_qubits, int r_max, int words, zkq_mps** out);
 /* zkq_mps_footprint: device bytes for admitting a simulation before it exists (the many concurrent gate
  * updates of Section 2.1 held resident): *state_bytes, what zkq_mps_create(n_qubits, r_max, words) allocates;
@@ -250,6 +267,8 @@ zkq_status zkq_mps_create(zkq_ctx* ctx, int n_qubits, int r_max, int words, zkq_
  * Host-side; allocates nothing.  Errors: ZKQ_EINVAL, ZKQ_ECUDA. */
 zkq_status zkq_mps_footprint(zkq_ctx* ctx, int n_qubits, int r_max, int words, int method, size_t* state_bytes,
                              size_t* gate_bytes);
+/* Frees the MPS's buffers in stream order after its last asynchronous call (apply1q); every other MPS call
+ * has synchronised its stream before returning.  NULL is accepted. */
 zkq_status zkq_mps_destroy(zkq_mps* mps);
 /* current bond dimensions chi[0..n-2] (host) */
 zkq_status zkq_mps_bond_dims(const zkq_mps* mps, int32_t* chi);
@@ -339,6 +358,10 @@ zkq_status zkq_mw_gemm(zkq_ctx* ctx, int count, const int32_t* m, const int32_t*
 zkq_status zkq_set_gemm_kernel(int which);
 int zkq_get_gemm_kernel(void);
 zkq_status zkq_check_device_waits(void);
+/* Tile width of the tcgen05 slice GEMM (process-wide): 256 or 128 output columns per tile for every batch, or
+ * 0 to restore the default (256 where it fits, or the table zkq_autotune_gemm filled is cleared).  Both widths
+ * give identical results.  Errors: ZKQ_EINVAL. */
+zkq_status zkq_set_gemm_tile_width(int width);
 
 /*
  * zkq_test_grid_barrier_hook: test hook of the bounded grid barrier of the cooperative-grid Jacobi class

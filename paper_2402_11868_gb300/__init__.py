@@ -89,6 +89,10 @@ def lib():
             L.zkq_ctx_workspace_bytes.argtypes = [P, P]
             L.zkq_autotune_jacobi.restype = I
             L.zkq_autotune_jacobi.argtypes = [P, I, P, I, I, P]
+            L.zkq_set_gemm_tile_width.restype = I
+            L.zkq_set_gemm_tile_width.argtypes = [I]
+            L.zkq_autotune_gemm.restype = I
+            L.zkq_autotune_gemm.argtypes = [P, I, P, I, I, P]
             L.zkq_plan_create.restype = I
             L.zkq_plan_create.argtypes = [P, I, P, P, I, I, ctypes.POINTER(P)]
             for nm in ("zkq_plan_execute", "zkq_plan_execute_graph"):
@@ -158,6 +162,14 @@ class Context:
         best = np.zeros(len(sz), dtype=np.int32)
         _check(lib().zkq_autotune_jacobi(self.handle, len(sz), sp, a_words, reps, best.ctypes.data),
                "zkq_autotune_jacobi")
+        return [int(x) for x in best]
+
+    def autotune_gemm(self, sizes, words: int = 4, reps: int = 2):
+        """Measure the split-product GEMM tile width per order (zkq_autotune_gemm); returns 256 or 128 each."""
+        import numpy as np
+        sz, sp = _host_array(sizes, ctypes.c_int32)
+        best = np.zeros(len(sz), dtype=np.int32)
+        _check(lib().zkq_autotune_gemm(self.handle, len(sz), sp, words, reps, best.ctypes.data), "zkq_autotune_gemm")
         return [int(x) for x in best]
 
     def workspace_bytes(self) -> int:
@@ -243,6 +255,10 @@ def zkq_mw_op(op: int, words: int, count: int, a, b, out, on_device: bool, strea
 
 def zkq_set_gemm_kernel(which: int):
     _check(lib().zkq_set_gemm_kernel(which), "zkq_set_gemm_kernel")
+
+
+def zkq_set_gemm_tile_width(width: int):
+    _check(lib().zkq_set_gemm_tile_width(width), "zkq_set_gemm_tile_width")
 
 
 def zkq_get_gemm_kernel() -> int:
@@ -417,6 +433,10 @@ def zkq_ctx_workspace_bytes(ctx: Context) -> int:
 
 def zkq_autotune_jacobi(ctx: Context, sizes, a_words: int = 4, reps: int = 2):
     return ctx.autotune_jacobi(sizes, a_words, reps)
+
+
+def zkq_autotune_gemm(ctx: Context, sizes, words: int = 4, reps: int = 2):
+    return ctx.autotune_gemm(sizes, words, reps)
 
 
 def zkq_plan_create(ctx: Context, n, a_off, a_words: int, target_words: int = 0) -> Plan:

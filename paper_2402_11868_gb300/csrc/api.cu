@@ -241,8 +241,8 @@ zkq_status zkq_workspace_size(zkq_ctx* ctx, int batch, const int32_t* n, int a_w
   size_t total = meta + ws;
   if (oa) {
     total += oa_grow_bytes(oa_state_bytes(batch, xe, le, target_words));
-    // split products of one iteration over every problem: P = A X, then S = X^H P with R = I - X^H X, then
-    // X + X E.  Later iterations run subsets of these products.  When the batch mixes K' = 2n above and
+    // split products of one iteration over every problem: P = A X (with R = I - X^H X when A has W words),
+    // then S = X^H P (with R otherwise), then X + X E.  Later iterations run subsets of these products.  When the batch mixes K' = 2n above and
     // below 1024, its products take the digit form while any order above 512 is still refining, and the CRT
     // form (with a modulus count set by the largest remaining K') once only orders up to 512 remain, so the
     // bound takes both.  Distinct dummy addresses stand for the distinct matrices of each problem.
@@ -259,7 +259,8 @@ zkq_status zkq_workspace_size(zkq_ctx* ctx, int batch, const int32_t* n, int a_w
         const int k = n[b];
         p1.push_back({k, k, k, 0, ptr(0, b), ptr(1, b), nullptr, nullptr, 1.0, 0});
         p2.push_back({k, k, k, 1, ptr(1, b), ptr(2, b), nullptr, nullptr, 1.0, 0});
-        p2.push_back({k, k, k, 1, ptr(1, b), ptr(1, b), nullptr, nullptr, -1.0, 1});
+        // R = I - X^H X joins the first call when A has the working precision's words (as oa_refine does)
+        (a_words == W ? p1 : p2).push_back({k, k, k, 1, ptr(1, b), ptr(1, b), nullptr, nullptr, -1.0, 1});
         p3.push_back({k, k, k, 0, ptr(1, b), ptr(3, b), nullptr, nullptr, 1.0, 0});
       }
       struct Call { const std::vector<MwProd>* p; int wa, wb; };
@@ -318,6 +319,12 @@ zkq_status zkq_set_gemm_kernel(int which) {
 int zkq_get_gemm_kernel(void) { return gemm_kernel_get(); }
 
 zkq_status zkq_check_device_waits(void) { return gemm_kernel_error() ? ZKQ_ETIMEOUT : ZKQ_OK; }
+zkq_status zkq_set_gemm_tile_width(int width) {
+  if (width != 0 && width != 128 && width != 256) return ZKQ_EINVAL;
+  if (width == 0) gemm_wide_table_set({});
+  else gemm_wide_table_set({{1 << 30, width == 256 ? 1 : 0}});
+  return ZKQ_OK;
+}
 zkq_status zkq_test_grid_barrier_hook(int extra_arrivals, int log2_poll_limit) {
   return set_grid_barrier_hook(extra_arrivals, log2_poll_limit);
 }

@@ -167,5 +167,8 @@ zkq_status api_exception(void* ctx) noexcept;
 int gemm_kernel_get();
 void gemm_kernel_set(int k);
 bool gemm_kernel_error();
+// tile-width table of the tcgen05 slice GEMM: (largest K' of a batch, 1 = 256-column tiles, 0 = 128)
+void gemm_wide_table_set(const std::vector<std::pair<int, int>>& t);
+std::vector<std::pair<int, int>> gemm_wide_table_get();
 
 }  // namespace zkq

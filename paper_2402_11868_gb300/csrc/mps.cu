@@ -15,6 +15,7 @@
 //   keep beta with sigma_beta^2 > tau sum sigma^2, at most r_max; lambda'_beta = sigma_beta / sqrt(sum kept).
 // The eigensolve of rho is the library's FP64 Jacobi + refinement to W words; products are split products.
 #include <new>
+#include <mutex>
 #include <vector>
 #include <algorithm>
 #include <cstring>
@@ -211,42 +212,72 @@ static GateScratch gate_scratch(int a, int c, int d, int W, bool svd) {
 }
 
 // |0...0> on the context's device; on failure the caller frees m (whatever it holds by then)
+// The MPS's buffers come from the device's stream-ordered pool (cudaMallocAsync / cudaFreeAsync), so that
+// creating or destroying a simulation does not synchronise the whole device: a serving loop admits and
+// retires simulations while other streams keep computing.  Freed memory stays cached in the pool for the
+// next simulation (release threshold raised once per device).
+static zkq_status pool_keep_memory(int dev) {
+  static std::mutex mu;
+  static std::vector<int> done;
+  std::lock_guard<std::mutex> g(mu);
+  if (std::find(done.begin(), done.end(), dev) != done.end()) return ZKQ_OK;
+  cudaMemPool_t pool;
+  ZKQ_CUDA_TRY(cudaDeviceGetDefaultMemPool(&pool, dev));
+  uint64_t thr = ~0ULL;
+  ZKQ_CUDA_TRY(cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr));
+  done.push_back(dev);
+  return ZKQ_OK;
+}
+
+namespace {
+struct TempStream {                       // a private stream, synchronised and destroyed on every exit path
+  cudaStream_t s = nullptr;
+  ~TempStream() { if (s) { cudaStreamSynchronize(s); cudaStreamDestroy(s); } }
+};
+}  // namespace
+
 static zkq_status mps_build(zkq_ctx* ctx, zkq_mps* m, int n_qubits, int r_max, int words) {
   m->n = n_qubits; m->r_max = r_max; m->W = words;
   m->device = ctx_device(ctx);
   ZKQ_CUDA_TRY(cudaSetDevice(m->device));
+  zkq_status ps = pool_keep_memory(m->device);
+  if (ps != ZKQ_OK) return ps;
   m->chi.assign(n_qubits - 1, 1);
   m->cap = mps_caps(n_qubits, r_max);
   m->gamma.reserve(n_qubits);                  // the push_backs below cannot throw and lose a device buffer
   m->lam.reserve(n_qubits - 1);
   const std::vector<double> one = [&] { std::vector<double> v(words, 0.0); v[0] = 1.0; return v; }();
+  std::vector<double*> tab(2 * n_qubits, nullptr);
+  TempStream ts;
+  ZKQ_CUDA_TRY(cudaStreamCreateWithFlags(&ts.s, cudaStreamNonBlocking));
+  const cudaStream_t st = ts.s;
   size_t wb = (size_t)words * sizeof(double);
   for (int l = 0; l < n_qubits; ++l) {
     size_t elems = (size_t)2 * left_cap(m, l) * right_cap(m, l);
     double* g = nullptr;
-    cudaError_t e = cudaMalloc(&g, elems * 2 * wb);
+    cudaError_t e = cudaMallocAsync(&g, elems * 2 * wb, st);
     if (e != cudaSuccess) { set_last_cuda_error(e); return ZKQ_ENOMEM; }
     m->gamma.push_back(g);
-    if (words == 2) mps_init_kernel<2><<<blocks<2>(elems), 256>>>(g, elems);
-    else mps_init_kernel<4><<<blocks<4>(elems), 256>>>(g, elems);
+    if (words == 2) mps_init_kernel<2><<<blocks<2>(elems), 256, 0, st>>>(g, elems);
+    else mps_init_kernel<4><<<blocks<4>(elems), 256, 0, st>>>(g, elems);
+    ZKQ_CUDA_TRY(cudaGetLastError());
   }
   for (int l = 0; l < n_qubits - 1; ++l) {
     double* v = nullptr;
-    cudaError_t e = cudaMalloc(&v, (size_t)m->cap[l] * wb);
+    cudaError_t e = cudaMallocAsync(&v, (size_t)m->cap[l] * wb, st);
     if (e != cudaSuccess) { set_last_cuda_error(e); return ZKQ_ENOMEM; }
     m->lam.push_back(v);
-    ZKQ_CUDA_TRY(cudaMemcpy(v, one.data(), wb, cudaMemcpyHostToDevice));
+    ZKQ_CUDA_TRY(cudaMemcpyAsync(v, one.data(), wb, cudaMemcpyHostToDevice, st));
   }
-  cudaError_t e = cudaMalloc(&m->gate, 16 * 2 * wb);
+  cudaError_t e = cudaMallocAsync(&m->gate, 16 * 2 * wb, st);
   if (e != cudaSuccess) { set_last_cuda_error(e); m->gate = nullptr; return ZKQ_ENOMEM; }
   // device tables of the site and bond pointers (fixed for the life of the MPS) and of the bond dimensions
-  e = cudaMalloc(&m->d_ptrs, (size_t)(2 * n_qubits) * sizeof(double*) + (size_t)(n_qubits + 1) * sizeof(int32_t));
+  e = cudaMallocAsync(&m->d_ptrs, (size_t)(2 * n_qubits) * sizeof(double*) + (size_t)(n_qubits + 1) * sizeof(int32_t), st);
   if (e != cudaSuccess) { set_last_cuda_error(e); m->d_ptrs = nullptr; return ZKQ_ENOMEM; }
-  std::vector<double*> tab(2 * n_qubits, nullptr);
   for (int l = 0; l < n_qubits; ++l) tab[l] = m->gamma[l];
   for (int l = 0; l < n_qubits - 1; ++l) tab[n_qubits + l] = m->lam[l];
-  ZKQ_CUDA_TRY(cudaMemcpy(m->d_ptrs, tab.data(), tab.size() * sizeof(double*), cudaMemcpyHostToDevice));
-  ZKQ_CUDA_TRY(cudaDeviceSynchronize());
+  ZKQ_CUDA_TRY(cudaMemcpyAsync(m->d_ptrs, tab.data(), tab.size() * sizeof(double*), cudaMemcpyHostToDevice, st));
+  ZKQ_CUDA_TRY(cudaStreamSynchronize(st));    // the buffers are ready for any stream from here on
   return ZKQ_OK;
 }
 
@@ -265,14 +296,22 @@ zkq_status zkq_mps_create(zkq_ctx* ctx, int n_qubits, int r_max, int words, zkq_
   return ZKQ_OK;
 }
 
+// Every MPS call but apply1q synchronises its stream before returning; apply1q records an event behind its
+// kernel.  Destroy orders the frees after that event on a private stream, so no device-wide
+// synchronisation is needed.
 zkq_status zkq_mps_destroy(zkq_mps* m) {
   if (!m) return ZKQ_OK;
   cudaSetDevice(m->device);
-  cudaDeviceSynchronize();
-  for (double* p : m->gamma) if (p) cudaFree(p);
-  for (double* p : m->lam) if (p) cudaFree(p);
-  if (m->gate) cudaFree(m->gate);
-  if (m->d_ptrs) cudaFree(m->d_ptrs);
+  cudaStream_t st = nullptr;
+  if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) st = nullptr;
+  if (st && m->done) cudaStreamWaitEvent(st, m->done, 0);
+  if (!st) cudaDeviceSynchronize();            // fallback: no stream could be made
+  for (double* p : m->gamma) if (p) cudaFreeAsync(p, st);
+  for (double* p : m->lam) if (p) cudaFreeAsync(p, st);
+  if (m->gate) cudaFreeAsync(m->gate, st);
+  if (m->d_ptrs) cudaFreeAsync(m->d_ptrs, st);
+  if (st) cudaStreamDestroy(st);               // released once its frees have run
+  if (m->done) cudaEventDestroy(m->done);
   delete m;
   return ZKQ_OK;
 }
@@ -330,10 +369,14 @@ zkq_status zkq_mps_apply1q(zkq_ctx* ctx, zkq_mps* m, int site, const double* U, 
   const int W = m->W;
   ZKQ_CUDA_TRY(cudaMemcpyAsync(m->gate, U, 4 * 2 * W * sizeof(double), cudaMemcpyHostToDevice, st));
   int rows = left_dim(m, site), cols = right_dim(m, site);
-  ProfScope ps(PC_MPS, st);
-  if (W == 2) mps_apply1_kernel<2><<<blocks<2>((size_t)rows * cols), 256, 0, st>>>(m->gamma[site], rows, cols, m->gate);
-  else mps_apply1_kernel<4><<<blocks<4>((size_t)rows * cols), 256, 0, st>>>(m->gamma[site], rows, cols, m->gate);
-  ZKQ_CUDA_TRY(cudaGetLastError());
+  {
+    ProfScope ps(PC_MPS, st);
+    if (W == 2) mps_apply1_kernel<2><<<blocks<2>((size_t)rows * cols), 256, 0, st>>>(m->gamma[site], rows, cols, m->gate);
+    else mps_apply1_kernel<4><<<blocks<4>((size_t)rows * cols), 256, 0, st>>>(m->gamma[site], rows, cols, m->gate);
+    ZKQ_CUDA_TRY(cudaGetLastError());
+  }
+  if (!m->done) ZKQ_CUDA_TRY(cudaEventCreateWithFlags(&m->done, cudaEventDisableTiming));
+  ZKQ_CUDA_TRY(cudaEventRecord(m->done, st));   // destroy waits for this
   return ZKQ_OK;
 }
 

@@ -2,6 +2,7 @@
 // (mps_measure.cu).
 #pragma once
 #include <vector>
+#include <cuda_runtime.h>
 #include "../../include/zkq.h"
 
 struct zkq_mps {
@@ -14,4 +15,5 @@ struct zkq_mps {
   // device table: gamma pointers [n], lambda pointers [n] (the last unused), then int32 dims [n + 1]
   // (dims[l] = chi[l-1], 1 at both ends; rewritten by the calls that read it)
   double** d_ptrs = nullptr;
+  cudaEvent_t done = nullptr;      // recorded behind the last asynchronous call (apply1q) for destroy
 };

@@ -502,23 +502,27 @@ zkq_status oa_refine_t(void* ctx, const OaBuffers& buf, int batch, const int32_t
     // P = A X ; S = X^H P ; R = I - X^H X
     // re-orthonormalising steps (polish 1) need R only: their lambda and couplings are not used, and the
     // final evaluation (polish 2) forms P and S again
+    // When A has the working precision's words, R joins the first call: X is then split once as the right
+    // operand of both A X and X^H X (the call splits an operand shared by several products once).
     std::vector<MwProd> p1, p2;
+    const bool r_first = wa == W;
     for (int b : act) {
-      if (polish[b] == 1) continue;
       const OaProb& q = probs[b];
       double* Xb = X + q.xoff * 2 * W;
-      p1.push_back({q.n, q.n, q.n, 0, A + q.a_off * 2 * wa, Xb, Pm + q.xoff * 2 * W, nullptr, 1.0, 0});
+      if (polish[b] != 1) p1.push_back({q.n, q.n, q.n, 0, A + q.a_off * 2 * wa, Xb, Pm + q.xoff * 2 * W, nullptr, 1.0, 0});
+      MwProd pr_{q.n, q.n, q.n, 1, Xb, Xb, Rm + q.xoff * 2 * W, nullptr, -1.0, 1};
+      pr_.hermitian = 1;                           // R = I - X^H X is Hermitian
+      (r_first ? p1 : p2).push_back(pr_);
     }
     s = mw_gemm_batched(p1.data(), (int)p1.size(), wa, W, W, p_bits, prod_method, buf.oz_ws, buf.oz_bytes, buf.oz_meta, buf.oz_meta_bytes, st, buf.stage);
     if (s != ZKQ_OK) return s;
     for (int b : act) {
       const OaProb& q = probs[b];
+      if (polish[b] == 1) continue;
       double* Xb = X + q.xoff * 2 * W;
       MwProd ps_{q.n, q.n, q.n, 1, Xb, Pm + q.xoff * 2 * W, Sm + q.xoff * 2 * W, nullptr, 1.0, 0};
-      MwProd pr_{q.n, q.n, q.n, 1, Xb, Xb, Rm + q.xoff * 2 * W, nullptr, -1.0, 1};
-      ps_.hermitian = 1; pr_.hermitian = 1;        // S = X^H A X and R = I - X^H X are Hermitian
-      if (polish[b] != 1) p2.push_back(ps_);
-      p2.push_back(pr_);
+      ps_.hermitian = 1;                           // S = X^H A X is Hermitian
+      p2.push_back(ps_);
     }
     s = mw_gemm_batched(p2.data(), (int)p2.size(), W, W, W, p_bits, prod_method, buf.oz_ws, buf.oz_bytes, buf.oz_meta, buf.oz_meta_bytes, st, buf.stage);
     if (s != ZKQ_OK) return s;

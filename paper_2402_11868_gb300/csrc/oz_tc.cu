@@ -175,10 +175,12 @@ __global__ void __launch_bounds__(TC_THREADS, 1) oz_tc_kernel(const OzProd* __re
   const int bn = ACC ? TC_BN : min(BN, 128 * tl.w);                // this tile's width
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int nk = p.kp / TC_BK;
-  const int total = npairs * nk;
+  // this CTA's pairs: tl.p0 .. tl.p1-1 of the list (all of them unless the host split the tile)
+  const int p0 = ACC ? 0 : max(0, min(tl.p0, npairs)), np_ = ACC ? npairs : max(0, min(tl.p1, npairs) - p0);
+  const int total = np_ * nk;
   volatile int* abort_v = &abort_flag;
 
-  for (int i = tid; i < npairs; i += TC_THREADS) pairs[i] = gpairs[i];
+  for (int i = tid; i < np_; i += TC_THREADS) pairs[i] = gpairs[p0 + i];
   if (tid == 0) {
     for (int s = 0; s < S_; ++s) { mbar_init(&full[s], TC_PRODUCERS); mbar_init(&empty[s], 1); }
     for (int b = 0; b < 2; ++b) { mbar_init(&accf[b], 1); mbar_init(&acce[b], 128); }
@@ -275,7 +277,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) oz_tc_kernel(const OzProd* __re
     int grp = 0;
     const uint32_t lane_base = tmem + ((uint32_t)(warp * 32) << 16);
     const int r = tl.ti * TC_BM + warp * 32 + lane;
-    for (int pi = 0; pi < npairs; ++pi) {
+    for (int pi = 0; pi < np_; ++pi) {
       const OzPair pr = pairs[pi];
       if (!(pr.flags & 1)) continue;
       const int buf = grp & 1;

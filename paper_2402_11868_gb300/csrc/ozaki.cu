@@ -253,6 +253,41 @@ constexpr int OZ_BM = 128, OZ_BN = 128, OZ_BK = 32, OZ_STAGES = 3;
 
 // slice-GEMM kernel: 0 mma.sync (legacy warp-level path), 1 tcgen05 (tensor memory accumulators)
 static int g_gemm_kernel = 1;
+// Tile-width table of the tcgen05 slice GEMM (zkq_autotune_gemm): (largest K' of a batch, 1 for 256-column
+// tiles / 0 for 128-column tiles), by increasing K'; a batch takes the first entry whose K' is >= its own,
+// else the last; empty: 256-column tiles wherever they fit.  Both widths compute the same exact integer
+// slice products, so the choice changes no result.  Process-wide, like the kernel choice.
+static std::mutex g_wide_mu;
+static std::vector<std::pair<int, int>> g_wide_table;
+static bool wide_tiles_for(int max_kp) {
+  std::lock_guard<std::mutex> g(g_wide_mu);
+  if (g_wide_table.empty()) return true;
+  for (const auto& e : g_wide_table) if (e.first >= max_kp) return e.second != 0;
+  return g_wide_table.back().second != 0;
+}
+// SM count of the current device (cached per device)
+static int device_sm_count() {
+  static std::mutex mu;
+  static int cache[64] = {};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 152;
+  std::lock_guard<std::mutex> g(mu);
+  if (!cache[dev]) {
+    int v = 0;
+    if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v <= 0) v = 152;
+    cache[dev] = v;
+  }
+  return cache[dev];
+}
+void gemm_wide_table_set(const std::vector<std::pair<int, int>>& t) {
+  std::lock_guard<std::mutex> g(g_wide_mu);
+  g_wide_table = t;
+  std::sort(g_wide_table.begin(), g_wide_table.end());
+}
+std::vector<std::pair<int, int>> gemm_wide_table_get() {
+  std::lock_guard<std::mutex> g(g_wide_mu);
+  return g_wide_table;
+}
 static int* g_oz_err = nullptr;              // device flag raised by a bounded wait that expired
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -898,7 +933,7 @@ zkq_status mw_gemm_batched(const MwProd* prods, int count, int wa, int wb, int w
   if (s != ZKQ_OK) return s;
   char* base = (char*)*ws;
   std::vector<OzTile> tiles, wide;                 // wide: 256-column tiles (CRT form on the tcgen05 kernel)
-  const bool use_wide = crt && g_gemm_kernel == 1;
+  const bool use_wide = crt && g_gemm_kernel == 1 && wide_tiles_for(max_kp);
   for (int i = 0; i < count; ++i) {
     OzProd& o = dp[i];
     o.Ahat = (__half*)(base + oA[i]); o.Bhat = (__half*)(base + oB[i]);
@@ -921,10 +956,10 @@ zkq_status mw_gemm_batched(const MwProd* prods, int count, int wa, int wb, int w
       const int units = o.np2 / OZ_BN;
       for (int tj = 0; tj < units;) {
         if (use_wide && tj + 1 < units) {
-          if (needed(ti, tj * OZ_BN, 2 * OZ_BN)) wide.push_back({i, ti, tj, 2});
+          if (needed(ti, tj * OZ_BN, 2 * OZ_BN)) wide.push_back({i, ti, tj, 2, 0, plan.npairs});
           tj += 2;
         } else {
-          if (needed(ti, tj * OZ_BN, OZ_BN)) tiles.push_back({i, ti, tj, 1});
+          if (needed(ti, tj * OZ_BN, OZ_BN)) tiles.push_back({i, ti, tj, 1, 0, plan.npairs});
           tj += 1;
         }
       }
@@ -933,8 +968,29 @@ zkq_status mw_gemm_batched(const MwProd* prods, int count, int wa, int wb, int w
   // biggest problems first (their tiles run longest: K' is larger)
   // one list: longest tiles first (K', then width), so the tail of the launch is short tiles
   tiles.insert(tiles.end(), wide.begin(), wide.end());
+  // A batch with fewer tiles than two per SM (one large product, as in an MPS gate update) would leave most SMs
+  // idle while each tile walks its 3r pairs: on the tcgen05 kernel's CRT form, where every pair is an
+  // independent level with its own residue planes, split each tile's pairs over several CTAs (at least six
+  // pairs each).
+  if (crt && g_gemm_kernel == 1) {
+    const int want = 2 * device_sm_count();
+    if (!tiles.empty() && (int)tiles.size() < want) {
+      const int G = std::min((want + (int)tiles.size() - 1) / (int)tiles.size(), std::max(1, plan.npairs / 6));
+      if (G > 1) {
+        std::vector<OzTile> split;
+        split.reserve(tiles.size() * G);
+        for (const OzTile& t : tiles)
+          for (int g = 0; g < G; ++g) {
+            OzTile u = t;
+            u.p0 = (int)((long)plan.npairs * g / G); u.p1 = (int)((long)plan.npairs * (g + 1) / G);
+            split.push_back(u);
+          }
+        tiles.swap(split);
+      }
+    }
+  }
   std::stable_sort(tiles.begin(), tiles.end(), [&](const OzTile& a, const OzTile& c) {
-    const long wa_ = (long)dp[a.prod].kp * a.w, wc_ = (long)dp[c.prod].kp * c.w;
+    const long wa_ = (long)dp[a.prod].kp * a.w * (a.p1 - a.p0), wc_ = (long)dp[c.prod].kp * c.w * (c.p1 - c.p0);
     return wa_ > wc_;
   });
   size_t m_p = al(sizeof(OzProd) * count), m_t = al(sizeof(OzTile) * std::max<size_t>(1, tiles.size())), m_q = al(sizeof(OzPair) * pairs.size());
@@ -1029,7 +1085,8 @@ zkq_status mw_gemm_batched(const MwProd* prods, int count, int wa, int wb, int w
 
 // Bytes that mw_gemm_batched needs for a product batch: the workspace (residue or digit planes of every
 // operand it splits, GEMM outputs, exponents) exactly as it lays them out, and an upper bound of the
-// metadata (products, at most one tile per 128 x 128 output block, pair list, CRT constants).  Operands are
+// metadata (products, at most one tile per 128 x 128 output block plus the split tiles of a small batch,
+// pair list, CRT constants).  Operands are
 // shared by the same pointer, role and shape test as in mw_gemm_batched; the pointers are only compared.
 zkq_status mw_gemm_workspace(const MwProd* prods, int count, int wa, int wb, int p_out_bits, int method,
                              size_t* ws_need, size_t* meta_need) {
@@ -1071,6 +1128,8 @@ zkq_status mw_gemm_workspace(const MwProd* prods, int count, int wa, int wb, int
     tiles += (size_t)(mp[i] / OZ_BM) * (np2[i] / OZ_BN);
   }
   *ws_need = off;
+  // a batch of few tiles may have its pairs split over up to 2 x SMs more (mw_gemm_batched)
+  tiles += crt ? (size_t)2 * device_sm_count() : 0;
   *meta_need = al(sizeof(OzProd) * count) + al(sizeof(OzTile) * std::max<size_t>(1, tiles)) +
                al(sizeof(OzPair) * npairs) + (crt ? al(sizeof(CrtConst)) : 0);
   return ZKQ_OK;

@@ -36,8 +36,10 @@ struct OzProd {
 
 struct OzPair { int16_t t, u; int16_t level; int16_t flags; };   // flags: 1 chunk end, 2 level end
 
-// one output tile: rows 128 ti.., columns 128 tj.. of product `prod`, w x 128 columns wide (w = 1 or 2)
-struct OzTile { int prod, ti, tj, w; };
+// one output tile: rows 128 ti.., columns 128 tj.. of product `prod`, w x 128 columns wide (w = 1 or 2), over
+// the pairs p0 .. p1-1 of the pair list (the tcgen05 kernel's CRT form may split a tile's pairs over several
+// CTAs: every pair there is its own level with its own output planes)
+struct OzTile { int prod, ti, tj, w, p0, p1; };
 
 struct OzPlan {
   int b;            // digit width (bits)

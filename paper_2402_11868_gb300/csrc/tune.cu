@@ -103,3 +103,92 @@ done:
 } catch (...) {
   return api_exception(ctx);
 }
+
+// ---------------------------------------------------------------------------------------------------
+// Autotuning of the split-product GEMM's tile width: for each requested order n (16..512, the CRT form's
+// range K' = 2n <= 1024), time a synthetic batch of n x n x n complex products in `words` words per real
+// (enough products to fill the GPU with 128-column tiles) with 256-column and with 128-column tiles on the
+// tcgen05 kernel, and keep the faster in the process-wide table that every later split product consults.
+#include "ozaki.cuh"
+
+namespace {
+__global__ void tune_fill_words_kernel(double* A, size_t elems, int words, uint64_t salt) {
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < elems; e += (size_t)gridDim.x * blockDim.x) {
+    double* q = A + e * 2 * words;
+    for (int p = 0; p < 2; ++p) {
+      const double h = hash01((e << 1 | p) ^ salt);
+      q[p * words] = h;
+      double r = h;                                       // lower words: scaled hashes below the leading ulp
+      for (int k = 1; k < words; ++k) { r = ldexp(hash01((e << 8 | p << 4 | k) ^ salt), -53 * k); q[p * words + k] = r; }
+    }
+  }
+}
+}  // namespace
+
+extern "C" zkq_status zkq_autotune_gemm(zkq_ctx* ctx, int nsizes, const int32_t* sizes, int words, int reps,
+                                        int32_t* best) try {
+  if (!ctx || nsizes < 1 || !sizes || !best || reps < 1) return ZKQ_EINVAL;
+  if (words != 1 && words != 2 && words != 4) return ZKQ_EINVAL;
+  for (int i = 0; i < nsizes; ++i) if (sizes[i] < 16 || sizes[i] > 512) return ZKQ_EINVAL;
+  if (gemm_kernel_get() != 1) return ZKQ_EINVAL;                 // the width choice is the tcgen05 kernel's
+  ZKQ_CUDA_TRY(cudaSetDevice(ctx_device(ctx)));
+  const std::vector<std::pair<int, int>> saved = gemm_wide_table_get();
+  std::vector<std::pair<int, int>> table;
+  table.reserve(nsizes);
+  OaBuffers ob = ctx_oa_buffers(ctx);
+  zkq_status s = ZKQ_OK;
+  double *A = nullptr, *B = nullptr, *C = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaStream_t st = nullptr;
+  auto cu = [&](cudaError_t e) { if (e != cudaSuccess) { set_last_cuda_error(e); s = ZKQ_ECUDA; } return e == cudaSuccess; };
+  if (!cu(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking)) || !cu(cudaEventCreate(&e0)) || !cu(cudaEventCreate(&e1)))
+    goto done;
+  for (int si = 0; si < nsizes && s == ZKQ_OK; ++si) {
+    const int n = sizes[si];
+    const int tiles_per = ((n + 127) / 128) * ((2 * n + 127) / 128);
+    const int count = std::max(1, std::min(256, 4 * ctx_num_sms(ctx) / std::max(1, tiles_per)));
+    const size_t el = (size_t)count * n * n;
+    if (!cu(cudaMalloc(&A, el * 2 * words * sizeof(double))) || !cu(cudaMalloc(&B, el * 2 * words * sizeof(double))) ||
+        !cu(cudaMalloc(&C, el * 2 * words * sizeof(double)))) { s = ZKQ_ENOMEM; break; }
+    tune_fill_words_kernel<<<ctx_num_sms(ctx) * 4, 256, 0, st>>>(A, el, words, 0x51ULL + n);
+    tune_fill_words_kernel<<<ctx_num_sms(ctx) * 4, 256, 0, st>>>(B, el, words, 0xB2ULL + n);
+    if (!cu(cudaGetLastError())) break;
+    std::vector<MwProd> pr;
+    for (int b = 0; b < count; ++b) {
+      const size_t o = (size_t)b * n * n * 2 * words;
+      pr.push_back({n, n, n, 0, A + o, B + o, C + o, nullptr, 1.0, 0});
+    }
+    float t_w[2] = {1e30f, 1e30f};
+    for (int wide = 1; wide >= 0 && s == ZKQ_OK; --wide) {
+      gemm_wide_table_set({{2 * n, wide}});
+      for (int r = 0; r <= reps && s == ZKQ_OK; ++r) {            // the first run warms up
+        if (!cu(cudaEventRecord(e0, st))) break;
+        try {
+          s = mw_gemm_batched(pr.data(), count, words, words, words, 53 * words + 6, 1, ob.oz_ws, ob.oz_bytes,
+                              ob.oz_meta, ob.oz_meta_bytes, st, ob.stage);
+        } catch (...) { s = api_exception(ctx); }
+        if (s != ZKQ_OK || !cu(cudaEventRecord(e1, st)) || !cu(cudaEventSynchronize(e1))) break;
+        float ms = 0;
+        if (!cu(cudaEventElapsedTime(&ms, e0, e1))) break;
+        if (r > 0) t_w[wide] = std::min(t_w[wide], ms);
+      }
+    }
+    cudaFree(A); cudaFree(B); cudaFree(C);
+    A = B = C = nullptr;
+    if (s != ZKQ_OK) break;
+    const int w = t_w[1] <= t_w[0] ? 1 : 0;
+    best[si] = w ? 256 : 128;
+    table.push_back({2 * n, w});
+  }
+done:
+  if (A) cudaFree(A);
+  if (B) cudaFree(B);
+  if (C) cudaFree(C);
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  if (st) cudaStreamDestroy(st);
+  gemm_wide_table_set(s == ZKQ_OK ? table : saved);
+  return s;
+} catch (...) {
+  return api_exception(ctx);
+}

@@ -1,6 +1,6 @@
-"""Autotuning of the Jacobi cluster width (zkq_autotune_jacobi): the chosen widths are valid, the context
-uses them, and the eigensolve's results do not depend on them (the same bits as with the built-in
-choice)."""
+"""Autotuning of the Jacobi cluster width (zkq_autotune_jacobi) and of the split-product GEMM tile width
+(zkq_autotune_gemm): the chosen widths are valid, the library uses them, and no result depends on them (the
+same bits as with the built-in choice)."""
 from __future__ import annotations
 
 import numpy as np
@@ -31,3 +31,41 @@ def test_autotuned_width_is_valid_and_results_do_not_change():
         assert np.array_equal(got["V"].cpu().numpy(), ref["V"].cpu().numpy())
     finally:
         tuned.close()
+
+
+def _products(Z, torch, ctx, n, count, seed, words=4):
+    """count n x n x n complex products C_i = A_i B_i (words per real) by the split products; returns C."""
+    rng = np.random.default_rng(seed)
+    el = n * n
+    A = torch.from_numpy(rng.standard_normal(count * el * 2 * words) * (0.5 ** np.tile(np.arange(words) * 53, count * el * 2))).cuda()
+    B = torch.from_numpy(rng.standard_normal(count * el * 2 * words) * (0.5 ** np.tile(np.arange(words) * 53, count * el * 2))).cuda()
+    C = torch.zeros(count * el * 2 * words, dtype=torch.float64, device="cuda")
+    offs = [i * el for i in range(count)]
+    Z.zkq_mw_gemm(ctx, [n] * count, [n] * count, [n] * count, [0] * count, A, offs, words, B, offs, words, C, offs,
+                  words, 53 * words + 6, 1)
+    torch.cuda.synchronize()
+    return C.cpu().numpy()
+
+
+def test_gemm_tile_width_autotune_is_valid_and_results_do_not_change():
+    """zkq_autotune_gemm picks 256- or 128-column tiles per order; every width gives the same bits (the slice
+    products are exact integers either way), forced widths and the tuned table alike."""
+    import torch
+    import paper_2402_11868_gb300 as Z
+    Z.build()
+    with Z.Context(0) as ctx:
+        try:
+            Z.zkq_set_gemm_tile_width(256)
+            ref = _products(Z, torch, ctx, 96, 6, 3)
+            ref2 = _products(Z, torch, ctx, 200, 3, 4)
+            Z.zkq_set_gemm_tile_width(128)
+            assert np.array_equal(_products(Z, torch, ctx, 96, 6, 3), ref)
+            assert np.array_equal(_products(Z, torch, ctx, 200, 3, 4), ref2)
+            best = ctx.autotune_gemm([96, 200], words=4, reps=1)
+            assert len(best) == 2 and all(b in (128, 256) for b in best), best
+            assert np.array_equal(_products(Z, torch, ctx, 96, 6, 3), ref)
+            assert np.array_equal(_products(Z, torch, ctx, 200, 3, 4), ref2)
+        finally:
+            Z.zkq_set_gemm_tile_width(0)
+    with pytest.raises(Z.ZkqError):
+        Z.zkq_set_gemm_tile_width(64)

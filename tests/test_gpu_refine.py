@@ -82,6 +82,54 @@ def test_split_products_match_exact(ctx, method, wa, wb, wc, kernel):
                     assert d <= bound, (i, ii, jj, part, d, bound)
 
 
+def dyadic_mw(rng, count, w, ibits, espread):
+    """complex entries (count, 2, w): integers below 2^ibits times 2^e with e in [-espread, espread] (the leading
+    word holds them exactly; lower words zero)"""
+    x = np.zeros((count, 2, w))
+    ints = rng.integers(-(1 << ibits) + 1, 1 << ibits, size=(count, 2)).astype(np.float64)
+    x[:, :, 0] = np.ldexp(ints, rng.integers(-espread, espread + 1, size=(count, 2)))
+    return x
+
+
+@pytest.mark.parametrize("kernel", [1, 0])
+@pytest.mark.parametrize("method", [1, 2])
+@pytest.mark.parametrize("w", [4, 2])
+def test_split_products_bit_exact_on_representable_products(ctx, method, w, kernel):
+    """Inputs whose every bit lies inside the split's fixed-point window (small integers times powers of two
+    within a window) make the slice products and their recombination exact: the CRT form's dropped low x low
+    product is zero and the digit form's dropped pairs are zero, and the exact result fits in w words.  Then
+    C must equal the exact product bit for bit (compared as exact rationals), for both slice-GEMM kernels,
+    including tiles whose pairs are split over several CTAs (one small product) and ragged shapes."""
+    import torch
+    import paper_2402_11868_gb300 as Z
+    Z.zkq_set_gemm_kernel(kernel)
+    ibits, espread = (19, 20) if w == 4 else (9, 10)
+    rng = np.random.default_rng(77 + 10 * w + method + 100 * kernel)
+    cases = [(1, 1, 1, 0), (5, 9, 13, 1), (128, 64, 96, 0), (33, 130, 70, 1), (200, 17, 512, 0)]
+    As, Bs = [], []
+    for (m, n, k, op) in cases:
+        As.append(dyadic_mw(rng, m * k, w, ibits, espread)); Bs.append(dyadic_mw(rng, k * n, w, ibits, espread))
+    a_off = np.cumsum([0] + [a.shape[0] for a in As[:-1]]); b_off = np.cumsum([0] + [b.shape[0] for b in Bs[:-1]])
+    c_sz = [m * n for (m, n, _, _) in cases]; c_off = np.cumsum([0] + c_sz[:-1])
+    dA = torch.from_numpy(np.concatenate([a.reshape(-1) for a in As])).cuda()
+    dB = torch.from_numpy(np.concatenate([b.reshape(-1) for b in Bs])).cuda()
+    dC = torch.full((sum(c_sz) * 2 * w,), np.nan, dtype=torch.float64, device="cuda")
+    try:
+        Z.zkq_mw_gemm(ctx, [c[0] for c in cases], [c[1] for c in cases], [c[2] for c in cases], [c[3] for c in cases],
+                      dA, a_off, w, dB, b_off, w, dC, c_off, w, 53 * w + 6, method)
+        torch.cuda.synchronize()
+        Z.zkq_check_device_waits()
+    finally:
+        Z.zkq_set_gemm_kernel(1)
+    Ch = dC.cpu().numpy()
+    for i, (m, n, k, op) in enumerate(cases):
+        ref = oracle.matmul(As[i], Bs[i], m, n, k, opA=op)
+        got = Ch[2 * w * c_off[i]: 2 * w * (c_off[i] + m * n)].reshape(m * n, 2, w)
+        for e in range(m * n):
+            for part in range(2):
+                assert fr(got[e, part]) == fr(ref[e, part]), (i, e, part)
+
+
 def oracle_eig(cache, key, p):
     if key not in cache:
         cache[key] = oracle.eigh(p.A, p.n)

@@ -1,6 +1,6 @@
-"""Multi-GPU host logic on CPU: the batch shards across ranks by problem (weak scaling, no data-path
-collective); ranks partition by a greedy N^3 balance and gather per-problem results for reporting.
-Runs two gloo ranks on the CPU."""
+"""Multi-GPU host logic on CPU: the batch shards across ranks by problem (no data-path collective); ranks
+partition with the package's greedy N^3 balance (paper_2402_11868_gb300.shard, which bench.py uses under
+torchrun) and gather per-problem results for reporting.  Runs two gloo ranks on the CPU."""
 from __future__ import annotations
 
 import os
@@ -11,14 +11,8 @@ import torch.multiprocessing as mp
 
 
 def shard(ns, world):
-    """Greedy longest-processing-time assignment of problems to ranks by N^3 (the Jacobi/OA cost law)."""
-    loads = [0.0] * world
-    owner = [0] * len(ns)
-    for b in sorted(range(len(ns)), key=lambda b: -ns[b] ** 3):
-        r = int(np.argmin(loads))
-        owner[b] = r
-        loads[r] += ns[b] ** 3
-    return owner, loads
+    from paper_2402_11868_gb300.shard import shard_by_cost
+    return shard_by_cost(ns, world)
 
 
 def _worker(rank, world, port, ns, out_q):
@@ -44,11 +38,17 @@ def _worker(rank, world, port, ns, out_q):
 
 def test_shard_balance_and_coverage():
     import workloads as W
+    from paper_2402_11868_gb300.shard import my_share
     ns = W.batch_sizes(1)
     for world in (1, 2, 4, 8):
         owner, loads = shard(ns, world)
         assert sorted(set(owner)) == list(range(world))
         assert max(loads) <= 1.1 * sum(loads) / world + max(n ** 3 for n in ns)
+        shares = [my_share(ns, world, r) for r in range(world)]
+        assert sorted(b for sh in shares for b in sh) == list(range(len(ns)))
+    # the greedy rule on a hand example: 4^3 to rank 0, 3^3 to rank 1, then 2^3 and 2^3 to rank 1
+    owner, loads = shard([2, 4, 3, 2], 2)
+    assert owner == [1, 0, 1, 1] and loads == [64, 43]
 
 
 def test_two_gloo_ranks_cover_every_problem_once():
