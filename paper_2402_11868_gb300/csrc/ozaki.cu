@@ -444,92 +444,75 @@ __global__ void oz_combine_kernel(const OzProd* __restrict__ P, int b, int S) {
 
 // ------------------------------------------------------------------------------------------------
 // CRT form: residue planes and reconstruction
-template <int L> struct BigL { uint64_t l[L]; };
+// The reconstruction works on signed integers held as 32-bit limbs in registers.  Every limb index is a
+// compile-time constant (runtime shifts go through a barrel shifter of predicated limb moves and funnel
+// shifts), so no limb array is placed in local memory.
 
-template <int L> __device__ __forceinline__ void bl_zero(BigL<L>& x) {
-#pragma unroll
-  for (int i = 0; i < L; ++i) x.l[i] = 0;
-}
-// x += c * w (c small, w nonnegative L-limb constant)
-template <int L> __device__ __forceinline__ void bl_add_mul(BigL<L>& x, uint64_t c, const uint64_t* w, int wl) {
-  uint64_t carry = 0;
-#pragma unroll
-  for (int i = 0; i < L; ++i) {
-    uint64_t wi = i < wl ? w[i] : 0;
-    uint64_t lo = wi * c, hi = __umul64hi(wi, c);
-    uint64_t t = x.l[i] + lo; uint64_t c1 = t < x.l[i];
-    uint64_t t2 = t + carry; uint64_t c2 = t2 < t;
-    x.l[i] = t2; carry = hi + c1 + c2;
-  }
-}
-// x -= c * w
-template <int L> __device__ __forceinline__ void bl_sub_mul(BigL<L>& x, uint64_t c, const uint64_t* w, int wl) {
-  uint64_t borrow = 0;
-#pragma unroll
-  for (int i = 0; i < L; ++i) {
-    uint64_t wi = i < wl ? w[i] : 0;
-    uint64_t lo = wi * c, hi = __umul64hi(wi, c);
-    uint64_t t = x.l[i] - lo; uint64_t b1 = x.l[i] < lo;
-    uint64_t t2 = t - borrow; uint64_t b2 = t < borrow;
-    x.l[i] = t2; borrow = hi + b1 + b2;
-  }
-}
-template <int L> __device__ __forceinline__ bool bl_neg(const BigL<L>& x) { return (int64_t)x.l[L - 1] < 0; }
-// compare nonnegative x with constant w (wl limbs): -1, 0, 1
-template <int L> __device__ __forceinline__ int bl_cmp(const BigL<L>& x, const uint64_t* w, int wl) {
-  for (int i = L - 1; i >= 0; --i) {
-    uint64_t wi = i < wl ? w[i] : 0;
-    if (x.l[i] != wi) return x.l[i] > wi ? 1 : -1;
-  }
-  return 0;
-}
-template <int L> __device__ __forceinline__ void bl_negate(BigL<L>& x) {
-  uint64_t c = 1;
-#pragma unroll
-  for (int i = 0; i < L; ++i) { uint64_t v = ~x.l[i] + c; c = (c && v == 0) ? 1 : 0; x.l[i] = v; }
-}
-template <int L> __device__ __forceinline__ int bl_top(const BigL<L>& x) {
-  for (int i = L - 1; i >= 0; --i) if (x.l[i]) return 64 * i + 63 - __clzll(x.l[i]);
-  return -1;
-}
-template <int L> __device__ __forceinline__ int bl_bit(const BigL<L>& x, int i) { return i < 0 ? 0 : (int)((x.l[i >> 6] >> (i & 63)) & 1); }
-// x += sgn * m * 2^sh  (m < 2^63)
-template <int L> __device__ __forceinline__ void bl_add_shifted(BigL<L>& x, uint64_t m, int sh, bool neg) {
-  uint64_t w[L];
-#pragma unroll
-  for (int i = 0; i < L; ++i) w[i] = 0;
-  int li = sh >> 6, bs = sh & 63;
-  if (li < L) w[li] = m << bs;
-  if (bs && li + 1 < L) w[li + 1] = m >> (64 - bs);
-  if (!neg) bl_add_mul<L>(x, 1, w, L); else bl_sub_mul<L>(x, 1, w, L);
-}
 // 2^e as a double for |e| <= 1022 (exponent field), else by ldexp
 __device__ __forceinline__ double pow2i(int e) {
   return (e >= -1022 && e <= 1023) ? __longlong_as_double((long long)(e + 1023) << 52) : ldexp(1.0, e);
 }
-// nearest double of the signed integer R times 2^scale; R -= that value
-template <int L> __device__ double bl_round_off(BigL<L>& R, int scale) {
-  bool ng = bl_neg(R);
-  BigL<L> Mg = R; if (ng) bl_negate(Mg);
-  int tb = bl_top(Mg);
-  if (tb < 0) return 0.0;
-  int lo = tb - 52;
-  uint64_t m;
-  if (lo >= 0) {
-    int li = lo >> 6, bs = lo & 63;
-    m = Mg.l[li] >> bs;
-    if (bs && li + 1 < L) m |= Mg.l[li + 1] << (64 - bs);
-    m &= (1ULL << 53) - 1;
-    int rnd = bl_bit(Mg, lo - 1);
-    bool sticky = false;
-    for (int i = 0; i < ((lo - 1) >> 6) && !sticky; ++i) sticky = Mg.l[i] != 0;
-    if (!sticky && lo - 1 > 0) { int l2 = (lo - 1) >> 6, b2 = (lo - 1) & 63; sticky = (Mg.l[l2] & ((1ULL << b2) - 1)) != 0; }
-    if (rnd && (sticky || (m & 1))) m += 1;
-  } else { m = Mg.l[0]; lo = 0; }
-  bl_add_shifted<L>(R, m, lo, !ng);
-  const int ev = lo + scale;                     // m < 2^54: the product is exact unless it underflows
-  double v = (ev >= -1022 && ev <= 1023) ? (double)m * pow2i(ev) : ldexp((double)m, ev);
-  return ng ? -v : v;
+// Y (M limbs) = X << sh, 0 <= sh < 32 M; bits shifted past limb M-1 are dropped
+template <int M>
+__device__ __forceinline__ void limbs_shl(uint32_t* Y, int sh) {
+  const int a = sh >> 5, b = sh & 31;
+#pragma unroll
+  for (int st = 16; st >= 1; st >>= 1) {
+    if (st < M && (a & st)) {
+#pragma unroll
+      for (int k = M - 1; k >= 0; --k) Y[k] = k >= st ? Y[k - st] : 0u;
+    }
+  }
+  if (a >= 32 || (M < 32 && a >= M)) {
+#pragma unroll
+    for (int k = 0; k < M; ++k) Y[k] = 0u;
+  }
+#pragma unroll
+  for (int k = M - 1; k >= 1; --k) Y[k] = __funnelshift_l(Y[k - 1], Y[k], b);
+  Y[0] <<= b;
+}
+// two's complement negation of M limbs
+template <int M>
+__device__ __forceinline__ void limbs_negate(uint32_t* Y) {
+  uint32_t c = 1;
+#pragma unroll
+  for (int k = 0; k < M; ++k) { const uint32_t v = ~Y[k] + c; c = (c && v == 0) ? 1u : 0u; Y[k] = v; }
+}
+// the WC leading words of the nearest-double expansion of the signed integer T (M limbs) times 2^scale:
+// each word is the nearest double (ties to even) of what the words before it left.  The remainder is kept
+// normalised (its top bit at bit 32 M - 1), so the 53 leading bits always sit in the two top limbs.
+template <int WC, int M>
+__device__ __forceinline__ mw<WC> limbs_round_words(uint32_t* T, int scale) {
+  mw<WC> out;
+  bool ng = (int32_t)T[M - 1] < 0;
+  if (ng) limbs_negate<M>(T);
+  int shifted = 0;                               // T (normalised) = |C'| 2^shifted
+#pragma unroll
+  for (int w = 0; w < WC; ++w) {
+    int tk = -1; uint32_t top = 0;
+#pragma unroll
+    for (int k = 0; k < M; ++k) if (T[k] != 0) { tk = k; top = T[k]; }
+    if (tk < 0) { out.x[w] = 0.0; continue; }
+    const int sh = 32 * M - 1 - (32 * tk + 31 - __clz(top));
+    limbs_shl<M>(T, sh);
+    shifted += sh;
+    const uint64_t v = ((uint64_t)T[M - 1] << 32) | T[M - 2];
+    uint64_t m = v >> 11;
+    bool sticky = (v & 0x3FFull) != 0;
+#pragma unroll
+    for (int k = 0; k < M - 2; ++k) sticky |= T[k] != 0;
+    const bool up = ((v >> 10) & 1) && (sticky || (m & 1));
+    m += up ? 1 : 0;                             // m <= 2^53: exact as a double
+    const int ev = 32 * M - 53 - shifted + scale;   // weight of m's last bit
+    const double d = (ev >= -1022 && ev <= 1023) ? (double)m * pow2i(ev) : ldexp((double)m, ev);
+    out.x[w] = ng ? -d : d;
+    // remainder: the two top limbs become (v mod 2^11) - (up ? 2^11 : 0), sign-extended; a negative
+    // remainder flips the sign of the words that follow
+    const int64_t dl = (int64_t)(v & 0x7FFull) - (up ? 2048 : 0);
+    T[M - 1] = (uint32_t)((uint64_t)dl >> 32); T[M - 2] = (uint32_t)(uint64_t)dl;
+    if (dl < 0) { limbs_negate<M>(T); ng = !ng; }
+  }
+  return out;
 }
 
 // Residue planes of the CRT form.  X (q-bit scaled integer of one operand entry) = A_h 2^s + A_l with
@@ -692,8 +675,10 @@ __device__ __forceinline__ void crt_sum32(Res&& residue, const CrtConst* __restr
   for (int k = 0; k < CRT_L32; ++k) { uint64_t v = acc[k] + carry; S[k] = (uint32_t)v; carry = v >> 32; }
   S[CRT_L32] = (uint32_t)carry; S[CRT_L32 + 1] = (uint32_t)(carry >> 32);
   // quotient estimate q = floor(S / M) (< 2^15) from the leading bits, exact correction after
-  int top = L - 1; while (top > 0 && S[top] == 0) --top;
-  double sd = (double)S[top] + (top > 0 ? (double)S[top - 1] * 0x1p-32 : 0.0) + (top > 1 ? (double)S[top - 2] * 0x1p-64 : 0.0);
+  int top = 0; uint32_t s0 = S[0], s1 = 0, s2 = 0;
+#pragma unroll
+  for (int k = 1; k < L; ++k) if (S[k] != 0) { top = k; s0 = S[k]; s1 = S[k - 1]; s2 = k > 1 ? S[k - 2] : 0u; }
+  double sd = (double)s0 + (double)s1 * 0x1p-32 + (double)s2 * 0x1p-64;
   const int qe = 32 * top - cc->Mexp;            // S / M ~ sd Mrcp 2^qe
   double qd = qe < -60 ? 0.0 : (qe > 60 ? 1e30 : sd * cc->Mrcp * pow2i(qe));
   int64_t qq = qd > 1.0 ? (int64_t)fmin(qd, 1e18) : 0;
@@ -717,22 +702,19 @@ __device__ __forceinline__ void crt_sum32(Res&& residue, const CrtConst* __restr
       S[k] = (uint32_t)v; cy = v >> 32;
     }
   };
-  auto geq = [&](const uint32_t* X) {           // S >= X for nonnegative S
-    for (int k = L - 1; k >= 0; --k) {
-      uint32_t x = k < CRT_L32 ? X[k] : 0;
-      if (S[k] != x) return S[k] > x;
+  auto cmp = [&](const uint32_t* X) {           // sign of S - X for nonnegative S (the highest differing limb)
+    int c = 0;
+#pragma unroll
+    for (int k = 0; k < L; ++k) {
+      const uint32_t x = k < CRT_L32 ? X[k] : 0u;
+      if (S[k] != x) c = S[k] > x ? 1 : -1;
     }
-    return true;
+    return c;
   };
+  auto geq = [&](const uint32_t* X) { return cmp(X) >= 0; };
   for (int it = 0; it < 3 && neg(); ++it) addM(1);
   for (int it = 0; it < 3 && geq(cc->M32); ++it) addM(-1);
-  auto gt = [&](const uint32_t* X) {            // S > X for nonnegative S
-    for (int k = L - 1; k >= 0; --k) {
-      uint32_t x = k < CRT_L32 ? X[k] : 0;
-      if (S[k] != x) return S[k] > x;
-    }
-    return false;
-  };
+  auto gt = [&](const uint32_t* X) { return cmp(X) > 0; };
   if (!neg() && gt(cc->Mhalf32)) addM(-1);      // symmetric representative
 #pragma unroll
   for (int k = 0; k < L; ++k) out[k] = S[k];
@@ -751,40 +733,21 @@ __device__ __forceinline__ mw<WC> crt_value(const OzProd& p, const CrtConst* __r
     const int v = (int)__ldg(D8 + (size_t)(r + t) * stride) + (int)__ldg(D8 + (size_t)(2 * r + t) * stride);
     return v >= cc->m[t] ? v - cc->m[t] : v;
   }, cc, sm);
-  // T = hh 2^(2s) + sm 2^s as a signed 64-bit-limb integer (sign-extended shifts of 32-bit limbs)
-  constexpr int L = LT;
-  BigL<L> T; bl_zero(T);
-  auto add_shifted32 = [&](const uint32_t* X, int sh) {
-    const bool ng = (int32_t)X[L32 - 1] < 0;
-    BigL<L> Y;
+  // C' = hh 2^(2s) + sm 2^s in M = 2 LT 32-bit limbs (two's complement; both shifted values fit, by tbits)
+  constexpr int M = 2 * LT;
+  uint32_t T[M], U[M];
+  const uint32_t fh = (int32_t)hh[L32 - 1] < 0 ? ~0u : 0u, fs = (int32_t)sm[L32 - 1] < 0 ? ~0u : 0u;
 #pragma unroll
-    for (int k = 0; k < L; ++k) Y.l[k] = ng ? ~0ULL : 0ULL;
-    // place X (L32 limbs of 32 bits) shifted by sh bits
-    for (int k = 0; k < L32; ++k) {
-      int bit = 32 * k + sh;
-      int li = bit >> 6, bs = bit & 63;
-      if (li >= L) break;
-      uint64_t x = X[k];
-      uint64_t mask_lo = 0xFFFFFFFFULL << bs;
-      Y.l[li] = (Y.l[li] & ~mask_lo) | ((x << bs) & mask_lo);
-      if (bs > 32 && li + 1 < L) {
-        uint64_t mask_hi = (1ULL << (bs - 32)) - 1;
-        Y.l[li + 1] = (Y.l[li + 1] & ~mask_hi) | (x >> (64 - bs));
-      }
-    }
-    // bits below sh are zero
-    for (int k = 0; k < L; ++k) {
-      int b0 = 64 * k;
-      if (b0 + 64 <= sh) Y.l[k] = 0;
-      else if (b0 < sh) Y.l[k] &= ~((1ULL << (sh - b0)) - 1);
-    }
-    bl_add_mul<L>(T, 1, Y.l, L);
-  };
-  add_shifted32(hh, 2 * s);
-  add_shifted32(sm, s);
-  mw<WC> out;
-  for (int k = 0; k < WC; ++k) out.x[k] = bl_round_off<L>(T, es - 2 * cc->q);
-  return out;
+  for (int k = 0; k < M; ++k) { T[k] = k < L32 ? hh[k] : fh; U[k] = k < L32 ? sm[k] : fs; }
+  limbs_shl<M>(T, 2 * s);
+  limbs_shl<M>(U, s);
+  uint32_t c = 0;
+#pragma unroll
+  for (int k = 0; k < M; ++k) {
+    const uint64_t v = (uint64_t)T[k] + U[k] + c;
+    T[k] = (uint32_t)v; c = (uint32_t)(v >> 32);
+  }
+  return limbs_round_words<WC, M>(T, es - 2 * cc->q);
 }
 
 template <int WC, int LW, int LT>
