@@ -37,13 +37,46 @@ __device__ __forceinline__ void big_negate(Big& x) {
   uint64_t c = 1;
   for (int i = 0; i < 5; ++i) { uint64_t v = ~x.l[i] + c; c = (c && v == 0) ? 1 : 0; x.l[i] = v; }
 }
-// x += (neg ? -1 : 1) * m * 2^shift   (m < 2^63, 0 <= shift, shift + 64 <= 320)
+// Y <<= sh (0 <= sh < 512; bits past 320 are dropped).  Runtime shifts go through predicated limb moves
+// and funnel shifts, so every limb index is a compile-time constant and Big stays in registers.
+__device__ __forceinline__ void big_shl(Big& Y, int sh) {
+  const int a = sh >> 6, b = sh & 63;
+#pragma unroll
+  for (int st = 4; st >= 1; st >>= 1) {
+    if (a & st) {
+#pragma unroll
+      for (int k = 4; k >= 0; --k) Y.l[k] = k >= st ? Y.l[k - st] : 0ULL;
+    }
+  }
+  if (b) {
+#pragma unroll
+    for (int k = 4; k >= 1; --k) Y.l[k] = (Y.l[k] << b) | (Y.l[k - 1] >> (64 - b));
+    Y.l[0] <<= b;
+  }
+}
+// arithmetic shift right by 0 <= sh < 320 bits
+__device__ __forceinline__ void big_sar_var(Big& Y, int sh) {
+  const uint64_t fill = (int64_t)Y.l[4] < 0 ? ~0ULL : 0ULL;
+  const int a = sh >> 6, b = sh & 63;
+#pragma unroll
+  for (int st = 4; st >= 1; st >>= 1) {
+    if (a & st) {
+#pragma unroll
+      for (int k = 0; k < 5; ++k) Y.l[k] = k + st <= 4 ? Y.l[k + st] : fill;
+    }
+  }
+  if (b) {
+#pragma unroll
+    for (int k = 0; k < 4; ++k) Y.l[k] = (Y.l[k] >> b) | (Y.l[k + 1] << (64 - b));
+    Y.l[4] = (uint64_t)((int64_t)Y.l[4] >> b);
+  }
+}
+// x += (neg ? -1 : 1) * m * 2^shift   (0 <= shift < 320; the part of m 2^shift past bit 320 is dropped)
 __device__ __forceinline__ void big_add_shifted(Big& x, uint64_t m, int shift, bool neg) {
-  if (m == 0) return;
-  uint64_t w[5] = {0, 0, 0, 0, 0};
-  int li = shift >> 6, bs = shift & 63;
-  if (li < 5) w[li] = m << bs;
-  if (bs && li + 1 < 5) w[li + 1] = m >> (64 - bs);
+  if (m == 0 || shift >= 320) return;
+  Big wb = {{m, 0, 0, 0, 0}};
+  big_shl(wb, shift);
+  const uint64_t* w = wb.l;
   if (!neg) {
     uint64_t c = 0;
     for (int i = 0; i < 5; ++i) { uint64_t a = x.l[i], t = a + w[i]; uint64_t c1 = t < a; uint64_t t2 = t + c; c = c1 | (t2 < t); x.l[i] = t2; }
@@ -530,18 +563,8 @@ __device__ __forceinline__ void crt_halves(const Big& X, int s, CrtHalves& o) {
     if (b0 >= s) lo.l[i] = 0;
     else if (b0 + 64 > s) lo.l[i] &= (s - b0 == 64) ? ~0ULL : ((1ULL << (s - b0)) - 1);
   }
-  Big hi;                                      // floor(X / 2^s): arithmetic shift
-  {
-    const int ls = s >> 6, bs = s & 63;
-    const uint64_t sx = big_neg(X) ? ~0ULL : 0ULL;
-#pragma unroll
-    for (int i = 0; i < 5; ++i) {
-      int src = i + ls;
-      uint64_t a = src < 5 ? X.l[src] : sx;
-      uint64_t b = src + 1 < 5 ? X.l[src + 1] : sx;
-      hi.l[i] = bs ? ((a >> bs) | (b << (64 - bs))) : a;
-    }
-  }
+  Big hi = X;                                  // floor(X / 2^s): arithmetic shift
+  big_sar_var(hi, s);
   o.nh = big_neg(hi);
   if (o.nh) big_negate(hi);
 #pragma unroll
@@ -621,7 +644,7 @@ __global__ void crt_slice_A_kernel(const OzProd* __restrict__ P, const CrtConst*
 
 // B planes: column j' of [Re | Im] output, rows [Re; Im] of K' (real embedding of the complex product)
 template <int WB, int HD>
-__global__ void __launch_bounds__(256, 5) crt_slice_B_kernel(const OzProd* __restrict__ P, const CrtConst* __restrict__ cc) {
+__global__ void __launch_bounds__(256, 4) crt_slice_B_kernel(const OzProd* __restrict__ P, const CrtConst* __restrict__ cc) {
   __shared__ uint32_t sc[CRT_MAXR * (HD + 2)];
   const OzProd p = P[blockIdx.y];
   if (!p.sliceB) return;
