@@ -125,8 +125,15 @@ __device__ void jacobi_problem(int n, const double* __restrict__ A_in, Mat<SMEM>
     __syncthreads();
     int my_rot = 0;
     for (int r = 0; r < m - 1; ++r) {
-      // phase 1: rotation parameters (every CTA computes all pairs into its own shared memory)
-      for (int k = tid; k < P; k += nth) {
+      // phase 1: rotation parameters.  A cluster's CTAs split the pairs: each computes its share into a
+      // staging area of its shared memory, and after the cluster barrier every CTA copies all pairs from
+      // their owners (distributed shared memory).  The staging area is rewritten only after the next
+      // cluster barrier, by which time every copy of it is done.  A single CTA, or the blocks of a
+      // cooperative grid (no distributed shared memory), compute every pair themselves.
+      const int per = SYNC == 1 ? (P + nparts - 1) / nparts : P;
+      const int k0 = SYNC == 1 ? part * per : 0, k1 = min(P, k0 + per);
+      RotParams* stage = SYNC == 1 ? rp + P : rp;
+      for (int k = k0 + tid; k < k1; k += nth) {
         int p, q; rr_pair(m, r, k, p, q);
         RotParams pr; pr.p = p; pr.q = q; pr.rot = 0; pr.c = 1.0; pr.tb = 0.0; pr.z1 = {0, 0}; pr.z2 = {0, 0};
         if (q < n) {
@@ -141,12 +148,23 @@ __device__ void jacobi_problem(int n, const double* __restrict__ A_in, Mat<SMEM>
             pr.c = c; pr.tb = t * ab; pr.rot = 1;
             pr.z1 = {s * er, -s * ei};
             pr.z2 = {s * er, s * ei};
-            ++my_rot;
           }
         }
-        rp[k] = pr;
+        stage[k - k0] = pr;
+        if (SYNC != 1) my_rot += pr.rot;
       }
       sync();
+      if constexpr (SYNC == 1) {
+        cg::cluster_group cl = cg::this_cluster();
+        for (int k = tid; k < P; k += nth) {
+          const int owner = k / per;
+          const RotParams* src = cl.map_shared_rank(rp + P, owner);
+          const RotParams pr = src[k - owner * per];
+          rp[k] = pr;
+          my_rot += pr.rot;                        // every CTA counts all pairs: the same total everywhere
+        }
+        __syncthreads();
+      }
       // phase 2: 2x2 block updates on the upper block triangle + V <- V J
       const int nblk = P * (P + 1) / 2;
       for (int it = gtid; it < nblk + n * P; it += gnth) {
@@ -338,7 +356,7 @@ static zkq_status launch_words(const JacobiBatch& jb, int n_small, int n_large, 
     return ZKQ_OK;
   }
   if (n_large > 0) {
-    size_t sm = (size_t)(max_large_n / 2 + 1) * sizeof(RotParams);
+    size_t sm = (size_t)2 * (max_large_n / 2 + 1) * sizeof(RotParams);   // pairs + staging share
     ZKQ_CUDA_TRY(smem_limit_max<jacobi_global_kernel<WA>>());
     if (cluster > 8)
       ZKQ_CUDA_TRY(cudaFuncSetAttribute(jacobi_global_kernel<WA>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
