@@ -109,11 +109,31 @@ __global__ void __launch_bounds__(256) oa_coupling_kernel(const OaProb* __restri
     cmw<2> num2 = c_zero<2>();
     if (i != j) {
       cmw<W> sv = c_load<W, W>(S + p.xoff * 2 * W, e);
-      mw<W> hs = mw_mul_d(mw_add(mw_load<W, W>(lam + p.loff * W, i), mw_load<W, W>(lam + p.loff * W, j)), 0.5);
-      cmw<W> num = c_add(sv, c_scale(r, hs));       // cancellation-sensitive: working precision
-      cpl = hypot(num.re.x[0], num.im.x[0]);
+      const double* lw = lam + p.loff * W;
+      // num is needed to an absolute 2^-(53 W) ||A|| (the residual it leaves is about its error).  When
+      // both terms are below 2^-(53 W - 100) ||A||, double-double (relative error about 2^-104) already
+      // reaches that, whatever the cancellation; otherwise the sum takes the working precision.
+      bool dd = false;
+      if constexpr (W > 2) {
+        const double hm = 0.5 * fabs(lw[(size_t)i * W] + lw[(size_t)j * W]);
+        const double mag = fmax(fmax(fabs(sv.re.x[0]), fabs(sv.im.x[0])), hm * fmax(fabs(r.re.x[0]), fabs(r.im.x[0])));
+        dd = mag <= ldexp(st[blockIdx.y].anorm, -(53 * W - 100));
+      }
+      if (dd) {
+        // the two leading words of a normalised expansion are a double-double within 2^-105 of it
+        auto lead2 = [](const double* w) { mw<2> t; t.x[0] = w[0]; t.x[1] = w[1]; return t; };
+        const cmw<2> s2 = c_make(lead2(sv.re.x), lead2(sv.im.x));
+        const cmw<2> r2 = c_make(lead2(r.re.x), lead2(r.im.x));
+        const mw<2> h2 = mw_mul_d(mw_add(lead2(lw + (size_t)i * W), lead2(lw + (size_t)j * W)), 0.5);
+        num2 = c_add(s2, c_scale(r2, h2));
+        cpl = hypot(num2.re.x[0], num2.im.x[0]);
+      } else {
+        mw<W> hs = mw_mul_d(mw_add(mw_load<W, W>(lw, i), mw_load<W, W>(lw, j)), 0.5);
+        cmw<W> num = c_add(sv, c_scale(r, hs));     // cancellation-sensitive: working precision
+        cpl = hypot(num.re.x[0], num.im.x[0]);
+        num2 = c_make(mw_from_words<2, W>(num.re.x), mw_from_words<2, W>(num.im.x));
+      }
       if (cpl > 0) atomicAdd(&csum[j - j0], cpl * cpl);
-      num2 = c_make(mw_from_words<2, W>(num.re.x), mw_from_words<2, W>(num.im.x));
     }
     c_store(NUM + p.xoff * 2 * 2, e, num2);
   }
@@ -196,14 +216,16 @@ __global__ void oa_E_kernel(const OaProb* __restrict__ pr, const double* __restr
     const int n = p.n, i = e % n, j = e / n;
     const int a = i < j ? i : j, b = i < j ? j : i;           // upper-triangle representative (a, b)
     const size_t eu = (size_t)a + (size_t)b * n;
-    cmw<W> r = c_load<W, W>(R + p.xoff * 2 * W, eu);
-    rmag = hypot(r.re.x[0], r.im.x[0]);
-    cmw<2> r2 = c_make(mw_from_words<2, W>(r.re.x), mw_from_words<2, W>(r.im.x));
+    // the two leading words of a normalised expansion are a double-double within 2^-105 of it
+    auto lead2 = [](const double* w) { mw<2> t; t.x[0] = w[0]; t.x[1] = w[1]; return t; };
+    const double* rp = R + (p.xoff + eu) * 2 * W;
+    const cmw<2> r2 = c_make(lead2(rp), lead2(rp + W));
+    rmag = hypot(rp[0], rp[W]);
     cmw<2> out;
     if (i == j) {
       out = c_scale_d(r2, 0.5);
       out.im = mw_zero<2>();
-      rmag = fabs(r.re.x[0]);
+      rmag = fabs(rp[0]);
     } else {
       // coupling num_ab (gap-free), evaluated in working precision by the coupling pass, kept as DD
       cmw<2> n2 = c_load<2, 2>(NUM + p.xoff * 2 * 2, eu);
@@ -212,9 +234,19 @@ __global__ void oa_E_kernel(const OaProb* __restrict__ pr, const double* __restr
       if (cl_start[p.loff + a] == cl_start[p.loff + b]) {
         incl = cpl;
       } else if (!no_rot) {
-        mw<W> la = mw_load<W, W>(lam + p.loff * W, a), lb = mw_load<W, W>(lam + p.loff * W, b);
-        mw<W> den = mw_sub(lb, la);
-        k = c_scale(n2, mw_recip(mw_from_words<2, W>(den.x)));
+        // gap lambda_b - lambda_a: in double-double when its error (2^-104 max|lambda| at most) moves
+        // k (gap) = num by less than 2^-(53 W + 2) ||A||, else in the working precision
+        const double* lw = lam + p.loff * W;
+        mw<2> den2 = mw_sub(lead2(lw + (size_t)b * W), lead2(lw + (size_t)a * W));
+        if constexpr (W > 2) {
+          const double lmax = fmax(fabs(lw[(size_t)a * W]), fabs(lw[(size_t)b * W]));
+          const double margin = fabs(den2.x[0]) - ldexp(lmax, -103);
+          if (!(margin > 0 && cpl * ldexp(lmax, -104) <= ldexp(st[blockIdx.y].anorm, -(53 * W + 2)) * margin)) {
+            const mw<W> den = mw_sub(mw_load<W, W>(lw, b), mw_load<W, W>(lw, a));
+            den2 = lead2(den.x);
+          }
+        }
+        k = c_scale(n2, mw_recip(den2));
       }
       cmw<2> half_r = c_scale_d(r2, 0.5);
       if (i < j) out = c_add(half_r, k);                       // e_ab = r_ab/2 + k_ab
