@@ -451,6 +451,19 @@ size_t oa_state_bytes(int batch, int64_t xe, int64_t le, int W) {
   return off;
 }
 
+// Bytes of the kept residue planes of A (one entry per problem, at the modulus count of the largest order):
+// nothing unless the products take the CRT form
+size_t oa_cache_bytes(int batch, const int32_t* n, int W, int prod_method) {
+  if (prod_method != 1 || batch <= 0) return 0;
+  int nmax = 0;
+  for (int b = 0; b < batch; ++b) nmax = std::max(nmax, n[b]);
+  const int r = crt_moduli(nmax, 53 * W + 6);
+  if (r == 0) return 0;
+  size_t total = 0;
+  for (int b = 0; b < batch; ++b) total += plane_cache_entry_bytes(n[b], n[b], r);
+  return total;
+}
+
 // Terms k (1..4) of the series (I - R)^{-1/2} = I + R/2 + 3R^2/8 + 5R^3/16 + 35R^4/128 + ... needed for the
 // polar factor of an n x n matrix with non-orthonormality max|r_ij| = maxR: with ||R||_2 <= n maxR, the first
 // dropped term is below (n maxR)^(k+1), which must be below 2^-(53W - 8); 0 when more than four terms would
@@ -499,9 +512,15 @@ zkq_status oa_refine_t(void* ctx, const OaBuffers& buf, int batch, const int32_t
   size_t oOO = take(sizeof(int32_t) * batch);                  // per active problem: orthonormalise only
   size_t oMU = take((size_t)le * W * sizeof(double));           // cluster means
   size_t oNUM = take((size_t)xe * 2 * 2 * sizeof(double));      // couplings (double-double)
+  // residue planes of A, which every iteration's P = A X and cluster products A X_J take as their left
+  // operand: split once and kept for the whole refinement (CRT form)
+  const size_t cache_bytes = oa_cache_bytes(batch, n, W, prod_method);
+  size_t oPC = take(cache_bytes);
   zkq_status s = grow_buf(buf.ws, buf.ws_bytes, off);
   if (s != ZKQ_OK) return s;
   char* base = (char*)*buf.ws;
+  PlaneCache pcache;
+  pcache.buf = base + oPC; pcache.bytes = cache_bytes;
   double *X = (double*)(base + oX), *X2 = (double*)(base + oX2), *Pm = (double*)(base + oP), *Sm = (double*)(base + oS),
          *Rm = (double*)(base + oR), *Em = (double*)(base + oE), *Lm = (double*)(base + oL);
   int32_t *CS = (int32_t*)(base + oCS), *CL = (int32_t*)(base + oCL), *WH = (int32_t*)(base + oWH), *TI = (int32_t*)(base + oTI);
@@ -541,12 +560,16 @@ zkq_status oa_refine_t(void* ctx, const OaBuffers& buf, int batch, const int32_t
     for (int b : act) {
       const OaProb& q = probs[b];
       double* Xb = X + q.xoff * 2 * W;
-      if (polish[b] != 1) p1.push_back({q.n, q.n, q.n, 0, A + q.a_off * 2 * wa, Xb, Pm + q.xoff * 2 * W, nullptr, 1.0, 0});
+      if (polish[b] != 1) {
+        MwProd pa{q.n, q.n, q.n, 0, A + q.a_off * 2 * wa, Xb, Pm + q.xoff * 2 * W, nullptr, 1.0, 0};
+        pa.keepA = 1;                                // A does not change: its planes are split once
+        p1.push_back(pa);
+      }
       MwProd pr_{q.n, q.n, q.n, 1, Xb, Xb, Rm + q.xoff * 2 * W, nullptr, -1.0, 1};
       pr_.hermitian = 1;                           // R = I - X^H X is Hermitian
       (r_first ? p1 : p2).push_back(pr_);
     }
-    s = mw_gemm_batched(p1.data(), (int)p1.size(), wa, W, W, p_bits, prod_method, buf.oz_ws, buf.oz_bytes, buf.oz_meta, buf.oz_meta_bytes, st, buf.stage);
+    s = mw_gemm_batched(p1.data(), (int)p1.size(), wa, W, W, p_bits, prod_method, buf.oz_ws, buf.oz_bytes, buf.oz_meta, buf.oz_meta_bytes, st, buf.stage, &pcache);
     if (s != ZKQ_OK) return s;
     for (int b : act) {
       const OaProb& q = probs[b];
@@ -760,14 +783,16 @@ zkq_status oa_refine_t(void* ctx, const OaBuffers& buf, int batch, const int32_t
         const OaProb& q = probs[c.prob];
         double* XJ = X2 + (q.xoff + (int64_t)c.start * q.n) * 2 * W;
         double* QJ = Pm + (q.xoff + (int64_t)c.start * q.n) * 2 * W;
-        p5.push_back({q.n, c.len, q.n, 0, A + q.a_off * 2 * wa, XJ, QJ, nullptr, 1.0, 0});
+        MwProd pa{q.n, c.len, q.n, 0, A + q.a_off * 2 * wa, XJ, QJ, nullptr, 1.0, 0};
+        pa.keepA = 1;
+        p5.push_back(pa);
         MwProd pt_{c.len, c.len, q.n, 1, XJ, QJ, CT + c.toff * 2 * W, nullptr, 1.0, 0};
         MwProd pg_{c.len, c.len, q.n, 1, XJ, XJ, CG + c.toff * 2 * W, nullptr, 1.0, 0};
         pt_.hermitian = 1; pg_.hermitian = 1;
         p6.push_back(pt_);
         p6.push_back(pg_);
       }
-      s = mw_gemm_batched(p5.data(), (int)p5.size(), wa, W, W, p_bits, prod_method, buf.oz_ws, buf.oz_bytes, buf.oz_meta, buf.oz_meta_bytes, st, buf.stage);
+      s = mw_gemm_batched(p5.data(), (int)p5.size(), wa, W, W, p_bits, prod_method, buf.oz_ws, buf.oz_bytes, buf.oz_meta, buf.oz_meta_bytes, st, buf.stage, &pcache);
       if (s != ZKQ_OK) return s;
       s = mw_gemm_batched(p6.data(), (int)p6.size(), W, W, W, p_bits, prod_method, buf.oz_ws, buf.oz_bytes, buf.oz_meta, buf.oz_meta_bytes, st, buf.stage);
       if (s != ZKQ_OK) return s;

@@ -827,9 +827,19 @@ static zkq_status grow(void** p, size_t* have, size_t need) {
 #define ZKQ_DISPATCH_W(w, F, ...) \
   do { if ((w) == 1) { F<1> __VA_ARGS__; } else if ((w) == 2) { F<2> __VA_ARGS__; } else { F<4> __VA_ARGS__; } } while (0)
 
+size_t plane_cache_entry_bytes(int m, int k, int r) {
+  const size_t mp = (size_t)(m + OZ_BM - 1) / OZ_BM * OZ_BM, kp = (size_t)(2 * k + 63) / 64 * 64;
+  return al((size_t)2 * r * mp * kp * sizeof(__half)) + al((size_t)m * sizeof(int32_t));
+}
+
+int crt_moduli(int k, int p_out_bits) {
+  CrtConst cc;
+  return crt_build(2 * k, p_out_bits, &cc) ? cc.r : 0;
+}
+
 zkq_status mw_gemm_batched(const MwProd* prods, int count, int wa, int wb, int wc, int p_out_bits, int method,
                            void** ws, size_t* ws_bytes, void** meta, size_t* meta_bytes, cudaStream_t st,
-                           HostStage* stage) {
+                           HostStage* stage, PlaneCache* cache) {
   // uploads of the batch description: pinned ring when available, else plain copies
   auto up = [&](void* dst, const void* src, size_t bytes) -> cudaError_t {
     if (stage) { stage->add(dst, src, bytes); return cudaSuccess; }
@@ -906,9 +916,33 @@ zkq_status mw_gemm_batched(const MwProd* prods, int count, int wa, int wb, int w
     if (srcA[i] != i) dp[i].sliceA = 0;
     if (srcB[i] != i) dp[i].sliceB = 0;
   }
+  // constant operands: planes and exponents from the caller's cache (kept by an earlier call), or split
+  // into a new cache entry by this call
+  std::vector<__half*> extP(count, nullptr);
+  std::vector<int32_t*> extE(count, nullptr);
+  if (crt && cache) {
+    for (int i = 0; i < count; ++i) {
+      if (srcA[i] != i || !prods[i].keepA) continue;
+      const OzProd& o = dp[i];
+      bool hit = false;
+      for (const PlaneCache::Entry& e : cache->entries)
+        if (e.A == o.A && e.opA == o.opA && e.m == o.m && e.k == o.k && e.q == cc.q && e.r == cc.r && e.s == cc.s) {
+          extP[i] = e.planes; extE[i] = e.exps; dp[i].sliceA = 0; hit = true;
+          break;
+        }
+      if (hit) continue;
+      const size_t need = plane_cache_entry_bytes(o.m, o.k, cc.r);
+      if (cache->used + need > cache->bytes) continue;
+      __half* planes = (__half*)(cache->buf + cache->used);
+      int32_t* exps = (int32_t*)(cache->buf + cache->used + al((size_t)plan.sA * o.mp * o.kp * sizeof(__half)));
+      cache->used += need;
+      cache->entries.push_back({o.A, o.opA, o.m, o.k, cc.q, cc.r, cc.s, planes, exps});
+      extP[i] = planes; extE[i] = exps;             // split into the entry by this call
+    }
+  }
   for (int i = 0; i < count; ++i) {
     OzProd& o = dp[i];
-    oA[i] = off; if (o.sliceA) off += al((size_t)plan.sA * o.mp * o.kp * sizeof(__half));
+    oA[i] = off; if (o.sliceA && !extP[i]) off += al((size_t)plan.sA * o.mp * o.kp * sizeof(__half));
     oB[i] = off; if (o.sliceB) off += al((size_t)plan.sB * o.np2 * o.kp * sizeof(__half));
     oD[i] = off; off += al(crt ? (size_t)3 * cc.r * o.mp * o.np2 : (size_t)(plan.S + 1) * o.mp * o.np2 * sizeof(int32_t));
     oe[i] = off; off += al((size_t)(o.m + o.n) * sizeof(int32_t));
@@ -924,6 +958,7 @@ zkq_status mw_gemm_batched(const MwProd* prods, int count, int wa, int wb, int w
     OzProd& o = dp[i];
     o.Ahat = (__half*)(base + oA[i]); o.Bhat = (__half*)(base + oB[i]);
     o.D = (int32_t*)(base + oD[i]); o.eA = (int32_t*)(base + oe[i]); o.eB = o.eA + o.m;
+    if (extP[i]) { o.Ahat = extP[i]; o.eA = extE[i]; }
   }
   for (int i = 0; i < count; ++i) {                // shared operands point at the first product's planes
     OzProd& o = dp[i];

@@ -2,6 +2,7 @@
 // the dense products A X, X^H X, X^H (A X) and X E of the refinement step.
 #pragma once
 #include <cstdint>
+#include <vector>
 #include <cuda_fp16.h>
 #include "common.cuh"
 
@@ -17,7 +18,26 @@ struct MwProd {
   double sgn; int base_identity;
   int hermitian = 0;             // C is Hermitian (m == n): only tiles touching i <= j are computed and the
                                  // lower triangle is written as the conjugate of the upper one
+  int keepA = 0;                 // op(A) does not change between calls: its residue planes may be kept in
+                                 // the caller's PlaneCache and reused (CRT form)
 };
+
+// Residue planes of operands that stay the same over several calls (the refinement's input matrix).  The
+// caller lends a device region for the whole sequence of calls; mw_gemm_batched keeps there the op(A)
+// planes and row exponents of products marked keepA, keyed by the operand (pointer, orientation, shape)
+// and the CRT constants, and later calls reuse them instead of splitting op(A) again.  The contents of a
+// cached operand must not change while its entry is in use; clear() forgets every entry.
+struct PlaneCache {
+  char* buf = nullptr;
+  size_t bytes = 0, used = 0;
+  struct Entry { const double* A; int opA, m, k, q, r, s; __half* planes; int32_t* exps; };
+  std::vector<Entry> entries;
+  void clear() { used = 0; entries.clear(); }
+};
+// bytes one cached operand of m rows and inner dimension k takes with r moduli (planes and exponents)
+size_t plane_cache_entry_bytes(int m, int k, int r);
+// moduli of the CRT form for inner dimension k at p_out_bits (0 when the digit form applies)
+int crt_moduli(int k, int p_out_bits);
 
 // device-side layout of one product inside the Ozaki workspace
 struct OzProd {
@@ -56,9 +76,10 @@ class HostStage;
 // multi-word GEMM on the FP64 pipe.  Metadata goes up through `stage` (pinned) when it is given.
 zkq_status mw_gemm_batched(const MwProd* prods, int count, int wa, int wb, int wc, int p_out_bits, int method,
                            void** ws, size_t* ws_bytes, void** meta, size_t* meta_bytes, cudaStream_t st,
-                           HostStage* stage);
-// Bytes mw_gemm_batched needs for the batch: its workspace exactly, its metadata as an upper bound
-// (host-side only; the operand pointers are compared, never read).
+                           HostStage* stage, PlaneCache* cache = nullptr);
+// Bytes mw_gemm_batched needs for the batch: its workspace exactly when no PlaneCache serves it (an upper
+// bound otherwise), its metadata as an upper bound (host-side only; the operand pointers are compared, never
+// read).
 zkq_status mw_gemm_workspace(const MwProd* prods, int count, int wa, int wb, int p_out_bits, int method,
                              size_t* ws_need, size_t* meta_need);
 // device bytes held once the split-product workspace or metadata has grown to `need` bytes from nothing
