@@ -241,7 +241,7 @@ zkq_status zkq_workspace_size(zkq_ctx* ctx, int batch, const int32_t* n, int a_w
   size_t total = meta + ws;
   if (oa) {
     total += oa_grow_bytes(oa_state_bytes(batch, xe, le, target_words) +
-                           oa_cache_bytes(batch, n, target_words, method == ZKQ_OA_OZAKI ? 1 : 0));
+                           2 * oa_cache_bytes(batch, n, target_words, method == ZKQ_OA_OZAKI ? 1 : 0));
     // split products of one iteration over every problem: P = A X (with R = I - X^H X when A has W words),
     // then S = X^H P (with R otherwise), then X + X E.  Later iterations run subsets of these products.  When the batch mixes K' = 2n above and
     // below 1024, its products take the digit form while any order above 512 is still refining, and the CRT

@@ -88,7 +88,7 @@ zkq_status oa_refine(void* ctx, const OaBuffers& buf, int batch, const int32_t* 
 // bytes of the refinement state oa_refine lays out (xe = sum n^2, le = sum n, W words per real), and the
 // device bytes its buffer holds once grown to `need` bytes from nothing
 size_t oa_state_bytes(int batch, int64_t xe, int64_t le, int W);
-// bytes of the refinement's kept residue planes of A (added to the state by oa_refine)
+// bytes of one of the refinement's two plane caches (A; X^H within an iteration), each added to the state
 size_t oa_cache_bytes(int batch, const int32_t* n, int W, int prod_method);
 size_t oa_grow_bytes(size_t need);
 

@@ -516,11 +516,14 @@ zkq_status oa_refine_t(void* ctx, const OaBuffers& buf, int batch, const int32_t
   // operand: split once and kept for the whole refinement (CRT form)
   const size_t cache_bytes = oa_cache_bytes(batch, n, W, prod_method);
   size_t oPC = take(cache_bytes);
+  // and those of X^H, shared within an iteration by R = I - X^H X (first call) and S = X^H P (second call)
+  size_t oXC = take(cache_bytes);
   zkq_status s = grow_buf(buf.ws, buf.ws_bytes, off);
   if (s != ZKQ_OK) return s;
   char* base = (char*)*buf.ws;
-  PlaneCache pcache;
+  PlaneCache pcache, xcache;
   pcache.buf = base + oPC; pcache.bytes = cache_bytes;
+  xcache.buf = base + oXC; xcache.bytes = cache_bytes;
   double *X = (double*)(base + oX), *X2 = (double*)(base + oX2), *Pm = (double*)(base + oP), *Sm = (double*)(base + oS),
          *Rm = (double*)(base + oR), *Em = (double*)(base + oE), *Lm = (double*)(base + oL);
   int32_t *CS = (int32_t*)(base + oCS), *CL = (int32_t*)(base + oCL), *WH = (int32_t*)(base + oWH), *TI = (int32_t*)(base + oTI);
@@ -567,9 +570,12 @@ zkq_status oa_refine_t(void* ctx, const OaBuffers& buf, int batch, const int32_t
       }
       MwProd pr_{q.n, q.n, q.n, 1, Xb, Xb, Rm + q.xoff * 2 * W, nullptr, -1.0, 1};
       pr_.hermitian = 1;                           // R = I - X^H X is Hermitian
+      pr_.keepA = r_first ? 2 : 0;                 // X^H's planes (xcache) serve S = X^H P in the second call
       (r_first ? p1 : p2).push_back(pr_);
     }
-    s = mw_gemm_batched(p1.data(), (int)p1.size(), wa, W, W, p_bits, prod_method, buf.oz_ws, buf.oz_bytes, buf.oz_meta, buf.oz_meta_bytes, st, buf.stage, &pcache);
+    xcache.clear();                                // X changed since the last iteration
+    PlaneCache* const caches[2] = {&pcache, &xcache};   // keepA 1: A's planes, 2: this iteration's X^H
+    s = mw_gemm_batched(p1.data(), (int)p1.size(), wa, W, W, p_bits, prod_method, buf.oz_ws, buf.oz_bytes, buf.oz_meta, buf.oz_meta_bytes, st, buf.stage, caches, 2);
     if (s != ZKQ_OK) return s;
     for (int b : act) {
       const OaProb& q = probs[b];
@@ -577,9 +583,10 @@ zkq_status oa_refine_t(void* ctx, const OaBuffers& buf, int batch, const int32_t
       double* Xb = X + q.xoff * 2 * W;
       MwProd ps_{q.n, q.n, q.n, 1, Xb, Pm + q.xoff * 2 * W, Sm + q.xoff * 2 * W, nullptr, 1.0, 0};
       ps_.hermitian = 1;                           // S = X^H A X is Hermitian
+      ps_.keepA = 2;                               // X^H's planes from the first call
       p2.push_back(ps_);
     }
-    s = mw_gemm_batched(p2.data(), (int)p2.size(), W, W, W, p_bits, prod_method, buf.oz_ws, buf.oz_bytes, buf.oz_meta, buf.oz_meta_bytes, st, buf.stage);
+    s = mw_gemm_batched(p2.data(), (int)p2.size(), W, W, W, p_bits, prod_method, buf.oz_ws, buf.oz_bytes, buf.oz_meta, buf.oz_meta_bytes, st, buf.stage, caches, 2);
     if (s != ZKQ_OK) return s;
     // statistics for every problem (inactive ones keep their last values: recompute is harmless but skipped)
     std::vector<OaProb> ap; for (int b : act) ap.push_back(probs[b]);
@@ -792,7 +799,8 @@ zkq_status oa_refine_t(void* ctx, const OaBuffers& buf, int batch, const int32_t
         p6.push_back(pt_);
         p6.push_back(pg_);
       }
-      s = mw_gemm_batched(p5.data(), (int)p5.size(), wa, W, W, p_bits, prod_method, buf.oz_ws, buf.oz_bytes, buf.oz_meta, buf.oz_meta_bytes, st, buf.stage, &pcache);
+      PlaneCache* const acache[1] = {&pcache};
+      s = mw_gemm_batched(p5.data(), (int)p5.size(), wa, W, W, p_bits, prod_method, buf.oz_ws, buf.oz_bytes, buf.oz_meta, buf.oz_meta_bytes, st, buf.stage, acache, 1);
       if (s != ZKQ_OK) return s;
       s = mw_gemm_batched(p6.data(), (int)p6.size(), W, W, W, p_bits, prod_method, buf.oz_ws, buf.oz_bytes, buf.oz_meta, buf.oz_meta_bytes, st, buf.stage);
       if (s != ZKQ_OK) return s;

@@ -839,7 +839,7 @@ int crt_moduli(int k, int p_out_bits) {
 
 zkq_status mw_gemm_batched(const MwProd* prods, int count, int wa, int wb, int wc, int p_out_bits, int method,
                            void** ws, size_t* ws_bytes, void** meta, size_t* meta_bytes, cudaStream_t st,
-                           HostStage* stage, PlaneCache* cache) {
+                           HostStage* stage, PlaneCache* const* caches, int ncaches) {
   // uploads of the batch description: pinned ring when available, else plain copies
   auto up = [&](void* dst, const void* src, size_t bytes) -> cudaError_t {
     if (stage) { stage->add(dst, src, bytes); return cudaSuccess; }
@@ -920,9 +920,10 @@ zkq_status mw_gemm_batched(const MwProd* prods, int count, int wa, int wb, int w
   // into a new cache entry by this call
   std::vector<__half*> extP(count, nullptr);
   std::vector<int32_t*> extE(count, nullptr);
-  if (crt && cache) {
+  if (crt && caches) {
     for (int i = 0; i < count; ++i) {
-      if (srcA[i] != i || !prods[i].keepA) continue;
+      if (srcA[i] != i || prods[i].keepA < 1 || prods[i].keepA > ncaches || !caches[prods[i].keepA - 1]) continue;
+      PlaneCache* cache = caches[prods[i].keepA - 1];
       const OzProd& o = dp[i];
       bool hit = false;
       for (const PlaneCache::Entry& e : cache->entries)

@@ -18,8 +18,8 @@ struct MwProd {
   double sgn; int base_identity;
   int hermitian = 0;             // C is Hermitian (m == n): only tiles touching i <= j are computed and the
                                  // lower triangle is written as the conjugate of the upper one
-  int keepA = 0;                 // op(A) does not change between calls: its residue planes may be kept in
-                                 // the caller's PlaneCache and reused (CRT form)
+  int keepA = 0;                 // k > 0: op(A) stays the same over several calls; its residue planes are
+                                 // kept in the caller's k-th PlaneCache and reused (CRT form)
 };
 
 // Residue planes of operands that stay the same over several calls (the refinement's input matrix).  The
@@ -76,7 +76,7 @@ class HostStage;
 // multi-word GEMM on the FP64 pipe.  Metadata goes up through `stage` (pinned) when it is given.
 zkq_status mw_gemm_batched(const MwProd* prods, int count, int wa, int wb, int wc, int p_out_bits, int method,
                            void** ws, size_t* ws_bytes, void** meta, size_t* meta_bytes, cudaStream_t st,
-                           HostStage* stage, PlaneCache* cache = nullptr);
+                           HostStage* stage, PlaneCache* const* caches = nullptr, int ncaches = 0);
 // Bytes mw_gemm_batched needs for the batch: its workspace exactly when no PlaneCache serves it (an upper
 // bound otherwise), its metadata as an upper bound (host-side only; the operand pointers are compared, never
 // read).
