@@ -311,18 +311,6 @@ __global__ void oa_promote_kernel(const OaCluster* __restrict__ cl, const double
   const double* v = V64 + (c.toff + e) * 2;
   c_store(Wm + c.toff * 2 * W, e, c_make(mw_from<W>(v[0]), mw_from<W>(v[1])));
 }
-// H = (3 I - G) / 2 in place (Newton-Schulz step for the unitary polar factor: W <- W H)
-template <int W>
-__global__ void oa_ns_kernel(const OaCluster* __restrict__ cl, double* __restrict__ G) {
-  const OaCluster c = cl[blockIdx.y];
-  int e = blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= c.len * c.len) return;
-  cmw<W> g = c_load<W, W>(G + c.toff * 2 * W, e);
-  g = c_scale_d(g, -0.5);
-  if (e % c.len == e / c.len) g.re = mw_add_d(g.re, 1.5);
-  c_store(G + c.toff * 2 * W, e, g);
-}
-
 // out = coef R (+ I): the terms of the polar (Loewdin) factor (X^H X)^{-1/2} = (I - R)^{-1/2} of a finishing
 // problem, evaluated by Horner's rule in R (see oa_refine_t); one grid row per listed problem
 template <int W>
@@ -812,28 +800,15 @@ zkq_status oa_refine_t(void* ctx, const OaBuffers& buf, int batch, const int32_t
       for (size_t c = 0; c < cls.size(); ++c) { cn[c] = cls[c].len; co[c] = cls[c].toff; }
       s = eigh_internal(ctx, (int)cls.size(), cn.data(), co.data(), T, 1, TW, TV, TI, st, PC_JACOBI_CLUSTER);
       if (s != ZKQ_OK) return s;
-      // The FP64 eigenvector matrix is unitary only to 2^-53; two Newton-Schulz steps W <- W (3I - W^H W)/2
-      // in W-word products make it unitary to working precision, so the rotation does not disturb the
-      // orthonormality of X (which would inflate the cluster thresholds of the next iteration).
+      // The FP64 eigenvector matrix W is unitary only to about 2^-53 sqrt(len).  It rotates X_J as it is: its
+      // departure from unitarity adds non-orthonormality to X_J, which the couplings do not see (they are
+      // insensitive to it at first order) and the next update's R/2 removes, and which is far below what
+      // every update leaves anyway (about E^H E, 10^-13 to 10^-10 in the peeling iterations of a graded
+      // spectrum).  Two Newton-Schulz steps making W unitary to the working precision cost four len^3
+      // products per cluster and changed neither the iterations nor the peeling.
       { ProfScope ps_(PC_OA, st); oa_promote_kernel<W><<<g, 256, 0, st>>>(CLD, TV, CT); }
       ZKQ_CUDA_TRY(cudaGetLastError());
-      double* Wcur = CT; double* Wnext = CW;
-      for (int ns = 0; ns < 2; ++ns) {
-        std::vector<MwProd> pg, pw;
-        for (auto& c : cls) {
-          MwProd g_{c.len, c.len, c.len, 1, Wcur + c.toff * 2 * W, Wcur + c.toff * 2 * W, CG + c.toff * 2 * W, nullptr, 1.0, 0};
-          g_.hermitian = 1;
-          pg.push_back(g_);
-        }
-        s = mw_gemm_batched(pg.data(), (int)pg.size(), W, W, W, p_bits, prod_method, buf.oz_ws, buf.oz_bytes, buf.oz_meta, buf.oz_meta_bytes, st, buf.stage);
-        if (s != ZKQ_OK) return s;
-        { ProfScope ps_(PC_OA, st); oa_ns_kernel<W><<<g, 256, 0, st>>>(CLD, CG); }
-        ZKQ_CUDA_TRY(cudaGetLastError());
-        for (auto& c : cls) pw.push_back({c.len, c.len, c.len, 0, Wcur + c.toff * 2 * W, CG + c.toff * 2 * W, Wnext + c.toff * 2 * W, nullptr, 1.0, 0});
-        s = mw_gemm_batched(pw.data(), (int)pw.size(), W, W, W, p_bits, prod_method, buf.oz_ws, buf.oz_bytes, buf.oz_meta, buf.oz_meta_bytes, st, buf.stage);
-        if (s != ZKQ_OK) return s;
-        std::swap(Wcur, Wnext);
-      }
+      const double* Wcur = CT;
       // Y_J = X2_J W_J into the X buffer (free now), then copy back into X2
       std::vector<MwProd> p4;
       for (auto& c : cls) {
