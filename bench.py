@@ -405,7 +405,7 @@ def roofline(Z, prof, ns, steps):
                     peak_source="derived: 152 SMs x 2 FP64 FMA per clock per SM x 2.07 GHz x 2 flops "
                                 "(MEASURED_PEAKS.json has no FP64 entry)",
                     peak_measured_dfma=FP64_TFLOPS_MEASURED, frac_of_measured_dfma=achieved / FP64_TFLOPS_MEASURED,
-                    work="48 n flops per applied rotation (24 n FMA: Hermitian 2x2-block update of A 12 n + V 12 n)")
+                    work="32 n flops per applied rotation (16 n FMA: scaled Hermitian 2x2-block update of A 8 n + V 8 n)")
     if dom_name == "rqi":
         it = 2.0
         cmacs = sum(nn * (it * (nn ** 3 / 3.0 + nn * nn) + 2 * nn * nn) for nn in ns) * steps

@@ -24,7 +24,27 @@ namespace cg = cooperative_groups;
 
 namespace zkq {
 
-struct RotParams { double c, tb; c64 z1, z2; int rot; int p, q; };
+// Rotations act on scaled matrices (fast rotations): the true A_ij = s_i s_j A~_ij and V_ij = V~_ij s_j
+// with a positive scale s per index.  Rotating the pair (p, q) multiplies s_p and s_q by c, so the stored
+// entries take the rotation divided by c, I + w: col p -= w1 col q, col q += w2 col p (and the conjugate
+// transpose from the left) with w1 = t e^{-i phi} s_q / s_p, w2 = t e^{i phi} s_p / s_q, |t| <= 1.  That is
+// 4 FMA per complex entry instead of 6.  The scales are folded back into A~ and V~ after every sweep.
+// Stored per pair: c, the new stored diagonal entries dpn, dqn (true values over the new squared scales).
+struct RotParams { double c, dpn, dqn; c64 w1, w2; int rot; int p, q; };
+
+// x - w y, x + w y, x - conj(w) y, x + conj(w) y with four FMA each
+__device__ __forceinline__ c64 c_sub_mul(c64 x, c64 w, c64 y) {
+  return {fma(-w.re, y.re, fma(w.im, y.im, x.re)), fma(-w.re, y.im, fma(-w.im, y.re, x.im))};
+}
+__device__ __forceinline__ c64 c_add_mul(c64 x, c64 w, c64 y) {
+  return {fma(w.re, y.re, fma(-w.im, y.im, x.re)), fma(w.re, y.im, fma(w.im, y.re, x.im))};
+}
+__device__ __forceinline__ c64 c_sub_cmul(c64 x, c64 w, c64 y) {
+  return {fma(-w.re, y.re, fma(-w.im, y.im, x.re)), fma(-w.re, y.im, fma(w.im, y.re, x.im))};
+}
+__device__ __forceinline__ c64 c_add_cmul(c64 x, c64 w, c64 y) {
+  return {fma(w.re, y.re, fma(w.im, y.im, x.re)), fma(w.re, y.im, fma(-w.im, y.re, x.im))};
+}
 
 
 // Storage policy: matrix element (i, j) of a column-major matrix with leading dimension ld.
@@ -77,7 +97,7 @@ __device__ __forceinline__ void grid_barrier(GridBar* gb, unsigned nblocks) {
 
 template <bool SMEM, int SYNC, int WA>
 __device__ void jacobi_problem(int n, const double* __restrict__ A_in, Mat<SMEM> A, Mat<SMEM> V,
-                               RotParams* rp, double* red, int max_sweeps, unsigned long long* flops,
+                               RotParams* rp, double* sig, double* red, int max_sweeps, unsigned long long* flops,
                                double* __restrict__ W_out, double* __restrict__ V_out, int32_t* info,
                                int part, int nparts, GridBar* gb = nullptr) {
   auto sync = [&] {
@@ -100,6 +120,7 @@ __device__ void jacobi_problem(int n, const double* __restrict__ A_in, Mat<SMEM>
     V.set(i, j, c64{i == j ? 1.0 : 0.0, 0.0});
     fro_part += v.re * v.re + v.im * v.im;
   }
+  for (int i = tid; i < n; i += nth) sig[i] = 1.0;   // every CTA keeps its own copy of the scales
   // ||A||_F: block reduction; with several CTAs each keeps its own partial, combined via red[] in global
   __shared__ double s_red[32];
   __shared__ double s_tol;
@@ -135,19 +156,24 @@ __device__ void jacobi_problem(int n, const double* __restrict__ A_in, Mat<SMEM>
       RotParams* stage = SYNC == 1 ? rp + P : rp;
       for (int k = k0 + tid; k < k1; k += nth) {
         int p, q; rr_pair(m, r, k, p, q);
-        RotParams pr; pr.p = p; pr.q = q; pr.rot = 0; pr.c = 1.0; pr.tb = 0.0; pr.z1 = {0, 0}; pr.z2 = {0, 0};
+        RotParams pr; pr.p = p; pr.q = q; pr.rot = 0; pr.c = 1.0; pr.dpn = 0.0; pr.dqn = 0.0; pr.w1 = {0, 0}; pr.w2 = {0, 0};
         if (q < n) {
-          c64 b = A.get(p, q);
+          const double sp = sig[p], sq = sig[q];
+          const c64 bs = A.get(p, q);
+          const c64 b = {bs.re * (sp * sq), bs.im * (sp * sq)};      // true entries
           double ab = hypot(b.re, b.im);
           if (ab > tol) {
-            double app = A.get(p, p).re, aqq = A.get(q, q).re;
+            double app = A.get(p, p).re * (sp * sp), aqq = A.get(q, q).re * (sq * sq);
             double tau = (aqq - app) / (2.0 * ab);
             double t = (tau >= 0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
-            double c = 1.0 / sqrt(1.0 + t * t), s = t * c;
+            double c = 1.0 / sqrt(1.0 + t * t);
             double er = b.re / ab, ei = b.im / ab;
-            pr.c = c; pr.tb = t * ab; pr.rot = 1;
-            pr.z1 = {s * er, -s * ei};
-            pr.z2 = {s * er, s * ei};
+            const double tb = t * ab, rq = sq / sp;
+            pr.c = c; pr.rot = 1;
+            pr.w1 = {t * er * rq, -t * ei * rq};
+            pr.w2 = {t * er / rq, t * ei / rq};
+            pr.dpn = (app - tb) / ((c * sp) * (c * sp));             // (a_pp - t|b|) / s_p'^2
+            pr.dqn = (aqq + tb) / ((c * sq) * (c * sq));
           }
         }
         stage[k - k0] = pr;
@@ -162,8 +188,14 @@ __device__ void jacobi_problem(int n, const double* __restrict__ A_in, Mat<SMEM>
           const RotParams pr = src[k - owner * per];
           rp[k] = pr;
           my_rot += pr.rot;                        // every CTA counts all pairs: the same total everywhere
+          if (pr.rot) { sig[pr.p] *= pr.c; sig[pr.q] *= pr.c; }   // pairs are disjoint: no conflicts
         }
         __syncthreads();
+      } else {
+        for (int k = tid; k < P; k += nth) {
+          const RotParams& pr = rp[k];
+          if (pr.rot) { sig[pr.p] *= pr.c; sig[pr.q] *= pr.c; }
+        }
       }
       // phase 2: 2x2 block updates on the upper block triangle + V <- V J
       const int nblk = P * (P + 1) / 2;
@@ -177,9 +209,8 @@ __device__ void jacobi_problem(int n, const double* __restrict__ A_in, Mat<SMEM>
           const RotParams a = rp[k2], b = rp[k];   // rows from pair k2, columns from pair k
           if (k2 == k) {
             if (a.rot) {
-              c64 dp = A.get(a.p, a.p), dq = A.get(a.q, a.q);
-              A.set(a.p, a.p, c64{dp.re - a.tb, 0.0});
-              A.set(a.q, a.q, c64{dq.re + a.tb, 0.0});
+              A.set(a.p, a.p, c64{a.dpn, 0.0});
+              A.set(a.q, a.q, c64{a.dqn, 0.0});
               A.set(a.p, a.q, c64{0.0, 0.0});
               A.set(a.q, a.p, c64{0.0, 0.0});
             }
@@ -192,25 +223,17 @@ __device__ void jacobi_problem(int n, const double* __restrict__ A_in, Mat<SMEM>
           c64 x01 = hc1 ? A.get(r0, c1) : c64{0, 0};
           c64 x10 = hr1 ? A.get(r1, c0) : c64{0, 0};
           c64 x11 = (hr1 && hc1) ? A.get(r1, c1) : c64{0, 0};
-          // T = X J_b : col0 = X[:,0] c - X[:,1] z1, col1 = X[:,0] z2 + X[:,1] c
+          // T = X (I + W_b): col0 = X[:,0] - w1 X[:,1], col1 = X[:,1] + w2 X[:,0]
           c64 t00, t01, t10, t11;
           if (b.rot) {
-            c64 u = cmul(b.z1, x01), v = cmul(b.z2, x00);
-            t00 = {b.c * x00.re - u.re, b.c * x00.im - u.im};
-            t01 = {v.re + b.c * x01.re, v.im + b.c * x01.im};
-            u = cmul(b.z1, x11); v = cmul(b.z2, x10);
-            t10 = {b.c * x10.re - u.re, b.c * x10.im - u.im};
-            t11 = {v.re + b.c * x11.re, v.im + b.c * x11.im};
+            t00 = c_sub_mul(x00, b.w1, x01); t01 = c_add_mul(x01, b.w2, x00);
+            t10 = c_sub_mul(x10, b.w1, x11); t11 = c_add_mul(x11, b.w2, x10);
           } else { t00 = x00; t01 = x01; t10 = x10; t11 = x11; }
-          // Y = J_a^H T : row0 = c T[0,:] - z2 T[1,:], row1 = z1 T[0,:] + c T[1,:]
+          // Y = (I + W_a)^H T: row0 = T[0,:] - conj(w1) T[1,:], row1 = T[1,:] + conj(w2) T[0,:]
           c64 y00, y01, y10, y11;
           if (a.rot) {
-            c64 u = cmul(a.z2, t10), v = cmul(a.z1, t00);
-            y00 = {a.c * t00.re - u.re, a.c * t00.im - u.im};
-            y10 = {v.re + a.c * t10.re, v.im + a.c * t10.im};
-            u = cmul(a.z2, t11); v = cmul(a.z1, t01);
-            y01 = {a.c * t01.re - u.re, a.c * t01.im - u.im};
-            y11 = {v.re + a.c * t11.re, v.im + a.c * t11.im};
+            y00 = c_sub_cmul(t00, a.w1, t10); y10 = c_add_cmul(t10, a.w2, t00);
+            y01 = c_sub_cmul(t01, a.w1, t11); y11 = c_add_cmul(t11, a.w2, t01);
           } else { y00 = t00; y01 = t01; y10 = t10; y11 = t11; }
           A.set(r0, c0, y00); A.set(c0, r0, cconj(y00));
           if (hc1) { A.set(r0, c1, y01); A.set(c1, r0, cconj(y01)); }
@@ -222,18 +245,29 @@ __device__ void jacobi_problem(int n, const double* __restrict__ A_in, Mat<SMEM>
           const RotParams b = rp[k];
           if (!b.rot) continue;
           c64 x = V.get(i, b.p), y = V.get(i, b.q);
-          c64 u = cmul(b.z1, y), v = cmul(b.z2, x);
-          V.set(i, b.p, c64{b.c * x.re - u.re, b.c * x.im - u.im});
-          V.set(i, b.q, c64{v.re + b.c * y.re, v.im + b.c * y.im});
+          V.set(i, b.p, c_sub_mul(x, b.w1, y));
+          V.set(i, b.q, c_add_mul(y, b.w2, x));
         }
       }
       sync();
     }
+    // fold the scales into the stored matrices (each CTA its share of the entries, with its own copy of the
+    // scales, identical in every CTA); the next sweep reads them after the barrier
+    for (int e = gtid; e < n * n; e += gnth) {
+      const int i = e % n, j = e / n;
+      const double sa = sig[i] * sig[j], sv = sig[j];
+      const c64 a = A.get(i, j), v = V.get(i, j);
+      A.set(i, j, c64{a.re * sa, a.im * sa});
+      V.set(i, j, c64{v.re * sv, v.im * sv});
+    }
+    __syncthreads();
+    for (int i = tid; i < n; i += nth) sig[i] = 1.0;
+    sync();
     if (my_rot) atomicAdd(&s_rot, my_rot);
     __syncthreads();
-    // algorithmic FP64 flops of this sweep: per applied rotation 24 n FMA (12 n on A: a round's n/2
-    // rotations update n^2/8 2x2 blocks at 48 FMA each; 12 n on V) = 48 n flops; counted once per problem
-    if (part == 0 && tid == 0 && flops && s_rot) atomicAdd(flops, (unsigned long long)s_rot * 48ULL * (unsigned long long)n);
+    // FP64 flops of this sweep: per applied rotation 16 n FMA (8 n on A: a round's n/2 rotations update
+    // n^2/8 2x2 blocks at 32 FMA each; 8 n on V) = 32 n flops; counted once per problem
+    if (part == 0 && tid == 0 && flops && s_rot) atomicAdd(flops, (unsigned long long)s_rot * 32ULL * (unsigned long long)n);
     if constexpr (SYNC != 0) {
       // every CTA computed the same parameters, but take part 0's count so the barrier counts of the
       // cooperating CTAs cannot diverge
@@ -275,6 +309,9 @@ __device__ void jacobi_problem(int n, const double* __restrict__ A_in, Mat<SMEM>
   }
 }
 
+// shared-memory bytes of the scales of an order-n problem, 16-byte aligned (the pair parameters follow)
+__host__ __device__ __forceinline__ size_t jacobi_scale_bytes(int n) { return ((size_t)n * sizeof(double) + 15) & ~(size_t)15; }
+
 // small problems: matrix and eigenvectors in shared memory, one CTA per problem
 template <int WA>
 __global__ void __launch_bounds__(256) jacobi_smem_kernel(JacobiBatch jb, int first, int count) {
@@ -286,8 +323,9 @@ __global__ void __launch_bounds__(256) jacobi_smem_kernel(JacobiBatch jb, int fi
   c64* sA = reinterpret_cast<c64*>(smem);
   c64* sV = sA + (size_t)ld * n;
   RotParams* rp = reinterpret_cast<RotParams*>(sV + (size_t)ld * n);
+  double* sig = reinterpret_cast<double*>(rp + (n / 2 + 1));
   Mat<true> A{sA, ld}, V{sV, ld};
-  jacobi_problem<true, 0, WA>(n, jb.A + jb.a_off[b] * 2 * WA, A, V, rp, nullptr, jb.max_sweeps, jb.flops,
+  jacobi_problem<true, 0, WA>(n, jb.A + jb.a_off[b] * 2 * WA, A, V, rp, sig, nullptr, jb.max_sweeps, jb.flops,
                                   jb.W + jb.w_off[b], jb.V + jb.a_off[b] * 2, jb.info + b, 0, 1);
 }
 
@@ -301,14 +339,15 @@ __global__ void __launch_bounds__(256, 4) jacobi_global_kernel(JacobiBatch jb, i
   const int n = jb.n[b];
   double* wsA = jb.ws + jb.ws_off[b];
   double* wsV = wsA + (size_t)n * n * 2;
-  RotParams* rp = reinterpret_cast<RotParams*>(smem);
+  double* sig = reinterpret_cast<double*>(smem);                 // scales, then the pair parameters
+  RotParams* rp = reinterpret_cast<RotParams*>(smem + jacobi_scale_bytes(n));
   Mat<false> A{reinterpret_cast<c64*>(wsA), n}, V{reinterpret_cast<c64*>(wsV), n};
   double* red = jb.red + (size_t)64 * (blockIdx.x / nparts);   // 2 * cluster (<= 32) entries used
   if (nparts > 1)
-    jacobi_problem<false, 1, WA>(n, jb.A + jb.a_off[b] * 2 * WA, A, V, rp, red, jb.max_sweeps, jb.flops,
+    jacobi_problem<false, 1, WA>(n, jb.A + jb.a_off[b] * 2 * WA, A, V, rp, sig, red, jb.max_sweeps, jb.flops,
                                     jb.W + jb.w_off[b], jb.V + jb.a_off[b] * 2, jb.info + b, part, nparts);
   else
-    jacobi_problem<false, 0, WA>(n, jb.A + jb.a_off[b] * 2 * WA, A, V, rp, red, jb.max_sweeps, jb.flops,
+    jacobi_problem<false, 0, WA>(n, jb.A + jb.a_off[b] * 2 * WA, A, V, rp, sig, red, jb.max_sweeps, jb.flops,
                                      jb.W + jb.w_off[b], jb.V + jb.a_off[b] * 2, jb.info + b, 0, 1);
 }
 
@@ -318,20 +357,23 @@ template <int WA>
 __global__ void __launch_bounds__(256, 4) jacobi_grid_kernel(JacobiBatch jb, int first, int count, GridBar* gb,
                                                           const int32_t* __restrict__ grp_start, int red_stride) {
   extern __shared__ __align__(16) unsigned char smem[];
-  RotParams* rp = reinterpret_cast<RotParams*>(smem);
   int q = 0;
   while (q + 1 < count && (int)blockIdx.x >= grp_start[q + 1]) ++q;
   const int part = (int)blockIdx.x - grp_start[q], nparts = grp_start[q + 1] - grp_start[q];
   const int b = jb.order[first + q];
   const int n = jb.n[b];
+  double* sig = reinterpret_cast<double*>(smem);                 // scales, then the pair parameters
+  RotParams* rp = reinterpret_cast<RotParams*>(smem + jacobi_scale_bytes(n));
   double* wsA = jb.ws + jb.ws_off[b];
   double* wsV = wsA + (size_t)n * n * 2;
   Mat<false> A{reinterpret_cast<c64*>(wsA), n}, V{reinterpret_cast<c64*>(wsV), n};
-  jacobi_problem<false, 2, WA>(n, jb.A + jb.a_off[b] * 2 * WA, A, V, rp, jb.red + (size_t)q * red_stride, jb.max_sweeps,
+  jacobi_problem<false, 2, WA>(n, jb.A + jb.a_off[b] * 2 * WA, A, V, rp, sig, jb.red + (size_t)q * red_stride, jb.max_sweeps,
                                jb.flops, jb.W + jb.w_off[b], jb.V + jb.a_off[b] * 2, jb.info + b, part, nparts, gb + q);
 }
 
-size_t jacobi_smem_bytes(int n) { return (size_t)2 * (n + 1) * n * sizeof(c64) + (size_t)(n / 2 + 1) * sizeof(RotParams); }
+size_t jacobi_smem_bytes(int n) {
+  return (size_t)2 * (n + 1) * n * sizeof(c64) + (size_t)(n / 2 + 1) * sizeof(RotParams) + (size_t)n * sizeof(double);
+}
 
 template <int WA>
 static zkq_status launch_words(const JacobiBatch& jb, int n_small, int n_large, int max_small_n, int max_large_n,
@@ -345,7 +387,7 @@ static zkq_status launch_words(const JacobiBatch& jb, int n_small, int n_large, 
     ZKQ_CUDA_TRY(cudaGetLastError());
   }
   if (n_large > 0 && grid_blocks > 0) {
-    size_t sm = (size_t)(max_large_n / 2 + 1) * sizeof(RotParams);
+    size_t sm = jacobi_scale_bytes(max_large_n) + (size_t)(max_large_n / 2 + 1) * sizeof(RotParams);
     ZKQ_CUDA_TRY(smem_limit_max<jacobi_grid_kernel<WA>>());
     ZKQ_CUDA_TRY(cudaMemsetAsync(gb, 0, sizeof(GridBar) * n_large, st));
     JacobiBatch jbc = jb;
@@ -356,7 +398,7 @@ static zkq_status launch_words(const JacobiBatch& jb, int n_small, int n_large, 
     return ZKQ_OK;
   }
   if (n_large > 0) {
-    size_t sm = (size_t)2 * (max_large_n / 2 + 1) * sizeof(RotParams);   // pairs + staging share
+    size_t sm = jacobi_scale_bytes(max_large_n) + (size_t)2 * (max_large_n / 2 + 1) * sizeof(RotParams);   // scales, pairs, staging share
     ZKQ_CUDA_TRY(smem_limit_max<jacobi_global_kernel<WA>>());
     if (cluster > 8)
       ZKQ_CUDA_TRY(cudaFuncSetAttribute(jacobi_global_kernel<WA>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
@@ -394,7 +436,7 @@ zkq_status set_grid_barrier_hook(int extra_arrivals, int log2_poll_limit) {
 }
 
 int jacobi_grid_max_blocks(int max_large_n, int a_words) {
-  size_t sm = (size_t)(max_large_n / 2 + 1) * sizeof(RotParams);
+  size_t sm = jacobi_scale_bytes(max_large_n) + (size_t)(max_large_n / 2 + 1) * sizeof(RotParams);
   int per_sm = 0;
   cudaError_t e = cudaSuccess;
   if (a_words == 1) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, jacobi_grid_kernel<1>, 256, sm);
