@@ -758,8 +758,11 @@ zkq_status oa_refine_t(void* ctx, const OaBuffers& buf, int batch, const int32_t
     for (int b : upd) {
       const OaProb& q = probs[b];
       // rotate only clusters whose members are still coupled (gap-free measure |s_ij + lambda_j r_ij|);
-      // non-orthonormality alone is removed by the r/2 part of E
-      bool need = hst[b].cl_off > tol * (hst[b].anorm > 0 ? hst[b].anorm : 1.0) && hst[b].nclusters > 0 && polish[b] == 0;
+      // non-orthonormality alone is removed by the r/2 part of E.  The bar is the one the polar finish sets
+      // for every coupling (sqrt(n) max|num| <= tol ||A|| / 16): a cluster left coupled just below tol would
+      // keep its problem from finishing and send it through the orthonormalising steps.
+      bool need = hst[b].cl_off * sqrt((double)q.n) > tol * (hst[b].anorm > 0 ? hst[b].anorm : 1.0) / 16.0 &&
+                  hst[b].nclusters > 0 && polish[b] == 0;
       if (!need) continue;
       for (int c = 0; c < q.n;) {
         int len = hcl_len[q.loff + c];
