@@ -297,19 +297,23 @@ def run_ours(args):
     # end to end through the C ABI: pinned host input -> device, hot path, results back to pinned host
     Wo_h = torch.empty(R.Wo.numel(), dtype=torch.float64).pin_memory()
     Vo_h = torch.empty(R.Vo.numel(), dtype=torch.float64).pin_memory()
-    e2e_ms = []
+    e2e_ms, parts = [], []
     for _ in range(max(1, min(args.steps, 3))):
-        e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+        ev[0].record(stream)
         with torch.cuda.stream(stream):
             R.A.copy_(R.A_host, non_blocking=True)
+            ev[1].record(stream)
             R.step(ctx, stream)
+            ev[2].record(stream)
             Wo_h.copy_(R.Wo, non_blocking=True)
             Vo_h.copy_(R.Vo, non_blocking=True)
-        e1.record(stream)
-        e1.synchronize()
-        e2e_ms.append(e0.elapsed_time(e1))
+        ev[3].record(stream)
+        ev[3].synchronize()
+        e2e_ms.append(ev[0].elapsed_time(ev[3]))
+        parts.append([ev[i].elapsed_time(ev[i + 1]) for i in range(3)])
     e2e_t = float(np.mean(e2e_ms))
+    h2d_ms, e2e_step_ms, d2h_ms = (float(x) for x in np.mean(parts, axis=0))
     if world > 1:
         t = torch.tensor([e2e_t], device=dev)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
@@ -331,7 +335,8 @@ def run_ours(args):
         "roofline": roof,
         "clocks": clk,
         "e2e": {"value": e2e_value, "unit": "eigenpairs/s", "h2d_bytes_per_step": int(in_bytes),
-                "d2h_bytes_per_step": int((R.Wo.numel() + R.Vo.numel()) * 8)},
+                "d2h_bytes_per_step": int((R.Wo.numel() + R.Vo.numel()) * 8),
+                "h2d_ms": h2d_ms, "step_ms": e2e_step_ms, "d2h_ms": d2h_ms},
         "gpu_launches": int(sum(v[1] for v in prof.values())),
     }
     if args.workload == "batch256_qd" and not args.no_compare:
