@@ -28,7 +28,8 @@ namespace zkq {
 // with a positive scale s per index.  Rotating the pair (p, q) multiplies s_p and s_q by c, so the stored
 // entries take the rotation divided by c, I + w: col p -= w1 col q, col q += w2 col p (and the conjugate
 // transpose from the left) with w1 = t e^{-i phi} s_q / s_p, w2 = t e^{i phi} s_p / s_q, |t| <= 1.  That is
-// 4 FMA per complex entry instead of 6.  The scales are folded back into A~ and V~ after every sweep.
+// 4 FMA per complex entry instead of 6.  The scales are folded back into A~ and V~ after every 256 rounds
+// and at the end of every sweep.
 // Stored per pair: c, the new stored diagonal entries dpn, dqn (true values over the new squared scales).
 struct RotParams { double c, dpn, dqn; c64 w1, w2; int rot; int p, q; };
 
@@ -250,19 +251,22 @@ __device__ void jacobi_problem(int n, const double* __restrict__ A_in, Mat<SMEM>
         }
       }
       sync();
+      // fold the scales into the stored matrices after every 256 rounds and at the end of the sweep (each
+      // CTA its share of the entries, with its own copy of the scales, identical in every CTA): c >= 2^-1/2,
+      // so the scales stay above 2^-128 and the stored entries below 2^256 times their true size
+      if ((r & 255) == 255 || r == m - 2) {
+        for (int e = gtid; e < n * n; e += gnth) {
+          const int i = e % n, j = e / n;
+          const double sa = sig[i] * sig[j], sv = sig[j];
+          const c64 a = A.get(i, j), v = V.get(i, j);
+          A.set(i, j, c64{a.re * sa, a.im * sa});
+          V.set(i, j, c64{v.re * sv, v.im * sv});
+        }
+        __syncthreads();
+        for (int i = tid; i < n; i += nth) sig[i] = 1.0;
+        sync();
+      }
     }
-    // fold the scales into the stored matrices (each CTA its share of the entries, with its own copy of the
-    // scales, identical in every CTA); the next sweep reads them after the barrier
-    for (int e = gtid; e < n * n; e += gnth) {
-      const int i = e % n, j = e / n;
-      const double sa = sig[i] * sig[j], sv = sig[j];
-      const c64 a = A.get(i, j), v = V.get(i, j);
-      A.set(i, j, c64{a.re * sa, a.im * sa});
-      V.set(i, j, c64{v.re * sv, v.im * sv});
-    }
-    __syncthreads();
-    for (int i = tid; i < n; i += nth) sig[i] = 1.0;
-    sync();
     if (my_rot) atomicAdd(&s_rot, my_rot);
     __syncthreads();
     // FP64 flops of this sweep: per applied rotation 16 n FMA (8 n on A: a round's n/2 rotations update

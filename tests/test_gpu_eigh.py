@@ -100,6 +100,32 @@ def test_jacobi_fp64_matches_oracle(ctx, oracle_cache):
             assert Vc[k, c].imag == 0 and Vc[k, c].real > 0
 
 
+def test_jacobi_large_order_keeps_its_scales_in_range(ctx):
+    """Order 1500 (one problem, cooperative-grid class): the fast rotations' scales shrink by c >= 2^-1/2
+    per rotation and a sweep has 1499 rotations per index, so they are folded back every 256 rounds.  The
+    FP64 eigenvalues match LAPACK's within 8 n 2^-53 ||A|| and V is orthonormal to the same level."""
+    import torch
+    import paper_2402_11868_gb300 as Z
+    n = 1500
+    rng = np.random.default_rng(15)
+    Zm = rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n))
+    A = (Zm + Zm.conj().T) / 2
+    ref = np.linalg.eigvalsh(A)[::-1]
+    words = np.zeros((n * n, 2, 1))
+    Af = A.reshape(-1, order="F")
+    words[:, 0, 0], words[:, 1, 0] = Af.real, Af.imag
+    class P:
+        def __init__(self, n, A): self.n, self.A = n, A
+    res = _gpu.eigh_batch(ctx, [P(n, words)], 1)
+    assert int(res["info"].cpu().numpy()[0]) == 0
+    lam, V = _gpu.problem_views(res, 0)
+    anorm = np.abs(ref).max()
+    assert np.all(np.isfinite(lam)) and np.abs(lam[:, 0] - ref).max() <= 8 * n * 2.0**-53 * anorm
+    Vc = (V[:, 0, 0] + 1j * V[:, 1, 0]).reshape(n, n, order="F")
+    assert np.abs(Vc.conj().T @ Vc - np.eye(n)).max() <= 8 * n * 2.0**-53
+    assert np.abs(A @ Vc - Vc * lam[:, 0]).max() <= 8 * n * 2.0**-53 * anorm
+
+
 def test_jacobi_degenerate_and_trivial_inputs(ctx):
     import torch
     import paper_2402_11868_gb300 as Z
