@@ -20,6 +20,7 @@
 // evaluation are reported.
 #include <vector>
 #include <algorithm>
+#include <cmath>
 #include <cstring>
 #include <cstdio>
 #include <cstdlib>
@@ -775,26 +776,58 @@ zkq_status oa_refine_t(void* ctx, const OaBuffers& buf, int batch, const int32_t
       hs.add(PR, probs.data(), sizeof(OaProb) * batch);
       hs.add(CLD, cls.data(), sizeof(OaCluster) * cls.size());
       ZKQ_CUDA_TRY(hs.flush(st));
-      // Q_J = A X2_J (into the P buffer's cluster columns), then CT = X2_J^H Q_J, CG = X2_J^H X2_J
-      std::vector<MwProd> p5, p6;
-      for (auto& c : cls) {
+      // Q_J = A X2_J (into the P buffer's cluster columns), then CT = X2_J^H Q_J, CG = X2_J^H X2_J.
+      // T = CT - mu CG is rounded to FP64, so it needs an absolute accuracy of about 2^-57 times the
+      // cluster's spread of eigenvalues; the products' error is 2^-p of the scale of A (times sqrt(n) for
+      // the inner dimension).  A cluster whose spread is 2^-d ||A|| therefore takes p = 64 + d +
+      // log2(n)/2 bits (rounded up to a multiple of 16, at most the working precision): the wide
+      // clusters of the first peeling steps of a graded spectrum need less than half the moduli.
+      std::vector<double> lam_h((size_t)le * W);
+      ZKQ_CUDA_TRY(hs.download_sync(lam_h.data(), Lm, sizeof(double) * lam_h.size(), st));
+      std::vector<int> cp(cls.size());
+      for (size_t k = 0; k < cls.size(); ++k) {
+        const OaCluster& c = cls[k];
         const OaProb& q = probs[c.prob];
-        double* XJ = X2 + (q.xoff + (int64_t)c.start * q.n) * 2 * W;
-        double* QJ = Pm + (q.xoff + (int64_t)c.start * q.n) * 2 * W;
-        MwProd pa{q.n, c.len, q.n, 0, A + q.a_off * 2 * wa, XJ, QJ, nullptr, 1.0, 0};
-        pa.keepA = 1;
-        p5.push_back(pa);
-        MwProd pt_{c.len, c.len, q.n, 1, XJ, QJ, CT + c.toff * 2 * W, nullptr, 1.0, 0};
-        MwProd pg_{c.len, c.len, q.n, 1, XJ, XJ, CG + c.toff * 2 * W, nullptr, 1.0, 0};
-        pt_.hermitian = 1; pg_.hermitian = 1;
-        p6.push_back(pt_);
-        p6.push_back(pg_);
+        double lo = 0, hi = 0;
+        for (int t = 0; t < c.len; ++t) {
+          const double l = lam_h[(size_t)(q.loff + c.start + t) * W];
+          if (t == 0 || l < lo) lo = l;
+          if (t == 0 || l > hi) hi = l;
+        }
+        const double an = hst[c.prob].anorm > 0 ? hst[c.prob].anorm : 1.0, spread = hi - lo;
+        int need = p_bits;
+        if (spread > 0) {
+          need = 64 + (int)std::ceil(std::log2(an / spread)) + (int)std::ceil(0.5 * std::log2((double)q.n));
+          need = std::min(p_bits, (need + 15) / 16 * 16);
+        }
+        cp[k] = std::max(need, 64);
       }
+      std::vector<int> levels(cp.begin(), cp.end());
+      std::sort(levels.begin(), levels.end());
+      levels.erase(std::unique(levels.begin(), levels.end()), levels.end());
       PlaneCache* const acache[1] = {&pcache};
-      s = mw_gemm_batched(p5.data(), (int)p5.size(), wa, W, W, p_bits, prod_method, buf.oz_ws, buf.oz_bytes, buf.oz_meta, buf.oz_meta_bytes, st, buf.stage, acache, 1);
-      if (s != ZKQ_OK) return s;
-      s = mw_gemm_batched(p6.data(), (int)p6.size(), W, W, W, p_bits, prod_method, buf.oz_ws, buf.oz_bytes, buf.oz_meta, buf.oz_meta_bytes, st, buf.stage);
-      if (s != ZKQ_OK) return s;
+      for (int pl : levels) {
+        std::vector<MwProd> p5, p6;
+        for (size_t k = 0; k < cls.size(); ++k) {
+          if (cp[k] != pl) continue;
+          const OaCluster& c = cls[k];
+          const OaProb& q = probs[c.prob];
+          double* XJ = X2 + (q.xoff + (int64_t)c.start * q.n) * 2 * W;
+          double* QJ = Pm + (q.xoff + (int64_t)c.start * q.n) * 2 * W;
+          MwProd pa{q.n, c.len, q.n, 0, A + q.a_off * 2 * wa, XJ, QJ, nullptr, 1.0, 0};
+          pa.keepA = 1;
+          p5.push_back(pa);
+          MwProd pt_{c.len, c.len, q.n, 1, XJ, QJ, CT + c.toff * 2 * W, nullptr, 1.0, 0};
+          MwProd pg_{c.len, c.len, q.n, 1, XJ, XJ, CG + c.toff * 2 * W, nullptr, 1.0, 0};
+          pt_.hermitian = 1; pg_.hermitian = 1;
+          p6.push_back(pt_);
+          p6.push_back(pg_);
+        }
+        s = mw_gemm_batched(p5.data(), (int)p5.size(), wa, W, W, pl, prod_method, buf.oz_ws, buf.oz_bytes, buf.oz_meta, buf.oz_meta_bytes, st, buf.stage, acache, 1);
+        if (s != ZKQ_OK) return s;
+        s = mw_gemm_batched(p6.data(), (int)p6.size(), W, W, W, pl, prod_method, buf.oz_ws, buf.oz_bytes, buf.oz_meta, buf.oz_meta_bytes, st, buf.stage);
+        if (s != ZKQ_OK) return s;
+      }
       dim3 g((maxl * maxl + 255) / 256, (unsigned)cls.size());
       { ProfScope ps_(PC_OA, st); oa_cluster_mu_kernel<W><<<(unsigned)((cls.size() + 127) / 128), 128, 0, st>>>(PR, CLD, (int)cls.size(), Lm, MUb); }
       { ProfScope ps_(PC_OA, st); oa_cluster_T_kernel<W><<<g, 256, 0, st>>>(PR, CLD, CT, CG, MUb, T); }
