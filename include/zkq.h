@@ -403,8 +403,9 @@ zkq_status zkq_mw_op(int op, int words, int64_t count, const double* a, const do
  *   zkq_profile_read(ms, n, w, k) waits for the recorded launches, writes per-class milliseconds, launch
  *                                counts and algorithmic work for the first k classes, then clears the
  *                                record.  Work: ozaki_gemm counts 2 m (2n) (2k) flops per exact slice
- *                                product (at launch); jacobi and jacobi_cluster count 48 n flops per
- *                                applied rotation (on the device); 0 where not counted
+ *                                product (at launch); jacobi and jacobi_cluster count 32 n flops per
+ *                                applied rotation, the scaled (fast-rotation) update of A and V (on the
+ *                                device); 0 where not counted
  * Errors: ZKQ_EINVAL (null arrays, k < 1), ZKQ_ECUDA.
  */
 int zkq_profile_classes(void);
