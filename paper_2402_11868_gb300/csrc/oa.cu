@@ -750,8 +750,14 @@ zkq_status oa_refine_t(void* ctx, const OaBuffers& buf, int batch, const int32_t
       double* Xb = X + q.xoff * 2 * W;
       p3.push_back({q.n, q.n, q.n, 0, Xb, Em + q.xoff * 2 * 2, X2 + q.xoff * 2 * W, Xb, 1.0, 0});
     }
-    // E is indexed by the active order in the E kernel: it wrote at each problem's own xoff, so p3 is direct
-    s = mw_gemm_batched(p3.data(), (int)p3.size(), W, 2, W, p_bits, prod_method, buf.oz_ws, buf.oz_bytes, buf.oz_meta, buf.oz_meta_bytes, st, buf.stage);
+    // E is indexed by the active order in the E kernel: it wrote at each problem's own xoff, so p3 is direct.
+    // X E is added to X, so it needs the working precision of X's scale only: its error is 2^-p of the
+    // scale of E's columns (at most sqrt(2) max|e|), and the product takes log2(1 / (2 max|e|)) bits fewer.
+    double emax = 0.0;
+    for (int b : upd) emax = std::max(emax, hst[b].maxE);
+    int p_xe = p_bits;
+    if (emax > 0 && emax < 0.25) p_xe = std::max(64, p_bits - (int)std::floor(-std::log2(2.0 * emax)));
+    s = mw_gemm_batched(p3.data(), (int)p3.size(), W, 2, W, p_xe, prod_method, buf.oz_ws, buf.oz_bytes, buf.oz_meta, buf.oz_meta_bytes, st, buf.stage);
     if (s != ZKQ_OK) return s;
     // clusters that still need separation
     std::vector<OaCluster> cls;
